@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks it against a
+printed number, a closed form, an exact series derived from the paper's
+Laplace transform, an invariant, or an independently assembled brute force.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+import synth
+from oracle import closed_forms as cf
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _slab(**kw):
+    return synth.scaled(synth.SLAB_2D, **kw)
+
+
+# --------------------------------------------------------------------------
+# printed numbers
+# --------------------------------------------------------------------------
+def test_printed_numbers():
+    g = json.load(open(os.path.join(GOLDEN, "paper_numbers.json")))
+    chk = {
+        "C_cr": cf.C_CR,
+        "xi_tr_coeff": cf.C_CR,
+        "gamma_one_third": math.gamma(1 / 3),
+        "transition_rate": (4 / 3) * math.sqrt(2 / 3),
+        "otsi_dominance_C": (4 / (3 * math.sqrt(3))) ** 3,
+        "theta_cr_G0p02": cf.C_CR * 0.02,
+        "cfi_peak_X2": cf.gamma_cfi(cf.sum_omega2([(-1, 1, 0.03), (1, 1, 0.03)], 2000.0), 25.0),
+        "cfi_extent_per_efold": cf.C_CR / ((4 / 3) * math.sqrt(2 / 3)),
+    }
+    for k, v in chk.items():
+        assert v == pytest.approx(g[k]["value"], rel=g[k]["rtol"]), k
+    for key in ("contour_example_C", "contour_example_C_large"):
+        e = g[key]
+        assert e["theta"] / e["Gamma"] == pytest.approx(e["C"], rel=1e-12)
+    # Gamma_CFI^2 = (16/3^(3/2)) Gamma_OTSI^3 for k -> infinity (Sec. III.A)
+    w2 = 3e-4
+    assert cf.gamma_cfi(w2, 1e12) ** 2 == pytest.approx(
+        16 / 3 ** 1.5 * cf.gamma_otsi(w2, 1e12, 1e9) ** 3, rel=1e-9)
+    # CFI/OTSI ratio sqrt(8/3)(w2/2)^(1/6) for k >> 1 (after Eq. 17)
+    assert cf.gamma_cfi(w2, 1e12) / cf.gamma_otsi(w2, 1e12, 1e9) == pytest.approx(
+        math.sqrt(8 / 3) * (w2 / 2) ** (1 / 6), rel=1e-9)
+
+
+def test_saddle_roots_cubic():
+    """Appendix B: roots of z^3+z^2-C^2 solve the cubic; all real iff C < C_cr."""
+    for C in (0.05, 0.25, 0.38, 0.39, 0.6, 2.0):
+        z = cf.saddle_roots(C)
+        assert np.max(np.abs(z ** 3 + z ** 2 - C ** 2)) < 1e-10
+        real = np.all(np.abs(z.imag) < 1e-9)
+        assert real == (C < cf.C_CR), C
+    z = cf.saddle_roots(0.25)
+    assert z[0].real < 0 and z[1].real < 0 and z[2].real > 0
+
+
+def test_philox_kat():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert oracle.philox4x32_10(w[0:4], w[4:6]) == w[6:10]
+
+
+def test_noise_statistics_and_hermitian_pairs():
+    p = synth.scaled(synth.BEAM_3D, nkx=16, nky=16, n_xi=256)
+    md = oracle.modes(p)
+    nb, th = oracle.seed_noise(p, seed=7, amplitude=1e-6)
+    assert np.all(th == 0)
+    x = nb.ravel() / 1e-6
+    n = x.size
+    assert abs(np.mean(np.abs(x) ** 2) - 1.0) < 6 / math.sqrt(n)
+    assert abs(np.mean(x.real)) < 6 / math.sqrt(2 * n) and abs(np.mean(x.imag)) < 6 / math.sqrt(2 * n)
+    assert abs(np.mean(x.real ** 2) - 0.5) < 0.05 and abs(np.mean(x.real * x.imag)) < 0.05
+    # partner modes (-k) carry the complex conjugate
+    pos = {int(i): j for j, i in enumerate(md["mode_id"])}
+    for j, (i, pi) in enumerate(zip(md["mode_id"], md["partner_id"])):
+        if int(pi) in pos:
+            assert np.array_equal(nb[j], np.conj(nb[pos[int(pi)]]))
+    # different seeds / instances differ
+    nb2, _ = oracle.seed_noise(p, seed=8, amplitude=1e-6)
+    nb3, _ = oracle.seed_noise(p, seed=7, amplitude=1e-6, inst=1)
+    assert not np.allclose(nb, nb2) and not np.allclose(nb, nb3)
+
+
+def test_kgrid_counts():
+    """Cell-centred disc grids: count the active modes by brute force."""
+    for n, kmax in ((256, 6.0), (64, 6.0), (8, 1.0)):
+        k = (np.arange(n) - (n - 1) / 2) * (2 * kmax / n)
+        brute = int(np.sum(k[:, None] ** 2 + k[None, :] ** 2 <= kmax ** 2))
+        p = synth.scaled(synth.BEAM_3D, nkx=n, nky=n, kmax=kmax)
+        assert len(oracle.modes(p)["k2"]) == brute
+    assert len(oracle.modes(synth.BEAM_3D)["k2"]) == 51468
+    assert len(oracle.modes(synth.BATCH_BASE)["k2"]) == 3228
+
+
+# --------------------------------------------------------------------------
+# closed forms of the scheme
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prof", ["flattop", "ramp"])
+def test_wake_step_exact(prof):
+    """Eq. (5) behind a sharp step of charge: rho0 (1 - cos xi), exact at cell
+    edges and centres; with a ramp the wake is the ramp's exact response."""
+    if prof == "flattop":
+        p = _slab(n_xi=800, dxi=0.05, length=40.0)
+        edge, mid = oracle.wake0(p)
+        xe = (np.arange(800) + 1) * 0.05
+        xm = (np.arange(800) + 0.5) * 0.05
+        assert np.max(np.abs(edge - cf.wake_step(xe, -0.01))) < 1e-15
+        assert np.max(np.abs(mid - cf.wake_step(xm, -0.01))) < 1e-15
+    else:
+        # two species of opposite charge and equal density: no net wake
+        p = _slab(species=[(-1.0, 1.0, 0.02), (1.0, 1.0, 0.02)], profile="ramp_flattop",
+                  ramp_len=2 * math.pi, n_xi=400, dxi=0.05, length=20.0)
+        edge, mid = oracle.wake0(p)
+        assert np.max(np.abs(edge)) < 1e-17 and np.max(np.abs(mid)) < 1e-17
+
+
+@pytest.mark.parametrize("species,model", [
+    ([(-1.0, 1.0, 0.01)], "full"),
+    ([(-1.0, 1.0, 0.01)], "reduced"),
+    ([(-1.0, 1.0, 0.02), (1.0, 1.0, 0.02)], "full"),
+    ([(-1.0, 1.0, 0.03), (1.0, 1836.15, 0.05)], "full"),
+])
+def test_temporal_cfi_exact(species, model):
+    """Equilibrium front + xi-uniform disturbance: n_p == rho at every cell
+    (fixed point of the exact cell propagator of Eq. 5), so each mode grows as
+    the discrete leapfrog of d_tau^2 rho = Gamma_CFI^2 rho, Eq. (17), exactly:
+    x_n = x_0 cosh(n theta), cosh theta = 1 + (Gamma dt)^2/2."""
+    ks = [0.3, 1.0, 2.5, 6.0]
+    p = _slab(species=species, model=model, front="equilibrium", n_xi=96, dxi=0.05,
+              length=4.8, k_list=ks, gamma_b=50.0)
+    ns = len(species)
+    nb = np.ones((len(ks), ns, 96), complex) * (0.7 - 0.2j)
+    if ns == 2:
+        nb[:, 1, :] *= 0.0   # only species 0 disturbed: rho = q0 nb0
+    th = np.zeros_like(nb)
+    nb0 = nb.copy()
+    steps = 250
+    oracle.sweep(p, nb, th, 0, steps)
+    w2 = cf.sum_omega2(species, p["gamma_b"])
+    for i, k in enumerate(ks):
+        G = cf.gamma_cfi(w2, k * k)
+        rho0 = species[0][0] * nb0[i, 0]
+        rho = sum(species[s][0] * nb[i, s] for s in range(ns))
+        expect = rho0 * cf.leapfrog_temporal(steps, G, p["dt"])
+        assert np.max(np.abs(rho / expect - 1)) < 5e-13, (k, G)
+    # the rate tends to (n_b/(n_p gamma))^(1/2) for k >> 1 (spec form)
+    G_inf = math.sqrt(0.01 / 1000.0)
+    G_big_k = cf.gamma_cfi(cf.sum_omega2([(-1, 1, 0.01)], 1000.0), 1e8)
+    assert G_big_k == pytest.approx(G_inf, rel=1e-8)
+
+
+def _impulse_np(D, dt, T, X, species, gamma, k, model):
+    N = int(round(X / D))
+    steps = int(round(T / dt))
+    p = _slab(species=species, gamma_b=gamma, model=model, n_xi=N, dxi=D, length=X, dt=dt,
+              k_list=[k])
+    nb, th = oracle.seed_impulse(p)
+    out = oracle.sweep(p, nb, th, 0, steps + 1, rec_stride=steps, record=("np",))
+    return out["np"][1, 0]
+
+
+def test_greens_function_reduced_second_order():
+    """Impulse response of Eq. (18): the oracle converges at second order in
+    (dxi, dt) to the exact series of the paper's double-Laplace Green's
+    function (Eq. 24).  The impulse sits in cell 0 (centre dxi/2), so the
+    cell-centre value j compares with G(tau, j dxi)."""
+    n0, gam, k = 0.08, 2.0, 1000.0
+    G = math.sqrt(n0 / gam * k * k / (1 + k * k))
+    xs = [1.0, 2.0, 3.0, 4.0]
+    exact = np.array([cf.greens_reduced(25.0, x, G) for x in xs])
+    errs = []
+    for D in (0.1, 0.05):
+        v = _impulse_np(D, D, 25.0, 5.0, [(-1.0, 1.0, n0)], gam, k, "reduced")
+        got = v[[int(round(x / D)) for x in xs]]
+        assert np.max(np.abs(got.imag)) == 0.0
+        errs.append(np.max(np.abs(got.real / exact - 1)))
+    assert errs[1] < 6e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_greens_function_full_second_order():
+    """Same with the gamma^-2 d_xi^2 term of Eq. (15) kept (small gamma so the
+    term matters): pins the f2 coupling, its sign and its gamma^-3 scaling."""
+    gam, n0, k = 1.2, 0.05, 1.0
+    w2 = n0 / gam
+    kap = 1 / (1 + k * k)
+    G2, eps = w2 * kap * k * k, w2 * kap / gam ** 2
+    xs = [2.5, 4.0, 5.5]
+    exact = np.array([cf.greens_full(30.0, x, G2, eps) for x in xs])
+    reduced = np.array([cf.greens_reduced(30.0, x, math.sqrt(G2)) for x in xs])
+    assert np.min(np.abs(exact / reduced - 1)) > 0.1    # the term is not negligible here
+    errs = []
+    for D in (0.1, 0.05):
+        v = _impulse_np(D, D, 30.0, 6.0, [(-1.0, 1.0, n0)], gam, k, "full")
+        got = v[[int(round(x / D)) for x in xs]].real
+        errs.append(np.max(np.abs(got / exact - 1)))
+    assert errs[1] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_series_matches_appendix_A_front_limit():
+    """For xi << 1 the +1 of Eq. (18) is negligible and the exact series tends
+    to Appendix A's [I0 - J0](2 sqrt(G xi tau)) / (2G) at fixed G xi tau."""
+    G = 1.0
+    for a in (4.0, 16.0):
+        r = []
+        for xi in (0.02, 0.01):
+            tau = a / (G * xi)
+            r.append(cf.greens_reduced(tau, xi, G) / cf.front_limit_exact(tau, xi, G))
+        assert abs(r[1] - 1) < abs(r[0] - 1) and abs(r[1] - 1) < 0.02
+    # and Appendix A's large-argument form
+    assert cf.front_limit_exact(1000.0, 0.5, 1.0) / cf.front_limit_asym(1000.0, 0.5, 1.0) == \
+        pytest.approx(1.0, rel=0.02)
+
+
+def test_asymptotes_against_exact_series():
+    """Eqs. (28) and (30) against the exact series in their regimes; the
+    OTSI law of Eq. (29) through its exponent coefficient and its e^{i xi}
+    oscillation (C >> C_cr)."""
+    G = 0.1
+    for Gt in (10.0, 20.0):
+        tau = Gt / G
+        for C in (0.03, 0.1):
+            assert cf.greens_reduced(tau, C * Gt, G) / cf.cfi_st(tau, C * Gt, G) == \
+                pytest.approx(1.0, rel=0.12)
+        assert cf.greens_reduced(tau, cf.C_CR * Gt, G) / cf.cfi_t(tau, G) == \
+            pytest.approx(1.0, rel=0.06)
+    # OTSI exponent: d ln|env| / d tau^(2/3) -> (3 sqrt3/4) G^(2/3) xi^(1/3)
+    xi = 80.0
+    taus = np.array([60.0, 80.0, 100.0, 120.0])
+    env = []
+    for t in taus:
+        xs = xi + np.linspace(0, 2 * np.pi, 17)
+        env.append(max(abs(cf.greens_reduced(t, x, G)) for x in xs))
+    slope = np.polyfit(taus ** (2 / 3), np.log(env), 1)[0]
+    assert slope / (0.75 * math.sqrt(3) * G ** (2 / 3) * xi ** (1 / 3)) == pytest.approx(1.0, rel=0.08)
+    # local xi-wavenumber 1 - C^(-2/3)/4 (phase of Eq. 29): zero-crossing spacing
+    tau = 80.0
+    xs = np.linspace(70.0, 90.0, 801)
+    g = np.array([cf.greens_reduced(tau, x, G) for x in xs])
+    zc = xs[:-1][np.sign(g[1:]) != np.sign(g[:-1])]
+    spacing = np.mean(np.diff(zc))
+    C = 80.0 / (G * tau)
+    assert spacing == pytest.approx(math.pi / (1 - C ** (-2 / 3) / 4), rel=0.03)
+
+
+# --------------------------------------------------------------------------
+# invariants
+# --------------------------------------------------------------------------
+def test_k_minus_k_symmetry_bitwise():
+    """Coefficients depend on k only through k^2 (Eq. 15): a conjugated seed
+    on the partner mode -k evolves into the exact conjugate."""
+    p = synth.scaled(synth.BEAM_3D, nkx=8, nky=8, kmax=3.0, n_xi=128, dxi=0.05, length=6.4)
+    md = oracle.modes(p)
+    nb, th = oracle.seed_noise(p, seed=3, amplitude=1e-3)
+    oracle.sweep(p, nb, th, 0, 40)
+    pos = {int(i): j for j, i in enumerate(md["mode_id"])}
+    n_pairs = 0
+    for j, pi in enumerate(md["partner_id"]):
+        jj = pos[int(pi)]
+        assert np.array_equal(nb[j], np.conj(nb[jj]))
+        assert np.array_equal(th[j], np.conj(th[jj]))
+        n_pairs += 1
+    assert n_pairs == len(md["k2"])
+
+
+def test_superposition_and_causality():
+    p = _slab(n_xi=200, dxi=0.05, length=10.0, k_list=[0.7, 3.0], gamma_b=20.0, dt=1.0)
+    a = synth.user_seed(2, 1, 200, 1, 1e-3)
+    b = synth.user_seed(2, 1, 200, 2, 1e-3)
+    b[:, :, :120] = 0.0   # seed b only behind cell 120
+    res = []
+    for x in (a, b, 2.0 * a - 3.0 * b):
+        nb = x.copy()
+        th = np.zeros_like(nb)
+        oracle.sweep(p, nb, th, 0, 60)
+        res.append((nb, th))
+    for i in (0, 1):
+        lin = 2.0 * res[0][i] - 3.0 * res[1][i]
+        assert np.max(np.abs(res[2][i] - lin)) <= 1e-13 * np.max(np.abs(lin))
+    # causality: cells ahead of the disturbance stay exactly zero
+    assert np.all(res[1][0][:, :, :120] == 0) and np.all(res[1][1][:, :, :120] == 0)
+
+
+def test_shift_invariance_bitwise():
+    """Flat-top beam, uniform grid: a disturbance at cell m gives the response
+    to the same disturbance at cell 0, shifted by m cells (lower-triangular
+    Toeplitz structure of Eq. 18 in xi)."""
+    p = _slab(n_xi=160, dxi=0.05, length=8.0, k_list=[1.5], gamma_b=5.0, dt=0.5)
+    base = np.zeros((1, 1, 160), complex)
+    base[0, 0, :10] = synth.user_seed(1, 1, 10, 4, 1.0)[0, 0]
+    outs = []
+    for m in (0, 37):
+        nb = np.roll(base, m, axis=2)
+        th = np.zeros_like(nb)
+        oracle.sweep(p, nb, th, 0, 30)
+        outs.append((nb, th))
+    assert np.array_equal(outs[1][0][..., 37:], outs[0][0][..., :160 - 37])
+    assert np.array_equal(outs[1][1][..., 37:], outs[0][1][..., :160 - 37])
+
+
+# --------------------------------------------------------------------------
+# brute force on tiny grids
+# --------------------------------------------------------------------------
+def _dense_operators(N, D, q, n0vec, f1, f2):
+    """Map rho -> n_p at cell centres, built from matrix exponentials of
+    Eq. (5) written as a first-order system in (n_p, n_p', rho)."""
+    A = np.array([[0.0, 1.0, 0.0], [-1.0, 0.0, 1.0], [0.0, 0.0, 0.0]])
+    Ef, Eh = scipy.linalg.expm(D * A), scipy.linalg.expm(0.5 * D * A)
+    Q = np.zeros((2, N))
+    L = np.zeros((N, N))
+    for j in range(N):
+        L[j] = Eh[0, 0] * Q[0] + Eh[0, 1] * Q[1]
+        L[j, j] += Eh[0, 2]
+        q0 = Ef[0, 0] * Q[0] + Ef[0, 1] * Q[1]
+        q1 = Ef[1, 0] * Q[0] + Ef[1, 1] * Q[1]
+        q0[j] += Ef[0, 2]
+        q1[j] += Ef[1, 2]
+        Q = np.array([q0, q1])
+    # d_tau Theta = f1 n_mid - f2 (rho - n_mid), rho = q n_b
+    K = q * (f1 * L - f2 * (np.eye(N) - L))
+    return K, np.diag(n0vec)
+
+
+def test_dense_one_step_matrix():
+    N, D, dt, gam, k, n0 = 24, 0.2, 0.7, 3.0, 1.3, 0.05
+    p = _slab(species=[(-1.0, 1.0, n0)], gamma_b=gam, n_xi=N, dxi=D, length=N * D, dt=dt,
+              k_list=[k], model="full")
+    kap = 1 / (1 + k * k)
+    f1, f2 = -1.0 * kap * k * k / gam, -1.0 * kap / gam ** 3
+    K, Dn = _dense_operators(N, D, -1.0, n0 * oracle.shape(p), f1, f2)
+    I = np.eye(N)
+    Z = np.zeros((N, N))
+
+    def step(h):
+        # Theta' = Theta + h K nb ; nb' = nb + dt Dn Theta'
+        return np.block([[I + dt * h * Dn @ K, dt * Dn], [h * K, I]])
+
+    x0 = np.concatenate([np.random.default_rng(0).standard_normal(N), np.zeros(N)])
+    x = step(0.5 * dt) @ x0
+    for _ in range(11):
+        x = step(dt) @ x
+    nb = x0[:N].reshape(1, 1, N).astype(complex)
+    th = np.zeros_like(nb)
+    oracle.sweep(p, nb, th, 0, 12)
+    assert np.max(np.abs(nb[0, 0].real - x[:N])) < 1e-13 * np.max(np.abs(x[:N]))
+    assert np.max(np.abs(th[0, 0].real - x[N:])) < 1e-13 * np.max(np.abs(x[N:]))
+    del Z
+
+
+def test_semidiscrete_ode_leapfrog_second_order():
+    """Slow-time integrator: against expm of the semi-discrete ODE
+    d(nb, Theta)/dtau = [[0, Dn], [K, 0]] (nb, Theta); error falls as dt^2."""
+    N, D, gam, k, n0, T = 20, 0.25, 2.0, 2.0, 0.1, 40.0
+    kap = 1 / (1 + k * k)
+    f1, f2 = -kap * k * k / gam, -kap / gam ** 3
+    p0 = _slab(species=[(-1.0, 1.0, n0)], gamma_b=gam, n_xi=N, dxi=D, length=N * D, k_list=[k])
+    K, Dn = _dense_operators(N, D, -1.0, n0 * oracle.shape(p0), f1, f2)
+    A = np.block([[np.zeros((N, N)), Dn], [K, np.zeros((N, N))]])
+    x0 = np.concatenate([np.random.default_rng(1).standard_normal(N), np.zeros(N)])
+    exact = scipy.linalg.expm(T * A) @ x0
+    errs = []
+    for dt in (0.5, 0.25):
+        p = synth.scaled(p0, dt=dt)
+        nb = x0[:N].reshape(1, 1, N).astype(complex)
+        th = np.zeros_like(nb)
+        oracle.sweep(p, nb, th, 0, int(round(T / dt)))
+        errs.append(np.max(np.abs(nb[0, 0].real - exact[:N])) / np.max(np.abs(exact[:N])))
+    assert errs[1] < 2e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_field_identities():
+    """Diagnostics: |F_perp| = |k| kappa |n_p| and |E_perp - (x x B)_perp| =
+    |F_perp| (F_perp = grad_perp Psi, Sec. III.C); magnitudes recorded."""
+    p = _slab(n_xi=64, dxi=0.1, length=6.4, k_list=[0.5, 2.0], gamma_b=10.0)
+    nb = synth.user_seed(2, 1, 64, 9, 1e-2)
+    rec = oracle.fields(p, nb)
+    kabs = np.array([0.5, 2.0])
+    kap = 1 / (1 + kabs ** 2)
+    npm = rec["np"]
+    F = rec["mag"][3]
+    assert np.allclose(F, (kabs * kap)[:, None] * np.abs(npm), rtol=1e-14, atol=0)
+    assert np.allclose(rec["mag"][0], np.abs(nb[:, 0, :]), rtol=1e-15, atol=0)
+    # |E|^2 = |E_x|^2 + |E_perp|^2 with E_perp = i k kappa (n_p - rho)
+    rho = -nb[:, 0, :]
+    Ep = (kabs * kap)[:, None] * np.abs(npm - rho)
+    assert np.allclose(rec["mag"][1] ** 2, rec["mag"][4] ** 2 + Ep ** 2, rtol=1e-12)
+    assert np.allclose(rec["mag"][2], (kabs * kap)[:, None] * np.abs(rho), rtol=1e-14)
