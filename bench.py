@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark: mode.xi-cell updates/s of the linearised QSA sweep on B300.
+
+Workload (the 3D uniform-beam case): one electron-like species, n_b/n_p =
+0.01, gamma_b = 1000, flat top of length 100 with a sharp front, 2048 xi
+cells, (kx, ky) grid 256 x 256 over |k| <= 6 (disc: 51,468 active modes),
+white-noise seed 1e-6 (seed 0), dt = 2.  One bench step = one whole job of
+2000 slow-time steps (one qs_step call, one kernel launch) on the FP32 +
+renormalisation path; the FP64 path is reported beside it on a shorter job.
+
+value  = updates / device time (state resident in HBM; the 1.7 GB state is
+         larger than L2, so no flush is needed between launches).
+e2e    = the same metric through the C ABI with host buffers: each step
+         restores the job's initial state from pinned host memory (H2D),
+         runs the job and reads the per-mode maxima back (D2H).
+Multi-GPU (torchrun): every rank runs an independent instance (seed = rank),
+no data-path collective; value = all ranks' updates / max rank time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "mode·ξ-cell updates/s, FP32 vs FP64 path at stated error; % of HBM roofline"
+UNIT = "updates/s"
+BYTES_PER_UPDATE_FP32 = 32.0 + 8.0 / 32.0   # read+write complex64 n_b and Theta, + exponents
+BYTES_PER_UPDATE_FP64 = 64.0
+KERNEL_SRC = os.path.join(ROOT, "paper_2607_24234_b300", "csrc", "qs_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_fp32_beam3d_traffic.json")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(n)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(problem, target_s=10.0, modes_sample=64, steps_cap=None):
+    """Time the FP64 oracle on a bounded sample: `modes_sample` lines of the
+    workload for as many slow-time steps as fit ~target_s seconds."""
+    import oracle
+    oracle.build()
+    md = oracle.modes(problem)
+    sel = np.linspace(0, len(md["k2"]) - 1, modes_sample).astype(int)
+    nb, th = oracle.seed_noise(problem, 0, problem["amplitude"], mode_sel=sel)
+    k2 = md["k2"][sel]
+    t0 = time.perf_counter()
+    oracle.sweep(problem, nb, th, 0, 1, k2=k2)
+    t1 = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(t1, 1e-6)))
+    if steps_cap:
+        steps = min(steps, steps_cap)
+    t0 = time.perf_counter()
+    oracle.sweep(problem, nb, th, 1, steps, k2=k2)
+    dt = time.perf_counter() - t0
+    upd = modes_sample * problem["n_xi"] * steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return upd / dt, cores, f"{modes_sample} of {len(md['k2'])} mode lines x {problem['n_xi']} cells x {steps} steps ({dt:.1f} s, FP64)"
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    p = synth.BEAM_3D
+    vals = []
+    desc = None
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        v, cores, desc = cpu_oracle_rate(p, target_s=args.ref_seconds, modes_sample=64)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": p["name"], "modes": 51468, "n_xi": p["n_xi"],
+                   "slow_time_steps_per_job": p["n_steps"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2607_24234_b300 as qs
+
+    p = synth.scaled(synth.BEAM_3D)
+    job = args.job_steps
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    s = qs.Solver(p, prec="fp32", stream=stream)
+    s.seed_noise(rank, p["amplitude"])
+    if args.tune:
+        s.tune(reps=2, cache_path=os.path.join(ROOT, "paper_2607_24234_b300", "tune_cache.json"))
+    launch = s.get_launch()
+    M, N = s.n_modes, p["n_xi"]
+    upd_job = M * N * job
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timing (FP32 path) ----
+    for _ in range(args.warmup):
+        s.seed_noise(rank, p["amplitude"])
+        s.step(job)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    n0 = s.launch_count()
+    clk = Clocks(local)
+    barrier()
+    t0 = time.perf_counter()
+    tstart = torch.cuda.Event(enable_timing=True)
+    tend = torch.cuda.Event(enable_timing=True)
+    tstart.record(stream)
+    for i in range(args.steps):
+        s.seed_noise(rank, p["amplitude"])      # not timed below: per-launch events
+        ev[i][0].record(stream)
+        s.step(job)
+        ev[i][1].record(stream)
+    tend.record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    s.sync()
+    launches = s.launch_count() - n0
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(kern_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * upd_job * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    avg_launch_s = float(np.mean(kern_ms)) / 1e3
+    pk, pk_kind = peaks()
+    achieved = BYTES_PER_UPDATE_FP32 * upd_job / avg_launch_s / 1e9
+    traffic = None
+    try:
+        tj = json.load(open(TRAFFIC_FILE))
+        if tj.get("kernel_sha256_16") == kernel_hash():
+            traffic = tj["dram_bytes_per_update"] * upd_job
+    except Exception:
+        pass
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if args.e2e and args.steps > 0:
+        s.seed_noise(rank, p["amplitude"])
+        ck = s.checkpoint()
+        pinned = torch.from_numpy(ck).pin_memory()
+        ck_np = pinned.numpy()
+        mm = np.empty(s.snapshot_doubles(qs.REC_MODEMAX), np.float64)
+        mm_t = torch.from_numpy(mm).pin_memory()
+        mm_np = mm_t.numpy()
+        import ctypes
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = qs.lib.qs_seed(s.ctx, 0, 0.0, qs.SEED_STATE, ck_np.ctypes.data_as(ctypes.c_void_p),
+                                ck_np.nbytes, 1)
+            assert st == 0
+            s.step(job)
+            st = qs.lib.qs_diag(s.ctx, qs.REC_MODEMAX, mm_np.ctypes.data_as(ctypes.c_void_p),
+                                mm_np.nbytes, 1)
+            assert st == 0
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": ws * upd_job * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(ck_np.nbytes), "d2h_bytes_per_step": int(mm_np.nbytes)}
+
+    # ---- FP64 path (shorter job, same workload) ----
+    fp64 = None
+    if args.fp64 and rank == 0:
+        s64 = qs.Solver(p, prec="fp64", stream=stream)
+        s64.seed_noise(0, p["amplitude"])
+        j64 = args.fp64_job_steps
+        s64.step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(j64)
+        e1.record(stream)
+        s64.sync()
+        ms64 = e0.elapsed_time(e1)
+        upd64 = M * N * j64
+        fp64 = {"value": upd64 / (ms64 / 1e3), "unit": UNIT, "slow_time_steps": j64,
+                "ms": ms64, "launch": s64.get_launch(),
+                "hbm_gbs_algorithmic": BYTES_PER_UPDATE_FP64 * upd64 / (ms64 / 1e3) / 1e9,
+                "error_vs_oracle": "<= 1e-9 relative per mode line (tests/test_gpu_parity.py)"}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu:
+        v, cores, desc = cpu_oracle_rate(p, target_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Philox noise on a flat-top beam)",
+            "config": {"workload": p["name"], "modes": M, "n_xi": N, "slow_time_steps_per_job": job,
+                       "precision_path": "FP32 mantissas + per-(mode, 32-cell) power-of-two exponents",
+                       "l2": "state 1.7 GB > 126 MB L2 (no flush needed)",
+                       "parallelism": f"replicas x{ws}", "launch": launch,
+                       "error_vs_oracle": "<= 1e-3 in log-amplitude, fitted rates <= 0.5% (tests)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                         "peak_source": pk_kind,
+                         "algorithmic_bytes_per_update": BYTES_PER_UPDATE_FP32,
+                         "kernel": "qsk::k_sweep<float,1,U,false>"},
+            "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "fp64": fp64,
+            "cpu_baseline": cpu, "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--job-steps", type=int, default=2000, help="slow-time steps per bench step")
+    ap.add_argument("--fp64-job-steps", type=int, default=200)
+    ap.add_argument("--no-fp64", dest="fp64", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and args.job_steps == 2000:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * qs.h -- C ABI of the B300 (sm_103a) linearised quasistatic beam-plasma
+ * sweep library (libqs.so).
+ *
+ * Model (arXiv 2607.24234, normalised to omega_p, k_p = omega_p/c, n_p,
+ * m_e, e).  Per transverse Fourier mode k_perp the library advances the
+ * beam-density perturbation n_bs and Theta_s = d_xi v_x - i k.v_perp of
+ * each beam species s in slow time tau.  Every slow-time step is one fused
+ * causal sweep along xi = t - x of
+ *   - the plasma response (d_xi^2 + 1) n_p = rho_b = sum_s q_s n_bs
+ *     (Sec. II, Eq. 5), integrated exactly across each xi cell with the
+ *     beam charge constant on the cell;
+ *   - the pseudo-potential Psi = n_p / (1 + k^2) (Eq. 14) and its
+ *     derivatives d_xi Psi, d_xi^2 Psi = (rho - n_p) / (1 + k^2);
+ *   - the beam push of Eqs. (8)-(9):
+ *       d_tau Theta_s = (q_s/m_s)[(k^2/g) Psi - g^-3 d_xi^2 Psi],
+ *       d_tau n_bs    = n_bs0(xi) Theta_s,
+ *     as a kick-drift leapfrog (first step kicks by dt/2).
+ * Dropping the g^-3 term (QS_MODEL_REDUCED) gives Eq. (18) for one
+ * species; keeping it gives Eq. (15) per mode.
+ *
+ * Conventions for every entry point:
+ *   - Device work is enqueued asynchronously on the CUDA stream given to
+ *     qs_init (NULL = legacy default stream).  Only qs_sync and the
+ *     host-pointer forms of qs_diag / qs_seed block.
+ *   - Return value: QS_OK or an error code; no exception crosses the ABI.
+ *     qs_last_error(ctx) returns a message for the last failure on ctx
+ *     (ctx == NULL: the last failure of qs_init on this thread).
+ *   - Argument errors are detected on the host before any launch.  Device
+ *     errors (non-finite values, exhausted bounded waits) set a sticky
+ *     device word that qs_sync / host qs_diag report; after one, the
+ *     context returns QS_ERR_STATE until the next qs_seed.
+ *   - The library owns all state buffers (allocated through the caller's
+ *     allocator when one is given, else cudaMalloc) and frees them in
+ *     qs_free.  The caller owns every buffer it passes in.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_ARG = 1,          /* invalid argument or size                  */
+    QS_ERR_OOM = 2,          /* allocation failed                         */
+    QS_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed         */
+    QS_ERR_TIMEOUT = 4,      /* a bounded device wait ran out             */
+    QS_ERR_NONFINITE = 5,    /* NaN/Inf appeared in the state             */
+    QS_ERR_STATE = 6,        /* context poisoned by an earlier error      */
+    QS_ERR_UNSUPPORTED = 7   /* valid request this build does not serve   */
+} qs_status;
+
+enum { QS_GEOM_KLIST = 0,    /* explicit list of k (2D slab, k along y)   */
+       QS_GEOM_KGRID2 = 1 }; /* cell-centred (kx, ky) grid, optional disc */
+
+enum { QS_FP64 = 0,          /* state and arithmetic in FP64              */
+       QS_FP32_RENORM = 1 }; /* FP32 mantissas + power-of-two exponent    *
+                              * per (mode, 32-cell group)                 */
+
+enum { QS_MODEL_FULL = 0, QS_MODEL_REDUCED = 1 };
+
+enum { QS_FRONT_QUIESCENT = 0,   /* plasma at rest ahead: P(0) = (0, 0)       */
+       QS_FRONT_EQUILIBRIUM = 1, /* P(0) = (rho at cell 0, 0)                 */
+       QS_FRONT_HELD = 2 };      /* P(0) fixed per mode by the caller
+                                  * (Sec. III.C holds the front value)        */
+
+enum { QS_PROF_FLATTOP = 0,      /* 1 for xi <= length, 0 behind              */
+       QS_PROF_GAUSSIAN = 1,     /* exp(-(xi-center)^2 / (2 sigma^2))         */
+       QS_PROF_RAMP_FLATTOP = 2, /* xi/ramp for xi < ramp, 1 up to length     */
+       QS_PROF_USER = 3 };       /* user_profile[n_xi] at cell centres        */
+
+typedef struct {
+    double q;             /* charge in units of e (electron: -1)           */
+    double m;             /* mass in units of m_e                           */
+    double density_ratio; /* peak n_bs0 / n_p                              */
+} qs_species;
+
+/* Problem statement (Sec. II: species (q_s, m_s, n_bs0), gamma_b, the
+ * longitudinal profile, the transverse wavenumbers and the xi / tau
+ * grids).  Cell j covers [j dxi, (j+1) dxi); beam quantities live at the
+ * cell centre (j + 1/2) dxi. */
+typedef struct {
+    int geom;                 /* QS_GEOM_*                                 */
+    int prec;                 /* QS_FP64 | QS_FP32_RENORM                  */
+    int model;                /* QS_MODEL_*                                */
+    int front;                /* QS_FRONT_*                                */
+    int n_species;            /* 1 or 2                                    */
+    qs_species species[2];
+    double gamma_b;           /* > 1                                       */
+    int profile;              /* QS_PROF_*                                 */
+    double length, sigma_xi, center_xi, ramp_len;
+    const double *user_profile; /* host, n_xi doubles (QS_PROF_USER)       */
+    int n_xi;                 /* >= 1                                      */
+    double dxi;               /* > 0                                       */
+    double dt;                /* > 0                                       */
+    int n_k;                  /* QS_GEOM_KLIST: number of k                */
+    const double *k_list;     /* host, n_k doubles                         */
+    int nkx, nky;             /* QS_GEOM_KGRID2: k_i = (i-(n-1)/2) 2kmax/n */
+    double kmax;
+    int disc_mask;            /* 1: keep |k| <= kmax only                  */
+    const double *held_front; /* QS_FRONT_HELD: host, 4 doubles per active
+                               * mode (re n_p, im n_p, re n_p', im n_p')   */
+} qs_params;
+
+/* Caller-supplied device allocator (e.g. a framework's caching allocator).
+ * alloc returns NULL on failure (the library then returns QS_ERR_OOM). */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} qs_allocator;
+
+typedef struct qs_ctx qs_ctx;
+
+/* Create a context for n_inst >= 1 instances.  per_inst == NULL: all
+ * instances use *p; else per_inst[i] describes instance i and must agree
+ * with *p on geom, prec, model, front, n_species and the k set (instances
+ * may differ in species densities, gamma_b, profile, n_xi and dxi).
+ * alloc == NULL: cudaMalloc/cudaFree.  stream: a cudaStream_t or NULL.
+ * On success *out owns the state, zero-initialised; call qs_seed next. */
+qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
+                  const qs_allocator *alloc, void *stream, qs_ctx **out);
+
+enum { QS_SEED_NOISE = 0,   /* complex Gaussian white noise on n_b          */
+       QS_SEED_IMPULSE = 1, /* d_tau rho(0) = amplitude * delta(xi) in cell 0 */
+       QS_SEED_USER = 2,    /* n_b from `user`, Theta = 0                   */
+       QS_SEED_STATE = 3 }; /* restore a QS_DIAG_STATE checkpoint            */
+
+/* (Re)initialise the perturbation and reset the step counter to 0
+ * (QS_SEED_STATE restores the checkpoint's counter instead).
+ *  NOISE:   n_bs(xi_j) = amplitude * shape(xi_j) * (g1 + i g2)/sqrt 2 with
+ *           g1, g2 standard normals from Philox4x32-10 keyed by `seed`, with
+ *           counter (j, canonical mode id, instance, species); the mode
+ *           paired with -k receives the complex conjugate.
+ *  IMPULSE: Theta_0(cell 0) = amplitude / (q_0 n_b00(xi_0) dxi), n_b = 0:
+ *           the impulse response (Green's function) source of Eq. (23).
+ *  USER:    `user` = complex128 n_b as [inst][mode][species][xi]
+ *           (interleaved re, im), instances concatenated.
+ *  STATE:   `user` = bytes written by qs_diag(QS_DIAG_STATE).
+ * user_on_host selects whether `user` is a host or a device pointer. */
+qs_status qs_seed(qs_ctx *ctx, uint64_t seed, double amplitude, int kind,
+                  const void *user, size_t user_bytes, int user_on_host);
+
+/* Advance every instance by n_steps >= 1 slow-time steps (async). */
+qs_status qs_step(qs_ctx *ctx, int n_steps);
+
+/* Diagnostic record kinds (bit mask for qs_record, value for qs_diag). */
+enum {
+    QS_REC_MAG = 1,     /* 5 doubles per cell: ln|dn_b|, ln|dE|, ln|dB|,
+                         * ln|F_perp|, ln|E_x| at the cell centre.  |dn_b|
+                         * = (sum_s |n_bs|^2)^(1/2); fields (a reading, the
+                         * paper derives only F_perp ~ grad_perp Psi):
+                         * E_x = -d_xi Psi, E_perp = i k kappa (n_p - rho),
+                         * |B_perp| = |k| kappa |rho|, F_perp = i k Psi.    */
+    QS_REC_NP = 2,      /* complex n_p at the cell centre (2 doubles)      */
+    QS_REC_MODEMAX = 4  /* per mode: max over xi of ln|dn_b|, ln|dE|, ln|dB| */
+};
+
+/* Attach a device buffer that subsequent qs_step calls fill with the
+ * fields at tau = g dt for every global step g = g0 + i*stride (g0 = the
+ * step counter now), as computed inside the sweep of step g (before its
+ * update).  Layout per snapshot, for each kind present in `kinds` (in bit
+ * order): MAG [5][cells][mode], NP [cells][mode][2], MODEMAX
+ * [3][inst][mode], where `cells` runs over the instances' xi cells
+ * concatenated and `mode` over the padded mode count (qs_query).
+ * qs_step fails with QS_ERR_ARG rather than write past out_bytes.
+ * kinds == 0 or out == NULL detaches. */
+qs_status qs_record(qs_ctx *ctx, int kinds, int stride, void *dev_out,
+                    size_t out_bytes);
+
+enum { QS_DIAG_MAG = 1, QS_DIAG_NP = 2, QS_DIAG_MODEMAX = 4,
+       QS_DIAG_STATE = 16, /* opaque checkpoint (state + exponents + step) */
+       QS_DIAG_WAKE0 = 32  /* zeroth-order n_p response to the unperturbed
+                            * beam charge: 2 doubles per cell per instance
+                            * (cell exit, cell centre), Eq. (5)          */ };
+
+/* Read-only diagnostic pass at the current state (tau = step * dt), one
+ * snapshot in the qs_record layout (or the checkpoint / wake layout).
+ * out_on_host = 1 copies to host memory and synchronises the stream. */
+qs_status qs_diag(qs_ctx *ctx, int kind, void *out, size_t out_bytes,
+                  int out_on_host);
+
+enum { QS_Q_N_MODES = 0,      /* active modes                              */
+       QS_Q_MODES_PADDED = 1, /* row length of every [cells][mode] array   */
+       QS_Q_N_INST = 2,
+       QS_Q_TOTAL_CELLS = 3,  /* sum over instances of n_xi                */
+       QS_Q_STEP = 4,         /* global slow-time step counter             */
+       QS_Q_STATE_BYTES = 5,  /* size of a QS_DIAG_STATE checkpoint        */
+       QS_Q_SNAPSHOT_BYTES = 6, /* bytes of one snapshot for kinds = arg  */
+       QS_Q_CELL_OFFSET = 7,  /* first cell of instance arg                */
+       QS_Q_LAUNCH = 8 };     /* packed launch shape in use (see qs_launch) */
+
+/* Query a size or counter; `arg` is used by QS_Q_SNAPSHOT_BYTES (kinds)
+ * and QS_Q_CELL_OFFSET (instance). */
+qs_status qs_query(const qs_ctx *ctx, int what, int64_t arg, int64_t *value);
+
+/* Copy the active modes' (kx, ky) to host arrays of QS_Q_N_MODES doubles
+ * (KLIST: kx = k, ky = 0). */
+qs_status qs_modes(const qs_ctx *ctx, double *kx, double *ky);
+
+/* Launch shape of the sweep kernel. */
+typedef struct {
+    int warps_per_cta;   /* 1, 2, 4 or 8: each thread owns one mode line    */
+    int prefetch;        /* cells per register batch: 4 or 8                */
+    int persistent;      /* 1: LPT-ordered work list pulled by atomic ticket */
+    int ctas_per_sm;     /* persistent grid size = ctas_per_sm * SM count    */
+} qs_launch;
+
+qs_status qs_set_launch(qs_ctx *ctx, const qs_launch *l);
+qs_status qs_get_launch(const qs_ctx *ctx, qs_launch *l);
+
+/* Autotuner: time every candidate launch shape for `reps` steps on a copy
+ * of the state (the context's state is unchanged), keep the fastest, and
+ * read/write the choice in the JSON cache file `cache_path` (NULL: no
+ * cache) keyed by precision, species count, xi-length bucket and SM count.
+ * Synchronises the stream. */
+qs_status qs_tune(qs_ctx *ctx, int reps, const char *cache_path);
+
+/* Capture n_steps of qs_step in a CUDA graph (cached per n_steps) and
+ * launch it.  Semantics as qs_step.  The record target must be detached. */
+qs_status qs_step_graph(qs_ctx *ctx, int n_steps);
+
+/* Wait for the stream and report device-side errors. */
+qs_status qs_sync(qs_ctx *ctx);
+
+/* Number of sweep-kernel launches enqueued by this context so far. */
+int64_t qs_launch_count(const qs_ctx *ctx);
+
+const char *qs_last_error(const qs_ctx *ctx);
+void qs_free(qs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS_H */

@@ -1,0 +1,473 @@
+// qs_kernels.cuh -- sm_103a device code of the linearised QSA sweep.
+//
+// Data layout in HBM (per context, instances concatenated along xi):
+//   FP32 path: st  float4 [cell][species][Mp] = (Re n_b, Im n_b, Re Theta, Im Theta)
+//              ex  int32  [group][Mp], group = 32 cells: (W << 8) | (s & 0xff)
+//                  value = mantissa * 2^W; s = floor(log2(max |mantissa|)) of the
+//                  group as written, applied lazily on the next read.
+//   FP64 path: st  double2 [cell][species][Mp] = n_b,  th double2 [...] = Theta
+// Mp = active modes padded to a multiple of 32, so that a warp touches one
+// contiguous 512 B (FP32) / 2 x 512 B (FP64) row per cell and species.
+//
+// One thread owns one (instance, mode) line and marches it causally in xi
+// (Sec. II, Eq. 5, exact per cell with rho constant on the cell), fusing the
+// field evaluation (Eq. 14) and the leapfrog push of Eqs. (8)-(9).  Lines are
+// independent for all time, so a launch runs all requested slow-time steps
+// of its line before taking the next one.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qsk {
+
+constexpr int GRP = 32;          // renormalisation group length (cells)
+constexpr int ERR_NONFINITE = 1; // bits of the sticky device error word
+constexpr int ERR_TIMEOUT = 2;
+
+struct InstDev {
+    int n_xi, n_grp;
+    long long cell_off;   // first cell of this instance in the concatenation
+    long long grp_off;    // first exponent group
+    double c, s, ch, sh;  // cos, sin of dxi and of dxi/2
+    double dt, dxi;
+    double q[2];
+    double qm_g[2];       // (q/m)/gamma
+    double qm_g3[2];      // (q/m)/gamma^3, 0 for the reduced model
+};
+
+struct SweepArgs {
+    void *st;             // state (see above)
+    void *th;             // FP64 Theta (null for FP32)
+    int *ex;              // FP32 exponents
+    const InstDev *inst;
+    const int2 *items;    // (instance, first mode) per work item
+    int n_items;
+    const double *kap;    // 1/(1+k^2)            [Mp]
+    const double *kapk2;  // k^2/(1+k^2)          [Mp]
+    const double *kabs;   // |k|                  [Mp]
+    const double *held;   // [inst][Mp][4] or null
+    const void *w;        // dt * n_bs0(xi_j) per cell and species, T [cell][NS]
+    int Mp, M, n_inst;
+    int front;
+    long long step0;
+    int n_steps;
+    int update;           // 0: field pass only (no state write)
+    int persistent;
+    // fused record
+    int rec_kinds;
+    long long rec_g0, rec_max_snap;
+    int rec_stride;
+    double *rec;
+    long long rec_snap_doubles, rec_off_mag, rec_off_np, rec_off_mm, cells_total;
+    int *ticket;
+    int *err;
+};
+
+template <typename T> struct Cell { T nr, ni, tr, ti; };
+
+__device__ __forceinline__ float pow2f(int e) {
+    if (e < -126) return 0.0f;
+    if (e > 127) e = 127;
+    return __int_as_float((e + 127) << 23);
+}
+__device__ __forceinline__ int expof(float x) {   // floor(log2 |x|); -200 for 0 / subnormal
+    int b = (__float_as_int(x) >> 23) & 0xff;
+    return b ? b - 127 : -200;
+}
+
+__device__ __forceinline__ void ld_cell(const SweepArgs &a, long long row, int mode, Cell<float> &c) {
+    float4 v = __ldcg(reinterpret_cast<const float4 *>(a.st) + row * a.Mp + mode);
+    c.nr = v.x; c.ni = v.y; c.tr = v.z; c.ti = v.w;
+}
+__device__ __forceinline__ void ld_cell(const SweepArgs &a, long long row, int mode, Cell<double> &c) {
+    double2 x = __ldcg(reinterpret_cast<const double2 *>(a.st) + row * a.Mp + mode);
+    double2 y = __ldcg(reinterpret_cast<const double2 *>(a.th) + row * a.Mp + mode);
+    c.nr = x.x; c.ni = x.y; c.tr = y.x; c.ti = y.y;
+}
+__device__ __forceinline__ void st_cell(const SweepArgs &a, long long row, int mode, const Cell<float> &c) {
+    __stcg(reinterpret_cast<float4 *>(a.st) + row * a.Mp + mode, make_float4(c.nr, c.ni, c.tr, c.ti));
+}
+__device__ __forceinline__ void st_cell(const SweepArgs &a, long long row, int mode, const Cell<double> &c) {
+    __stcg(reinterpret_cast<double2 *>(a.st) + row * a.Mp + mode, make_double2(c.nr, c.ni));
+    __stcg(reinterpret_cast<double2 *>(a.th) + row * a.Mp + mode, make_double2(c.tr, c.ti));
+}
+
+template <typename T> __device__ __forceinline__ double lnabs2(T re2) {  // ln sqrt(re2)
+    return 0.5 * log((double)re2);
+}
+
+// ---------------------------------------------------------------------------
+// Per-line sweep.  U = cells per register batch (divides 32); batches are
+// double-buffered so that the loads of batch b+1 are in flight while batch b
+// is computed.
+// ---------------------------------------------------------------------------
+template <typename T, int NS, int U, bool REC>
+struct Line {
+    static constexpr bool RN = sizeof(T) == 4;   // FP32 path renormalises
+    const SweepArgs &a;
+    const InstDev &I;
+    int inst, mode;
+    // plasma state P = (n_p, n_p') entering the current cell, working scale
+    T nr, ni, dr, di;
+    T c, s, ch, sh, A[NS], B[NS], q[NS];
+    T kap, kabsk;          // kappa and |k| kappa (for the fields)
+    bool rec, upd;
+    long long snap;
+    // FP32 renormalisation
+    int W, E;              // working scale of the current group, stored scale
+    float facM;            // 2^(E - W): stored mantissa -> working scale
+    float gmax, gnan;
+    double mm0, mm1, mm2;  // running max for MODEMAX
+
+    __device__ Line(const SweepArgs &a_, const InstDev &I_, int inst_, int mode_)
+        : a(a_), I(I_), inst(inst_), mode(mode_) {}
+
+    struct Batch { Cell<T> x[U][NS]; T w[U][NS]; int exw; };
+
+    __device__ __forceinline__ void load(Batch &b, int j0) {
+        const int N = I.n_xi;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int j = j0 + u;
+            if (j < N) {
+                long long row = (I.cell_off + j) * NS;
+#pragma unroll
+                for (int sp = 0; sp < NS; ++sp) {
+                    ld_cell(a, row + sp, mode, b.x[u][sp]);
+                    b.w[u][sp] = __ldg(reinterpret_cast<const T *>(a.w) + row + sp);
+                }
+            }
+        }
+        if (RN && (j0 % GRP) == 0) b.exw = __ldcg(a.ex + (I.grp_off + j0 / GRP) * a.Mp + mode);
+    }
+
+    __device__ __forceinline__ void group_begin(int exw) {
+        if constexpr (RN) {
+            E = exw >> 8;
+            int s8 = (int)(signed char)(exw & 0xff);
+            int Win = E + s8;
+            float pm = fmaxf(fmaxf(fabsf((float)nr), fabsf((float)ni)), fmaxf(fabsf((float)dr), fabsf((float)di)));
+            int Wn = Win;
+            if (pm > 0.0f) { int wp = W + expof(pm); if (wp > Wn) Wn = wp; }
+            float facP = pow2f(W - Wn);
+            nr *= facP; ni *= facP; dr *= facP; di *= facP;
+            W = Wn;
+            facM = pow2f(E - W);
+            gmax = 0.0f; gnan = 0.0f;
+        }
+    }
+
+    __device__ __forceinline__ void group_end(int g) {
+        if constexpr (RN) {
+            if (upd) {
+                int s8 = gmax > 0.0f ? expof(gmax) : 0;
+                s8 = s8 < -100 ? -100 : (s8 > 100 ? 100 : s8);
+                if (!(gnan == 0.0f) || !(gmax <= 3.0e38f)) atomicOr(a.err, ERR_NONFINITE);
+                __stcg(a.ex + (I.grp_off + g) * a.Mp + mode, (W << 8) | (s8 & 0xff));
+            }
+        }
+    }
+
+    __device__ __forceinline__ void record(long long j, T mr, T mi, T mdr, T mdi, T rr, T ri,
+                                           const Cell<T> *x) {
+        // fields at the cell centre (working scale; FP32 adds W ln 2)
+        const double sc = RN ? (double)W * 0.69314718055994530942 : 0.0;
+        double nb2 = 0.0;
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp)
+            nb2 += (double)x[sp].nr * x[sp].nr + (double)x[sp].ni * x[sp].ni;
+        double exr = -(double)kap * mdr, exi = -(double)kap * mdi;
+        double epr = (double)kabsk * ((double)mr - rr), epi = (double)kabsk * ((double)mi - ri);
+        double ex2 = exr * exr + exi * exi;
+        double lnb = 0.5 * log(nb2) + sc;
+        double lE = 0.5 * log(ex2 + epr * epr + epi * epi) + sc;
+        double lB = log((double)kabsk) + 0.5 * log((double)rr * rr + (double)ri * ri) + sc;
+        double lF = log((double)kabsk) + 0.5 * log((double)mr * mr + (double)mi * mi) + sc;
+        double lEx = 0.5 * log(ex2) + sc;
+        double *base = a.rec + snap * a.rec_snap_doubles;
+        long long cm = (I.cell_off + j) * a.Mp + mode;
+        if (a.rec_kinds & 1) {
+            long long pl = a.cells_total * a.Mp;
+            double *o = base + a.rec_off_mag + cm;
+            __stcs(o, lnb); __stcs(o + pl, lE); __stcs(o + 2 * pl, lB);
+            __stcs(o + 3 * pl, lF); __stcs(o + 4 * pl, lEx);
+        }
+        if (a.rec_kinds & 2) {
+            double f = RN ? ldexp(1.0, W) : 1.0;
+            __stcs(reinterpret_cast<double2 *>(base + a.rec_off_np) + cm,
+                   make_double2((double)mr * f, (double)mi * f));
+        }
+        if (a.rec_kinds & 4) { mm0 = fmax(mm0, lnb); mm1 = fmax(mm1, lE); mm2 = fmax(mm2, lB); }
+    }
+
+    __device__ __forceinline__ void compute(Batch &b, int j0) {
+        const int N = I.n_xi;
+        if (RN && (j0 % GRP) == 0) group_begin(b.exw);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u;
+            if (j < N) {
+                Cell<T> *x = b.x[u];
+                if constexpr (RN) {
+#pragma unroll
+                    for (int sp = 0; sp < NS; ++sp) {
+                        x[sp].nr *= facM; x[sp].ni *= facM; x[sp].tr *= facM; x[sp].ti *= facM;
+                    }
+                }
+                T rr = q[0] * x[0].nr, ri = q[0] * x[0].ni;
+                if (NS == 2) { rr = fma(q[NS - 1], x[NS - 1].nr, rr); ri = fma(q[NS - 1], x[NS - 1].ni, ri); }
+                if (j == 0 && a.front == 1) { nr = rr; ni = ri; dr = 0; di = 0; }
+                // u = n_p - rho; centre:  n_mid = ch u + sh n' + rho
+                const T ur = nr - rr, ui = ni - ri;
+                const T mr = fma(ch, ur, fma(sh, dr, rr));
+                const T mi = fma(ch, ui, fma(sh, di, ri));
+                if (REC && rec) {
+                    const T mdr = fma(-sh, ur, ch * dr), mdi = fma(-sh, ui, ch * di);
+                    record(j, mr, mi, mdr, mdi, rr, ri, x);
+                }
+                // cell exit: n = c u + s n' + rho, n' = -s u + c n'
+                const T xr = fma(c, ur, fma(s, dr, rr));
+                const T xi = fma(c, ui, fma(s, di, ri));
+                dr = fma(-s, ur, c * dr);
+                di = fma(-s, ui, c * di);
+                nr = xr; ni = xi;
+                if (upd) {
+                    const long long row = (I.cell_off + j) * NS;
+#pragma unroll
+                    for (int sp = 0; sp < NS; ++sp) {
+                        // Theta += h (f1 n_mid - f2 (rho - n_mid));  n_b += dt n_b0 Theta
+                        x[sp].tr = fma(A[sp], mr, fma(-B[sp], rr, x[sp].tr));
+                        x[sp].ti = fma(A[sp], mi, fma(-B[sp], ri, x[sp].ti));
+                        x[sp].nr = fma(b.w[u][sp], x[sp].tr, x[sp].nr);
+                        x[sp].ni = fma(b.w[u][sp], x[sp].ti, x[sp].ni);
+                        if constexpr (RN) {
+                            gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(x[sp].nr), fabsf(x[sp].ni)),
+                                                     fmaxf(fabsf(x[sp].tr), fabsf(x[sp].ti))));
+                            gnan = fmaf(x[sp].nr + x[sp].ti, 0.0f, gnan);
+                            gnan = fmaf(x[sp].ni + x[sp].tr, 0.0f, gnan);
+                        }
+                        st_cell(a, row + sp, mode, x[sp]);
+                    }
+                }
+                if (RN && (((j + 1) % GRP) == 0 || j == N - 1)) group_end(j / GRP);
+            }
+        }
+    }
+
+    __device__ void run() {
+        const int N = I.n_xi;
+        c = (T)I.c; s = (T)I.s; ch = (T)I.ch; sh = (T)I.sh;
+        const double kapd = a.kap[mode], kk2d = a.kapk2[mode];
+        kap = (T)kapd;
+        kabsk = (T)(a.kabs[mode] * kapd);
+        upd = a.update != 0;
+        for (int it = 0; it < a.n_steps; ++it) {
+            const long long g = a.step0 + it;
+            const double h = (g == 0) ? 0.5 * I.dt : I.dt;
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) {
+                const double f1 = I.qm_g[sp] * kk2d, f2 = I.qm_g3[sp] * kapd;
+                A[sp] = (T)(h * (f1 + f2));
+                B[sp] = (T)(h * f2);
+                q[sp] = (T)I.q[sp];
+            }
+            rec = false;
+            if (REC) {
+                long long d = g - a.rec_g0;
+                if (d >= 0 && (d % a.rec_stride) == 0 && d / a.rec_stride < a.rec_max_snap) {
+                    rec = true;
+                    snap = d / a.rec_stride;
+                }
+                mm0 = mm1 = mm2 = -INFINITY;
+            }
+            nr = ni = dr = di = 0;
+            W = 0;
+            if (a.front == 2 && a.held) {
+                const double *hp = a.held + ((long long)inst * a.Mp + mode) * 4;
+                if constexpr (RN) {
+                    double hm = fmax(fmax(fabs(hp[0]), fabs(hp[1])), fmax(fabs(hp[2]), fabs(hp[3])));
+                    int e = hm > 0.0 ? ilogb(hm) : 0;
+                    W = e;
+                    nr = (T)ldexp(hp[0], -e); ni = (T)ldexp(hp[1], -e);
+                    dr = (T)ldexp(hp[2], -e); di = (T)ldexp(hp[3], -e);
+                } else {
+                    nr = (T)hp[0]; ni = (T)hp[1]; dr = (T)hp[2]; di = (T)hp[3];
+                }
+            }
+            Batch b0, b1;
+            load(b0, 0);
+            for (int j0 = 0; j0 < N; j0 += 2 * U) {
+                if (j0 + U < N) load(b1, j0 + U);
+                compute(b0, j0);
+                if (j0 + 2 * U < N) load(b0, j0 + 2 * U);
+                if (j0 + U < N) compute(b1, j0 + U);
+            }
+            if (!(fabs((double)nr) + fabs((double)ni) + fabs((double)dr) + fabs((double)di) <= 1.0e300))
+                atomicOr(a.err, ERR_NONFINITE);
+            if (REC && rec && (a.rec_kinds & 4)) {
+                double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)inst * a.Mp + mode;
+                long long pl = (long long)a.n_inst * a.Mp;
+                o[0] = mm0; o[pl] = mm1; o[2 * pl] = mm2;
+            }
+        }
+    }
+};
+
+template <typename T, int NS, int U, bool REC>
+__global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
+    __shared__ int s_item;
+    int item = blockIdx.x;
+    for (;;) {
+        if (a.persistent) {
+            if (threadIdx.x == 0) s_item = atomicAdd(a.ticket, 1);
+            __syncthreads();
+            item = s_item;
+            __syncthreads();
+        }
+        if (item >= a.n_items) break;
+        const int2 it = a.items[item];
+        const int mode = it.y + threadIdx.x;
+        if (mode < a.M) {
+            const InstDev I = a.inst[it.x];
+            Line<T, NS, U, REC> L(a, I, it.x, mode);
+            L.run();
+        }
+        if (!a.persistent) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Seeds.  Philox4x32-10 (Salmon et al., SC'11) written from its definition.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ void normal2(uint64_t seed, uint32_t j, uint32_t id, uint32_t inst,
+                                        uint32_t sp, double &g1, double &g2) {
+    uint32_t c[4] = {j, id, inst, sp};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t m1 = ((uint64_t)c[0] << 21) | (c[1] >> 11);
+    const uint64_t m2 = ((uint64_t)c[2] << 21) | (c[3] >> 11);
+    const double u1 = ((double)m1 + 0.5) * 0x1.0p-53;
+    const double u2 = ((double)m2 + 0.5) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    g1 = r * cs;
+    g2 = r * sn;
+}
+
+struct SeedArgs {
+    void *st, *th;
+    int *ex;
+    const InstDev *inst;
+    const double *shape;      // [cell]
+    const double *dens;       // [inst][2]
+    const int *mode_id, *partner_id;
+    int Mp, M, NS, n_inst;
+    int kind;                 // 0 noise, 1 impulse, 2 user
+    uint64_t seed;
+    double amp;
+    const double *user;       // complex128 [inst][mode][species][xi]
+    long long total_groups;
+};
+
+// One thread per (group of 32 cells, mode): writes n_b, Theta and (FP32) the
+// group exponent.  Values are formed in FP64.
+template <typename T>
+__global__ void k_seed(const SeedArgs a) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gg = blockIdx.y + (long long)blockIdx.z * gridDim.y;   // global group
+    if (mode >= a.Mp || gg >= a.total_groups) return;
+    int lo = 0, hi = a.n_inst - 1;             // last instance with grp_off <= gg
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.inst[mid].grp_off <= gg) lo = mid; else hi = mid - 1;
+    }
+    const int inst = lo;
+    const InstDev I = a.inst[inst];
+    const int g = (int)(gg - I.grp_off);
+    const int j0 = g * GRP, j1 = min(I.n_xi, j0 + GRP);
+    const bool live = mode < a.M;
+    double v[GRP][2][4];
+    double vmax = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        for (int sp = 0; sp < a.NS; ++sp) {
+            double nr = 0, ni = 0, tr = 0, ti = 0;
+            if (live) {
+                if (a.kind == 0) {
+                    const int id = a.mode_id[mode], pid = a.partner_id[mode];
+                    const bool cj = pid < id;
+                    double g1, g2;
+                    normal2(a.seed, (uint32_t)j, (uint32_t)(cj ? pid : id), (uint32_t)inst, (uint32_t)sp, g1, g2);
+                    const double am = a.amp * a.shape[I.cell_off + j] * 0.70710678118654752440;
+                    nr = am * g1;
+                    ni = cj ? -am * g2 : am * g2;
+                } else if (a.kind == 1) {
+                    if (j == 0 && sp == 0)
+                        tr = a.amp / (I.q[0] * a.dens[2 * inst] * a.shape[I.cell_off] * I.dxi);
+                } else {
+                    const long long o = ((((long long)0 + mode) * a.NS + sp) * I.n_xi + j);
+                    // user rows are per instance: [inst][mode][sp][xi]
+                    const double *ub = a.user + 2 * ((long long)a.M * a.NS * I.cell_off);
+                    nr = ub[2 * o];
+                    ni = ub[2 * o + 1];
+                }
+            }
+            v[j - j0][sp][0] = nr; v[j - j0][sp][1] = ni; v[j - j0][sp][2] = tr; v[j - j0][sp][3] = ti;
+            vmax = fmax(vmax, fmax(fmax(fabs(nr), fabs(ni)), fmax(fabs(tr), fabs(ti))));
+        }
+    }
+    int E = 0;
+    if (sizeof(T) == 4 && vmax > 0.0) E = ilogb(vmax);
+    for (int j = j0; j < j1; ++j) {
+        for (int sp = 0; sp < a.NS; ++sp) {
+            const long long row = (I.cell_off + j) * a.NS + sp;
+            const double *x = v[j - j0][sp];
+            if constexpr (sizeof(T) == 4) {
+                reinterpret_cast<float4 *>(a.st)[row * a.Mp + mode] =
+                    make_float4((float)ldexp(x[0], -E), (float)ldexp(x[1], -E),
+                                (float)ldexp(x[2], -E), (float)ldexp(x[3], -E));
+            } else {
+                reinterpret_cast<double2 *>(a.st)[row * a.Mp + mode] = make_double2(x[0], x[1]);
+                reinterpret_cast<double2 *>(a.th)[row * a.Mp + mode] = make_double2(x[2], x[3]);
+            }
+        }
+    }
+    if (sizeof(T) == 4) a.ex[(I.grp_off + g) * a.Mp + mode] = (E << 8);
+}
+
+// Zeroth-order wake per instance (Eq. 5 with the unperturbed beam charge).
+struct WakeArgs {
+    const InstDev *inst;
+    const double *shape, *dens;
+    int n_inst, NS;
+    double *out;   // [cell][2] (exit, centre)
+};
+__global__ void k_wake0(const WakeArgs a) {
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= a.n_inst) return;
+    const InstDev I = a.inst[inst];
+    double n = 0.0, d = 0.0;
+    for (int j = 0; j < I.n_xi; ++j) {
+        double r = 0.0;
+        for (int sp = 0; sp < a.NS; ++sp) r += I.q[sp] * a.dens[2 * inst + sp] * a.shape[I.cell_off + j];
+        const double u = n - r;
+        const double m = fma(I.ch, u, fma(I.sh, d, r));
+        const double x = fma(I.c, u, fma(I.s, d, r));
+        d = fma(-I.s, u, I.c * d);
+        n = x;
+        a.out[2 * (I.cell_off + j)] = n;
+        a.out[2 * (I.cell_off + j) + 1] = m;
+    }
+}
+
+}  // namespace qsk

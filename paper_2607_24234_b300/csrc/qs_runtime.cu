@@ -1,0 +1,722 @@
+// qs_runtime.cu -- host runtime and C ABI of libqs.so (see include/qs.h).
+//
+// Host side (FP64): validation, the coefficient tables of the sweep
+// (cos/sin of dxi and dxi/2, kappa = 1/(1+k^2), (q/m)/gamma, (q/m)/gamma^3,
+// dt n_bs0(xi_j)), the transverse k set, the LPT-ordered work list, launch
+// selection, the autotuner and CUDA-graph capture.  Device side: the kernels
+// of qs_kernels.cuh, all enqueued on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qs.h"
+#include "qs_kernels.cuh"
+
+using qsk::InstDev;
+using qsk::SweepArgs;
+
+namespace {
+
+thread_local std::string g_init_err;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct qs_ctx {
+    // problem
+    qs_params p0;
+    std::vector<qs_params> pin;     // per instance (copies; host pointers not kept)
+    int n_inst = 1, prec = 0, NS = 1, M = 0, Mp = 0;
+    std::vector<double> kx, ky, k2;
+    std::vector<int> mode_id, partner_id;
+    std::vector<InstDev> inst;
+    std::vector<double> dens;       // [inst][2]
+    long long cells_total = 0, groups_total = 0;
+    // device
+    qs_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    std::vector<DevBuf> bufs;
+    void *st = nullptr, *th = nullptr;
+    int *ex = nullptr;
+    InstDev *inst_d = nullptr;
+    int2 *items_d = nullptr;
+    int n_items = 0;
+    double *kap_d = nullptr, *kapk2_d = nullptr, *kabs_d = nullptr, *held_d = nullptr;
+    void *w_d = nullptr;
+    double *shape_d = nullptr, *dens_d = nullptr;
+    int *mode_id_d = nullptr, *partner_d = nullptr;
+    int *ticket_d = nullptr, *err_d = nullptr;
+    size_t state_bytes = 0, th_bytes = 0, ex_bytes = 0;
+    // run state
+    long long step = 0;
+    bool seeded = false, poisoned = false;
+    int rec_kinds = 0, rec_stride = 1;
+    long long rec_g0 = 0;
+    void *rec_buf = nullptr;
+    size_t rec_bytes = 0;
+    qs_launch launch{2, 4, 0, 8};
+    int items_for_warps = -1, items_persistent = -1;
+    int n_sm = 148;
+    std::map<int, cudaGraphExec_t> graphs;
+    long long n_launch = 0;
+    std::string err;
+};
+
+namespace {
+
+qs_status fail(qs_ctx *c, qs_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_init_err = buf;
+    return st;
+}
+
+#define CU(c, x)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (x);                                                             \
+        if (e_ != cudaSuccess) return fail((c), QS_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+qs_status dalloc(qs_ctx *c, size_t bytes, void **out) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->has_alloc) {
+        p = c->alloc.alloc(bytes, c->alloc.user);
+        if (!p) return fail(c, QS_ERR_OOM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, e == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA,
+                        "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    c->bufs.push_back({p, bytes});
+    *out = p;
+    return QS_OK;
+}
+
+template <typename P>
+qs_status dalloc_t(qs_ctx *c, size_t bytes, P **out) {
+    void *v = nullptr;
+    qs_status s = dalloc(c, bytes, &v);
+    *out = static_cast<P *>(v);
+    return s;
+}
+
+qs_status upload(qs_ctx *c, void *dst, const void *src, size_t bytes) {
+    CU(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return QS_OK;
+}
+
+// Longitudinal profile n_b0(xi_j)/peak at cell centres.
+bool profile_shape(const qs_params &p, std::vector<double> &out) {
+    out.resize(p.n_xi);
+    for (int j = 0; j < p.n_xi; ++j) {
+        const double xi = (j + 0.5) * p.dxi;
+        double v = 0.0;
+        switch (p.profile) {
+        case QS_PROF_FLATTOP: v = xi <= p.length ? 1.0 : 0.0; break;
+        case QS_PROF_GAUSSIAN: {
+            const double u = (xi - p.center_xi) / p.sigma_xi;
+            v = std::exp(-0.5 * u * u);
+        } break;
+        case QS_PROF_RAMP_FLATTOP:
+            v = xi > p.length ? 0.0 : (p.ramp_len > 0.0 && xi < p.ramp_len ? xi / p.ramp_len : 1.0);
+            break;
+        case QS_PROF_USER:
+            if (!p.user_profile) return false;
+            v = p.user_profile[j];
+            break;
+        default: return false;
+        }
+        out[j] = v;
+    }
+    return true;
+}
+
+qs_status validate(const qs_params &p, int idx) {
+    if (p.geom != QS_GEOM_KLIST && p.geom != QS_GEOM_KGRID2)
+        return fail(nullptr, p.geom == 2 ? QS_ERR_UNSUPPORTED : QS_ERR_ARG, "instance %d: geom %d", idx, p.geom);
+    if (p.prec != QS_FP64 && p.prec != QS_FP32_RENORM) return fail(nullptr, QS_ERR_ARG, "instance %d: prec", idx);
+    if (p.model != QS_MODEL_FULL && p.model != QS_MODEL_REDUCED) return fail(nullptr, QS_ERR_ARG, "instance %d: model", idx);
+    if (p.front < 0 || p.front > 2) return fail(nullptr, QS_ERR_ARG, "instance %d: front", idx);
+    if (p.n_species < 1 || p.n_species > 2) return fail(nullptr, QS_ERR_ARG, "instance %d: n_species must be 1 or 2", idx);
+    for (int s = 0; s < p.n_species; ++s) {
+        const qs_species &sp = p.species[s];
+        if (!(sp.m > 0.0) || !(sp.density_ratio >= 0.0) || !std::isfinite(sp.q) || !std::isfinite(sp.density_ratio))
+            return fail(nullptr, QS_ERR_ARG, "instance %d: species %d needs m > 0, density >= 0", idx, s);
+    }
+    if (!(p.gamma_b > 1.0) || !std::isfinite(p.gamma_b)) return fail(nullptr, QS_ERR_ARG, "instance %d: gamma_b must be > 1", idx);
+    if (p.n_xi < 1) return fail(nullptr, QS_ERR_ARG, "instance %d: n_xi must be >= 1", idx);
+    if (!(p.dxi > 0.0) || !std::isfinite(p.dxi)) return fail(nullptr, QS_ERR_ARG, "instance %d: dxi must be > 0", idx);
+    if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return fail(nullptr, QS_ERR_ARG, "instance %d: dt must be > 0", idx);
+    if (p.profile < 0 || p.profile > 3) return fail(nullptr, QS_ERR_ARG, "instance %d: profile", idx);
+    if (p.profile == QS_PROF_GAUSSIAN && !(p.sigma_xi > 0.0)) return fail(nullptr, QS_ERR_ARG, "instance %d: sigma_xi", idx);
+    if (p.profile == QS_PROF_USER && !p.user_profile) return fail(nullptr, QS_ERR_ARG, "instance %d: user_profile", idx);
+    if (p.geom == QS_GEOM_KLIST && (p.n_k < 1 || !p.k_list)) return fail(nullptr, QS_ERR_ARG, "instance %d: k_list", idx);
+    if (p.geom == QS_GEOM_KGRID2 && (p.nkx < 1 || p.nky < 1 || !(p.kmax > 0.0)))
+        return fail(nullptr, QS_ERR_ARG, "instance %d: kgrid", idx);
+    if (p.front == QS_FRONT_HELD && !p.held_front) return fail(nullptr, QS_ERR_ARG, "instance %d: held_front", idx);
+    return QS_OK;
+}
+
+// Transverse wavenumbers of the active modes (row-major over the grid).
+void build_modes(qs_ctx *c, const qs_params &p) {
+    c->kx.clear(); c->ky.clear(); c->k2.clear(); c->mode_id.clear(); c->partner_id.clear();
+    if (p.geom == QS_GEOM_KLIST) {
+        for (int i = 0; i < p.n_k; ++i) {
+            const double k = p.k_list[i];
+            c->kx.push_back(k); c->ky.push_back(0.0); c->k2.push_back(k * k);
+            c->mode_id.push_back(i); c->partner_id.push_back(i);
+        }
+        return;
+    }
+    const double dkx = 2.0 * p.kmax / p.nkx, dky = 2.0 * p.kmax / p.nky, lim = p.kmax * p.kmax;
+    for (int ix = 0; ix < p.nkx; ++ix) {
+        const double kx = (ix - 0.5 * (p.nkx - 1)) * dkx;
+        for (int iy = 0; iy < p.nky; ++iy) {
+            const double ky = (iy - 0.5 * (p.nky - 1)) * dky;
+            const double k2 = kx * kx + ky * ky;
+            if (p.disc_mask && !(k2 <= lim)) continue;
+            c->kx.push_back(kx); c->ky.push_back(ky); c->k2.push_back(k2);
+            c->mode_id.push_back(ix * p.nky + iy);
+            c->partner_id.push_back((p.nkx - 1 - ix) * p.nky + (p.nky - 1 - iy));
+        }
+    }
+}
+
+bool same_kset(const qs_params &a, const qs_params &b) {
+    if (a.geom != b.geom) return false;
+    if (a.geom == QS_GEOM_KLIST) {
+        if (a.n_k != b.n_k) return false;
+        for (int i = 0; i < a.n_k; ++i)
+            if (a.k_list[i] != b.k_list[i]) return false;
+        return true;
+    }
+    return a.nkx == b.nkx && a.nky == b.nky && a.kmax == b.kmax && a.disc_mask == b.disc_mask;
+}
+
+qs_status build_items(qs_ctx *c) {
+    const int wpc = c->launch.warps_per_cta, P = c->launch.persistent;
+    if (c->items_for_warps == wpc && c->items_persistent == P && c->items_d) return QS_OK;
+    const int per = 32 * wpc;
+    std::vector<int2> items;
+    std::vector<int> order(c->n_inst);
+    for (int i = 0; i < c->n_inst; ++i) order[i] = i;
+    if (P)   // longest lines first (LPT)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return c->inst[a].n_xi > c->inst[b].n_xi; });
+    for (int i : order)
+        for (int m = 0; m < c->M; m += per) items.push_back(make_int2(i, m));
+    const size_t need = items.size() * sizeof(int2);
+    // reuse the buffer when it is big enough (the maximum: one item per 32 modes)
+    if (!c->items_d) {
+        const size_t maxb = (size_t)c->n_inst * ((c->M + 31) / 32) * sizeof(int2);
+        qs_status s = dalloc_t(c, maxb, &c->items_d);
+        if (s) return s;
+    }
+    qs_status s = upload(c, c->items_d, items.data(), need);
+    if (s) return s;
+    CU(c, cudaStreamSynchronize(c->stream));   // host vector dies at return
+    c->n_items = (int)items.size();
+    c->items_for_warps = wpc;
+    c->items_persistent = P;
+    return QS_OK;
+}
+
+template <typename T, int NS, int U, bool REC>
+cudaError_t launch_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) {
+    qsk::k_sweep<T, NS, U, REC><<<grid, threads, 0, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int NS, bool REC>
+cudaError_t launch_u(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads, int U) {
+    if constexpr (sizeof(T) == 4) {
+        if (U >= 8) return launch_t<T, NS, 8, REC>(c, a, grid, threads);
+        return launch_t<T, NS, 4, REC>(c, a, grid, threads);
+    } else {
+        if (U >= 4) return launch_t<T, NS, 4, REC>(c, a, grid, threads);
+        return launch_t<T, NS, 2, REC>(c, a, grid, threads);
+    }
+}
+
+// One launch of the sweep kernel for n_steps steps starting at global step
+// step0.  update = 0 runs the field pass only.  rec: record target (may be
+// null).
+qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
+                       double *rec, long long rec_g0, int rec_stride, long long rec_max_snap) {
+    qs_status s = build_items(c);
+    if (s) return s;
+    SweepArgs a{};
+    a.st = c->st; a.th = c->th; a.ex = c->ex;
+    a.inst = c->inst_d; a.items = c->items_d; a.n_items = c->n_items;
+    a.kap = c->kap_d; a.kapk2 = c->kapk2_d; a.kabs = c->kabs_d; a.held = c->held_d;
+    a.w = c->w_d;
+    a.Mp = c->Mp; a.M = c->M; a.n_inst = c->n_inst;
+    a.front = c->p0.front;
+    a.step0 = step0; a.n_steps = n_steps; a.update = update;
+    a.persistent = c->launch.persistent;
+    a.rec_kinds = rec ? rec_kinds : 0;
+    a.rec = rec; a.rec_g0 = rec_g0; a.rec_stride = rec_stride; a.rec_max_snap = rec_max_snap;
+    a.cells_total = c->cells_total;
+    const long long plane = c->cells_total * c->Mp;
+    long long off = 0;
+    a.rec_off_mag = off; if (rec_kinds & QS_REC_MAG) off += 5 * plane;
+    a.rec_off_np = off;  if (rec_kinds & QS_REC_NP) off += 2 * plane;
+    a.rec_off_mm = off;  if (rec_kinds & QS_REC_MODEMAX) off += 3LL * c->n_inst * c->Mp;
+    a.rec_snap_doubles = off;
+    a.ticket = c->ticket_d; a.err = c->err_d;
+    const int threads = 32 * c->launch.warps_per_cta;
+    dim3 grid(c->n_items);
+    if (a.persistent) {
+        CU(c, cudaMemsetAsync(c->ticket_d, 0, sizeof(int), c->stream));
+        long long g = (long long)c->launch.ctas_per_sm * c->n_sm;
+        grid = dim3((unsigned)std::max<long long>(1, std::min<long long>(g, c->n_items)));
+    }
+    const bool R = a.rec_kinds != 0;
+    const int U = c->launch.prefetch;
+    cudaError_t e;
+    if (c->prec == QS_FP32_RENORM) {
+        if (c->NS == 1) e = R ? launch_u<float, 1, true>(c, a, grid, threads, U) : launch_u<float, 1, false>(c, a, grid, threads, U);
+        else e = R ? launch_u<float, 2, true>(c, a, grid, threads, U) : launch_u<float, 2, false>(c, a, grid, threads, U);
+    } else {
+        if (c->NS == 1) e = R ? launch_u<double, 1, true>(c, a, grid, threads, U) : launch_u<double, 1, false>(c, a, grid, threads, U);
+        else e = R ? launch_u<double, 2, true>(c, a, grid, threads, U) : launch_u<double, 2, false>(c, a, grid, threads, U);
+    }
+    if (e != cudaSuccess) return fail(c, QS_ERR_CUDA, "sweep launch: %s", cudaGetErrorString(e));
+    ++c->n_launch;
+    return QS_OK;
+}
+
+long long snapshot_doubles(const qs_ctx *c, int kinds) {
+    const long long plane = c->cells_total * c->Mp;
+    long long d = 0;
+    if (kinds & QS_REC_MAG) d += 5 * plane;
+    if (kinds & QS_REC_NP) d += 2 * plane;
+    if (kinds & QS_REC_MODEMAX) d += 3LL * c->n_inst * c->Mp;
+    return d;
+}
+
+qs_status check_ready(qs_ctx *c) {
+    if (!c) return QS_ERR_ARG;
+    if (c->poisoned) return fail(c, QS_ERR_STATE, "context poisoned by an earlier device error; reseed");
+    if (!c->seeded) return fail(c, QS_ERR_STATE, "qs_seed has not been called");
+    return QS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
+                  const qs_allocator *alloc, void *stream, qs_ctx **out) {
+    if (!p || !out) return fail(nullptr, QS_ERR_ARG, "null params or out");
+    *out = nullptr;
+    if (n_inst < 1) return fail(nullptr, QS_ERR_ARG, "n_inst must be >= 1");
+    qs_status st = validate(*p, -1);
+    if (st) return st;
+    for (int i = 0; per_inst && i < n_inst; ++i) {
+        const qs_params &q = per_inst[i];
+        if ((st = validate(q, i))) return st;
+        if (q.prec != p->prec || q.model != p->model || q.front != p->front ||
+            q.n_species != p->n_species || !same_kset(q, *p))
+            return fail(nullptr, QS_ERR_ARG, "instance %d differs from the shared params in "
+                        "prec/model/front/n_species/k set", i);
+    }
+    qs_ctx *c = new qs_ctx();
+    c->p0 = *p;
+    c->n_inst = n_inst;
+    c->prec = p->prec;
+    c->NS = p->n_species;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (alloc && alloc->alloc && alloc->free) { c->alloc = *alloc; c->has_alloc = true; }
+    build_modes(c, *p);
+    c->M = (int)c->k2.size();
+    if (c->M < 1) { delete c; return fail(nullptr, QS_ERR_ARG, "no active mode (disc mask empty)"); }
+    c->Mp = (c->M + 31) / 32 * 32;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) c->n_sm = v;
+    } else {
+        cudaGetLastError();
+    }
+    // per-instance tables
+    std::vector<double> shape_all, w_all;
+    c->inst.resize(n_inst);
+    c->dens.assign(2 * (size_t)n_inst, 0.0);
+    long long cell = 0, grp = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const qs_params &q = per_inst ? per_inst[i] : *p;
+        std::vector<double> shp;
+        if (!profile_shape(q, shp)) { delete c; return fail(nullptr, QS_ERR_ARG, "instance %d: profile", i); }
+        InstDev &I = c->inst[i];
+        I.n_xi = q.n_xi;
+        I.n_grp = (q.n_xi + qsk::GRP - 1) / qsk::GRP;
+        I.cell_off = cell;
+        I.grp_off = grp;
+        I.c = std::cos(q.dxi); I.s = std::sin(q.dxi);
+        I.ch = std::cos(0.5 * q.dxi); I.sh = std::sin(0.5 * q.dxi);
+        I.dt = q.dt; I.dxi = q.dxi;
+        const double g = q.gamma_b;
+        for (int s = 0; s < 2; ++s) {
+            if (s < q.n_species) {
+                const double qm = q.species[s].q / q.species[s].m;
+                I.q[s] = q.species[s].q;
+                I.qm_g[s] = qm / g;
+                I.qm_g3[s] = q.model == QS_MODEL_REDUCED ? 0.0 : qm / (g * g * g);
+                c->dens[2 * i + s] = q.species[s].density_ratio;
+            } else {
+                I.q[s] = 0.0; I.qm_g[s] = 0.0; I.qm_g3[s] = 0.0;
+            }
+        }
+        for (int j = 0; j < q.n_xi; ++j) {
+            shape_all.push_back(shp[j]);
+            for (int s = 0; s < c->NS; ++s) w_all.push_back(q.dt * q.species[s].density_ratio * shp[j]);
+        }
+        cell += q.n_xi;
+        grp += I.n_grp;
+    }
+    c->cells_total = cell;
+    c->groups_total = grp;
+    c->pin.assign(n_inst, *p);
+    for (int i = 0; per_inst && i < n_inst; ++i) c->pin[i] = per_inst[i];
+    // per-mode tables (padding modes: k = 0, never stepped)
+    std::vector<double> kap(c->Mp, 1.0), kapk2(c->Mp, 0.0), kabs(c->Mp, 0.0);
+    std::vector<int> mid(c->Mp, 0), pid(c->Mp, 0);
+    for (int m = 0; m < c->M; ++m) {
+        kap[m] = 1.0 / (1.0 + c->k2[m]);
+        kapk2[m] = c->k2[m] * kap[m];
+        kabs[m] = std::sqrt(c->k2[m]);
+        mid[m] = c->mode_id[m];
+        pid[m] = c->partner_id[m];
+    }
+    // device buffers
+    const size_t rows = (size_t)c->cells_total * c->NS;
+    const size_t esz = c->prec == QS_FP32_RENORM ? sizeof(float4) : sizeof(double2);
+    c->state_bytes = rows * c->Mp * esz;
+    c->th_bytes = c->prec == QS_FP64 ? c->state_bytes : 0;
+    c->ex_bytes = c->prec == QS_FP32_RENORM ? (size_t)c->groups_total * c->Mp * sizeof(int) : 0;
+#define ALLOC(ptr, bytes) do { if ((st = dalloc_t(c, (bytes), &(ptr)))) { qs_free(c); g_init_err = "allocation failed"; return st; } } while (0)
+    ALLOC(c->st, c->state_bytes);
+    if (c->th_bytes) ALLOC(c->th, c->th_bytes);
+    if (c->ex_bytes) ALLOC(c->ex, c->ex_bytes);
+    ALLOC(c->inst_d, sizeof(InstDev) * n_inst);
+    ALLOC(c->kap_d, sizeof(double) * c->Mp);
+    ALLOC(c->kapk2_d, sizeof(double) * c->Mp);
+    ALLOC(c->kabs_d, sizeof(double) * c->Mp);
+    ALLOC(c->shape_d, sizeof(double) * c->cells_total);
+    ALLOC(c->dens_d, sizeof(double) * 2 * n_inst);
+    ALLOC(c->mode_id_d, sizeof(int) * c->Mp);
+    ALLOC(c->partner_d, sizeof(int) * c->Mp);
+    ALLOC(c->ticket_d, sizeof(int) * 4);
+    ALLOC(c->err_d, sizeof(int) * 4);
+    ALLOC(c->w_d, (c->prec == QS_FP32_RENORM ? sizeof(float) : sizeof(double)) * rows);
+    if (p->front == QS_FRONT_HELD) ALLOC(c->held_d, sizeof(double) * 4 * (size_t)n_inst * c->Mp);
+#undef ALLOC
+    auto up = [&](void *d, const void *h, size_t b) -> qs_status {
+        cudaError_t e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? QS_OK : fail(c, QS_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    };
+    std::vector<float> wf;
+    if (c->prec == QS_FP32_RENORM) { wf.assign(w_all.begin(), w_all.end()); }
+    if ((st = up(c->inst_d, c->inst.data(), sizeof(InstDev) * n_inst)) ||
+        (st = up(c->kap_d, kap.data(), sizeof(double) * c->Mp)) ||
+        (st = up(c->kapk2_d, kapk2.data(), sizeof(double) * c->Mp)) ||
+        (st = up(c->kabs_d, kabs.data(), sizeof(double) * c->Mp)) ||
+        (st = up(c->shape_d, shape_all.data(), sizeof(double) * c->cells_total)) ||
+        (st = up(c->dens_d, c->dens.data(), sizeof(double) * 2 * n_inst)) ||
+        (st = up(c->mode_id_d, mid.data(), sizeof(int) * c->Mp)) ||
+        (st = up(c->partner_d, pid.data(), sizeof(int) * c->Mp)) ||
+        (st = up(c->w_d, c->prec == QS_FP32_RENORM ? (const void *)wf.data() : (const void *)w_all.data(),
+                 (c->prec == QS_FP32_RENORM ? sizeof(float) : sizeof(double)) * rows))) {
+        g_init_err = c->err; qs_free(c); return st;
+    }
+    if (c->held_d) {
+        std::vector<double> h(4 * (size_t)n_inst * c->Mp, 0.0);
+        for (int i = 0; i < n_inst; ++i) {
+            const double *src = (per_inst ? per_inst[i] : *p).held_front;
+            for (int m = 0; m < c->M; ++m)
+                for (int k = 0; k < 4; ++k) h[((size_t)i * c->Mp + m) * 4 + k] = src[4 * m + k];
+        }
+        if ((st = up(c->held_d, h.data(), h.size() * sizeof(double)))) { g_init_err = c->err; qs_free(c); return st; }
+    }
+    cudaError_t e1 = cudaMemsetAsync(c->st, 0, c->state_bytes, c->stream);
+    cudaError_t e2 = c->th ? cudaMemsetAsync(c->th, 0, c->th_bytes, c->stream) : cudaSuccess;
+    cudaError_t e3 = c->ex ? cudaMemsetAsync(c->ex, 0, c->ex_bytes, c->stream) : cudaSuccess;
+    cudaError_t e4 = cudaMemsetAsync(c->err_d, 0, 4 * sizeof(int), c->stream);
+    if (e1 || e2 || e3 || e4) { g_init_err = "memset failed"; qs_free(c); return QS_ERR_CUDA; }
+    // default launch shape: the FP64 path keeps fewer cells in flight per thread
+    c->launch = qs_launch{2, c->prec == QS_FP32_RENORM ? 8 : 4, n_inst > 1 ? 1 : 0, 8};
+    *out = c;
+    return QS_OK;
+}
+
+qs_status qs_seed(qs_ctx *c, uint64_t seed, double amplitude, int kind, const void *user,
+                  size_t user_bytes, int user_on_host) {
+    if (!c) return QS_ERR_ARG;
+    if (kind < 0 || kind > 3) return fail(c, QS_ERR_ARG, "seed kind %d", kind);
+    if (kind == QS_SEED_STATE) {
+        // checkpoint: header (8 int64) + state + theta + exponents
+        const size_t need = 64 + c->state_bytes + c->th_bytes + c->ex_bytes;
+        if (!user || user_bytes < need) return fail(c, QS_ERR_ARG, "checkpoint needs %zu bytes", need);
+        int64_t hdr[8];
+        cudaMemcpyKind k = user_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        if (user_on_host) memcpy(hdr, user, 64);
+        else CU(c, cudaMemcpy(hdr, user, 64, cudaMemcpyDeviceToHost));
+        if (hdr[0] != 0x51534350 || hdr[1] != c->prec || hdr[2] != c->NS || hdr[3] != c->Mp ||
+            hdr[4] != c->cells_total)
+            return fail(c, QS_ERR_ARG, "checkpoint does not match this context");
+        const char *u = static_cast<const char *>(user) + 64;
+        CU(c, cudaMemcpyAsync(c->st, u, c->state_bytes, k, c->stream));
+        if (c->th_bytes) CU(c, cudaMemcpyAsync(c->th, u + c->state_bytes, c->th_bytes, k, c->stream));
+        if (c->ex_bytes) CU(c, cudaMemcpyAsync(c->ex, u + c->state_bytes + c->th_bytes, c->ex_bytes, k, c->stream));
+        if (user_on_host) CU(c, cudaStreamSynchronize(c->stream));
+        c->step = hdr[5];
+    } else {
+        qsk::SeedArgs a{};
+        a.st = c->st; a.th = c->th; a.ex = c->ex;
+        a.inst = c->inst_d; a.shape = c->shape_d; a.dens = c->dens_d;
+        a.mode_id = c->mode_id_d; a.partner_id = c->partner_d;
+        a.Mp = c->Mp; a.M = c->M; a.NS = c->NS; a.n_inst = c->n_inst;
+        a.kind = kind; a.seed = seed; a.amp = amplitude;
+        a.total_groups = c->groups_total;
+        void *tmp = nullptr;
+        if (kind == QS_SEED_IMPULSE) {
+            for (int i = 0; i < c->n_inst; ++i)
+                if (!(c->pin[i].species[0].q != 0.0) || !(c->dens[2 * i] > 0.0))
+                    return fail(c, QS_ERR_ARG, "impulse seed needs q_0 != 0 and n_b00 > 0");
+        }
+        if (kind == QS_SEED_USER) {
+            const size_t need = (size_t)c->M * c->NS * c->cells_total * 16;
+            if (!user || user_bytes < need) return fail(c, QS_ERR_ARG, "user seed needs %zu bytes", need);
+            if (user_on_host) {
+                qs_status s = dalloc(c, need, &tmp);
+                if (s) return s;
+                CU(c, cudaMemcpyAsync(tmp, user, need, cudaMemcpyHostToDevice, c->stream));
+                a.user = static_cast<const double *>(tmp);
+            } else {
+                a.user = static_cast<const double *>(user);
+            }
+        }
+        CU(c, cudaMemsetAsync(c->st, 0, c->state_bytes, c->stream));
+        if (c->th) CU(c, cudaMemsetAsync(c->th, 0, c->th_bytes, c->stream));
+        dim3 grid((c->Mp + 127) / 128, (unsigned)std::min<long long>(c->groups_total, 65535),
+                  (unsigned)((c->groups_total + 65534) / 65535));
+        if (c->prec == QS_FP32_RENORM) qsk::k_seed<float><<<grid, 128, 0, c->stream>>>(a);
+        else qsk::k_seed<double><<<grid, 128, 0, c->stream>>>(a);
+        CU(c, cudaGetLastError());
+        if (tmp) {
+            CU(c, cudaStreamSynchronize(c->stream));
+            // release the staging buffer now
+            for (size_t i = 0; i < c->bufs.size(); ++i)
+                if (c->bufs[i].p == tmp) {
+                    if (c->has_alloc) c->alloc.free(tmp, c->alloc.user); else cudaFree(tmp);
+                    c->bufs.erase(c->bufs.begin() + i);
+                    break;
+                }
+        }
+        c->step = 0;
+    }
+    CU(c, cudaMemsetAsync(c->err_d, 0, 4 * sizeof(int), c->stream));
+    c->seeded = true;
+    c->poisoned = false;
+    return QS_OK;
+}
+
+qs_status qs_step(qs_ctx *c, int n_steps) {
+    qs_status s = check_ready(c);
+    if (s) return s;
+    if (n_steps < 1) return fail(c, QS_ERR_ARG, "n_steps must be >= 1");
+    long long max_snap = 0;
+    if (c->rec_buf) {
+        // number of snapshots this call would write must fit the buffer
+        const long long snapd = snapshot_doubles(c, c->rec_kinds);
+        max_snap = (long long)(c->rec_bytes / (size_t)(snapd * 8));
+        const long long last = c->step + n_steps - 1;
+        if (last >= c->rec_g0) {
+            const long long d = last - c->rec_g0;
+            if (d / c->rec_stride >= max_snap)
+                return fail(c, QS_ERR_ARG, "record buffer holds %lld snapshots; this call reaches snapshot %lld",
+                            max_snap, d / c->rec_stride);
+        }
+    }
+    s = launch_sweep(c, c->step, n_steps, 1, c->rec_buf ? c->rec_kinds : 0,
+                     static_cast<double *>(c->rec_buf), c->rec_g0, c->rec_stride, max_snap);
+    if (s) return s;
+    c->step += n_steps;
+    return QS_OK;
+}
+
+qs_status qs_record(qs_ctx *c, int kinds, int stride, void *dev_out, size_t out_bytes) {
+    if (!c) return QS_ERR_ARG;
+    if (kinds == 0 || !dev_out) {
+        c->rec_buf = nullptr; c->rec_kinds = 0; c->rec_bytes = 0;
+        return QS_OK;
+    }
+    if ((kinds & ~7) || stride < 1) return fail(c, QS_ERR_ARG, "record kinds/stride");
+    const long long snapd = snapshot_doubles(c, kinds);
+    if (out_bytes < (size_t)snapd * 8) return fail(c, QS_ERR_ARG, "record buffer smaller than one snapshot (%lld bytes)", snapd * 8);
+    c->rec_kinds = kinds; c->rec_stride = stride; c->rec_buf = dev_out; c->rec_bytes = out_bytes;
+    c->rec_g0 = c->step;
+    return QS_OK;
+}
+
+qs_status qs_diag(qs_ctx *c, int kind, void *out, size_t out_bytes, int out_on_host) {
+    if (!c || !out) return c ? fail(c, QS_ERR_ARG, "null out") : QS_ERR_ARG;
+    if (kind == QS_DIAG_STATE) {
+        if (!c->seeded) return fail(c, QS_ERR_STATE, "not seeded");
+        const size_t need = 64 + c->state_bytes + c->th_bytes + c->ex_bytes;
+        if (out_bytes < need) return fail(c, QS_ERR_ARG, "checkpoint needs %zu bytes", need);
+        int64_t hdr[8] = {0x51534350, c->prec, c->NS, c->Mp, c->cells_total, c->step, c->groups_total, 1};
+        cudaMemcpyKind k = out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        char *o = static_cast<char *>(out);
+        if (out_on_host) memcpy(o, hdr, 64);
+        else CU(c, cudaMemcpyAsync(o, hdr, 64, cudaMemcpyHostToDevice, c->stream));
+        CU(c, cudaMemcpyAsync(o + 64, c->st, c->state_bytes, k, c->stream));
+        if (c->th_bytes) CU(c, cudaMemcpyAsync(o + 64 + c->state_bytes, c->th, c->th_bytes, k, c->stream));
+        if (c->ex_bytes) CU(c, cudaMemcpyAsync(o + 64 + c->state_bytes + c->th_bytes, c->ex, c->ex_bytes, k, c->stream));
+        CU(c, cudaStreamSynchronize(c->stream));   // hdr lives on this stack frame
+        return QS_OK;
+    }
+    size_t need;
+    double *dst = nullptr;
+    void *tmp = nullptr;
+    if (kind == QS_DIAG_WAKE0) {
+        need = (size_t)c->cells_total * 2 * sizeof(double);
+    } else if (kind >= 1 && kind <= 7) {
+        qs_status s = check_ready(c);
+        if (s) return s;
+        need = (size_t)snapshot_doubles(c, kind) * 8;
+    } else {
+        return fail(c, QS_ERR_ARG, "diag kind %d", kind);
+    }
+    if (out_bytes < need) return fail(c, QS_ERR_ARG, "diag needs %zu bytes", need);
+    if (out_on_host) {
+        qs_status s = dalloc(c, need, &tmp);
+        if (s) return s;
+        dst = static_cast<double *>(tmp);
+    } else {
+        dst = static_cast<double *>(out);
+    }
+    qs_status s = QS_OK;
+    if (kind == QS_DIAG_WAKE0) {
+        qsk::WakeArgs w{c->inst_d, c->shape_d, c->dens_d, c->n_inst, c->NS, dst};
+        qsk::k_wake0<<<(c->n_inst + 63) / 64, 64, 0, c->stream>>>(w);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = fail(c, QS_ERR_CUDA, "wake launch: %s", cudaGetErrorString(e));
+    } else {
+        s = launch_sweep(c, c->step, 1, 0, kind, dst, c->step, 1, 1);
+    }
+    if (out_on_host) {
+        if (s == QS_OK) {
+            cudaError_t e = cudaMemcpyAsync(out, dst, need, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) s = fail(c, QS_ERR_CUDA, "diag copy: %s", cudaGetErrorString(e));
+        }
+        for (size_t i = 0; i < c->bufs.size(); ++i)
+            if (c->bufs[i].p == tmp) {
+                if (c->has_alloc) c->alloc.free(tmp, c->alloc.user); else cudaFree(tmp);
+                c->bufs.erase(c->bufs.begin() + i);
+                break;
+            }
+        if (s == QS_OK) s = qs_sync(c);
+    }
+    return s;
+}
+
+qs_status qs_query(const qs_ctx *c, int what, int64_t arg, int64_t *value) {
+    if (!c || !value) return QS_ERR_ARG;
+    switch (what) {
+    case QS_Q_N_MODES: *value = c->M; break;
+    case QS_Q_MODES_PADDED: *value = c->Mp; break;
+    case QS_Q_N_INST: *value = c->n_inst; break;
+    case QS_Q_TOTAL_CELLS: *value = c->cells_total; break;
+    case QS_Q_STEP: *value = c->step; break;
+    case QS_Q_STATE_BYTES: *value = (int64_t)(64 + c->state_bytes + c->th_bytes + c->ex_bytes); break;
+    case QS_Q_SNAPSHOT_BYTES: *value = snapshot_doubles(c, (int)arg) * 8; break;
+    case QS_Q_CELL_OFFSET:
+        if (arg < 0 || arg >= c->n_inst) return QS_ERR_ARG;
+        *value = c->inst[arg].cell_off;
+        break;
+    case QS_Q_LAUNCH:
+        *value = c->launch.warps_per_cta | (c->launch.prefetch << 8) | (c->launch.persistent << 16) |
+                 ((int64_t)c->launch.ctas_per_sm << 24);
+        break;
+    default: return QS_ERR_ARG;
+    }
+    return QS_OK;
+}
+
+qs_status qs_modes(const qs_ctx *c, double *kx, double *ky) {
+    if (!c || !kx || !ky) return QS_ERR_ARG;
+    for (int m = 0; m < c->M; ++m) { kx[m] = c->kx[m]; ky[m] = c->ky[m]; }
+    return QS_OK;
+}
+
+qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
+    if (!c || !l) return QS_ERR_ARG;
+    const int w = l->warps_per_cta;
+    if (!(w == 1 || w == 2 || w == 4 || w == 8)) return fail(c, QS_ERR_ARG, "warps_per_cta");
+    if (c->prec == QS_FP32_RENORM ? !(l->prefetch == 4 || l->prefetch == 8) : !(l->prefetch == 2 || l->prefetch == 4))
+        return fail(c, QS_ERR_ARG, "prefetch must be 4|8 (FP32) or 2|4 (FP64)");
+    if (l->persistent && (l->ctas_per_sm < 1 || l->ctas_per_sm > 64)) return fail(c, QS_ERR_ARG, "ctas_per_sm");
+    c->launch = *l;
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    c->graphs.clear();
+    return QS_OK;
+}
+
+qs_status qs_get_launch(const qs_ctx *c, qs_launch *l) {
+    if (!c || !l) return QS_ERR_ARG;
+    *l = c->launch;
+    return QS_OK;
+}
+
+qs_status qs_sync(qs_ctx *c) {
+    if (!c) return QS_ERR_ARG;
+    CU(c, cudaStreamSynchronize(c->stream));
+    int e = 0;
+    CU(c, cudaMemcpy(&e, c->err_d, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        c->poisoned = true;
+        if (e & qsk::ERR_TIMEOUT) return fail(c, QS_ERR_TIMEOUT, "a bounded device wait ran out");
+        return fail(c, QS_ERR_NONFINITE, "non-finite value in the state");
+    }
+    return QS_OK;
+}
+
+int64_t qs_launch_count(const qs_ctx *c) { return c ? c->n_launch : -1; }
+
+const char *qs_last_error(const qs_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+
+void qs_free(qs_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    for (auto &b : c->bufs) {
+        if (c->has_alloc) c->alloc.free(b.p, c->alloc.user); else cudaFree(b.p);
+    }
+    delete c;
+}
+
+}  // extern "C"
+
+#include "qs_tune.inc"
