@@ -234,6 +234,46 @@ int64_t qs_launch_count(const qs_ctx *ctx);
 const char *qs_last_error(const qs_ctx *ctx);
 void qs_free(qs_ctx *ctx);
 
+/* Allocation-free sweep (the paper has no counterpart; this is a service to
+ * callers that must not allocate device memory when they step the solver,
+ * e.g. a host framework whose memory pool forbids driver allocations in its
+ * steady-state loop, or code where an allocation could synchronise the
+ * device or fail mid-run).  No context is created and nothing is allocated:
+ * no cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * The caller owns the state, in the library's internal layout with
+ * Mp = active modes rounded up to a multiple of 32:
+ *   QS_FP32_RENORM: state = float4 [n_xi][n_species][Mp]
+ *                   (Re n_b, Im n_b, Re Theta, Im Theta) and exponents =
+ *                   int32 [ceil(n_xi/32)][Mp] (value = mantissa * 2^(e >> 8));
+ *                   theta = NULL.
+ *   QS_FP64:        state = double2 n_b [n_xi][n_species][Mp],
+ *                   theta = double2 Theta [n_xi][n_species][Mp];
+ *                   exponents = NULL.
+ * (the same bytes qs_diag(QS_DIAG_STATE) writes after its 64-byte header).
+ * The call advances them in place by n_steps slow-time steps starting at
+ * global step step0 (step 0 kicks by dt/2), asynchronously on `stream`.
+ * If dev_status is not NULL, the device error bits of this call (1:
+ * non-finite value) are copied to that device int at the end.
+ *
+ * Everything else the sweep needs -- mode tables, profile weights, work
+ * list, scheduler ticket, error word -- lives in one fixed 4 MiB device
+ * array of this library, held by every GPU that loads it until the process
+ * exits.  Limits: it must hold 3*Mp doubles + ceil(M/64) work items +
+ * n_xi*n_species profile weights (about 4 MiB in total, e.g. Mp up to
+ * ~150,000 with n_xi = 8,192); larger problems are rejected with QS_ERR_ARG
+ * before anything is enqueued.  QS_FRONT_HELD is not supported here
+ * (QS_ERR_UNSUPPORTED); one instance per call.
+ *
+ * The first call on a device looks up the array's address once
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture.  Every call reuses the same array and leaves
+ * its contents behind (the ticket and error word are cleared at the start
+ * of each call), so calls whose work overlaps on the GPU, e.g. on two
+ * streams, race on it. */
+qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *theta, int *exponents,
+                           int64_t step0, int n_steps, int *dev_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,9 @@ def _load():
     L.qs_last_error.restype = ctypes.c_char_p
     L.qs_free.argtypes = [vp]
     L.qs_free.restype = None
+    L.qs_sweep_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, ctypes.POINTER(ctypes.c_int), i64,
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
+    L.qs_sweep_noalloc.restype = ctypes.c_int
     for name in ("qs_init", "qs_seed", "qs_step", "qs_record", "qs_diag", "qs_query", "qs_modes",
                  "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_sync"):
         getattr(L, name).restype = ctypes.c_int

@@ -452,7 +452,7 @@ struct WakeArgs {
     int n_inst, NS;
     double *out;   // [cell][2] (exit, centre)
 };
-__global__ void k_wake0(const WakeArgs a) {
+static __global__ void k_wake0(const WakeArgs a) {
     const int inst = blockIdx.x * blockDim.x + threadIdx.x;
     if (inst >= a.n_inst) return;
     const InstDev I = a.inst[inst];
