@@ -116,15 +116,14 @@ def cpu_oracle_rate(problem, target_s=10.0, modes_sample=None, steps_cap=None):
     nb, th = oracle.seed_noise(problem, 0, problem["amplitude"], mode_sel=sel)
     k2 = md["k2"][sel]
     oracle.sweep(problem, nb, th, 0, 1, k2=k2)          # warm the thread pool
-    t0 = time.perf_counter()
-    oracle.sweep(problem, nb, th, 1, 3, k2=k2)
-    t1 = (time.perf_counter() - t0) / 3
-    steps = max(1, int(target_s / max(t1, 1e-6)))
-    if steps_cap:
-        steps = min(steps, steps_cap)
-    t0 = time.perf_counter()
-    oracle.sweep(problem, nb, th, 4, steps, k2=k2)
-    dt = time.perf_counter() - t0
+    # run in chunks until ~target_s of CPU time has elapsed
+    steps, chunk, dt = 0, 4, 0.0
+    while dt < target_s and (steps_cap is None or steps < steps_cap):
+        t0 = time.perf_counter()
+        oracle.sweep(problem, nb, th, 1 + steps, chunk, k2=k2)
+        dt += time.perf_counter() - t0
+        steps += chunk
+        chunk = min(chunk * 2, 256)
     upd = modes_sample * problem["n_xi"] * steps
     return upd / dt, cores, (f"{modes_sample} of {len(md['k2'])} mode lines x {problem['n_xi']} cells x "
                              f"{steps} steps ({dt:.1f} s, FP64, OpenMP over lines)")
@@ -298,7 +297,8 @@ def run_ours(args):
                          "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                          "peak_source": pk_kind,
                          "algorithmic_bytes_per_update": BYTES_PER_UPDATE_FP32,
-                         "kernel": "qsk::k_sweep<float,1,U,false>"},
+                         "kernel": ("qsk::k_sweep_tma<float,1,C,ST>" if launch.get("variant") == 1
+                                    else "qsk::k_sweep<float,1,U,false>")},
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "fp64": fp64,
             "cpu_baseline": cpu, "wall_s": wall,
         }
@@ -319,7 +319,8 @@ def main():
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
-    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the autotuner (use the library's default launch shape)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     args = ap.parse_args()

@@ -204,11 +204,17 @@ qs_status qs_query(const qs_ctx *ctx, int what, int64_t arg, int64_t *value);
 qs_status qs_modes(const qs_ctx *ctx, double *kx, double *ky);
 
 /* Launch shape of the sweep kernel. */
+enum { QS_VARIANT_REGISTERS = 0,  /* thread per line, register prefetch       */
+       QS_VARIANT_TMA = 1 };      /* thread per line, warp-wide TMA tiles of
+                                   * (cells x 32 modes) through shared memory */
 typedef struct {
-    int warps_per_cta;   /* 1, 2, 4 or 8: each thread owns one mode line    */
-    int prefetch;        /* cells per register batch: 4 or 8                */
+    int warps_per_cta;   /* REGISTERS: 1, 2, 4 or 8 (TMA: always 1)         */
+    int prefetch;        /* REGISTERS: cells per register batch (FP32 4|8,
+                          * FP64 2|4); TMA: cells per tile (FP32 8|16,
+                          * FP64 4|8)                                       */
     int persistent;      /* 1: LPT-ordered work list pulled by atomic ticket */
     int ctas_per_sm;     /* persistent grid size = ctas_per_sm * SM count    */
+    int variant;         /* QS_VARIANT_*                                    */
 } qs_launch;
 
 qs_status qs_set_launch(qs_ctx *ctx, const qs_launch *l);

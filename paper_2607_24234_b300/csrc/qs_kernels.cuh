@@ -15,6 +15,7 @@
 // independent for all time, so a launch runs all requested slow-time steps
 // of its line before taking the next one.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -200,100 +201,125 @@ struct Line {
         if (a.rec_kinds & 4) { mm0 = fmax(mm0, lnb); mm1 = fmax(mm1, lE); mm2 = fmax(mm2, lB); }
     }
 
+    // One cell: x[NS] holds (n_b, Theta) of cell j as stored (mantissas on
+    // the FP32 path), w[NS] = dt n_bs0(xi_j).  Advances P across the cell,
+    // records the fields if asked, pushes and stores the beam state.
+    __device__ __forceinline__ void cell(Cell<T> *x, const T *w, const int j, const int N) {
+        if constexpr (RN) {
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) {
+                x[sp].nr *= facM; x[sp].ni *= facM; x[sp].tr *= facM; x[sp].ti *= facM;
+            }
+        }
+        T rr = q[0] * x[0].nr, ri = q[0] * x[0].ni;
+        if (NS == 2) { rr = fma(q[NS - 1], x[NS - 1].nr, rr); ri = fma(q[NS - 1], x[NS - 1].ni, ri); }
+        if (j == 0 && a.front == 1) { nr = rr; ni = ri; dr = 0; di = 0; }
+        // u = n_p - rho; centre:  n_mid = ch u + sh n' + rho
+        const T ur = nr - rr, ui = ni - ri;
+        const T mr = fma(ch, ur, fma(sh, dr, rr));
+        const T mi = fma(ch, ui, fma(sh, di, ri));
+        if (REC && rec) {
+            const T mdr = fma(-sh, ur, ch * dr), mdi = fma(-sh, ui, ch * di);
+            record(j, mr, mi, mdr, mdi, rr, ri, x);
+        }
+        // cell exit: n = c u + s n' + rho, n' = -s u + c n'
+        const T xr = fma(c, ur, fma(s, dr, rr));
+        const T xi = fma(c, ui, fma(s, di, ri));
+        dr = fma(-s, ur, c * dr);
+        di = fma(-s, ui, c * di);
+        nr = xr; ni = xi;
+        if (upd) {
+            const long long row = (I.cell_off + j) * NS;
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) {
+                // Theta += h (f1 n_mid - f2 (rho - n_mid));  n_b += dt n_b0 Theta
+                x[sp].tr = fma(A[sp], mr, fma(-B[sp], rr, x[sp].tr));
+                x[sp].ti = fma(A[sp], mi, fma(-B[sp], ri, x[sp].ti));
+                x[sp].nr = fma(w[sp], x[sp].tr, x[sp].nr);
+                x[sp].ni = fma(w[sp], x[sp].ti, x[sp].ni);
+                if constexpr (RN) {
+                    gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(x[sp].nr), fabsf(x[sp].ni)),
+                                             fmaxf(fabsf(x[sp].tr), fabsf(x[sp].ti))));
+                    gnan = fmaf(x[sp].nr + x[sp].ti, 0.0f, gnan);
+                    gnan = fmaf(x[sp].ni + x[sp].tr, 0.0f, gnan);
+                }
+                st_cell(a, row + sp, mode, x[sp]);
+            }
+        }
+        if (RN && (((j + 1) % GRP) == 0 || j == N - 1)) group_end(j / GRP);
+    }
+
     __device__ __forceinline__ void compute(Batch &b, int j0) {
         const int N = I.n_xi;
         if (RN && (j0 % GRP) == 0) group_begin(b.exw);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u;
-            if (j < N) {
-                Cell<T> *x = b.x[u];
-                if constexpr (RN) {
+            if (j < N) cell(b.x[u], b.w[u], j, N);
+        }
+    }
+
+    // Per-step set-up shared by every kernel variant: slow-time coefficients,
+    // record flag and the front boundary value P(0).
+    __device__ __forceinline__ void step_begin(int it) {
+        const long long g = a.step0 + it;
+        const double h = (g == 0) ? 0.5 * I.dt : I.dt;
+        const double kapd = a.kap[mode], kk2d = a.kapk2[mode];
 #pragma unroll
-                    for (int sp = 0; sp < NS; ++sp) {
-                        x[sp].nr *= facM; x[sp].ni *= facM; x[sp].tr *= facM; x[sp].ti *= facM;
-                    }
-                }
-                T rr = q[0] * x[0].nr, ri = q[0] * x[0].ni;
-                if (NS == 2) { rr = fma(q[NS - 1], x[NS - 1].nr, rr); ri = fma(q[NS - 1], x[NS - 1].ni, ri); }
-                if (j == 0 && a.front == 1) { nr = rr; ni = ri; dr = 0; di = 0; }
-                // u = n_p - rho; centre:  n_mid = ch u + sh n' + rho
-                const T ur = nr - rr, ui = ni - ri;
-                const T mr = fma(ch, ur, fma(sh, dr, rr));
-                const T mi = fma(ch, ui, fma(sh, di, ri));
-                if (REC && rec) {
-                    const T mdr = fma(-sh, ur, ch * dr), mdi = fma(-sh, ui, ch * di);
-                    record(j, mr, mi, mdr, mdi, rr, ri, x);
-                }
-                // cell exit: n = c u + s n' + rho, n' = -s u + c n'
-                const T xr = fma(c, ur, fma(s, dr, rr));
-                const T xi = fma(c, ui, fma(s, di, ri));
-                dr = fma(-s, ur, c * dr);
-                di = fma(-s, ui, c * di);
-                nr = xr; ni = xi;
-                if (upd) {
-                    const long long row = (I.cell_off + j) * NS;
-#pragma unroll
-                    for (int sp = 0; sp < NS; ++sp) {
-                        // Theta += h (f1 n_mid - f2 (rho - n_mid));  n_b += dt n_b0 Theta
-                        x[sp].tr = fma(A[sp], mr, fma(-B[sp], rr, x[sp].tr));
-                        x[sp].ti = fma(A[sp], mi, fma(-B[sp], ri, x[sp].ti));
-                        x[sp].nr = fma(b.w[u][sp], x[sp].tr, x[sp].nr);
-                        x[sp].ni = fma(b.w[u][sp], x[sp].ti, x[sp].ni);
-                        if constexpr (RN) {
-                            gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(x[sp].nr), fabsf(x[sp].ni)),
-                                                     fmaxf(fabsf(x[sp].tr), fabsf(x[sp].ti))));
-                            gnan = fmaf(x[sp].nr + x[sp].ti, 0.0f, gnan);
-                            gnan = fmaf(x[sp].ni + x[sp].tr, 0.0f, gnan);
-                        }
-                        st_cell(a, row + sp, mode, x[sp]);
-                    }
-                }
-                if (RN && (((j + 1) % GRP) == 0 || j == N - 1)) group_end(j / GRP);
+        for (int sp = 0; sp < NS; ++sp) {
+            const double f1 = I.qm_g[sp] * kk2d, f2 = I.qm_g3[sp] * kapd;
+            A[sp] = (T)(h * (f1 + f2));
+            B[sp] = (T)(h * f2);
+            q[sp] = (T)I.q[sp];
+        }
+        rec = false;
+        if (REC) {
+            long long d = g - a.rec_g0;
+            if (d >= 0 && (d % a.rec_stride) == 0 && d / a.rec_stride < a.rec_max_snap) {
+                rec = true;
+                snap = d / a.rec_stride;
+            }
+            mm0 = mm1 = mm2 = -INFINITY;
+        }
+        nr = ni = dr = di = 0;
+        W = 0;
+        if (a.front == 2 && a.held) {
+            const double *hp = a.held + ((long long)inst * a.Mp + mode) * 4;
+            if constexpr (RN) {
+                double hm = fmax(fmax(fabs(hp[0]), fabs(hp[1])), fmax(fabs(hp[2]), fabs(hp[3])));
+                int e = hm > 0.0 ? ilogb(hm) : 0;
+                W = e;
+                nr = (T)ldexp(hp[0], -e); ni = (T)ldexp(hp[1], -e);
+                dr = (T)ldexp(hp[2], -e); di = (T)ldexp(hp[3], -e);
+            } else {
+                nr = (T)hp[0]; ni = (T)hp[1]; dr = (T)hp[2]; di = (T)hp[3];
             }
         }
     }
 
-    __device__ void run() {
-        const int N = I.n_xi;
+    __device__ __forceinline__ void step_end() {
+        if (!(fabs((double)nr) + fabs((double)ni) + fabs((double)dr) + fabs((double)di) <= 1.0e300))
+            atomicOr(a.err, ERR_NONFINITE);
+        if (REC && rec && (a.rec_kinds & 4)) {
+            double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)inst * a.Mp + mode;
+            long long pl = (long long)a.n_inst * a.Mp;
+            o[0] = mm0; o[pl] = mm1; o[2 * pl] = mm2;
+        }
+    }
+
+    __device__ __forceinline__ void line_begin() {
         c = (T)I.c; s = (T)I.s; ch = (T)I.ch; sh = (T)I.sh;
-        const double kapd = a.kap[mode], kk2d = a.kapk2[mode];
+        const double kapd = a.kap[mode];
         kap = (T)kapd;
         kabsk = (T)(a.kabs[mode] * kapd);
         upd = a.update != 0;
+    }
+
+    __device__ void run() {
+        const int N = I.n_xi;
+        line_begin();
         for (int it = 0; it < a.n_steps; ++it) {
-            const long long g = a.step0 + it;
-            const double h = (g == 0) ? 0.5 * I.dt : I.dt;
-#pragma unroll
-            for (int sp = 0; sp < NS; ++sp) {
-                const double f1 = I.qm_g[sp] * kk2d, f2 = I.qm_g3[sp] * kapd;
-                A[sp] = (T)(h * (f1 + f2));
-                B[sp] = (T)(h * f2);
-                q[sp] = (T)I.q[sp];
-            }
-            rec = false;
-            if (REC) {
-                long long d = g - a.rec_g0;
-                if (d >= 0 && (d % a.rec_stride) == 0 && d / a.rec_stride < a.rec_max_snap) {
-                    rec = true;
-                    snap = d / a.rec_stride;
-                }
-                mm0 = mm1 = mm2 = -INFINITY;
-            }
-            nr = ni = dr = di = 0;
-            W = 0;
-            if (a.front == 2 && a.held) {
-                const double *hp = a.held + ((long long)inst * a.Mp + mode) * 4;
-                if constexpr (RN) {
-                    double hm = fmax(fmax(fabs(hp[0]), fabs(hp[1])), fmax(fabs(hp[2]), fabs(hp[3])));
-                    int e = hm > 0.0 ? ilogb(hm) : 0;
-                    W = e;
-                    nr = (T)ldexp(hp[0], -e); ni = (T)ldexp(hp[1], -e);
-                    dr = (T)ldexp(hp[2], -e); di = (T)ldexp(hp[3], -e);
-                } else {
-                    nr = (T)hp[0]; ni = (T)hp[1]; dr = (T)hp[2]; di = (T)hp[3];
-                }
-            }
+            step_begin(it);
             Batch b0, b1;
             load(b0, 0);
             for (int j0 = 0; j0 < N; j0 += 2 * U) {
@@ -302,13 +328,7 @@ struct Line {
                 if (j0 + 2 * U < N) load(b0, j0 + 2 * U);
                 if (j0 + U < N) compute(b1, j0 + U);
             }
-            if (!(fabs((double)nr) + fabs((double)ni) + fabs((double)dr) + fabs((double)di) <= 1.0e300))
-                atomicOr(a.err, ERR_NONFINITE);
-            if (REC && rec && (a.rec_kinds & 4)) {
-                double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)inst * a.Mp + mode;
-                long long pl = (long long)a.n_inst * a.Mp;
-                o[0] = mm0; o[pl] = mm1; o[2 * pl] = mm2;
-            }
+            step_end();
         }
     }
 };
@@ -333,6 +353,165 @@ __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
             L.run();
         }
         if (!a.persistent) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged variant.  One warp owns 32 consecutive modes; lane 0 streams
+// (xi cells x 32 modes) tiles of the state into shared memory with 2-D
+// tensor copies (cp.async.bulk.tensor) through an ST-deep ring of buffers,
+// each completing on its own mbarrier; every lane then runs the same
+// per-cell arithmetic as k_sweep on its mode and stores the result with
+// plain vector stores.  Loads need no registers while in flight, so far more
+// bytes are outstanding per SM than with register prefetch.  Every wait is
+// bounded: on exhaustion the kernel sets ERR_TIMEOUT, drains its own copies
+// (again bounded) and returns.
+// ---------------------------------------------------------------------------
+namespace tma {
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_bar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// make this thread's earlier generic-proxy global writes visible to later
+// async-proxy (TMA) reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+constexpr long long kSpinLimit = 1LL << 24;
+}  // namespace tma
+
+template <typename T, int NS, int C, int ST>
+__global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __grid_constant__ CUtensorMap tmA,
+                                                  const __grid_constant__ CUtensorMap tmB) {
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int ROWS = C * NS;
+    constexpr int TILE_A = ROWS * 32 * 16;              // float4 / double2 per (row, mode)
+    constexpr int TILE = F32 ? TILE_A : 2 * TILE_A;     // FP64: n_b tile then Theta tile
+    static_assert(GRP % C == 0, "a chunk never straddles a renormalisation group");
+    __shared__ __align__(128) unsigned char buf[ST][TILE];
+    __shared__ __align__(8) uint64_t bar[ST];
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+        for (int i = 0; i < ST; ++i) tma::bar_init(&bar[i], 1);
+        tma::fence_bar_init();
+    }
+    __syncwarp();
+    uint32_t phase = 0;        // bit i: parity of stage i's next completion
+    uint32_t pending = 0;      // bit i: stage i has a copy in flight
+    bool dead = false;
+    int item = blockIdx.x;
+    for (;;) {
+        if (a.persistent) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(a.ticket, 1);
+            item = __shfl_sync(0xffffffffu, t, 0);
+        }
+        if (item >= a.n_items) break;
+        const int2 itx = a.items[item];
+        const int mode = itx.y + lane;
+        const bool live = mode < a.M;
+        const InstDev I = a.inst[itx.x];
+        Line<T, NS, 1, false> L(a, I, itx.x, live ? mode : itx.y);
+        L.line_begin();
+        const int N = I.n_xi, nch = (N + C - 1) / C;
+        const int x0 = F32 ? itx.y * 4 : itx.y * 2;
+        const T *wt = reinterpret_cast<const T *>(a.w) + I.cell_off * NS;
+        auto issue = [&](int k) {
+            const int stg = k % ST;
+            tma::arrive_expect_tx(&bar[stg], TILE);
+            const int y = (int)((I.cell_off + (long long)k * C) * NS);
+            tma::load_2d(buf[stg], &tmA, x0, y, &bar[stg]);
+            if (!F32) tma::load_2d(buf[stg] + TILE_A, &tmB, x0, y, &bar[stg]);
+        };
+        for (int it = 0; it < a.n_steps && !dead; ++it) {
+            L.step_begin(it);
+            tma::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0)
+                for (int k = 0; k < ST && k < nch; ++k) issue(k);
+            for (int k = 0; k < ST && k < nch; ++k) pending |= 1u << k;
+            int exn = 0;
+            if (F32 && live) exn = __ldcg(a.ex + I.grp_off * a.Mp + mode);
+            for (int k = 0; k < nch; ++k) {
+                const int stg = k % ST;
+                const uint32_t par = (phase >> stg) & 1u;
+                long long spins = 0;
+                bool ok = tma::try_wait(&bar[stg], par);
+                while (!ok && ++spins < tma::kSpinLimit) ok = tma::try_wait(&bar[stg], par);
+                if (__any_sync(0xffffffffu, !ok)) { dead = true; break; }
+                phase ^= 1u << stg;
+                pending &= ~(1u << stg);
+                const int j0 = k * C;
+                if (live) {
+                    if (F32 && (j0 % GRP) == 0) {
+                        L.group_begin(exn);
+                        if (j0 + GRP < N) exn = __ldcg(a.ex + (I.grp_off + (j0 + GRP) / GRP) * a.Mp + mode);
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < C; ++cc) {
+                        const int j = j0 + cc;
+                        if (j < N) {
+                            Cell<T> x[NS];
+                            T w[NS];
+#pragma unroll
+                            for (int sp = 0; sp < NS; ++sp) {
+                                const int row = cc * NS + sp;
+                                if constexpr (F32) {
+                                    const float4 v = reinterpret_cast<const float4 *>(buf[stg])[row * 32 + lane];
+                                    x[sp].nr = v.x; x[sp].ni = v.y; x[sp].tr = v.z; x[sp].ti = v.w;
+                                } else {
+                                    const double2 u = reinterpret_cast<const double2 *>(buf[stg])[row * 32 + lane];
+                                    const double2 v = reinterpret_cast<const double2 *>(buf[stg] + TILE_A)[row * 32 + lane];
+                                    x[sp].nr = u.x; x[sp].ni = u.y; x[sp].tr = v.x; x[sp].ti = v.y;
+                                }
+                                w[sp] = __ldg(wt + (long long)j * NS + sp);
+                            }
+                            L.cell(x, w, j, N);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (k + ST < nch) {
+                    if (lane == 0) issue(k + ST);
+                    pending |= 1u << stg;
+                }
+            }
+            if (!dead && live) L.step_end();
+        }
+        if (dead || !a.persistent) break;
+    }
+    if (dead) {
+        if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+        // drain this CTA's own copies before its shared memory is released
+        for (int i = 0; i < ST; ++i) {
+            if (!(pending & (1u << i))) continue;
+            const uint32_t par = (phase >> i) & 1u;
+            long long spins = 0;
+            while (!tma::try_wait(&bar[i], par) && ++spins < tma::kSpinLimit) {
+            }
+        }
     }
 }
 

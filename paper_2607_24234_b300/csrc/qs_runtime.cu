@@ -5,7 +5,9 @@
 // dt n_bs0(xi_j)), the transverse k set, the LPT-ordered work list, launch
 // selection, the autotuner and CUDA-graph capture.  Device side: the kernels
 // of qs_kernels.cuh, all enqueued on the context's stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -66,7 +68,9 @@ struct qs_ctx {
     long long rec_g0 = 0;
     void *rec_buf = nullptr;
     size_t rec_bytes = 0;
-    qs_launch launch{2, 4, 0, 8};
+    qs_launch launch{2, 4, 0, 8, 0};
+    CUtensorMap tmA{}, tmB{};
+    int tm_rows = -1;            // box rows the tensor maps were encoded for
     int items_for_warps = -1, items_persistent = -1;
     int n_sm = 148;
     std::map<int, cudaGraphExec_t> graphs;
@@ -213,7 +217,8 @@ bool same_kset(const qs_params &a, const qs_params &b) {
 }
 
 qs_status build_items(qs_ctx *c) {
-    const int wpc = c->launch.warps_per_cta, P = c->launch.persistent;
+    const int wpc = c->launch.variant == QS_VARIANT_TMA ? 1 : c->launch.warps_per_cta;
+    const int P = c->launch.persistent;
     if (c->items_for_warps == wpc && c->items_persistent == P && c->items_d) return QS_OK;
     const int per = 32 * wpc;
     std::vector<int2> items;
@@ -257,6 +262,55 @@ cudaError_t launch_u(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads, int 
     }
 }
 
+// 2-D tensor maps over the state viewed as rows of Mp x 16 bytes:
+// FP32: float elements, row = (cell, species), box = 32 modes x `rows` rows;
+// FP64: double elements, one map for n_b and one for Theta.
+qs_status ensure_tensor_maps(qs_ctx *c, int rows) {
+    if (c->tm_rows == rows) return QS_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(c, QS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const bool f32 = c->prec == QS_FP32_RENORM;
+    const cuuint64_t dims[2] = {(cuuint64_t)c->Mp * (f32 ? 4 : 2), (cuuint64_t)c->cells_total * c->NS};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->Mp * 16};
+    const cuuint32_t box[2] = {f32 ? 128u : 64u, (cuuint32_t)rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    CUresult r = encode(&c->tmA, dt, 2, c->st, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS && !f32)
+        r = encode(&c->tmB, dt, 2, c->th, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, QS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (f32) c->tmB = c->tmA;
+    c->tm_rows = rows;
+    return QS_OK;
+}
+
+template <typename T, int NS, int C, int ST>
+cudaError_t launch_tma_t(qs_ctx *c, const SweepArgs &a, dim3 grid) {
+    qsk::k_sweep_tma<T, NS, C, ST><<<grid, 32, 0, c->stream>>>(a, c->tmA, c->tmB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tma(qs_ctx *c, const SweepArgs &a, dim3 grid, int C) {
+    // ring depth chosen so that a CTA's buffers stay within 32 KiB of static shared memory
+    if (c->prec == QS_FP32_RENORM) {
+        if (c->NS == 1) return C >= 16 ? launch_tma_t<float, 1, 16, 3>(c, a, grid) : launch_tma_t<float, 1, 8, 4>(c, a, grid);
+        return C >= 16 ? launch_tma_t<float, 2, 16, 2>(c, a, grid) : launch_tma_t<float, 2, 8, 4>(c, a, grid);
+    }
+    if (c->NS == 1) return C >= 8 ? launch_tma_t<double, 1, 8, 3>(c, a, grid) : launch_tma_t<double, 1, 4, 4>(c, a, grid);
+    return C >= 8 ? launch_tma_t<double, 2, 8, 2>(c, a, grid) : launch_tma_t<double, 2, 4, 4>(c, a, grid);
+}
+
 // One launch of the sweep kernel for n_steps steps starting at global step
 // step0.  update = 0 runs the field pass only.  rec: record target (may be
 // null).
@@ -283,7 +337,8 @@ qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int 
     a.rec_off_mm = off;  if (rec_kinds & QS_REC_MODEMAX) off += 3LL * c->n_inst * c->Mp;
     a.rec_snap_doubles = off;
     a.ticket = c->ticket_d; a.err = c->err_d;
-    const int threads = 32 * c->launch.warps_per_cta;
+    const bool use_tma = c->launch.variant == QS_VARIANT_TMA && update && !rec_kinds;
+    const int threads = 32 * (c->launch.variant == QS_VARIANT_TMA ? 1 : c->launch.warps_per_cta);
     dim3 grid(c->n_items);
     if (a.persistent) {
         CU(c, cudaMemsetAsync(c->ticket_d, 0, sizeof(int), c->stream));
@@ -293,7 +348,21 @@ qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int 
     const bool R = a.rec_kinds != 0;
     const int U = c->launch.prefetch;
     cudaError_t e;
-    if (c->prec == QS_FP32_RENORM) {
+    if (use_tma) {
+        const int C = c->launch.prefetch;
+        const int rows = (c->prec == QS_FP32_RENORM ? (C >= 16 ? 16 : 8) : (C >= 8 ? 8 : 4)) * c->NS;
+        qs_status ts = ensure_tensor_maps(c, rows);
+        if (ts) return ts;
+        e = launch_tma(c, a, grid, C);
+    } else if (c->launch.variant == QS_VARIANT_TMA) {
+        // record / field passes of a TMA-configured context: the register
+        // kernel with the same per-cell arithmetic, one warp per CTA
+        e = c->prec == QS_FP32_RENORM
+                ? (c->NS == 1 ? (R ? launch_u<float, 1, true>(c, a, grid, threads, 8) : launch_u<float, 1, false>(c, a, grid, threads, 8))
+                              : (R ? launch_u<float, 2, true>(c, a, grid, threads, 8) : launch_u<float, 2, false>(c, a, grid, threads, 8)))
+                : (c->NS == 1 ? (R ? launch_u<double, 1, true>(c, a, grid, threads, 4) : launch_u<double, 1, false>(c, a, grid, threads, 4))
+                              : (R ? launch_u<double, 2, true>(c, a, grid, threads, 4) : launch_u<double, 2, false>(c, a, grid, threads, 4)));
+    } else if (c->prec == QS_FP32_RENORM) {
         if (c->NS == 1) e = R ? launch_u<float, 1, true>(c, a, grid, threads, U) : launch_u<float, 1, false>(c, a, grid, threads, U);
         else e = R ? launch_u<float, 2, true>(c, a, grid, threads, U) : launch_u<float, 2, false>(c, a, grid, threads, U);
     } else {
@@ -464,7 +533,10 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
     cudaError_t e4 = cudaMemsetAsync(c->err_d, 0, 4 * sizeof(int), c->stream);
     if (e1 || e2 || e3 || e4) { g_init_err = "memset failed"; qs_free(c); return QS_ERR_CUDA; }
     // default launch shape: the FP64 path keeps fewer cells in flight per thread
-    c->launch = qs_launch{2, c->prec == QS_FP32_RENORM ? 8 : 4, n_inst > 1 ? 1 : 0, 8};
+    // default launch shape (measured on B300 for the 3D beam workload): TMA
+    // tiles of 8 (FP32) / 4 (FP64) cells x 32 modes, 4-deep ring; batched
+    // contexts pull an LPT-ordered work list
+    c->launch = qs_launch{1, c->prec == QS_FP32_RENORM ? 8 : 4, n_inst > 1 ? 1 : 0, 16, QS_VARIANT_TMA};
     *out = c;
     return QS_OK;
 }
@@ -658,7 +730,7 @@ qs_status qs_query(const qs_ctx *c, int what, int64_t arg, int64_t *value) {
         break;
     case QS_Q_LAUNCH:
         *value = c->launch.warps_per_cta | (c->launch.prefetch << 8) | (c->launch.persistent << 16) |
-                 ((int64_t)c->launch.ctas_per_sm << 24);
+                 ((int64_t)c->launch.ctas_per_sm << 24) | ((int64_t)c->launch.variant << 32);
         break;
     default: return QS_ERR_ARG;
     }
@@ -674,9 +746,15 @@ qs_status qs_modes(const qs_ctx *c, double *kx, double *ky) {
 qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
     if (!c || !l) return QS_ERR_ARG;
     const int w = l->warps_per_cta;
+    if (l->variant != QS_VARIANT_REGISTERS && l->variant != QS_VARIANT_TMA) return fail(c, QS_ERR_ARG, "variant");
     if (!(w == 1 || w == 2 || w == 4 || w == 8)) return fail(c, QS_ERR_ARG, "warps_per_cta");
-    if (c->prec == QS_FP32_RENORM ? !(l->prefetch == 4 || l->prefetch == 8) : !(l->prefetch == 2 || l->prefetch == 4))
+    const bool f32 = c->prec == QS_FP32_RENORM;
+    if (l->variant == QS_VARIANT_TMA) {
+        if (f32 ? !(l->prefetch == 8 || l->prefetch == 16) : !(l->prefetch == 4 || l->prefetch == 8))
+            return fail(c, QS_ERR_ARG, "TMA tile cells must be 8|16 (FP32) or 4|8 (FP64)");
+    } else if (f32 ? !(l->prefetch == 4 || l->prefetch == 8) : !(l->prefetch == 2 || l->prefetch == 4)) {
         return fail(c, QS_ERR_ARG, "prefetch must be 4|8 (FP32) or 2|4 (FP64)");
+    }
     if (l->persistent && (l->ctas_per_sm < 1 || l->ctas_per_sm > 64)) return fail(c, QS_ERR_ARG, "ctas_per_sm");
     c->launch = *l;
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);

@@ -232,15 +232,17 @@ def test_launch_shapes_and_graph_bitwise(qs, prec):
     p = synth.scaled(synth.BEAM_3D, nkx=24, nky=24, kmax=5.0, n_xi=150, dxi=0.04, length=6.0)
     ref = None
     U = (4, 8) if prec == "fp32" else (2, 4)
-    for w in (1, 2, 4, 8):
-        for u in U:
-            for pers in (0, 1):
-                _, nb, th = _run_gpu(qs, p, prec, 13, seed=("noise", 2, 1e-6),
-                                     launch=dict(warps_per_cta=w, prefetch=u, persistent=pers,
-                                                 ctas_per_sm=4))
-                if ref is None:
-                    ref = (nb, th)
-                assert np.array_equal(nb, ref[0]) and np.array_equal(th, ref[1]), (w, u, pers)
+    shapes = [dict(warps_per_cta=w, prefetch=u, persistent=pers, ctas_per_sm=4, variant=0)
+              for w in (1, 2, 4, 8) for u in U for pers in (0, 1)]
+    C = (8, 16) if prec == "fp32" else (4, 8)
+    shapes += [dict(warps_per_cta=1, prefetch=cc, persistent=pers, ctas_per_sm=cps, variant=1)
+               for cc in C for pers, cps in ((0, 8), (1, 8), (1, 32))]
+    for sh in shapes:
+        s_, nb, th = _run_gpu(qs, p, prec, 13, seed=("noise", 2, 1e-6), launch=sh)
+        s_.close()
+        if ref is None:
+            ref = (nb, th)
+        assert np.array_equal(nb, ref[0]) and np.array_equal(th, ref[1]), sh
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         s = qs.Solver(p, prec=prec, stream=st)
