@@ -383,3 +383,41 @@ def test_autotuner_cache_roundtrip(qs, tmp_path):
     assert s2.tune(reps=2, cache_path=cache) == best
     s.close()
     s2.close()
+
+
+@pytest.mark.slow
+def test_batched_512_instances_full_size_sampled(qs):
+    """The batched workload at full size: 512 instances (n_b/n_p, gamma, L
+    drawn with seed 0; 200..8000 cells at dxi = 0.025), the 64 x 64 disc grid
+    (3,228 modes), 1000 steps, FP32, one persistent LPT launch.  Checked on
+    sampled (instance, mode) lines against the oracle through the per-mode
+    maxima over xi of ln|n_b|, ln|dE|, ln|dB|, and on every mode through the
+    k/-k pairing (bitwise equal maxima)."""
+    insts = synth.batch_instances(512, param_seed=0)
+    steps = 1000
+    s = qs.Solver(insts, prec="fp32")
+    assert s.n_modes == 3228
+    s.seed_noise(0, 1e-6)
+    s.step(steps)
+    s.sync()
+    mm = s.split_snapshot(s.diag(qs.REC_MODEMAX), qs.REC_MODEMAX)["modemax"][:, :, :s.n_modes]
+    assert np.all(np.isfinite(mm))
+    md = oracle.modes(insts[0])
+    pos = {int(i): j for j, i in enumerate(md["mode_id"])}
+    partner = np.array([pos[int(p)] for p in md["partner_id"]])
+    assert np.array_equal(mm, mm[:, :, partner])
+    rng = np.random.default_rng(5)
+    lens = np.array([p["n_xi"] for p in insts])
+    picks = [int(np.argmax(lens)), int(np.argmin(lens))] + list(rng.choice(512, 10, replace=False))
+    worst = 0.0
+    for i in picks:
+        p = insts[i]
+        sel = rng.choice(s.n_modes, 2, replace=False)
+        nb, th = oracle.seed_noise(p, 0, 1e-6, inst=i, mode_sel=sel)
+        oracle.sweep(p, nb, th, 0, steps, k2=md["k2"][sel])
+        f = oracle.fields(p, nb, k2=md["k2"][sel])
+        ref = np.log(np.max(f["mag"][[0, 1, 2]], axis=2))      # [3][2 modes]
+        got = mm[:, i, sel]
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+    assert worst <= 1e-3, worst
+    s.close()
