@@ -240,6 +240,63 @@ int64_t qs_launch_count(const qs_ctx *ctx);
 const char *qs_last_error(const qs_ctx *ctx);
 void qs_free(qs_ctx *ctx);
 
+/* ---------------------------------------------------------------------
+ * Learned surrogate (the paper has no learned component; this serves
+ * parameter screening with the solver as fallback and judge).
+ * A small MLP n_in -> width (depth hidden layers, GELU erf form) -> 2
+ * (regression output: log growth envelope; logit: CFI (0) / OTSI (1)),
+ * BF16 weights and activations, FP32 accumulation on the tensor cores,
+ * FP32 master weights, Adam; an ensemble of independent members (different
+ * initial weights).  Loss per sample: (p0 - y0')^2 + BCE-with-logits(p1, y1)
+ * with y0' the standardised target.  All pointers to samples are device
+ * pointers: X [n][n_in] fp32, Y [n][2] fp32.
+ * ------------------------------------------------------------------- */
+typedef struct qs_mlp qs_mlp;
+
+/* n_in <= 32, width multiple of 16, 1 <= depth <= 8, n_out = 2,
+ * 1 <= ensemble <= 16, max_batch rows per training step / inference chunk. */
+qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble, int max_batch,
+                        uint64_t seed, const qs_allocator *alloc, void *stream, qs_mlp **out);
+/* Input standardisation statistics (and regression-target statistics if Y
+ * is not NULL) computed on the device from n training rows. */
+qs_status qs_mlp_set_norm(qs_mlp *m, const float *X, int64_t n, const float *Y);
+/* Copy member `member`'s fp32 master parameters to (set = 0) or from
+ * (set = 1) a host array of qs_mlp_layout's nparam floats; setting also
+ * refreshes the BF16 copy. */
+qs_status qs_mlp_params(qs_mlp *m, int member, float *host, int64_t n, int set);
+/* nparam per member; offsets[2l], offsets[2l+1] = start of W_l [out][in]
+ * and b_l (layer 0's `in` is n_in rounded up to 16, extra columns zero);
+ * norm[64]: input mean[0..31], inverse std[32..63] with norm[62], norm[63]
+ * = regression target mean and std. */
+qs_status qs_mlp_layout(const qs_mlp *m, int64_t *nparam, int64_t *offsets, float *norm);
+/* One step on n <= max_batch rows: forward, loss, backward for every member;
+ * Adam update if do_update.  loss_host (optional) receives the mean loss
+ * over members (synchronises the stream). */
+qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n, float lr, int do_update,
+                            float *loss_host);
+/* Gradients of member `member` from the last train step (host copy). */
+qs_status qs_mlp_grads(qs_mlp *m, int member, float *host_grad, int64_t n);
+/* Ensemble inference: mean/var [n][2] on the device (output 0 in target
+ * units); mask[i] = 1 marks rows whose output-0 variance exceeds
+ * var_threshold, to be answered by the solver instead. */
+qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float *var, uint8_t *mask,
+                       float var_threshold);
+const char *qs_mlp_last_error(const qs_mlp *m);
+void qs_mlp_free(qs_mlp *m);
+
+/* Training samples for the surrogate from one snapshot of ctx (the
+ * device buffer `snap` written by qs_diag(QS_DIAG_MAG) at the current step;
+ * snap_bytes its size).  n samples, cells drawn uniformly over all
+ * instances' cells and modes uniformly (Philox4x32-10 keyed by seed).
+ * X [n][7] fp32 device: ln(n_b0/n_p), ln gamma_b, L, xi, t, |k|, atan2(ky,kx).
+ * Y [n][2] fp32 device: ln(RMS of |dn_b| over xi +- 1) - ln(amplitude), and
+ * 1 (OTSI) / 0 (CFI): whether the mode oscillates in xi over one plasma
+ * wavelength, Re sum conj(Psi) d_xi^2 Psi < 0 (the d_xi^2 ~ -1 regime of
+ * Sec. III.A), evaluated from the recorded F_perp, E_perp and B_perp.
+ * Synchronises the stream. */
+qs_status qs_sur_points(qs_ctx *ctx, const double *snap, size_t snap_bytes, double amplitude,
+                        int64_t n, uint64_t seed, float *X, float *Y);
+
 /* Allocation-free sweep (the paper has no counterpart; this is a service to
  * callers that must not allocate device memory when they step the solver,
  * e.g. a host framework whose memory pool forbids driver allocations in its

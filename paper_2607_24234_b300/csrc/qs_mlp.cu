@@ -1,0 +1,602 @@
+// qs_mlp.cu -- BF16 MLP surrogate: training and ensemble inference kernels.
+//
+// Network (one ensemble member): n_in -> width (x depth hidden layers, GELU
+// erf form) -> n_out, BF16 weights and activations, FP32 accumulation, FP32
+// master weights, Adam.  Loss per sample: (p0 - y0)^2 + BCE-with-logits(p1,
+// y1).  Inputs are standardised in the first kernel with stored statistics.
+// GEMMs run on the tensor cores (mma.sync m16n8k16 BF16 -> FP32) from
+// shared-memory tiles; bias, GELU, GELU' and the casts are fused into the
+// GEMM epilogues.  The members of an ensemble are independent networks
+// (different initial weights) trained on the same batches.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qs.h"
+
+namespace mlp {
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+// Accessors: element (row r, col k) of a K-reduction operand.
+//   T = 0: X[r * ld + k]   (k contiguous)      T = 1: X[k * ld + r]
+template <int T>
+__device__ __forceinline__ float ld_op(const __nv_bfloat16 *X, int ld, int r, int k, int R, int K) {
+    if (r >= R || k >= K) return 0.0f;
+    return __bfloat162float(T == 0 ? X[(long long)r * ld + k] : X[(long long)k * ld + r]);
+}
+
+enum { EPI_STORE = 0,      // C fp32 = acc
+       EPI_BIAS_GELU = 1,  // Z fp32 = acc + b; H bf16 = gelu(Z)
+       EPI_BIAS = 2,       // C fp32 = acc + b
+       EPI_DGELU = 3 };    // G bf16 = acc * gelu'(Z)
+
+struct GemmArgs {
+    const __nv_bfloat16 *A, *B;
+    int lda, ldb;
+    int M, N, K;
+    float *C;             // fp32 output [M][ldc]
+    int ldc;
+    const float *bias;    // [N]
+    const float *Z;       // EPI_DGELU: pre-activation [M][ldc]
+    __nv_bfloat16 *H;     // bf16 output [M][ldh]
+    int ldh;
+    int epi;
+    int accumulate;       // C += acc (EPI_STORE only)
+};
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float dgelu(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16 *p) {
+    return *reinterpret_cast<const uint32_t *>(p);
+}
+
+// C[M][N] = sum_k A(m,k) B(n,k), 4 warps (2 x 2), each 32 x 32 of the tile.
+template <int TA, int TB>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        for (int i = tid; i < BM * BK; i += 128) {
+            const int r = i / BK, k = i % BK;
+            As[r][k] = __float2bfloat16(ld_op<TA>(g.A, g.lda, m0 + r, k0 + k, g.M, g.K));
+        }
+        for (int i = tid; i < BN * BK; i += 128) {
+            const int r = i / BK, k = i % BK;
+            Bs[r][k] = __float2bfloat16(ld_op<TB>(g.B, g.ldb, n0 + r, k0 + k, g.N, g.K));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + gq;
+                af[i][0] = pack2(&As[r][kk + 2 * tq]);
+                af[i][1] = pack2(&As[r + 8][kk + 2 * tq]);
+                af[i][2] = pack2(&As[r][kk + 2 * tq + 8]);
+                af[i][3] = pack2(&As[r + 8][kk + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + gq;
+                bfr[j][0] = pack2(&Bs[c][kk + 2 * tq]);
+                bfr[j][1] = pack2(&Bs[c][kk + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                        : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]),
+                          "r"(bfr[j][1]));
+        }
+        __syncthreads();
+    }
+    // epilogue: acc[i][j][e] sits at row wm+16i+gq (+8 for e>=2), col wn+8j+2tq+(e&1)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = m0 + wm + i * 16 + gq + (e >= 2 ? 8 : 0);
+                const int n = n0 + wn + j * 8 + 2 * tq + (e & 1);
+                if (m >= g.M || n >= g.N) continue;
+                float v = acc[i][j][e];
+                const long long oc = (long long)m * g.ldc + n;
+                switch (g.epi) {
+                case EPI_STORE: g.C[oc] = g.accumulate ? g.C[oc] + v : v; break;
+                case EPI_BIAS: g.C[oc] = v + g.bias[n]; break;
+                case EPI_BIAS_GELU: {
+                    const float z = v + g.bias[n];
+                    g.C[oc] = z;
+                    g.H[(long long)m * g.ldh + n] = __float2bfloat16(gelu(z));
+                } break;
+                case EPI_DGELU:
+                    g.H[(long long)m * g.ldh + n] = __float2bfloat16(v * dgelu(g.Z[oc]));
+                    break;
+                }
+            }
+}
+
+// x (fp32, [n][n_in]) -> standardised bf16 [n][kin_pad] (zero padded)
+__global__ void k_standardise(const float *x, int n, int n_in, int kpad, const float *mean,
+                              const float *inv_std, __nv_bfloat16 *out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)n * kpad) return;
+    const int r = (int)(i / kpad), k = (int)(i % kpad);
+    const float v = k < n_in ? (x[(long long)r * n_in + k] - mean[k]) * inv_std[k] : 0.0f;
+    out[i] = __float2bfloat16(v);
+}
+
+// loss and output gradient; out [n][2] = (regression, logit), y [n][2]
+__global__ void k_loss(const float *out, const float *y, int n, float ymean, float yinv, float *dout_f,
+                       __nv_bfloat16 *dout, float *loss_acc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (i < n) {
+        const float p = out[2 * i], t = (y[2 * i] - ymean) * yinv;
+        const float z = out[2 * i + 1], c = y[2 * i + 1];
+        const float d0 = p - t;
+        const float sig = 1.0f / (1.0f + expf(-z));
+        l = d0 * d0 + fmaxf(z, 0.0f) - z * c + log1pf(expf(-fabsf(z)));
+        const float g0 = 2.0f * d0 / n, g1 = (sig - c) / n;
+        dout_f[2 * i] = g0;
+        dout_f[2 * i + 1] = g1;
+        dout[2 * i] = __float2bfloat16(g0);
+        dout[2 * i + 1] = __float2bfloat16(g1);
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, l / n);
+}
+
+// column sums of a bf16 [n][cols] matrix into fp32 out[cols]
+__global__ void k_colsum(const __nv_bfloat16 *g, int n, int cols, float *out) {
+    const int c = blockIdx.x;
+    float s = 0.0f;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s += __bfloat162float(g[(long long)r * cols + c]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// Adam on fp32 master weights; refreshes the bf16 copy.
+__global__ void k_adam(float *w, float *m, float *v, const float *g, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2, __nv_bfloat16 *wb) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float *w, long long n, __nv_bfloat16 *wb) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+// uniform(-a, a) initialisation from a counter hash (splitmix64 of (seed, i))
+__global__ void k_init_uniform(float *w, long long n, float a, unsigned long long seed) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const float u = (float)((z >> 40) * (1.0 / 16777216.0));
+    w[i] = (2.0f * u - 1.0f) * a;
+}
+
+// ensemble statistics: outs [E][n][2] -> mean, var of both outputs, mask
+__global__ void k_ensemble(const float *outs, long long member_stride, int E, int n, float ymean, float ystd,
+                           float *mean, float *var, unsigned char *mask, float thr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int o = 0; o < 2; ++o) {
+        float s = 0.0f, s2 = 0.0f;
+        for (int e = 0; e < E; ++e) {
+            float v = outs[e * member_stride + (long long)i * 2 + o];
+            if (o == 0) v = v * ystd + ymean;
+            s += v;
+            s2 += v * v;
+        }
+        const float mu = s / E;
+        const float va = fmaxf(s2 / E - mu * mu, 0.0f);
+        mean[2 * i + o] = mu;
+        var[2 * i + o] = va;
+        if (o == 0 && mask) mask[i] = va > thr ? 1 : 0;
+    }
+}
+
+// column mean / inverse std of x [n][d] (d <= 32), one block per column
+__global__ void k_colstats(const float *x, long long n, int d, float *mean, float *inv_std) {
+    const int c = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+        const double v = x[r * d + c];
+        s += v;
+        s2 += v * v;
+    }
+    __shared__ double a[256], b[256];
+    a[threadIdx.x] = s;
+    b[threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) { a[threadIdx.x] += a[threadIdx.x + o]; b[threadIdx.x] += b[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mu = a[0] / n, va = b[0] / n - mu * mu;
+        mean[c] = (float)mu;
+        inv_std[c] = va > 1e-30 ? (float)(1.0 / sqrt(va)) : 1.0f;
+    }
+}
+
+}  // namespace mlp
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct qs_mlp {
+    int n_in = 7, width = 256, depth = 3, n_out = 2, E = 4, kin = 16;
+    int max_batch = 0;
+    cudaStream_t stream = nullptr;
+    qs_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> bufs;
+    // per layer l (0..depth): W [out][in] fp32 master + bf16 copy, b [out], m/v
+    std::vector<int> lin, lout;
+    std::vector<long long> woff, boff;   // offsets into the parameter block (per member)
+    long long nparam = 0;                // per member
+    float *P = nullptr, *Mm = nullptr, *Vv = nullptr, *G = nullptr;   // [E][nparam]
+    __nv_bfloat16 *Pb = nullptr;         // [E][nparam]
+    // activations for max_batch
+    __nv_bfloat16 *X0 = nullptr;         // [B][kin]
+    std::vector<float *> Z;              // per hidden layer [B][width]
+    std::vector<__nv_bfloat16 *> H;      // per hidden layer [B][width]
+    float *OUT = nullptr;                // [E][B][n_out]
+    float *DOUTF = nullptr;
+    __nv_bfloat16 *DOUT = nullptr;       // [B][n_out]
+    __nv_bfloat16 *DG0 = nullptr, *DG1 = nullptr;   // [B][width] ping-pong of dZ
+    float *DH = nullptr;                 // scratch (unused by the fused path)
+    float *stats = nullptr;              // mean[32], inv_std[32]
+    float ymean = 0.0f, ystd = 1.0f;
+    float *loss = nullptr;
+    long long step = 0;
+    std::string err;
+};
+
+namespace {
+
+qs_status mfail(qs_mlp *m, qs_status s, const char *msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+qs_status malloc_dev(qs_mlp *m, size_t bytes, void **p) {
+    if (m->has_alloc) {
+        *p = m->alloc.alloc(bytes, m->alloc.user);
+        if (!*p) return QS_ERR_OOM;
+    } else if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return QS_ERR_OOM;
+    }
+    m->bufs.push_back(*p);
+    return QS_OK;
+}
+
+template <typename P>
+qs_status mdev(qs_mlp *m, size_t bytes, P **p) {
+    void *v = nullptr;
+    qs_status s = malloc_dev(m, bytes, &v);
+    *p = static_cast<P *>(v);
+    return s;
+}
+
+void gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g) {
+    dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM);
+    if (TA == 0 && TB == 0) mlp::k_gemm<0, 0><<<grid, 128, 0, m->stream>>>(g);
+    else if (TA == 0 && TB == 1) mlp::k_gemm<0, 1><<<grid, 128, 0, m->stream>>>(g);
+    else if (TA == 1 && TB == 0) mlp::k_gemm<1, 0><<<grid, 128, 0, m->stream>>>(g);
+    else mlp::k_gemm<1, 1><<<grid, 128, 0, m->stream>>>(g);
+}
+
+// forward of member e on n rows of X0 (already standardised); fills OUT[e]
+void forward(qs_mlp *m, int e, int n) {
+    const float *Pe = m->P + (long long)e * m->nparam;
+    const __nv_bfloat16 *Pbe = m->Pb + (long long)e * m->nparam;
+    for (int l = 0; l <= m->depth; ++l) {
+        mlp::GemmArgs g{};
+        g.A = l == 0 ? m->X0 : m->H[l - 1];
+        g.lda = l == 0 ? m->kin : m->width;
+        g.B = Pbe + m->woff[l];
+        g.ldb = m->lin[l];
+        g.M = n; g.N = m->lout[l]; g.K = m->lin[l];
+        g.bias = Pe + m->boff[l];
+        if (l < m->depth) {
+            g.C = m->Z[l]; g.ldc = m->width;
+            g.H = m->H[l]; g.ldh = m->width;
+            g.epi = mlp::EPI_BIAS_GELU;
+        } else {
+            g.C = m->OUT + (long long)e * m->max_batch * m->n_out; g.ldc = m->n_out;
+            g.epi = mlp::EPI_BIAS;
+        }
+        gemm(m, 0, 0, g);
+    }
+}
+
+// backward of member e (after forward + loss); gradients into G[e]
+void backward(qs_mlp *m, int e, int n) {
+    float *Ge = m->G + (long long)e * m->nparam;
+    const __nv_bfloat16 *Pbe = m->Pb + (long long)e * m->nparam;
+    const __nv_bfloat16 *dz = m->DOUT;   // dL/dz of the current layer, bf16 [n][lout]
+    __nv_bfloat16 *ping[2] = {m->DG0, m->DG1};
+    for (int l = m->depth; l >= 0; --l) {
+        const int in = m->lin[l], out = m->lout[l];
+        const __nv_bfloat16 *act = l == 0 ? m->X0 : m->H[l - 1];
+        const int lda_act = l == 0 ? m->kin : m->width;
+        // dW[o][i] = sum_b dz[b][o] act[b][i]
+        mlp::GemmArgs gw{};
+        gw.A = dz; gw.lda = out;          // A(m=o, k=b) = dz[b*out + o]  (TA = 1)
+        gw.B = act; gw.ldb = lda_act;     // B(n=i, k=b) = act[b*ld + i]  (TB = 1)
+        gw.M = out; gw.N = in; gw.K = n;
+        gw.C = Ge + m->woff[l]; gw.ldc = in;
+        gw.epi = mlp::EPI_STORE;
+        gemm(m, 1, 1, gw);
+        mlp::k_colsum<<<out, 256, 0, m->stream>>>(dz, n, out, Ge + m->boff[l]);
+        if (l == 0) break;
+        // dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * gelu'(Z[l-1][b][i])
+        mlp::GemmArgs gx{};
+        gx.A = dz; gx.lda = out;                       // A(m=b, k=o), TA = 0
+        gx.B = Pbe + m->woff[l]; gx.ldb = in;          // B(n=i, k=o) = W[o*in + i], TB = 1
+        gx.M = n; gx.N = in; gx.K = out;
+        gx.C = m->Z[l - 1]; gx.ldc = m->width;         // read as Z in the epilogue
+        gx.Z = m->Z[l - 1];
+        __nv_bfloat16 *dst = ping[l & 1];
+        gx.H = dst; gx.ldh = m->width;
+        gx.epi = mlp::EPI_DGELU;
+        gemm(m, 0, 1, gx);
+        dz = dst;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble, int max_batch,
+                        uint64_t seed, const qs_allocator *alloc, void *stream, qs_mlp **out) {
+    if (!out || n_in < 1 || n_in > 32 || width < 16 || width % 16 || depth < 1 || depth > 8 || n_out != 2 ||
+        ensemble < 1 || ensemble > 16 || max_batch < 1)
+        return QS_ERR_ARG;
+    *out = nullptr;
+    qs_mlp *m = new qs_mlp();
+    m->n_in = n_in; m->width = width; m->depth = depth; m->n_out = n_out; m->E = ensemble;
+    m->kin = (n_in + 15) / 16 * 16;
+    m->max_batch = max_batch;
+    m->stream = static_cast<cudaStream_t>(stream);
+    if (alloc && alloc->alloc && alloc->free) { m->alloc = *alloc; m->has_alloc = true; }
+    long long off = 0;
+    for (int l = 0; l <= depth; ++l) {
+        const int in = l == 0 ? m->kin : width, o = l == depth ? n_out : width;
+        m->lin.push_back(in);
+        m->lout.push_back(o);
+        m->woff.push_back(off); off += (long long)in * o;
+        m->boff.push_back(off); off += o;
+        off = (off + 7) / 8 * 8;
+    }
+    m->nparam = off;
+    const size_t pb = sizeof(float) * (size_t)off * ensemble;
+    qs_status s = QS_OK;
+    if ((s = mdev(m, pb, &m->P)) || (s = mdev(m, pb, &m->Mm)) || (s = mdev(m, pb, &m->Vv)) ||
+        (s = mdev(m, pb, &m->G)) || (s = mdev(m, pb / 2, &m->Pb)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * m->kin, &m->X0)) ||
+        (s = mdev(m, sizeof(float) * (size_t)ensemble * max_batch * n_out, &m->OUT)) ||
+        (s = mdev(m, sizeof(float) * (size_t)max_batch * n_out, &m->DOUTF)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * n_out, &m->DOUT)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG0)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG1)) ||
+        (s = mdev(m, sizeof(float) * 64, &m->stats)) || (s = mdev(m, sizeof(float) * 4, &m->loss))) {
+        qs_mlp_free(m);
+        return s;
+    }
+    for (int l = 0; l < depth; ++l) {
+        float *z; __nv_bfloat16 *h;
+        if ((s = mdev(m, sizeof(float) * (size_t)max_batch * width, &z)) ||
+            (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &h))) {
+            qs_mlp_free(m);
+            return s;
+        }
+        m->Z.push_back(z);
+        m->H.push_back(h);
+    }
+    // initialisation: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) over the real
+    // inputs (padding columns zero), b = 0; per member seed
+    cudaMemsetAsync(m->P, 0, pb, m->stream);
+    cudaMemsetAsync(m->Mm, 0, pb, m->stream);
+    cudaMemsetAsync(m->Vv, 0, pb, m->stream);
+    std::vector<float> stat(64, 0.0f);
+    for (int i = 0; i < 32; ++i) stat[32 + i] = 1.0f;
+    cudaMemcpyAsync(m->stats, stat.data(), 64 * sizeof(float), cudaMemcpyHostToDevice, m->stream);
+    for (int e = 0; e < ensemble; ++e)
+        for (int l = 0; l <= depth; ++l) {
+            const int fan = l == 0 ? n_in : width;
+            const long long nw = (long long)m->lin[l] * m->lout[l];
+            mlp::k_init_uniform<<<(unsigned)((nw + 255) / 256), 256, 0, m->stream>>>(
+                m->P + (long long)e * off + m->woff[l], nw, 1.0f / sqrtf((float)fan),
+                seed * 1000003ull + (unsigned long long)(e * 64 + l));
+        }
+    // zero the padding input columns of layer 0
+    if (m->kin != n_in) {
+        std::vector<float> w0;
+        for (int e = 0; e < ensemble; ++e) {
+            const long long nw = (long long)m->lin[0] * m->lout[0];
+            w0.resize(nw);
+            float *dst = m->P + (long long)e * off + m->woff[0];
+            cudaMemcpyAsync(w0.data(), dst, nw * sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+            cudaStreamSynchronize(m->stream);
+            for (int o = 0; o < m->lout[0]; ++o)
+                for (int i = n_in; i < m->kin; ++i) w0[(long long)o * m->kin + i] = 0.0f;
+            cudaMemcpyAsync(dst, w0.data(), nw * sizeof(float), cudaMemcpyHostToDevice, m->stream);
+            cudaStreamSynchronize(m->stream);
+        }
+    }
+    const long long tot = off * ensemble;
+    mlp::k_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, m->stream>>>(m->P, tot, m->Pb);
+    if (cudaGetLastError() != cudaSuccess) { qs_mlp_free(m); return QS_ERR_CUDA; }
+    *out = m;
+    return QS_OK;
+}
+
+qs_status qs_mlp_set_norm(qs_mlp *m, const float *X, int64_t n, const float *Y) {
+    if (!m || !X || n < 1) return QS_ERR_ARG;
+    mlp::k_colstats<<<m->n_in, 256, 0, m->stream>>>(X, n, m->n_in, m->stats, m->stats + 32);
+    if (Y) {
+        // target statistics of the regression output (column 0 of a 2-wide Y)
+        mlp::k_colstats<<<2, 256, 0, m->stream>>>(Y, n, 2, m->stats + 24, m->stats + 56);
+        float h[64];
+        if (cudaMemcpyAsync(h, m->stats, sizeof h, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaStreamSynchronize(m->stream) != cudaSuccess)
+            return QS_ERR_CUDA;
+        m->ymean = h[24];
+        m->ystd = 1.0f / h[56];
+    }
+    return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+qs_status qs_mlp_params(qs_mlp *m, int member, float *host, int64_t n, int set) {
+    if (!m || !host || member < 0 || member >= m->E || n != m->nparam) return QS_ERR_ARG;
+    float *dst = m->P + (long long)member * m->nparam;
+    cudaError_t e;
+    if (set) {
+        e = cudaMemcpyAsync(dst, host, n * sizeof(float), cudaMemcpyHostToDevice, m->stream);
+        mlp::k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(dst, n, m->Pb + (long long)member * m->nparam);
+    } else {
+        e = cudaMemcpyAsync(host, dst, n * sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    return e == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+qs_status qs_mlp_layout(const qs_mlp *m, int64_t *nparam, int64_t *offsets, float *norm) {
+    if (!m || !nparam) return QS_ERR_ARG;
+    *nparam = m->nparam;
+    if (offsets)
+        for (int l = 0; l <= m->depth; ++l) { offsets[2 * l] = m->woff[l]; offsets[2 * l + 1] = m->boff[l]; }
+    if (norm) {
+        float h[64];
+        if (cudaMemcpy(h, m->stats, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return QS_ERR_CUDA;
+        for (int i = 0; i < 64; ++i) norm[i] = h[i];
+        norm[62] = m->ymean;
+        norm[63] = m->ystd;
+    }
+    return QS_OK;
+}
+
+// One training step on n <= max_batch rows (device X [n][n_in], Y [n][2]).
+// do_update = 0 computes gradients only (member `member`, or all if < 0).
+qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n, float lr, int do_update,
+                            float *loss_host) {
+    if (!m || !X || !Y || n < 1 || n > m->max_batch) return QS_ERR_ARG;
+    const int nb = (int)n;
+    mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(
+        X, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0);
+    cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream);
+    ++m->step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
+    for (int e = 0; e < m->E; ++e) {
+        forward(m, e, nb);
+        mlp::k_loss<<<(nb + 255) / 256, 256, 0, m->stream>>>(m->OUT + (long long)e * m->max_batch * 2, Y, nb,
+                                                              m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss);
+        backward(m, e, nb);
+        if (do_update) {
+            const long long off = (long long)e * m->nparam;
+            mlp::k_adam<<<(unsigned)((m->nparam + 255) / 256), 256, 0, m->stream>>>(
+                m->P + off, m->Mm + off, m->Vv + off, m->G + off, m->nparam, lr, b1, b2, 1e-8f, c1, c2,
+                m->Pb + off);
+        }
+    }
+    if (!do_update) --m->step;
+    if (cudaGetLastError() != cudaSuccess) return mfail(m, QS_ERR_CUDA, "mlp launch failed");
+    if (loss_host) {
+        float l = 0.0f;
+        if (cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaStreamSynchronize(m->stream) != cudaSuccess)
+            return QS_ERR_CUDA;
+        *loss_host = l / m->E;
+    }
+    return QS_OK;
+}
+
+qs_status qs_mlp_grads(qs_mlp *m, int member, float *host_grad, int64_t n) {
+    if (!m || !host_grad || member < 0 || member >= m->E || n != m->nparam) return QS_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(host_grad, m->G + (long long)member * m->nparam, n * sizeof(float),
+                                    cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    return e == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+// Ensemble inference on n rows (device X [n][n_in]); writes device mean/var
+// [n][2] (output 0 de-standardised) and, if mask != NULL, mask[i] = 1 where
+// the ensemble variance of output 0 exceeds var_threshold (solver fallback).
+qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float *var, uint8_t *mask,
+                       float var_threshold) {
+    if (!m || !X || !mean || !var || n < 1) return QS_ERR_ARG;
+    for (int64_t r0 = 0; r0 < n; r0 += m->max_batch) {
+        const int nb = (int)std::min<int64_t>(m->max_batch, n - r0);
+        mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(
+            X + r0 * m->n_in, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0);
+        for (int e = 0; e < m->E; ++e) forward(m, e, nb);
+        mlp::k_ensemble<<<(nb + 255) / 256, 256, 0, m->stream>>>(
+            m->OUT, (long long)m->max_batch * 2, m->E, nb, m->ymean, m->ystd, mean + r0 * 2, var + r0 * 2,
+            mask ? mask + r0 : nullptr, var_threshold);
+    }
+    return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+const char *qs_mlp_last_error(const qs_mlp *m) { return m ? m->err.c_str() : ""; }
+
+void qs_mlp_free(qs_mlp *m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream); else cudaDeviceSynchronize();
+    for (void *p : m->bufs) {
+        if (m->has_alloc) m->alloc.free(p, m->alloc.user); else cudaFree(p);
+    }
+    delete m;
+}
+
+}  // extern "C"

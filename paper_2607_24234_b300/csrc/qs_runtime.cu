@@ -798,3 +798,4 @@ void qs_free(qs_ctx *c) {
 }  // extern "C"
 
 #include "qs_tune.inc"
+#include "qs_surdata.inc"

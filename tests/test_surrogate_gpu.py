@@ -1,0 +1,148 @@
+"""GPU checks of the learned surrogate.
+
+- Forward outputs and gradients of the BF16 tensor-core kernels against the
+  FP64 CPU backprop (itself pinned by finite differences) on identical
+  BF16-rounded weights and inputs: forward rel. L2 <= 1e-2, gradients
+  rel. L2 <= 2e-2 per tensor.
+- Training samples drawn on the GPU against the CPU restatement of the
+  targets on the oracle's own fields.
+- A trained ensemble on held-out parameter sets: envelope error, class
+  accuracy, the solver fallback, and the time it saves over the solver.
+"""
+import ctypes
+import math
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp as omlp
+from oracle import surdata
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2607_24234_b300 as qs
+    from paper_2607_24234_b300 import surrogate
+    return qs, surrogate
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_forward_and_gradients_match_fp64(sg):
+    import torch
+    qs, sur = sg
+    rng = np.random.default_rng(0)
+    n = 1000
+    X = (rng.standard_normal((n, 7)) * np.array([1.0, 2.0, 50.0, 30.0, 500.0, 2.0, 1.5])
+         + np.array([-4.0, 6.0, 100.0, 40.0, 900.0, 3.0, 0.0])).astype(np.float32)
+    Y = np.stack([10 * rng.standard_normal(n) + 20, (rng.random(n) > 0.4)], axis=1).astype(np.float32)
+    Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    m = sur.MLP(width=256, depth=3, ensemble=2, max_batch=1024, seed=1)
+    m.set_norm(Xt, Yt)
+    flat = m.params(0)
+    for W, b in m.layers(flat):
+        b[:] = 0.1 * rng.standard_normal(b.shape)
+    m.set_params(flat, 0)
+    m.set_params(flat, 1)
+    m.train_step(Xt, Yt, 0.0, update=False)
+    g = m.grads(0)
+    mean, inv_std, ymean, ystd = m.norm()
+    xs = np.zeros((n, 16))
+    xs[:, :7] = omlp.bf16((X - mean[:7].astype(np.float32)) * inv_std[:7].astype(np.float32))
+    layers = [(omlp.bf16(W), b.astype(np.float64)) for W, b in m.layers(flat)]
+    _, grads, out = omlp.loss_and_grads(layers, xs, Y.astype(np.float64), ymean, ystd)
+    for l, ((gW, gb), (oW, ob)) in enumerate(zip(m.layers(g), grads)):
+        assert _rel(gW, oW) <= 2e-2, ("W", l, _rel(gW, oW))
+        assert _rel(gb, ob) <= 2e-2, ("b", l, _rel(gb, ob))
+    mu, var, mask = m.infer(Xt)
+    mu = mu.cpu().numpy()
+    assert _rel(mu[:, 0], out[:, 0] * ystd + ymean) <= 1e-2
+    assert _rel(mu[:, 1], out[:, 1]) <= 1e-2
+    assert float(var.max()) <= 1e-6 * max(1.0, float(np.max(np.abs(mu)))) ** 2
+    m.close()
+
+
+def test_training_samples_match_oracle_targets(sg):
+    import torch
+    qs, sur = sg
+    insts = synth.batch_instances(3, param_seed=7, base=synth.scaled(synth.BATCH_BASE, nkx=12, nky=12),
+                                  dxi=0.1)
+    steps, amp, n = 60, 1e-6, 3000
+    s = qs.Solver(insts, prec="fp64")
+    s.seed_noise(0, amp)
+    s.step(steps)
+    snap = s.diag(qs.REC_MAG, host=False)
+    X = torch.empty((n, 7), dtype=torch.float32, device="cuda")
+    Y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    st = qs.lib.qs_sur_points(s.ctx, ctypes.c_void_p(snap.data_ptr()), snap.numel() * 8, amp, n, 5,
+                              ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()))
+    assert st == 0
+    X, Y = X.cpu().numpy(), Y.cpu().numpy()
+    md = oracle.modes(insts[0])
+    ang = np.arctan2(md["ky"], md["kx"]).astype(np.float32)
+    kab = np.sqrt(md["kx"] ** 2 + md["ky"] ** 2).astype(np.float32)
+    mags = []
+    for i, p in enumerate(insts):
+        nb, th = oracle.seed_noise(p, 0, amp, inst=i)
+        oracle.sweep(p, nb, th, 0, steps)
+        mags.append(oracle.fields(p, nb)["mag"])
+    feats = np.array([[np.float32(np.log(p["species"][0][2])), np.float32(np.log(p["gamma_b"]))]
+                      for p in insts])
+    bad0, bad1 = 0, 0
+    for r in range(n):
+        i = int(np.argmin(np.abs(feats[:, 0] - X[r, 0]) + np.abs(feats[:, 1] - X[r, 1])))
+        p = insts[i]
+        j = int(round(X[r, 3] / p["dxi"] - 0.5))
+        mo = int(np.argmin(np.abs(kab - X[r, 5]) + np.abs(ang - X[r, 6])))
+        y0, y1 = surdata.targets(mags[i][:, mo, :], p["dxi"], j, amp)
+        bad0 += abs(y0 - Y[r, 0]) > 1e-4 * max(1.0, abs(y0))
+        bad1 += y1 != Y[r, 1]
+    assert bad0 == 0
+    assert bad1 <= n // 200
+    s.close()
+
+
+@pytest.mark.slow
+def test_surrogate_learns_and_screens_heldout(sg):
+    """Train on solver sweeps of 16 parameter sets, evaluate on 8 held-out
+    sets (parameter seed 1): the ensemble answers screening queries far
+    faster than the solver produces them, at a stated error; flagged queries
+    fall back to the solver."""
+    import torch
+    qs, sur = sg
+    base = synth.scaled(synth.BATCH_BASE, nkx=32, nky=32)
+    snaps = [200, 400, 600, 800, 1000]
+    tr = synth.batch_instances(16, param_seed=0, base=base, dxi=0.05)
+    ho = synth.batch_instances(8, param_seed=1, base=base, dxi=0.05)
+    Xtr, Ytr, _ = sur.generate(tr, snaps, 1 << 16, seed=1)
+    Xho, Yho, solver_s = sur.generate(ho, snaps, 1 << 14, seed=2, noise_seed=1)
+    assert torch.isfinite(Xtr).all() and torch.isfinite(Ytr).all()
+    m, losses = sur.train(Xtr, Ytr, epochs=12, batch=8192, lr=2e-3, ensemble=4, seed=3)
+    assert losses[-1] < 0.5 * losses[0]
+    res = sur.evaluate(m, Xho, Yho)
+    mu, var, _ = m.infer(Xho)                 # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mu, var, _ = m.infer(Xho)
+    torch.cuda.synchronize()
+    infer_s = time.perf_counter() - t0
+    thr = float(torch.quantile(var[:, 0], 0.9))
+    res_fb = sur.evaluate(m, Xho, Yho, var_threshold=thr)
+    print({"heldout": res, "with_fallback_at_p90_var": res_fb, "solver_s": solver_s, "infer_s": infer_s})
+    assert res["rmse"] < 0.35 * res["target_std"]
+    assert res["accuracy"] > 0.8
+    assert res_fb["rmse_with_fallback"] <= res["rmse"]
+    assert 0.05 < res_fb["flagged_fraction"] < 0.2
+    assert infer_s < 0.1 * solver_s          # screening gain over running the solver
+    assert math.isfinite(res["rmse"])
+    m.close()
