@@ -199,6 +199,58 @@ def run_batch(args):
     s.close()
 
 
+def run_surrogate(args):
+    """Learned surrogate, full size: 2^22 training samples from solver
+    sweeps of batched-workload parameter sets (64 x 64 disc grid, dxi =
+    0.025, snapshots every 100 of 1000 steps), a validation split that
+    sets the fallback threshold (10% of queries flagged), 64 held-out runs
+    (parameter seed 1), 1e7 inference queries."""
+    import torch
+    from paper_2607_24234_b300 import surrogate as sur
+    base = synth.scaled(synth.BATCH_BASE)
+    snaps = list(range(100, 1001, 100))
+    n_train = 1 << 22
+    tr = synth.batch_instances(args.sur_train_inst, param_seed=0, base=base)
+    ho = synth.batch_instances(64, param_seed=1, base=base)
+    t0 = time.perf_counter()
+    X, Y, solver_tr = sur.generate(tr, snaps, (n_train + (1 << 18)) // len(snaps) + 1, seed=1)
+    gen_s = time.perf_counter() - t0
+    Xv, Yv = X[n_train:].contiguous(), Y[n_train:].contiguous()
+    X, Y = X[:n_train].contiguous(), Y[:n_train].contiguous()
+    Xh, Yh, solver_ho = sur.generate(ho, snaps, (1 << 20) // len(snaps), seed=2, noise_seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m, losses = sur.train(X, Y, epochs=args.sur_epochs, batch=16384, lr=2e-3, ensemble=4, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    _, var_v, _ = m.infer(Xv)
+    thr = float(torch.quantile(var_v[:, 0].float(), 0.9))
+    res = sur.evaluate(m, Xh, Yh)
+    res_fb = sur.evaluate(m, Xh, Yh, var_threshold=thr)
+    q = Xh.repeat((10_000_000 + Xh.shape[0] - 1) // Xh.shape[0], 1)[:10_000_000].contiguous()
+    m.infer(q[:1 << 16])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.infer(q, thr)
+    torch.cuda.synchronize()
+    inf_s = time.perf_counter() - t0
+    steps_per_epoch = n_train // 16384
+    flops_step = 6.0 * m.nparam * 16384 * 4
+    print(json.dumps({
+        "metric": "surrogate: held-out error and inference queries/s", "workload": "surrogate_2p22",
+        "unit": "queries/s", "value": 1e7 / inf_s, "higher_is_better": True,
+        "train": {"samples": n_train, "epochs": args.sur_epochs, "seconds": train_s,
+                  "loss_first": losses[0], "loss_last": losses[-1],
+                  "tflops": flops_step * steps_per_epoch * args.sur_epochs / train_s / 1e12,
+                  "ensemble": 4, "width": 256, "depth": 3},
+        "data": {"train_instances": len(tr), "snapshots": snaps, "generation_s": gen_s,
+                 "solver_s_train": solver_tr, "heldout_runs": len(ho), "solver_s_heldout": solver_ho},
+        "heldout": res, "fallback": {"var_threshold": thr, "chosen_on": "validation split, 90% coverage",
+                                     **res_fb},
+        "inference": {"queries": 10_000_000, "seconds": inf_s}}), flush=True)
+    m.close()
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -364,7 +416,9 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (use the library's default launch shape)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="beam3d", choices=["beam3d", "batch"])
+    ap.add_argument("--workload", default="beam3d", choices=["beam3d", "batch", "surrogate"])
+    ap.add_argument("--sur-train-inst", type=int, default=64)
+    ap.add_argument("--sur-epochs", type=int, default=8)
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-job-steps", type=int, default=1000)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
@@ -375,6 +429,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -241,6 +241,43 @@ const char *qs_last_error(const qs_ctx *ctx);
 void qs_free(qs_ctx *ctx);
 
 /* ---------------------------------------------------------------------
+ * Finite-width beam on a periodic transverse grid (Sec. IV.B: narrow
+ * beams, self-modulation and hosing).  One species with a Gaussian (or
+ * uniform) transverse profile n_b0(y, z), flat top in xi.  Per step: the
+ * plasma response (Eq. 5) per transverse point, then per xi slice the
+ * screened Poisson solve of Eq. (14) by 2-D FFT with spectral gradients,
+ * and the push d_tau G = -(q/(m gamma)) [n_b0 (Psi - n_p) + grad n_b0 .
+ * grad Psi], d_tau n_b = G (Eqs. 8-9 with the transverse divergence in
+ * conservative form; the gamma^-3 term is dropped).  FP32 state
+ * [xi][y][z], z fastest; cell centres y_i = (i + 1/2) L/N - L/2.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    qs_species species;   /* q, m, peak n_b0/n_p                           */
+    double gamma_b;
+    int n_xi;
+    double dxi, dt;
+    int n_perp;           /* N = 32, 64, 128 or 256 points per transverse axis */
+    double L_perp;        /* periodic box size (both axes)                  */
+    double sigma_r;       /* rms of the Gaussian profile                    */
+    int uniform;          /* 1: n_b0 = peak everywhere                       */
+} qs_r2_params;
+typedef struct qs_r2 qs_r2;
+
+qs_status qs_r2_init(const qs_r2_params *p, const qs_allocator *alloc, void *stream, qs_r2 **out);
+/* n_b = amplitude (n_b0/peak) g + [n_b0(y - offset, z) - n_b0(y, z)], G = 0,
+ * step counter reset; g standard normals from Philox4x32-10 keyed by seed
+ * (counter (cell, point)), or the float32 field `user` [n_xi][N][N] (host
+ * or device) when not NULL.  Synchronises the stream. */
+qs_status qs_r2_seed(qs_r2 *c, uint64_t seed, double amplitude, double centroid_offset, const float *user,
+                     size_t user_bytes, int user_on_host);
+qs_status qs_r2_step(qs_r2 *c, int n_steps);
+/* what: 0 n_b, 1 G, 2 n_p (cell centres, last step) -> float32 [n_xi][N][N]. */
+qs_status qs_r2_read(qs_r2 *c, int what, float *out, size_t out_bytes, int on_host);
+qs_status qs_r2_sync(qs_r2 *c);   /* QS_ERR_NONFINITE if a value overflowed */
+int64_t qs_r2_launch_count(const qs_r2 *c);
+void qs_r2_free(qs_r2 *c);
+
+/* ---------------------------------------------------------------------
  * Learned surrogate (the paper has no learned component; this serves
  * parameter screening with the solver as fallback and judge).
  * A small MLP n_in -> width (depth hidden layers, GELU erf form) -> 2

@@ -55,6 +55,19 @@ BATCH_BASE = dict(
 )
 
 
+# Finite-width narrow beam (self-modulation / hosing): one electron species,
+# Gaussian transverse profile of rms 0.5 and peak n_b/n_p = 0.05, gamma =
+# 2e4, flat top of length 400 (16,000 cells), periodic 256 x 256 transverse
+# grid over +-8 sigma_r, 500 steps; seeded by a 0.01 sigma_r centroid offset
+# plus white noise 1e-6 (relative to the local density).
+NARROW_BEAM = dict(
+    name="narrow_beam_256sq_16000xi_500steps",
+    species=[(-1.0, 1.0, 0.05)], gamma_b=2.0e4, n_xi=16000, dxi=0.025, dt=2.0,
+    ny=256, nz=256, Ly=8.0, Lz=8.0, sigma_r=0.5, transverse="gaussian",
+    n_steps=500, seed=0, amplitude=1e-6, offset=0.005,
+)
+
+
 def batch_instances(n_inst: int = 512, param_seed: int = 0, base: dict | None = None,
                     dxi: float = 0.025):
     """Seeded parameter draw for the batched sweep (reading: NumPy PCG64 with
@@ -83,6 +96,11 @@ def scaled(problem: dict, **kw) -> dict:
     p = copy.deepcopy(problem)
     p.update(kw)
     return p
+
+
+def normals(shape, seed: int):
+    """Standard normals (NumPy PCG64) for seeds passed in as data."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(shape)
 
 
 def user_seed(n_modes: int, n_species: int, n_xi: int, seed: int, amplitude: float):
