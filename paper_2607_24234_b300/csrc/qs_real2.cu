@@ -67,6 +67,157 @@ __device__ float2 *fft_rows(float2 *src, float2 *dst, int rows, const float2 *tw
     return src;
 }
 
+// ---------------------------------------------------------------------------
+// 256-point FFT by a team of 16 threads (four-step, 256 = 16 x 16): thread t
+// holds x[t + 16 m] (m = 0..15), does a 16-point DFT over m in registers,
+// multiplies by W256^(t k1), exchanges through a padded [16][17] buffer, and
+// does the 16-point DFT over t; thread t then holds X[t + 16 k2].  The
+// 16-point DFT is radix 4 x 4.  tw256[j] = exp(-2 pi i j / 256).
+// ---------------------------------------------------------------------------
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+    const float2 t0 = make_float2(a0.x + a2.x, a0.y + a2.y), t1 = make_float2(a0.x - a2.x, a0.y - a2.y);
+    const float2 t2 = make_float2(a1.x + a3.x, a1.y + a3.y), t3 = make_float2(a1.x - a3.x, a1.y - a3.y);
+    const float2 m3 = make_float2(t3.y, -t3.x);   // -i t3
+    a0 = make_float2(t0.x + t2.x, t0.y + t2.y);
+    a2 = make_float2(t0.x - t2.x, t0.y - t2.y);
+    if (INV) {
+        a1 = make_float2(t1.x - m3.x, t1.y - m3.y);
+        a3 = make_float2(t1.x + m3.x, t1.y + m3.y);
+    } else {
+        a1 = make_float2(t1.x + m3.x, t1.y + m3.y);
+        a3 = make_float2(t1.x - m3.x, t1.y - m3.y);
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 twid(const float2 *tw256, int j) {
+    float2 w = tw256[j & 255];
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// x[k] <- sum_m x[m] W16^(m k) (conjugate twiddles when INV)
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&x)[16], const float2 *tw256) {
+    float2 y[16];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float2 a0 = x[b], a1 = x[4 + b], a2 = x[8 + b], a3 = x[12 + b];
+        dft4<INV>(a0, a1, a2, a3);
+        y[4 * b + 0] = a0;
+        y[4 * b + 1] = cmul(a1, twid<INV>(tw256, 16 * b));
+        y[4 * b + 2] = cmul(a2, twid<INV>(tw256, 32 * b));
+        y[4 * b + 3] = cmul(a3, twid<INV>(tw256, 48 * b));
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float2 a0 = y[c], a1 = y[4 + c], a2 = y[8 + c], a3 = y[12 + c];
+        dft4<INV>(a0, a1, a2, a3);
+        x[c] = a0; x[c + 4] = a1; x[c + 8] = a2; x[c + 12] = a3;
+    }
+}
+
+// in-place FFT of one 256-entry row in shared memory by a 16-thread team;
+// every thread of the warp must call it (both half-warp teams in step)
+template <bool INV>
+__device__ __forceinline__ void fft256_team(float2 *row, float2 *T, const float2 *tw256, int t) {
+    float2 x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = row[t + 16 * m];
+    dft16<INV>(x, tw256);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) T[k1 * 17 + t] = cmul(x[k1], twid<INV>(tw256, t * k1));
+    __syncwarp();
+#pragma unroll
+    for (int tt = 0; tt < 16; ++tt) x[tt] = T[t * 17 + tt];
+    dft16<INV>(x, tw256);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) row[t + 16 * k2] = x[k2];
+    __syncwarp();
+}
+
+__device__ __forceinline__ void make_tw256(float2 *tw) {
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) {
+        float s, c;
+        sincospif(-2.0f * j / 256.0f, &s, &c);
+        tw[j] = make_float2(c, s);
+    }
+}
+
+// K1 for N = 256: 32 rows (16 packed) per CTA, 16 teams
+__global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np, float2 *__restrict__ S1) {
+    constexpr int N = 256, NH = 129, PR = 16;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *A = sm + 256, *T = A + PR * N;
+    const long long slice = blockIdx.y;
+    const int r0 = blockIdx.x * 2 * PR;
+    const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
+    make_tw256(tw);
+    const float *src = np + slice * (long long)N * N;
+    for (int i = threadIdx.x; i < PR * N; i += blockDim.x) {
+        const int pr = i >> 8, x = i & 255;
+        A[i] = make_float2(__ldcg(src + (long long)(r0 + 2 * pr) * N + x), __ldcg(src + (long long)(r0 + 2 * pr + 1) * N + x));
+    }
+    __syncthreads();
+    fft256_team<false>(A + team * N, T + team * 272, tw, t);
+    __syncthreads();
+    float2 *dst = S1 + slice * (long long)N * NH;
+    for (int i = threadIdx.x; i < PR * NH; i += blockDim.x) {
+        const int pr = i / NH, k = i - pr * NH;
+        const float2 Z = A[pr * N + k], Zc = A[pr * N + ((N - k) & (N - 1))];
+        dst[(long long)(r0 + 2 * pr) * NH + k] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y));
+        dst[(long long)(r0 + 2 * pr + 1) * NH + k] = make_float2(0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x));
+    }
+}
+
+// K2 for N = 256: 16 spectral columns per CTA, one team per column
+__global__ void __launch_bounds__(256) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
+                                                   float2 *__restrict__ T2, float ly, float lz) {
+    constexpr int N = 256, NH = 129, CBn = 16;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *A = sm + 256, *A2 = A + CBn * N, *T = A2 + CBn * N;
+    const long long slice = blockIdx.y;
+    const int c0 = blockIdx.x * CBn;
+    const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
+    make_tw256(tw);
+    const float2 *src = S1 + slice * (long long)N * NH;
+    for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
+        const int y = i >> 4, c = i & 15;
+        A[c * N + y] = (c0 + c < NH) ? __ldcg(src + (long long)y * NH + c0 + c) : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    float2 *col = A + team * N, *col2 = A2 + team * N;
+    fft256_team<false>(col, T + team * 272, tw, t);
+    const int kzi = c0 + team;
+    const float inv = 1.0f / (256.0f * 256.0f);
+    const float ty = 6.283185307179586f / ly, tz = 6.283185307179586f / lz;
+    const float kz = tz * (float)(kzi == 128 ? -128 : kzi);
+#pragma unroll 4
+    for (int m = 0; m < 16; ++m) {
+        const int jy = t + 16 * m;
+        const float sy = (float)(jy < 128 ? jy : jy - 256);
+        const float ky = ty * sy, kyd = jy == 128 ? 0.0f : ky;
+        const float kap = inv / (1.0f + ky * ky + kz * kz);
+        const float2 X = col[jy];
+        const float2 P = make_float2(kap * X.x, kap * X.y);
+        col[jy] = P;
+        col2[jy] = make_float2(-kyd * P.y, kyd * P.x);
+    }
+    __syncwarp();
+    fft256_team<true>(col, T + team * 272, tw, t);
+    fft256_team<true>(col2, T + team * 272, tw, t);
+    __syncthreads();
+    float2 *d1 = T1 + slice * (long long)N * NH, *d2 = T2 + slice * (long long)N * NH;
+    for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
+        const int y = i >> 4, c = i & 15;
+        if (c0 + c < NH) {
+            __stcg(d1 + (long long)y * NH + c0 + c, A[c * N + y]);
+            __stcg(d2 + (long long)y * NH + c0 + c, A2[c * N + y]);
+        }
+    }
+}
+
 // signed spectral index and its derivative version (Nyquist zeroed)
 template <int N>
 __device__ __forceinline__ float sidx(int j) { return (float)(j < N / 2 ? j : j - N); }
@@ -240,6 +391,60 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
     if (bad) atomicOr(a.err, 1);
 }
 
+// K3 for N = 256: 16 rows per CTA -> 16 Z1 rows + 8 Z2 rows; teams 0..7
+// transform two rows, teams 8..15 one (uniform within each warp).
+__global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
+                                                        const PushArgs a) {
+    constexpr int N = 256, NH = 129, RBn = 16;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm, *A = sm + 256, *T = A + (RBn + RBn / 2) * N;
+    const long long slice = blockIdx.y;
+    const int r0 = blockIdx.x * RBn;
+    const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
+    make_tw256(tw);
+    const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
+    const float tz = 6.283185307179586f / a.lz;
+    for (int i = threadIdx.x; i < RBn * N; i += blockDim.x) {
+        const int r = i >> 8, k = i & 255;
+        const bool lo = k <= 128;
+        const int kk = lo ? k : N - k;
+        float2 X = __ldcg(t1 + (long long)(r0 + r) * NH + kk);
+        if (!lo) X.y = -X.y;
+        const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
+        A[r * N + k] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
+    }
+    for (int i = threadIdx.x; i < (RBn / 2) * N; i += blockDim.x) {
+        const int pr = i >> 8, k = i & 255;
+        const bool lo = k <= 128;
+        const int kk = lo ? k : N - k;
+        float2 U = __ldcg(t2 + (long long)(r0 + 2 * pr) * NH + kk), V = __ldcg(t2 + (long long)(r0 + 2 * pr + 1) * NH + kk);
+        if (!lo) { U.y = -U.y; V.y = -V.y; }
+        A[(RBn + pr) * N + k] = make_float2(U.x - V.y, U.y + V.x);
+    }
+    __syncthreads();
+    fft256_team<true>(A + team * N, T + team * 272, tw, t);
+    if (team < 8) fft256_team<true>(A + (RBn + team) * N, T + team * 272, tw, t);
+    __syncthreads();
+    const long long base = slice * (long long)N * N;
+    bool bad = false;
+    for (int i = threadIdx.x; i < RBn * N; i += blockDim.x) {
+        const int r = i >> 8, z = i & 255;
+        const int y = r0 + r;
+        const float2 Z1 = A[r * N + z];
+        const float2 Z2 = A[(RBn + (r >> 1)) * N + z];
+        const float psi = Z1.x, dz = Z1.y, dy = (r & 1) ? Z2.y : Z2.x;
+        const long long o = base + (long long)y * N + z;
+        const int q = y * N + z;
+        const float S = a.coef * (a.nb0[q] * (psi - __ldcg(a.np + o)) + a.gy[q] * dy + a.gz[q] * dz);
+        const float g = fmaf(a.h, S, __ldcg(a.G + o));
+        const float n = fmaf(a.dt, g, __ldcg(a.nb + o));
+        __stcg(a.G + o, g);
+        __stcg(a.nb + o, n);
+        bad |= !(fabsf(n) <= 3.0e38f) || !(fabsf(g) <= 3.0e38f);
+    }
+    if (bad) atomicOr(a.err, 1);
+}
+
 // Philox4x32-10 (Salmon et al., SC'11) and the seed: n_b = A (n_b0/peak) g +
 // base(y, z), G = 0; g a standard normal per (cell, point) or a user field.
 __device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -302,8 +507,18 @@ size_t smem_k2() { return sizeof(float2) * (N / 2 + 4 * CB * N); }
 template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
+constexpr size_t SMEM_K1_256 = sizeof(float2) * (256 + 16 * 256 + 16 * 272);
+constexpr size_t SMEM_K2_256 = sizeof(float2) * (256 + 2 * 16 * 256 + 16 * 272);
+constexpr size_t SMEM_K3_256 = sizeof(float2) * (256 + 24 * 256 + 16 * 272);
+
 template <int N>
 cudaError_t set_attrs() {
+    if constexpr (N == 256) {
+        cudaError_t e = cudaFuncSetAttribute(r2::k_rowfft256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K1_256);
+        if (!e) e = cudaFuncSetAttribute(r2::k_colfft256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K2_256);
+        if (!e) e = cudaFuncSetAttribute(r2::k_rowinv_push256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K3_256);
+        return e;
+    }
     cudaError_t e = cudaFuncSetAttribute(r2::k_rowfft<N, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k1<N>());
     if (!e) e = cudaFuncSetAttribute(r2::k_colfft<N, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k2<N>());
     if (!e) e = cudaFuncSetAttribute(r2::k_rowinv_push<N, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k3<N>());
@@ -319,11 +534,19 @@ cudaError_t step_n(qs_r2 *c, float h) {
         c->nb, c->np, c->P, p.n_xi, q, (float)std::cos(D), (float)std::sin(D), (float)std::cos(0.5 * D),
         (float)std::sin(0.5 * D));
     constexpr int NH = N / 2 + 1;
+    r2::PushArgs a{c->np, c->nb, c->G, c->nb0, c->gy, c->gz,
+                   (float)(-p.species.q / (p.species.m * p.gamma_b)), h, (float)p.dt, (float)p.L_perp, c->err};
+    if constexpr (N == 256) {
+        r2::k_rowfft256<<<dim3(256 / 32, p.n_xi), 256, SMEM_K1_256, c->stream>>>(c->np, c->S1);
+        r2::k_colfft256<<<dim3((129 + 15) / 16, p.n_xi), 256, SMEM_K2_256, c->stream>>>(
+            c->S1, c->T1, c->T2, (float)p.L_perp, (float)p.L_perp);
+        r2::k_rowinv_push256<<<dim3(256 / 16, p.n_xi), 256, SMEM_K3_256, c->stream>>>(c->T1, c->T2, a);
+        c->launches += 4;
+        return cudaGetLastError();
+    }
     r2::k_rowfft<N, RB><<<dim3(N / RB, p.n_xi), 256, smem_k1<N>(), c->stream>>>(c->np, c->S1);
     r2::k_colfft<N, CB><<<dim3((NH + CB - 1) / CB, p.n_xi), 256, smem_k2<N>(), c->stream>>>(
         c->S1, c->T1, c->T2, (float)p.L_perp, (float)p.L_perp);
-    r2::PushArgs a{c->np, c->nb, c->G, c->nb0, c->gy, c->gz,
-                   (float)(-p.species.q / (p.species.m * p.gamma_b)), h, (float)p.dt, (float)p.L_perp, c->err};
     r2::k_rowinv_push<N, RB><<<dim3(N / RB, p.n_xi), 256, smem_k3<N>(), c->stream>>>(c->T1, c->T2, a);
     c->launches += 4;
     return cudaGetLastError();
