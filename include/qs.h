@@ -205,8 +205,11 @@ qs_status qs_modes(const qs_ctx *ctx, double *kx, double *ky);
 
 /* Launch shape of the sweep kernel. */
 enum { QS_VARIANT_REGISTERS = 0,  /* thread per line, register prefetch       */
-       QS_VARIANT_TMA = 1 };      /* thread per line, warp-wide TMA tiles of
+       QS_VARIANT_TMA = 1,        /* thread per line, warp-wide TMA tiles of
                                    * (cells x 32 modes) through shared memory */
+       QS_VARIANT_SCAN = 2 };     /* FP64 only, for few lines: the lanes of a
+                                   * warp split xi into sub-chunks joined by a
+                                   * shuffle scan of the cell propagators      */
 typedef struct {
     int warps_per_cta;   /* REGISTERS: 1, 2, 4 or 8 (TMA: always 1)         */
     int prefetch;        /* REGISTERS: cells per register batch (FP32 4|8,
@@ -215,6 +218,8 @@ typedef struct {
     int persistent;      /* 1: LPT-ordered work list pulled by atomic ticket */
     int ctas_per_sm;     /* persistent grid size = ctas_per_sm * SM count    */
     int variant;         /* QS_VARIANT_*                                    */
+    int scan_cells;      /* SCAN: cells per lane per sub-chunk (1..64); the
+                          * lanes per mode along xi are `prefetch` (2..32)  */
 } qs_launch;
 
 qs_status qs_set_launch(qs_ctx *ctx, const qs_launch *l);

@@ -67,7 +67,8 @@ class Allocator(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int), ("prefetch", ctypes.c_int),
-                ("persistent", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("variant", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("variant", ctypes.c_int),
+                ("scan_cells", ctypes.c_int)]
 
 
 def _load():
@@ -273,15 +274,15 @@ class Solver:
     def launch_count(self):
         return int(lib.qs_launch_count(self.ctx))
 
-    def set_launch(self, warps_per_cta=2, prefetch=8, persistent=0, ctas_per_sm=8, variant=0):
-        l = Launch(warps_per_cta, prefetch, persistent, ctas_per_sm, variant)
+    def set_launch(self, warps_per_cta=2, prefetch=8, persistent=0, ctas_per_sm=8, variant=0, scan_cells=8):
+        l = Launch(warps_per_cta, prefetch, persistent, ctas_per_sm, variant, scan_cells)
         self._chk(lib.qs_set_launch(self.ctx, ctypes.byref(l)))
 
     def get_launch(self):
         l = Launch()
         self._chk(lib.qs_get_launch(self.ctx, ctypes.byref(l)))
         return dict(warps_per_cta=l.warps_per_cta, prefetch=l.prefetch, persistent=l.persistent,
-                    ctas_per_sm=l.ctas_per_sm, variant=l.variant)
+                    ctas_per_sm=l.ctas_per_sm, variant=l.variant, scan_cells=l.scan_cells)
 
     def tune(self, reps: int = 2, cache_path: str | None = None):
         self._chk(lib.qs_tune(self.ctx, int(reps), cache_path.encode() if cache_path else None))

@@ -62,6 +62,7 @@ struct SweepArgs {
     long long rec_snap_doubles, rec_off_mag, rec_off_np, rec_off_mm, cells_total;
     int *ticket;
     int *err;
+    int scan_v;           // scan variant: cells per lane per sub-chunk
 };
 
 template <typename T> struct Cell { T nr, ni, tr, ti; };
@@ -512,6 +513,126 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
             while (!tma::try_wait(&bar[i], par) && ++spins < tma::kSpinLimit) {
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chunked parallel-scan variant (FP64), for problems with few lines.  A warp
+// owns MB = 32/S modes; its S lanes per mode split each super-chunk of
+// S*V cells into S sub-chunks of V cells.  Pass 1: every lane runs the
+// exact cell propagator of Eq. (5) over its V cells from a zero state, which
+// gives the affine aggregate B (the transition of V cells is the rotation
+// R^V, the same for every lane).  A Hillis-Steele scan over the S lanes of a
+// mode (shuffles at distance MB * 2^k, composing with R^(V 2^k)) turns the
+// aggregates into each sub-chunk's entry state, R^(V sigma) P_in + sum of
+// the earlier aggregates.  Pass 2 re-runs the same per-cell update as
+// k_sweep (fields, push, stores) from that entry state; the super-chunk's
+// exit state is carried to the next one.
+// ---------------------------------------------------------------------------
+struct Rot { double c, s; };
+__device__ __forceinline__ Rot rot(double ang) { Rot r; sincos(ang, &r.s, &r.c); return r; }
+// (n, n') <- R(d) (n, n') for the real and the imaginary parts
+__device__ __forceinline__ void rotate(const Rot &R, double &nr, double &ni, double &dr, double &di) {
+    const double xr = R.c * nr + R.s * dr, xi = R.c * ni + R.s * di;
+    const double yr = -R.s * nr + R.c * dr, yi = -R.s * ni + R.c * di;
+    nr = xr; ni = xi; dr = yr; di = yi;
+}
+
+template <int NS, int S>
+__global__ void __launch_bounds__(128) k_sweep_scan(const SweepArgs a) {
+    constexpr int MB = 32 / S;
+    const int lane = threadIdx.x & 31;
+    const int sig = lane / MB, mm = lane - sig * MB;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= a.n_items) return;                       // uniform per warp
+    const int2 itx = a.items[item];
+    const int mode = itx.y + mm;
+    const bool live = mode < a.M;
+    const InstDev I = a.inst[itx.x];
+    Line<double, NS, 1, false> L(a, I, itx.x, live ? mode : itx.y);
+    L.line_begin();
+    const int N = I.n_xi, V = a.scan_v, C = S * V;
+    const double D = I.dxi;
+    const Rot Rsig = rot(D * V * sig), RC = rot(D * C);
+    Rot Rlev[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Rlev[k] = rot(D * V * (1 << k));
+    const double c = I.c, s = I.s;
+    double q[NS];
+#pragma unroll
+    for (int sp = 0; sp < NS; ++sp) q[sp] = I.q[sp];
+    const double *wt = reinterpret_cast<const double *>(a.w) + I.cell_off * NS;
+    for (int it = 0; it < a.n_steps; ++it) {
+        L.step_begin(it);
+        double Pr = L.nr, Pi = L.ni, Qr = L.dr, Qi = L.di;   // super-chunk entry state
+        if (a.front == 1 && live) {
+            double rr = 0, ri = 0;
+            for (int sp = 0; sp < NS; ++sp) {
+                Cell<double> x;
+                ld_cell(a, I.cell_off * NS + sp, mode, x);
+                rr = fma(q[sp], x.nr, rr);
+                ri = fma(q[sp], x.ni, ri);
+            }
+            Pr = rr; Pi = ri; Qr = 0; Qi = 0;
+        }
+        for (int J = 0; J < N; J += C) {
+            const int j0 = J + sig * V;
+            // pass 1: aggregate of this lane's V cells from a zero state
+            double br = 0, bi = 0, er = 0, ei = 0;
+            for (int v = 0; v < V; ++v) {
+                const int j = j0 + v;
+                if (j >= N || !live) break;
+                double rr = 0, ri = 0;
+                for (int sp = 0; sp < NS; ++sp) {
+                    const double2 x = __ldcg(reinterpret_cast<const double2 *>(a.st) +
+                                             ((I.cell_off + j) * NS + sp) * a.Mp + mode);
+                    rr = fma(q[sp], x.x, rr);
+                    ri = fma(q[sp], x.y, ri);
+                }
+                const double ur = br - rr, ui = bi - ri;
+                const double xr = fma(c, ur, fma(s, er, rr)), xi = fma(c, ui, fma(s, ei, ri));
+                er = fma(-s, ur, c * er);
+                ei = fma(-s, ui, c * ei);
+                br = xr; bi = xi;
+            }
+            // inclusive scan over the S lanes of this mode
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int d = 1 << k;
+                if (d >= S) break;
+                double ur = __shfl_up_sync(0xffffffffu, br, d * MB), ui = __shfl_up_sync(0xffffffffu, bi, d * MB);
+                double vr = __shfl_up_sync(0xffffffffu, er, d * MB), vi = __shfl_up_sync(0xffffffffu, ei, d * MB);
+                if (sig >= d) {
+                    rotate(Rlev[k], ur, ui, vr, vi);
+                    br += ur; bi += ui; er += vr; ei += vi;
+                }
+            }
+            // exclusive prefix, entry state, and the chunk's exit aggregate
+            double xr = __shfl_up_sync(0xffffffffu, br, MB), xi = __shfl_up_sync(0xffffffffu, bi, MB);
+            double yr = __shfl_up_sync(0xffffffffu, er, MB), yi = __shfl_up_sync(0xffffffffu, ei, MB);
+            if (sig == 0) { xr = xi = yr = yi = 0; }
+            const int last = (S - 1) * MB + mm;
+            const double Br = __shfl_sync(0xffffffffu, br, last), Bi = __shfl_sync(0xffffffffu, bi, last);
+            const double Er = __shfl_sync(0xffffffffu, er, last), Ei = __shfl_sync(0xffffffffu, ei, last);
+            double nr = Pr, ni = Pi, dr = Qr, di = Qi;
+            rotate(Rsig, nr, ni, dr, di);
+            L.nr = nr + xr; L.ni = ni + xi; L.dr = dr + yr; L.di = di + yi;
+            // pass 2: the real per-cell update
+            for (int v = 0; v < V; ++v) {
+                const int j = j0 + v;
+                if (j >= N || !live) break;
+                Cell<double> x[NS];
+                double w[NS];
+                for (int sp = 0; sp < NS; ++sp) {
+                    ld_cell(a, (I.cell_off + j) * NS + sp, mode, x[sp]);
+                    w[sp] = __ldg(wt + (long long)j * NS + sp);
+                }
+                L.cell(x, w, j, N);
+            }
+            rotate(RC, Pr, Pi, Qr, Qi);
+            Pr += Br; Pi += Bi; Qr += Er; Qi += Ei;
+        }
+        if (live) L.step_end();
     }
 }
 

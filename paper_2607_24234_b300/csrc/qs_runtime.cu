@@ -68,7 +68,7 @@ struct qs_ctx {
     long long rec_g0 = 0;
     void *rec_buf = nullptr;
     size_t rec_bytes = 0;
-    qs_launch launch{2, 4, 0, 8, 0};
+    qs_launch launch{2, 4, 0, 8, 0, 8};
     CUtensorMap tmA{}, tmB{};
     int tm_rows = -1;            // box rows the tensor maps were encoded for
     int items_for_warps = -1, items_persistent = -1;
@@ -217,10 +217,13 @@ bool same_kset(const qs_params &a, const qs_params &b) {
 }
 
 qs_status build_items(qs_ctx *c) {
-    const int wpc = c->launch.variant == QS_VARIANT_TMA ? 1 : c->launch.warps_per_cta;
+    // modes per work item: 32 x warps (thread per line), 32 (TMA), 32/S (scan)
+    const int wpc = c->launch.variant == QS_VARIANT_TMA ? 1
+                  : c->launch.variant == QS_VARIANT_SCAN ? -c->launch.prefetch
+                  : c->launch.warps_per_cta;
     const int P = c->launch.persistent;
     if (c->items_for_warps == wpc && c->items_persistent == P && c->items_d) return QS_OK;
-    const int per = 32 * wpc;
+    const int per = wpc > 0 ? 32 * wpc : 32 / (-wpc);
     std::vector<int2> items;
     std::vector<int> order(c->n_inst);
     for (int i = 0; i < c->n_inst; ++i) order[i] = i;
@@ -232,7 +235,7 @@ qs_status build_items(qs_ctx *c) {
     const size_t need = items.size() * sizeof(int2);
     // reuse the buffer when it is big enough (the maximum: one item per 32 modes)
     if (!c->items_d) {
-        const size_t maxb = (size_t)c->n_inst * ((c->M + 31) / 32) * sizeof(int2);
+        const size_t maxb = (size_t)c->n_inst * c->M * sizeof(int2);
         qs_status s = dalloc_t(c, maxb, &c->items_d);
         if (s) return s;
     }
@@ -311,6 +314,22 @@ cudaError_t launch_tma(qs_ctx *c, const SweepArgs &a, dim3 grid, int C) {
     return C >= 8 ? launch_tma_t<double, 2, 8, 2>(c, a, grid) : launch_tma_t<double, 2, 4, 4>(c, a, grid);
 }
 
+template <int NS>
+cudaError_t scan_ns(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads, int S) {
+    switch (S) {
+    case 2: qsk::k_sweep_scan<NS, 2><<<grid, threads, 0, c->stream>>>(a); break;
+    case 4: qsk::k_sweep_scan<NS, 4><<<grid, threads, 0, c->stream>>>(a); break;
+    case 8: qsk::k_sweep_scan<NS, 8><<<grid, threads, 0, c->stream>>>(a); break;
+    case 16: qsk::k_sweep_scan<NS, 16><<<grid, threads, 0, c->stream>>>(a); break;
+    default: qsk::k_sweep_scan<NS, 32><<<grid, threads, 0, c->stream>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t scan_dispatch(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads, int S) {
+    return c->NS == 1 ? scan_ns<1>(c, a, grid, threads, S) : scan_ns<2>(c, a, grid, threads, S);
+}
+
 // One launch of the sweep kernel for n_steps steps starting at global step
 // step0.  update = 0 runs the field pass only.  rec: record target (may be
 // null).
@@ -337,7 +356,19 @@ qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int 
     a.rec_off_mm = off;  if (rec_kinds & QS_REC_MODEMAX) off += 3LL * c->n_inst * c->Mp;
     a.rec_snap_doubles = off;
     a.ticket = c->ticket_d; a.err = c->err_d;
+    a.scan_v = c->launch.scan_cells;
     const bool use_tma = c->launch.variant == QS_VARIANT_TMA && update && !rec_kinds;
+    const bool use_scan = c->launch.variant == QS_VARIANT_SCAN && update && !rec_kinds && c->prec == QS_FP64;
+    if (c->launch.variant == QS_VARIANT_SCAN && !use_scan) {
+        // field / record passes of a scan-configured context run the register
+        // kernel (same per-cell arithmetic) with its own work list
+        const qs_launch keep = c->launch;
+        c->launch = qs_launch{1, c->prec == QS_FP32_RENORM ? 8 : 4, 0, 8, QS_VARIANT_REGISTERS, 8};
+        qs_status r = launch_sweep(c, step0, n_steps, update, rec_kinds, rec, rec_g0, rec_stride, rec_max_snap);
+        c->launch = keep;
+        c->items_for_warps = -1000;   // force the scan work list to be rebuilt
+        return r;
+    }
     const int threads = 32 * (c->launch.variant == QS_VARIANT_TMA ? 1 : c->launch.warps_per_cta);
     dim3 grid(c->n_items);
     if (a.persistent) {
@@ -348,7 +379,13 @@ qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int 
     const bool R = a.rec_kinds != 0;
     const int U = c->launch.prefetch;
     cudaError_t e;
-    if (use_tma) {
+    if (use_scan) {
+        const int S = c->launch.prefetch;
+        const int wpb = c->launch.warps_per_cta;
+        a.persistent = 0;
+        const dim3 g2((unsigned)((c->n_items + wpb - 1) / wpb));
+        e = scan_dispatch(c, a, g2, 32 * wpb, S);
+    } else if (use_tma) {
         const int C = c->launch.prefetch;
         const int rows = (c->prec == QS_FP32_RENORM ? (C >= 16 ? 16 : 8) : (C >= 8 ? 8 : 4)) * c->NS;
         qs_status ts = ensure_tensor_maps(c, rows);
@@ -536,7 +573,7 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
     // default launch shape (measured on B300 for the 3D beam workload): TMA
     // tiles of 8 (FP32) / 4 (FP64) cells x 32 modes, 4-deep ring; batched
     // contexts pull an LPT-ordered work list
-    c->launch = qs_launch{1, c->prec == QS_FP32_RENORM ? 8 : 4, n_inst > 1 ? 1 : 0, 16, QS_VARIANT_TMA};
+    c->launch = qs_launch{1, c->prec == QS_FP32_RENORM ? 8 : 4, n_inst > 1 ? 1 : 0, 16, QS_VARIANT_TMA, 8};
     *out = c;
     return QS_OK;
 }
@@ -730,7 +767,8 @@ qs_status qs_query(const qs_ctx *c, int what, int64_t arg, int64_t *value) {
         break;
     case QS_Q_LAUNCH:
         *value = c->launch.warps_per_cta | (c->launch.prefetch << 8) | (c->launch.persistent << 16) |
-                 ((int64_t)c->launch.ctas_per_sm << 24) | ((int64_t)c->launch.variant << 32);
+                 ((int64_t)c->launch.ctas_per_sm << 24) | ((int64_t)c->launch.variant << 32) |
+                 ((int64_t)c->launch.scan_cells << 40);
         break;
     default: return QS_ERR_ARG;
     }
@@ -746,7 +784,18 @@ qs_status qs_modes(const qs_ctx *c, double *kx, double *ky) {
 qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
     if (!c || !l) return QS_ERR_ARG;
     const int w = l->warps_per_cta;
-    if (l->variant != QS_VARIANT_REGISTERS && l->variant != QS_VARIANT_TMA) return fail(c, QS_ERR_ARG, "variant");
+    if (l->variant < QS_VARIANT_REGISTERS || l->variant > QS_VARIANT_SCAN) return fail(c, QS_ERR_ARG, "variant");
+    if (l->variant == QS_VARIANT_SCAN) {
+        if (c->prec != QS_FP64) return fail(c, QS_ERR_UNSUPPORTED, "the scan variant is FP64 only");
+        const int S = l->prefetch;
+        if (!(S == 2 || S == 4 || S == 8 || S == 16 || S == 32) || l->scan_cells < 1 || l->scan_cells > 64 ||
+            !(l->warps_per_cta >= 1 && l->warps_per_cta <= 4))
+            return fail(c, QS_ERR_ARG, "scan: prefetch = lanes per mode (2..32), scan_cells 1..64, 1..4 warps");
+        c->launch = *l;
+        for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+        c->graphs.clear();
+        return QS_OK;
+    }
     if (!(w == 1 || w == 2 || w == 4 || w == 8)) return fail(c, QS_ERR_ARG, "warps_per_cta");
     const bool f32 = c->prec == QS_FP32_RENORM;
     if (l->variant == QS_VARIANT_TMA) {

@@ -421,3 +421,49 @@ def test_batched_512_instances_full_size_sampled(qs):
         worst = max(worst, float(np.max(np.abs(got - ref))))
     assert worst <= 1e-3, worst
     s.close()
+
+
+@pytest.mark.parametrize("S,V", [(2, 1), (4, 5), (8, 16), (32, 3)])
+@pytest.mark.parametrize("case", [SMALL[0], SMALL[2], SMALL[3], SMALL[5], SMALL[6]],
+                         ids=lambda c: f"nxi{c[0]}-m{len(c[1])}-s{len(c[2])}-{c[4]}")
+def test_scan_variant_fp64(qs, case, S, V):
+    """FP64 chunked-scan variant (lanes split xi, shuffle scan of the cell
+    propagators) against the oracle at 1e-9."""
+    p, held, user, sd, steps = _small_problem(case)
+    s, nb, th = _run_gpu(qs, p, "fp64", steps, seed=sd, held=held, user=user,
+                         launch=dict(warps_per_cta=2, prefetch=S, persistent=0, ctas_per_sm=8, variant=2,
+                                     scan_cells=V))
+    nb_o, th_o = _run_oracle(p, steps, seed=sd, held=held, user=user)
+    assert _line_rel(nb, nb_o) <= FP64_TOL
+    assert _line_rel(th, th_o) <= FP64_TOL
+    s.close()
+
+
+def test_scan_variant_slab2d_full_size(qs):
+    """The 2D slab workload (64 modes x 512 cells x 400 steps, FP64): the
+    scan variant against the oracle, and its time against thread-per-line."""
+    import torch
+    p = synth.SLAB_2D
+    nb_o, th_o = oracle.seed_noise(p, 0, 1e-6)
+    oracle.sweep(p, nb_o, th_o, 0, 400)
+    times = {}
+    for name, launch in (("line", dict(warps_per_cta=1, prefetch=4, persistent=0, ctas_per_sm=8, variant=1)),
+                         ("scan", dict(warps_per_cta=1, prefetch=32, persistent=0, ctas_per_sm=8, variant=2,
+                                       scan_cells=4))):
+        s = qs.Solver(p, prec="fp64")
+        s.set_launch(**launch)
+        s.seed_noise(0, 1e-6)
+        s.step(2)
+        s.seed_noise(0, 1e-6)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(400)
+        e1.record()
+        s.sync()
+        times[name] = e0.elapsed_time(e1)
+        nb, th = s.state_arrays()
+        assert _line_rel(nb, nb_o) <= FP64_TOL and _line_rel(th, th_o) <= FP64_TOL
+        s.close()
+    print({"slab2d_fp64_ms": times})
+    assert times["scan"] < times["line"]
