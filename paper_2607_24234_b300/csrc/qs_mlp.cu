@@ -75,14 +75,47 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
-        for (int i = tid; i < BM * BK; i += 128) {
-            const int r = i / BK, k = i % BK;
-            As[r][k] = __float2bfloat16(ld_op<TA>(g.A, g.lda, m0 + r, k0 + k, g.M, g.K));
+    // split-K over gridDim.z: this CTA reduces k in [kb, ke)
+    const int kchunk = ((g.K + gridDim.z * BK - 1) / (gridDim.z * BK)) * BK;
+    const int kb = blockIdx.z * kchunk, ke = min(g.K, kb + kchunk);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        // K-contiguous operands: 16-byte vectors of 8 bf16; transposed
+        // operands: the fastest thread index runs along the contiguous rows
+        if (TA == 0) {
+            for (int i = tid; i < BM * BK / 8; i += 128) {
+                const int r = i / (BK / 8), k = (i % (BK / 8)) * 8;
+                const int gr = m0 + r, gk = k0 + k;
+                if (gr < g.M && gk + 8 <= ke && (g.lda % 8) == 0) {
+                    *reinterpret_cast<uint4 *>(&As[r][k]) =
+                        __ldg(reinterpret_cast<const uint4 *>(g.A + (long long)gr * g.lda + gk));
+                } else {
+                    for (int e = 0; e < 8; ++e)
+                        As[r][k + e] = __float2bfloat16(gk + e < ke ? ld_op<0>(g.A, g.lda, gr, gk + e, g.M, g.K) : 0.0f);
+                }
+            }
+        } else {
+            for (int i = tid; i < BM * BK; i += 128) {
+                const int r = i % BM, k = i / BM;
+                As[r][k] = __float2bfloat16(k0 + k < ke ? ld_op<1>(g.A, g.lda, m0 + r, k0 + k, g.M, g.K) : 0.0f);
+            }
         }
-        for (int i = tid; i < BN * BK; i += 128) {
-            const int r = i / BK, k = i % BK;
-            Bs[r][k] = __float2bfloat16(ld_op<TB>(g.B, g.ldb, n0 + r, k0 + k, g.N, g.K));
+        if (TB == 0) {
+            for (int i = tid; i < BN * BK / 8; i += 128) {
+                const int r = i / (BK / 8), k = (i % (BK / 8)) * 8;
+                const int gr = n0 + r, gk = k0 + k;
+                if (gr < g.N && gk + 8 <= ke && (g.ldb % 8) == 0) {
+                    *reinterpret_cast<uint4 *>(&Bs[r][k]) =
+                        __ldg(reinterpret_cast<const uint4 *>(g.B + (long long)gr * g.ldb + gk));
+                } else {
+                    for (int e = 0; e < 8; ++e)
+                        Bs[r][k + e] = __float2bfloat16(gk + e < ke ? ld_op<0>(g.B, g.ldb, gr, gk + e, g.N, g.K) : 0.0f);
+                }
+            }
+        } else {
+            for (int i = tid; i < BN * BK; i += 128) {
+                const int r = i % BN, k = i / BN;
+                Bs[r][k] = __float2bfloat16(k0 + k < ke ? ld_op<1>(g.B, g.ldb, n0 + r, k0 + k, g.N, g.K) : 0.0f);
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -128,7 +161,10 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                 float v = acc[i][j][e];
                 const long long oc = (long long)m * g.ldc + n;
                 switch (g.epi) {
-                case EPI_STORE: g.C[oc] = g.accumulate ? g.C[oc] + v : v; break;
+                case EPI_STORE:
+                    if (gridDim.z > 1) atomicAdd(g.C + oc, v);
+                    else g.C[oc] = g.accumulate ? g.C[oc] + v : v;
+                    break;
                 case EPI_BIAS: g.C[oc] = v + g.bias[n]; break;
                 case EPI_BIAS_GELU: {
                     const float z = v + g.bias[n];
@@ -326,8 +362,9 @@ qs_status mdev(qs_mlp *m, size_t bytes, P **p) {
     return s;
 }
 
-void gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g) {
-    dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM);
+void gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g, int split = 1) {
+    dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM, split);
+    if (split > 1) cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.ldc, m->stream);
     if (TA == 0 && TB == 0) mlp::k_gemm<0, 0><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 0 && TB == 1) mlp::k_gemm<0, 1><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 1 && TB == 0) mlp::k_gemm<1, 0><<<grid, 128, 0, m->stream>>>(g);
@@ -375,7 +412,12 @@ void backward(qs_mlp *m, int e, int n) {
         gw.M = out; gw.N = in; gw.K = n;
         gw.C = Ge + m->woff[l]; gw.ldc = in;
         gw.epi = mlp::EPI_STORE;
-        gemm(m, 1, 1, gw);
+        // the weight gradient reduces over the batch: split it so that the
+        // (out x in) output tiles fill the GPU
+        const int tiles = ((out + mlp::BM - 1) / mlp::BM) * ((in + mlp::BN - 1) / mlp::BN);
+        int split = std::max(1, std::min(64, 296 / std::max(1, tiles)));
+        split = std::min(split, std::max(1, n / 256));
+        gemm(m, 1, 1, gw, split);
         mlp::k_colsum<<<out, 256, 0, m->stream>>>(dz, n, out, Ge + m->boff[l]);
         if (l == 0) break;
         // dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * gelu'(Z[l-1][b][i])
