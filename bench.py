@@ -414,9 +414,18 @@ def run_ours(args):
         s64.sync()
         ms64 = e0.elapsed_time(e1)
         upd64 = M * N * j64
+        # FP64 is bound by the FP64 units: 22 DP instructions per update (per
+        # real part: 3 MUL/ADD + 8 FMA, Line::cell); peak = the nominal 1.25
+        # TFLOP/s FP64 of B300 as 2 DP instructions/clock/SM at the max SM clock
+        pk, _ = peaks()
+        dp_peak = 2.0 * 148 * pk.get("sm_max_mhz", 2032.0) * 1e6
+        dp_ach = 22.0 * upd64 / (ms64 / 1e3)
         fp64 = {"value": upd64 / (ms64 / 1e3), "unit": UNIT, "slow_time_steps": j64,
                 "ms": ms64, "launch": s64.get_launch(),
                 "hbm_gbs_algorithmic": BYTES_PER_UPDATE_FP64 * upd64 / (ms64 / 1e3) / 1e9,
+                "roofline": {"bound": "alu", "achieved": dp_ach / 1e12, "peak": dp_peak / 1e12,
+                             "unit": "T DP-instr/s", "frac": dp_ach / dp_peak,
+                             "peak_source": "derived: nominal 1.25 TFLOP/s FP64 = 2 DP instr/clk/SM x 148 SMs x max SM clock"},
                 "error_vs_oracle": "<= 1e-9 relative per mode line (tests/test_gpu_parity.py)"}
         s64.close()
 

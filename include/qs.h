@@ -239,6 +239,16 @@ qs_status qs_step_graph(qs_ctx *ctx, int n_steps);
 /* Wait for the stream and report device-side errors. */
 qs_status qs_sync(qs_ctx *ctx);
 
+/* Test hook for the bounded waits of the TMA variant (failure detection
+ * without a GPU fault).  Every mbarrier wait of that kernel gives up after
+ * spin_limit polls (default 2^24); with unsatisfiable = 1 each tile's
+ * barrier expects 16 bytes more than its tensor copy delivers, so the first
+ * wait runs out: the kernel records QS_ERR_TIMEOUT in the device error word,
+ * drains its copies (again bounded) and returns, and qs_sync reports
+ * QS_ERR_TIMEOUT.  The context is usable again after qs_debug_waits(ctx,
+ * limit, 0) and a reseed.  Other kernels have no device-side waits. */
+qs_status qs_debug_waits(qs_ctx *ctx, int64_t spin_limit, int unsatisfiable);
+
 /* Number of sweep-kernel launches enqueued by this context so far. */
 int64_t qs_launch_count(const qs_ctx *ctx);
 

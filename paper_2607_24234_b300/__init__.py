@@ -91,6 +91,8 @@ def _load():
     L.qs_tune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p]
     L.qs_step_graph.argtypes = [vp, ctypes.c_int]
     L.qs_sync.argtypes = [vp]
+    L.qs_debug_waits.argtypes = [vp, i64, ctypes.c_int]
+    L.qs_debug_waits.restype = ctypes.c_int
     L.qs_launch_count.argtypes = [vp]
     L.qs_launch_count.restype = i64
     L.qs_last_error.argtypes = [vp]
@@ -273,6 +275,9 @@ class Solver:
 
     def launch_count(self):
         return int(lib.qs_launch_count(self.ctx))
+
+    def debug_waits(self, spin_limit=1 << 24, unsatisfiable=False):
+        self._chk(lib.qs_debug_waits(self.ctx, int(spin_limit), 1 if unsatisfiable else 0))
 
     def set_launch(self, warps_per_cta=2, prefetch=8, persistent=0, ctas_per_sm=8, variant=0, scan_cells=8):
         l = Launch(warps_per_cta, prefetch, persistent, ctas_per_sm, variant, scan_cells)

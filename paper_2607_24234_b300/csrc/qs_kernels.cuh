@@ -63,6 +63,8 @@ struct SweepArgs {
     int *ticket;
     int *err;
     int scan_v;           // scan variant: cells per lane per sub-chunk
+    long long spin_limit; // TMA variant: bound on every mbarrier wait (iterations)
+    int tx_extra;         // test hook: extra bytes each tile barrier expects (0)
 };
 
 template <typename T> struct Cell { T nr, ni, tr, ti; };
@@ -119,7 +121,8 @@ struct Line {
     int W, E;              // working scale of the current group, stored scale
     float facM;            // 2^(E - W): stored mantissa -> working scale
     float gmax, gnan;
-    double mm0, mm1, mm2;  // running max for MODEMAX
+    double mm0, mm1, mm2;  // running max for MODEMAX (ln of magnitudes)
+    double gm0, gm1, gm2;  // running max of squared magnitudes in the current scale
 
     __device__ Line(const SweepArgs &a_, const InstDev &I_, int inst_, int mode_)
         : a(a_), I(I_), inst(inst_), mode(mode_) {}
@@ -172,34 +175,49 @@ struct Line {
 
     __device__ __forceinline__ void record(long long j, T mr, T mi, T mdr, T mdi, T rr, T ri,
                                            const Cell<T> *x) {
-        // fields at the cell centre (working scale; FP32 adds W ln 2)
-        const double sc = RN ? (double)W * 0.69314718055994530942 : 0.0;
+        // fields at the cell centre, in the working scale (FP32: x 2^W)
         double nb2 = 0.0;
 #pragma unroll
         for (int sp = 0; sp < NS; ++sp)
             nb2 += (double)x[sp].nr * x[sp].nr + (double)x[sp].ni * x[sp].ni;
-        double exr = -(double)kap * mdr, exi = -(double)kap * mdi;
-        double epr = (double)kabsk * ((double)mr - rr), epi = (double)kabsk * ((double)mi - ri);
-        double ex2 = exr * exr + exi * exi;
-        double lnb = 0.5 * log(nb2) + sc;
-        double lE = 0.5 * log(ex2 + epr * epr + epi * epi) + sc;
-        double lB = log((double)kabsk) + 0.5 * log((double)rr * rr + (double)ri * ri) + sc;
-        double lF = log((double)kabsk) + 0.5 * log((double)mr * mr + (double)mi * mi) + sc;
-        double lEx = 0.5 * log(ex2) + sc;
-        double *base = a.rec + snap * a.rec_snap_doubles;
-        long long cm = (I.cell_off + j) * a.Mp + mode;
-        if (a.rec_kinds & 1) {
-            long long pl = a.cells_total * a.Mp;
-            double *o = base + a.rec_off_mag + cm;
-            __stcs(o, lnb); __stcs(o + pl, lE); __stcs(o + 2 * pl, lB);
-            __stcs(o + 3 * pl, lF); __stcs(o + 4 * pl, lEx);
+        const double exr = -(double)kap * mdr, exi = -(double)kap * mdi;
+        const double epr = (double)kabsk * ((double)mr - rr), epi = (double)kabsk * ((double)mi - ri);
+        const double ex2 = exr * exr + exi * exi;
+        const double e2 = ex2 + epr * epr + epi * epi;
+        const double kk = (double)kabsk * kabsk;
+        const double b2 = kk * ((double)rr * rr + (double)ri * ri);
+        if (a.rec_kinds & 3) {
+            const double sc = RN ? (double)W * 0.69314718055994530942 : 0.0;
+            double *base = a.rec + snap * a.rec_snap_doubles;
+            const long long cm = (I.cell_off + j) * a.Mp + mode;
+            if (a.rec_kinds & 1) {
+                const long long pl = a.cells_total * a.Mp;
+                double *o = base + a.rec_off_mag + cm;
+                __stcs(o, 0.5 * log(nb2) + sc);
+                __stcs(o + pl, 0.5 * log(e2) + sc);
+                __stcs(o + 2 * pl, 0.5 * log(b2) + sc);
+                __stcs(o + 3 * pl, 0.5 * log(kk * ((double)mr * mr + (double)mi * mi)) + sc);
+                __stcs(o + 4 * pl, 0.5 * log(ex2) + sc);
+            }
+            if (a.rec_kinds & 2) {
+                const double f = RN ? ldexp(1.0, W) : 1.0;
+                __stcs(reinterpret_cast<double2 *>(base + a.rec_off_np) + cm,
+                       make_double2((double)mr * f, (double)mi * f));
+            }
         }
-        if (a.rec_kinds & 2) {
-            double f = RN ? ldexp(1.0, W) : 1.0;
-            __stcs(reinterpret_cast<double2 *>(base + a.rec_off_np) + cm,
-                   make_double2((double)mr * f, (double)mi * f));
+        // per-mode maxima: squared magnitudes within a scale group, one log per group
+        if (a.rec_kinds & 4) { gm0 = fmax(gm0, nb2); gm1 = fmax(gm1, e2); gm2 = fmax(gm2, b2); }
+    }
+
+    // fold the squared-magnitude maxima of the current scale into the log maxima
+    __device__ __forceinline__ void fold_max() {
+        if (REC && rec && (a.rec_kinds & 4)) {
+            const double sc = RN ? (double)W * 0.69314718055994530942 : 0.0;
+            if (gm0 > 0.0) mm0 = fmax(mm0, 0.5 * log(gm0) + sc);
+            if (gm1 > 0.0) mm1 = fmax(mm1, 0.5 * log(gm1) + sc);
+            if (gm2 > 0.0) mm2 = fmax(mm2, 0.5 * log(gm2) + sc);
+            gm0 = gm1 = gm2 = 0.0;
         }
-        if (a.rec_kinds & 4) { mm0 = fmax(mm0, lnb); mm1 = fmax(mm1, lE); mm2 = fmax(mm2, lB); }
     }
 
     // One cell: x[NS] holds (n_b, Theta) of cell j as stored (mantissas on
@@ -247,7 +265,10 @@ struct Line {
                 st_cell(a, row + sp, mode, x[sp]);
             }
         }
-        if (RN && (((j + 1) % GRP) == 0 || j == N - 1)) group_end(j / GRP);
+        if (RN && (((j + 1) % GRP) == 0 || j == N - 1)) {
+            fold_max();
+            group_end(j / GRP);
+        }
     }
 
     __device__ __forceinline__ void compute(Batch &b, int j0) {
@@ -281,6 +302,7 @@ struct Line {
                 snap = d / a.rec_stride;
             }
             mm0 = mm1 = mm2 = -INFINITY;
+            gm0 = gm1 = gm2 = 0.0;
         }
         nr = ni = dr = di = 0;
         W = 0;
@@ -299,6 +321,7 @@ struct Line {
     }
 
     __device__ __forceinline__ void step_end() {
+        if (!RN) fold_max();
         if (!(fabs((double)nr) + fabs((double)ni) + fabs((double)dr) + fabs((double)di) <= 1.0e300))
             atomicOr(a.err, ERR_NONFINITE);
         if (REC && rec && (a.rec_kinds & 4)) {
@@ -441,7 +464,7 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
         const T *wt = reinterpret_cast<const T *>(a.w) + I.cell_off * NS;
         auto issue = [&](int k) {
             const int stg = k % ST;
-            tma::arrive_expect_tx(&bar[stg], TILE);
+            tma::arrive_expect_tx(&bar[stg], TILE + a.tx_extra);
             const int y = (int)((I.cell_off + (long long)k * C) * NS);
             tma::load_2d(buf[stg], &tmA, x0, y, &bar[stg]);
             if (!F32) tma::load_2d(buf[stg] + TILE_A, &tmB, x0, y, &bar[stg]);
@@ -460,7 +483,7 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
                 const uint32_t par = (phase >> stg) & 1u;
                 long long spins = 0;
                 bool ok = tma::try_wait(&bar[stg], par);
-                while (!ok && ++spins < tma::kSpinLimit) ok = tma::try_wait(&bar[stg], par);
+                while (!ok && ++spins < a.spin_limit) ok = tma::try_wait(&bar[stg], par);
                 if (__any_sync(0xffffffffu, !ok)) { dead = true; break; }
                 phase ^= 1u << stg;
                 pending &= ~(1u << stg);
@@ -510,7 +533,7 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
             if (!(pending & (1u << i))) continue;
             const uint32_t par = (phase >> i) & 1u;
             long long spins = 0;
-            while (!tma::try_wait(&bar[i], par) && ++spins < tma::kSpinLimit) {
+            while (!tma::try_wait(&bar[i], par) && ++spins < a.spin_limit) {
             }
         }
     }

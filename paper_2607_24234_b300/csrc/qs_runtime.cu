@@ -75,6 +75,8 @@ struct qs_ctx {
     int n_sm = 148;
     std::map<int, cudaGraphExec_t> graphs;
     long long n_launch = 0;
+    long long spin_limit = 1LL << 24;
+    int tx_extra = 0;
     std::string err;
 };
 
@@ -357,6 +359,8 @@ qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int 
     a.rec_snap_doubles = off;
     a.ticket = c->ticket_d; a.err = c->err_d;
     a.scan_v = c->launch.scan_cells;
+    a.spin_limit = c->spin_limit;
+    a.tx_extra = c->tx_extra;
     const bool use_tma = c->launch.variant == QS_VARIANT_TMA && update && !rec_kinds;
     const bool use_scan = c->launch.variant == QS_VARIANT_SCAN && update && !rec_kinds && c->prec == QS_FP64;
     if (c->launch.variant == QS_VARIANT_SCAN && !use_scan) {
@@ -831,6 +835,15 @@ qs_status qs_sync(qs_ctx *c) {
 }
 
 int64_t qs_launch_count(const qs_ctx *c) { return c ? c->n_launch : -1; }
+
+qs_status qs_debug_waits(qs_ctx *c, int64_t spin_limit, int unsatisfiable) {
+    if (!c || spin_limit < 1) return QS_ERR_ARG;
+    c->spin_limit = spin_limit;
+    c->tx_extra = unsatisfiable ? 16 : 0;
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+    c->graphs.clear();
+    return QS_OK;
+}
 
 const char *qs_last_error(const qs_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 

@@ -467,3 +467,27 @@ def test_scan_variant_slab2d_full_size(qs):
         s.close()
     print({"slab2d_fp64_ms": times})
     assert times["scan"] < times["line"]
+
+
+def test_bounded_wait_timeout_reported_and_recovered(qs):
+    """Failure detection without a fault: the TMA kernel's tile barriers are
+    made to expect more bytes than their copies deliver; every wait runs out
+    after a short bound, the kernel reports QS_ERR_TIMEOUT and returns, and
+    the context works again after the hook is cleared and the state reseeded."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=64, k_list=[0.5, 1.5, 3.0])
+    s = qs.Solver(p, prec="fp32")
+    s.set_launch(warps_per_cta=1, prefetch=8, persistent=0, ctas_per_sm=8, variant=1)
+    s.seed_noise(3, 1e-6)
+    s.debug_waits(spin_limit=2000, unsatisfiable=True)
+    s.step(1)
+    with pytest.raises(qs.QSError) as e:
+        s.sync()
+    assert e.value.status == qs.QS_ERR_TIMEOUT
+    s.debug_waits()
+    s.seed_noise(3, 1e-6)
+    s.step(10)
+    s.sync()
+    nb, th = s.state_arrays()
+    nb_o, th_o = _run_oracle(p, 10, seed=("noise", 3, 1e-6))
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL
+    s.close()
