@@ -74,7 +74,7 @@ class Launch(ctypes.Structure):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
-                          f"`python -m paper_2607_24234_b300.build` (nvcc, sm_103a)")
+                          f"`python paper_2607_24234_b300/build.py` (nvcc, sm_103a)")
     L = ctypes.CDLL(LIB_PATH)
     vp, i64 = ctypes.c_void_p, ctypes.c_int64
     L.qs_init.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(Params),
