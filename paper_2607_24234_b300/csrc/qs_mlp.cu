@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
 #include "qs.h"
 
 namespace mlp {
@@ -178,6 +180,161 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
             }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 GEMM for K-major operands (the fifth-generation tensor cores):
+// C[M][NT tile] = A[M][K] . B[N][K]^T, bf16 in, fp32 accumulated in tensor
+// memory.  One CTA (4 warps) owns 128 rows x NT columns: operands are staged
+// in shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes per core matrix; K-adjacent cores 128 B apart, 8-row groups
+// (K/8)*128 B apart), one thread issues K/16 tcgen05.mma (M = 128, N = NT,
+// K = 16), commits to an mbarrier (bounded wait), and each warp reads its
+// 32 accumulator lanes back with tcgen05.ld for the fused epilogue.
+// ---------------------------------------------------------------------------
+namespace tc {
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+}  // namespace tc
+
+template <int K, int NT>
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
+    extern __shared__ __align__(1024) unsigned char smtc[];
+    unsigned char *As = smtc, *Bs = smtc + 128 * K * 2;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
+    constexpr uint32_t SBO = (K / 8) * 128, LBO = 128;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&taddr_s)), "r"(NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // stage both operands with asynchronous 16-byte copies (all in flight at
+    // once; rows past M or N are zero-filled)
+#pragma unroll 4
+    for (int i = tid; i < 128 * (K / 8); i += 128) {
+        const int r = i / (K / 8), kc = i % (K / 8);
+        const bool in = m0 + r < g.M;
+        const __nv_bfloat16 *src = g.A + (long long)(in ? m0 + r : 0) * g.lda + kc * 8;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + kc * LBO + (r % 8) * 16)),
+                     "l"(src), "r"(in ? 16 : 0) : "memory");
+    }
+#pragma unroll 4
+    for (int i = tid; i < NT * (K / 8); i += 128) {
+        const int r = i / (K / 8), kc = i % (K / 8);
+        const bool in = n0 + r < g.N;
+        const __nv_bfloat16 *src = g.B + (long long)(in ? n0 + r : 0) * g.ldb + kc * 8;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + kc * LBO + (r % 8) * 16)),
+                     "l"(src), "r"(in ? 16 : 0) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    if (tid == 0) {
+        constexpr uint32_t id = tc::idesc_bf16(128, NT);
+#pragma unroll
+        for (int kk = 0; kk < K / 16; ++kk) {
+            const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
+            const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
+                     : "memory");
+    }
+    uint32_t ok = 0;
+    for (long long spin = 0; spin < (1LL << 24) && !ok; ++spin)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok) : "r"(tc::su32(&bar)) : "memory");
+    if (!ok && lane == 0) atomicOr(err, 2);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16) + c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+                "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+                  "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+                  "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                  "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // the host routes only N % 128 == 0 and ldc, ldh % 8 == 0 here, so
+            // every 32-column chunk is in range and vector stores are aligned
+            if (m < g.M) {
+                const int nb = n0 + c0;
+                const long long oc = (long long)m * g.ldc + nb;
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                if (g.epi == EPI_DGELU) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 z = *reinterpret_cast<const float4 *>(g.Z + oc + j);
+                        v[j] *= dgelu(z.x); v[j + 1] *= dgelu(z.y); v[j + 2] *= dgelu(z.z); v[j + 3] *= dgelu(z.w);
+                    }
+                } else if (g.epi != EPI_STORE) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] += g.bias[nb + j];
+                }
+                if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS || g.epi == EPI_STORE) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4 *>(g.C + oc + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+                if (g.epi == EPI_BIAS_GELU || g.epi == EPI_DGELU) {
+                    __nv_bfloat16 *h = g.H + (long long)m * g.ldh + nb;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 8) {
+                        __nv_bfloat162 q[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const float a0 = g.epi == EPI_BIAS_GELU ? gelu(v[j + 2 * t]) : v[j + 2 * t];
+                            const float a1 = g.epi == EPI_BIAS_GELU ? gelu(v[j + 2 * t + 1]) : v[j + 2 * t + 1];
+                            q[t] = __floats2bfloat162_rn(a0, a1);
+                        }
+                        *reinterpret_cast<uint4 *>(h + j) = *reinterpret_cast<const uint4 *>(q);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(NT));
+    }
+}
+
+// W [out][in] fp32 -> W^T [in][out] bf16 (K-major operand for dX = dz W)
+__global__ void k_transpose_bf16(const float *W, int out, int in, __nv_bfloat16 *WT) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)out * in) return;
+    const int o = (int)(i / in), c = (int)(i % in);
+    WT[(long long)c * out + o] = __float2bfloat16(W[i]);
+}
+
 // x (fp32, [n][n_in]) -> standardised bf16 [n][kin_pad] (zero padded)
 __global__ void k_standardise(const float *x, int n, int n_in, int kpad, const float *mean,
                               const float *inv_std, __nv_bfloat16 *out) {
@@ -331,6 +488,9 @@ struct qs_mlp {
     float *stats = nullptr;              // mean[32], inv_std[32]
     float ymean = 0.0f, ystd = 1.0f;
     float *loss = nullptr;
+    __nv_bfloat16 *PT = nullptr;         // [E][nparam]: W^T copies (bf16) for dX
+    int *errw = nullptr;                 // device error word (bounded waits)
+    bool use_tc = true;
     long long step = 0;
     std::string err;
 };
@@ -362,13 +522,35 @@ qs_status mdev(qs_mlp *m, size_t bytes, P **p) {
     return s;
 }
 
+bool gemm_tc(qs_mlp *m, const mlp::GemmArgs &g) {
+    if (!m->use_tc || g.N % 128 != 0 || !(g.K == 16 || g.K == 256) || (g.lda % 8) || (g.ldb % 8) ||
+        (g.ldc % 8) || (g.epi != mlp::EPI_STORE && g.epi != mlp::EPI_BIAS && g.ldh % 8))
+        return false;
+    const dim3 grid((g.M + 127) / 128, g.N / 128);
+    const size_t smem = (size_t)(128 + 128) * g.K * 2;
+    if (g.K == 16) mlp::k_gemm_tc<16, 128><<<grid, 128, smem, m->stream>>>(g, m->errw);
+    else mlp::k_gemm_tc<256, 128><<<grid, 128, smem, m->stream>>>(g, m->errw);
+    return true;
+}
+
 void gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g, int split = 1) {
+    if (TA == 0 && TB == 0 && split == 1 && gemm_tc(m, g)) return;
     dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM, split);
     if (split > 1) cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.ldc, m->stream);
     if (TA == 0 && TB == 0) mlp::k_gemm<0, 0><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 0 && TB == 1) mlp::k_gemm<0, 1><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 1 && TB == 0) mlp::k_gemm<1, 0><<<grid, 128, 0, m->stream>>>(g);
     else mlp::k_gemm<1, 1><<<grid, 128, 0, m->stream>>>(g);
+}
+
+// bf16 W^T of every layer of member e (the K-major B operand of dX)
+void refresh_wt(qs_mlp *m, int e) {
+    for (int l = 1; l <= m->depth; ++l) {
+        const long long nw = (long long)m->lin[l] * m->lout[l];
+        mlp::k_transpose_bf16<<<(unsigned)((nw + 255) / 256), 256, 0, m->stream>>>(
+            m->P + (long long)e * m->nparam + m->woff[l], m->lout[l], m->lin[l],
+            m->PT + (long long)e * m->nparam + m->woff[l]);
+    }
 }
 
 // forward of member e on n rows of X0 (already standardised); fills OUT[e]
@@ -423,14 +605,14 @@ void backward(qs_mlp *m, int e, int n) {
         // dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * gelu'(Z[l-1][b][i])
         mlp::GemmArgs gx{};
         gx.A = dz; gx.lda = out;                       // A(m=b, k=o), TA = 0
-        gx.B = Pbe + m->woff[l]; gx.ldb = in;          // B(n=i, k=o) = W[o*in + i], TB = 1
+        gx.B = m->PT + (long long)e * m->nparam + m->woff[l]; gx.ldb = out;   // B(n=i, k=o) = W^T[i*out + o]
         gx.M = n; gx.N = in; gx.K = out;
         gx.C = m->Z[l - 1]; gx.ldc = m->width;         // read as Z in the epilogue
         gx.Z = m->Z[l - 1];
         __nv_bfloat16 *dst = ping[l & 1];
         gx.H = dst; gx.ldh = m->width;
         gx.epi = mlp::EPI_DGELU;
-        gemm(m, 0, 1, gx);
+        gemm(m, 0, 0, gx);
         dz = dst;
     }
 }
@@ -471,7 +653,8 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * n_out, &m->DOUT)) ||
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG0)) ||
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG1)) ||
-        (s = mdev(m, sizeof(float) * 64, &m->stats)) || (s = mdev(m, sizeof(float) * 4, &m->loss))) {
+        (s = mdev(m, sizeof(float) * 64, &m->stats)) || (s = mdev(m, sizeof(float) * 4, &m->loss)) ||
+        (s = mdev(m, pb / 2, &m->PT)) || (s = mdev(m, sizeof(int) * 4, &m->errw))) {
         qs_mlp_free(m);
         return s;
     }
@@ -518,6 +701,12 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     }
     const long long tot = off * ensemble;
     mlp::k_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, m->stream>>>(m->P, tot, m->Pb);
+    cudaMemsetAsync(m->PT, 0, pb / 2, m->stream);
+    cudaMemsetAsync(m->errw, 0, sizeof(int) * 4, m->stream);
+    for (int e = 0; e < ensemble; ++e) refresh_wt(m, e);
+    cudaFuncSetAttribute(mlp::k_gemm_tc<256, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 256 * 2);
+    cudaFuncSetAttribute(mlp::k_gemm_tc<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 16 * 2);
+    if (const char *v = getenv("QS_MLP_NO_TCGEN05")) m->use_tc = v[0] == '0';
     if (cudaGetLastError() != cudaSuccess) { qs_mlp_free(m); return QS_ERR_CUDA; }
     *out = m;
     return QS_OK;
@@ -546,6 +735,7 @@ qs_status qs_mlp_params(qs_mlp *m, int member, float *host, int64_t n, int set) 
     if (set) {
         e = cudaMemcpyAsync(dst, host, n * sizeof(float), cudaMemcpyHostToDevice, m->stream);
         mlp::k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(dst, n, m->Pb + (long long)member * m->nparam);
+        refresh_wt(m, member);
     } else {
         e = cudaMemcpyAsync(host, dst, n * sizeof(float), cudaMemcpyDeviceToHost, m->stream);
     }
@@ -590,6 +780,7 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
             mlp::k_adam<<<(unsigned)((m->nparam + 255) / 256), 256, 0, m->stream>>>(
                 m->P + off, m->Mm + off, m->Vv + off, m->G + off, m->nparam, lr, b1, b2, 1e-8f, c1, c2,
                 m->Pb + off);
+            refresh_wt(m, e);
         }
     }
     if (!do_update) --m->step;
