@@ -174,6 +174,8 @@ qs_status qs_record(qs_ctx *ctx, int kinds, int stride, void *dev_out,
                     size_t out_bytes);
 
 enum { QS_DIAG_MAG = 1, QS_DIAG_NP = 2, QS_DIAG_MODEMAX = 4,
+       QS_DIAG_XIMAX = 8,  /* per xi cell: max over modes of ln|dn_b|, ln|dE|,
+                            * ln|dB| as [3][cells] (read-only pass only)     */
        QS_DIAG_STATE = 16, /* opaque checkpoint (state + exponents + step) */
        QS_DIAG_WAKE0 = 32  /* zeroth-order n_p response to the unperturbed
                             * beam charge: 2 doubles per cell per instance

@@ -26,7 +26,7 @@ FRONT = {"quiescent": 0, "equilibrium": 1, "held": 2}
 PROFILE = {"flattop": 0, "gaussian": 1, "ramp_flattop": 2, "user": 3}
 SEED_NOISE, SEED_IMPULSE, SEED_USER, SEED_STATE = range(4)
 REC_MAG, REC_NP, REC_MODEMAX = 1, 2, 4
-DIAG_STATE, DIAG_WAKE0 = 16, 32
+DIAG_XIMAX, DIAG_STATE, DIAG_WAKE0 = 8, 16, 32
 Q_N_MODES, Q_MODES_PADDED, Q_N_INST, Q_TOTAL_CELLS, Q_STEP, Q_STATE_BYTES, Q_SNAPSHOT_BYTES, \
     Q_CELL_OFFSET, Q_LAUNCH = range(9)
 
@@ -314,6 +314,8 @@ class Solver:
         """One read-only snapshot at the current step (host NumPy or device tensor)."""
         if kind == DIAG_WAKE0:
             n = self.cells * 2
+        elif kind == DIAG_XIMAX:
+            n = self.cells * 3
         else:
             n = self.snapshot_doubles(kind)
         if host:

@@ -768,6 +768,30 @@ __global__ void k_seed(const SeedArgs a) {
     if (sizeof(T) == 4) a.ex[(I.grp_off + g) * a.Mp + mode] = (E << 8);
 }
 
+// Per-xi maxima over the active modes of ln|dn_b|, ln|dE|, ln|dB| from a MAG
+// snapshot [5][cells][Mp]: one CTA per cell.  out [3][cells].
+static __global__ void k_ximax(const double *mag, long long cells, int Mp, int M, double *out) {
+    const long long cell = blockIdx.x;
+    __shared__ double red[3][256];
+    double m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY;
+    const long long plane = cells * Mp;
+    for (int mo = threadIdx.x; mo < M; mo += blockDim.x) {
+        const long long o = cell * Mp + mo;
+        m0 = fmax(m0, mag[o]);
+        m1 = fmax(m1, mag[o + plane]);
+        m2 = fmax(m2, mag[o + 2 * plane]);
+    }
+    red[0][threadIdx.x] = m0; red[1][threadIdx.x] = m1; red[2][threadIdx.x] = m2;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = fmax(red[k][threadIdx.x], red[k][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[k * cells + cell] = red[k][0];
+}
+
 // Zeroth-order wake per instance (Eq. 5 with the unperturbed beam charge).
 struct WakeArgs {
     const InstDev *inst;

@@ -709,6 +709,36 @@ qs_status qs_diag(qs_ctx *c, int kind, void *out, size_t out_bytes, int out_on_h
         CU(c, cudaStreamSynchronize(c->stream));   // hdr lives on this stack frame
         return QS_OK;
     }
+    if (kind == QS_DIAG_XIMAX) {
+        // field pass into a temporary MAG snapshot, then max over modes per cell
+        qs_status s0 = check_ready(c);
+        if (s0) return s0;
+        const size_t need_x = (size_t)c->cells_total * 3 * sizeof(double);
+        if (out_bytes < need_x) return fail(c, QS_ERR_ARG, "diag needs %zu bytes", need_x);
+        void *mag = nullptr, *res = nullptr;
+        if ((s0 = dalloc(c, (size_t)snapshot_doubles(c, QS_REC_MAG) * 8, &mag))) return s0;
+        if (out_on_host && (s0 = dalloc(c, need_x, &res))) return s0;
+        double *dres = out_on_host ? static_cast<double *>(res) : static_cast<double *>(out);
+        s0 = launch_sweep(c, c->step, 1, 0, QS_REC_MAG, static_cast<double *>(mag), c->step, 1, 1);
+        if (!s0) {
+            qsk::k_ximax<<<(unsigned)c->cells_total, 256, 0, c->stream>>>(static_cast<const double *>(mag), c->cells_total,
+                                                                          c->Mp, c->M, dres);
+            cudaError_t e = cudaGetLastError();
+            if (!e && out_on_host) e = cudaMemcpyAsync(out, dres, need_x, cudaMemcpyDeviceToHost, c->stream);
+            if (!e) e = cudaStreamSynchronize(c->stream);
+            if (e) s0 = fail(c, QS_ERR_CUDA, "ximax: %s", cudaGetErrorString(e));
+        }
+        for (void *p : {mag, res}) {
+            if (!p) continue;
+            for (size_t i = 0; i < c->bufs.size(); ++i)
+                if (c->bufs[i].p == p) {
+                    if (c->has_alloc) c->alloc.free(p, c->alloc.user); else cudaFree(p);
+                    c->bufs.erase(c->bufs.begin() + i);
+                    break;
+                }
+        }
+        return s0 ? s0 : (out_on_host ? qs_sync(c) : QS_OK);
+    }
     size_t need;
     double *dst = nullptr;
     void *tmp = nullptr;
@@ -764,7 +794,9 @@ qs_status qs_query(const qs_ctx *c, int what, int64_t arg, int64_t *value) {
     case QS_Q_TOTAL_CELLS: *value = c->cells_total; break;
     case QS_Q_STEP: *value = c->step; break;
     case QS_Q_STATE_BYTES: *value = (int64_t)(64 + c->state_bytes + c->th_bytes + c->ex_bytes); break;
-    case QS_Q_SNAPSHOT_BYTES: *value = snapshot_doubles(c, (int)arg) * 8; break;
+    case QS_Q_SNAPSHOT_BYTES:
+        *value = arg == QS_DIAG_XIMAX ? 3 * c->cells_total * 8 : snapshot_doubles(c, (int)arg) * 8;
+        break;
     case QS_Q_CELL_OFFSET:
         if (arg < 0 || arg >= c->n_inst) return QS_ERR_ARG;
         *value = c->inst[arg].cell_off;

@@ -491,3 +491,35 @@ def test_bounded_wait_timeout_reported_and_recovered(qs):
     nb_o, th_o = _run_oracle(p, 10, seed=("noise", 3, 1e-6))
     assert _log_err(nb, nb_o) <= FP32_LOG_TOL
     s.close()
+
+
+def test_per_xi_maxima_and_persistent_graph(qs):
+    """Per-xi maxima over modes against the oracle's fields, and CUDA-graph
+    stepping of a batched persistent launch against plain stepping."""
+    import torch
+    p = synth.scaled(synth.BEAM_3D, nkx=20, nky=20, kmax=5.0, n_xi=100, dxi=0.05, length=5.0)
+    s = qs.Solver(p, prec="fp64")
+    s.seed_noise(6, 1e-6)
+    s.step(30)
+    xm = s.diag(qs.DIAG_XIMAX).reshape(3, -1)
+    nb_o, th_o = oracle.seed_noise(p, 6, 1e-6)
+    oracle.sweep(p, nb_o, th_o, 0, 30)
+    f = oracle.fields(p, nb_o)["mag"]
+    ref = np.log(np.max(f[[0, 1, 2]], axis=1))          # [3][xi]
+    assert np.max(np.abs(xm - ref)) <= 1e-9
+    s.close()
+    insts = synth.batch_instances(5, param_seed=4, base=synth.scaled(synth.BATCH_BASE, nkx=8, nky=8), dxi=0.5)
+    st = torch.cuda.Stream()
+    outs = []
+    for graph in (False, True):
+        with torch.cuda.stream(st):
+            s = qs.Solver(insts, prec="fp32", stream=st)
+            s.set_launch(warps_per_cta=1, prefetch=8, persistent=1, ctas_per_sm=2, variant=1)
+            s.seed_noise(2, 1e-6)
+            for _ in range(3):
+                (s.step_graph if graph else s.step)(4)
+            s.sync()
+            outs.append(s.state_arrays())
+            s.close()
+    for i in range(5):
+        assert np.array_equal(outs[0][0][i], outs[1][0][i]) and np.array_equal(outs[0][1][i], outs[1][1][i])
