@@ -174,9 +174,9 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
 // K2 for N = 256: 16 spectral columns per CTA, one team per column
 __global__ void __launch_bounds__(256) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
                                                    float2 *__restrict__ T2, float ly, float lz) {
-    constexpr int N = 256, NH = 129, CBn = 16;
+    constexpr int N = 256, NH = 129, CBn = 16, LD = N + 1;   // padded column stride
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + 256, *A2 = A + CBn * N, *T = A2 + CBn * N;
+    float2 *tw = sm, *A = sm + 256, *A2 = A + CBn * LD, *T = A2 + CBn * LD;
     const long long slice = blockIdx.y;
     const int c0 = blockIdx.x * CBn;
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
@@ -184,10 +184,10 @@ __global__ void __launch_bounds__(256) k_colfft256(const float2 *__restrict__ S1
     const float2 *src = S1 + slice * (long long)N * NH;
     for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
         const int y = i >> 4, c = i & 15;
-        A[c * N + y] = (c0 + c < NH) ? __ldcg(src + (long long)y * NH + c0 + c) : make_float2(0.0f, 0.0f);
+        A[c * LD + y] = (c0 + c < NH) ? __ldcg(src + (long long)y * NH + c0 + c) : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    float2 *col = A + team * N, *col2 = A2 + team * N;
+    float2 *col = A + team * LD, *col2 = A2 + team * LD;
     fft256_team<false>(col, T + team * 272, tw, t);
     const int kzi = c0 + team;
     const float inv = 1.0f / (256.0f * 256.0f);
@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(256) k_colfft256(const float2 *__restrict__ S1
     for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
         const int y = i >> 4, c = i & 15;
         if (c0 + c < NH) {
-            __stcg(d1 + (long long)y * NH + c0 + c, A[c * N + y]);
-            __stcg(d2 + (long long)y * NH + c0 + c, A2[c * N + y]);
+            __stcg(d1 + (long long)y * NH + c0 + c, A[c * LD + y]);
+            __stcg(d2 + (long long)y * NH + c0 + c, A2[c * LD + y]);
         }
     }
 }
@@ -402,6 +402,18 @@ __global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict
     const int r0 = blockIdx.x * RBn;
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
     make_tw256(tw);
+    // issue the push operands' loads first: they land while the transforms run
+    const long long base = slice * (long long)N * N;
+    constexpr int PER = RBn * N / 256;          // 16 elements per thread
+    float pnp[PER], pnb[PER], pg[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * 256;
+        const long long o = base + (long long)(r0 + (i >> 8)) * N + (i & 255);
+        pnp[u] = __ldcg(a.np + o);
+        pnb[u] = __ldcg(a.nb + o);
+        pg[u] = __ldcg(a.G + o);
+    }
     const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
     const float tz = 6.283185307179586f / a.lz;
     for (int i = threadIdx.x; i < RBn * N; i += blockDim.x) {
@@ -425,9 +437,10 @@ __global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict
     fft256_team<true>(A + team * N, T + team * 272, tw, t);
     if (team < 8) fft256_team<true>(A + (RBn + team) * N, T + team * 272, tw, t);
     __syncthreads();
-    const long long base = slice * (long long)N * N;
     bool bad = false;
-    for (int i = threadIdx.x; i < RBn * N; i += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * 256;
         const int r = i >> 8, z = i & 255;
         const int y = r0 + r;
         const float2 Z1 = A[r * N + z];
@@ -435,9 +448,9 @@ __global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict
         const float psi = Z1.x, dz = Z1.y, dy = (r & 1) ? Z2.y : Z2.x;
         const long long o = base + (long long)y * N + z;
         const int q = y * N + z;
-        const float S = a.coef * (a.nb0[q] * (psi - __ldcg(a.np + o)) + a.gy[q] * dy + a.gz[q] * dz);
-        const float g = fmaf(a.h, S, __ldcg(a.G + o));
-        const float n = fmaf(a.dt, g, __ldcg(a.nb + o));
+        const float S = a.coef * (a.nb0[q] * (psi - pnp[u]) + a.gy[q] * dy + a.gz[q] * dz);
+        const float g = fmaf(a.h, S, pg[u]);
+        const float n = fmaf(a.dt, g, pnb[u]);
         __stcg(a.G + o, g);
         __stcg(a.nb + o, n);
         bad |= !(fabsf(n) <= 3.0e38f) || !(fabsf(g) <= 3.0e38f);
@@ -508,7 +521,7 @@ template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
 constexpr size_t SMEM_K1_256 = sizeof(float2) * (256 + 16 * 256 + 16 * 272);
-constexpr size_t SMEM_K2_256 = sizeof(float2) * (256 + 2 * 16 * 256 + 16 * 272);
+constexpr size_t SMEM_K2_256 = sizeof(float2) * (256 + 2 * 16 * 257 + 16 * 272);
 constexpr size_t SMEM_K3_256 = sizeof(float2) * (256 + 24 * 256 + 16 * 272);
 
 template <int N>
