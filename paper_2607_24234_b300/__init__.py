@@ -350,11 +350,15 @@ class Solver:
         sl = np.take(sl, np.arange(self.n_modes), axis=-1)
         return np.swapaxes(sl, -1, -2)
 
-    def state_arrays(self):
+    def state_arrays(self, modes=None):
         """Decode a checkpoint into complex128 n_b and Theta arrays, each
         [inst][mode][species][xi] (the library stores FP32 mantissas m with a
-        power-of-two scale W per 32-cell group: value = m * 2**W)."""
+        power-of-two scale W per 32-cell group: value = m * 2**W).
+        `modes`: optional index array of active modes to decode (others are
+        skipped, which keeps host memory small for large contexts)."""
         raw = self.checkpoint()
+        if modes is not None:
+            return self._decode_modes(raw, np.asarray(modes))
         hdr = raw[:64].view(np.int64)
         ns, Mp, cells = int(hdr[2]), int(hdr[3]), int(hdr[4])
         body = raw[64:]
@@ -384,6 +388,32 @@ class Solver:
                 c0, n = self.cell_off[i], self._nxi(i)
                 x = arr[c0:c0 + n, :, :self.n_modes]          # [xi][sp][mode]
                 per.append(np.transpose(x, (2, 1, 0)))         # [mode][sp][xi]
+            outs.append(per if self.n_inst > 1 else per[0])
+        return outs[0], outs[1]
+
+    def _decode_modes(self, raw, sel):
+        hdr = raw[:64].view(np.int64)
+        ns, Mp, cells = int(hdr[2]), int(hdr[3]), int(hdr[4])
+        body = raw[64:]
+        if self.prec == "fp32":
+            st = body[:cells * ns * Mp * 16].view(np.float32).reshape(cells, ns, Mp, 4)[:, :, sel, :]
+            st = st.astype(np.float64)
+            W = (body[cells * ns * Mp * 16:].view(np.int32).reshape(-1, Mp)[:, sel] >> 8).astype(np.int64)
+            rows = []
+            for i in range(self.n_inst):
+                g0 = sum((self._nxi(k) + 31) // 32 for k in range(i))
+                rows.append(W[g0 + np.arange(self._nxi(i)) // 32])
+            st = np.ldexp(st, np.concatenate(rows, axis=0)[:, None, :, None])
+            nb, th = st[..., 0] + 1j * st[..., 1], st[..., 2] + 1j * st[..., 3]
+        else:
+            half = cells * ns * Mp * 16
+            a = body[:half].view(np.float64).reshape(cells, ns, Mp, 2)[:, :, sel, :]
+            b = body[half:2 * half].view(np.float64).reshape(cells, ns, Mp, 2)[:, :, sel, :]
+            nb, th = a[..., 0] + 1j * a[..., 1], b[..., 0] + 1j * b[..., 1]
+        outs = []
+        for arr in (nb, th):
+            per = [np.transpose(arr[self.cell_off[i]:self.cell_off[i] + self._nxi(i)], (2, 1, 0))
+                   for i in range(self.n_inst)]
             outs.append(per if self.n_inst > 1 else per[0])
         return outs[0], outs[1]
 

@@ -523,3 +523,35 @@ def test_per_xi_maxima_and_persistent_graph(qs):
             s.close()
     for i in range(5):
         assert np.array_equal(outs[0][0][i], outs[1][0][i]) and np.array_equal(outs[0][1][i], outs[1][1][i])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_beam3d_full_size_sampled(qs, prec):
+    """The benchmark workload at full size in the launch shape bench.py uses
+    (tuned): 51,468 modes x 2048 cells x 2000 steps.  Sampled mode lines
+    against the oracle; every mode through the k/-k pairing of the per-mode
+    maxima (bitwise equal)."""
+    import torch
+    p = synth.BEAM_3D
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = qs.Solver(p, prec=prec, stream=st)
+        s.seed_noise(0, 1e-6)
+        s.tune(reps=1)
+        s.step(p["n_steps"])
+        s.sync()
+        mm = s.split_snapshot(s.diag(qs.REC_MODEMAX), qs.REC_MODEMAX)["modemax"][:, 0, :s.n_modes]
+        md = oracle.modes(p)
+        sel = np.sort(np.random.default_rng(11).choice(s.n_modes, 12, replace=False))
+        nb, th = s.state_arrays(modes=sel)
+        s.close()
+    pos = {int(i): j for j, i in enumerate(md["mode_id"])}
+    partner = np.array([pos[int(q)] for q in md["partner_id"]])
+    assert np.array_equal(mm, mm[:, partner])
+    nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, mode_sel=sel)
+    oracle.sweep(p, nb_o, th_o, 0, p["n_steps"], k2=md["k2"][sel])
+    if prec == "fp64":
+        assert _line_rel(nb, nb_o) <= FP64_TOL and _line_rel(th, th_o) <= FP64_TOL
+    else:
+        assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
