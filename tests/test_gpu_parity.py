@@ -90,6 +90,8 @@ SMALL = [
      "gaussian", "noise", 30),
     (100, [0.7, 1.9], [(-1.0, 1.0, 0.03), (1.0, 1836.0, 0.05)], "full", "held", "ramp_flattop", "user", 21),
     (257, list(np.linspace(0.5, 6, 40)), [(-1.0, 1.0, 0.1)], "full", "quiescent", "flattop", "noise", 60),
+    # k = 0: the two-stream instability (only the gamma^-3 coupling acts)
+    (90, [0.0, 0.0, 1e-3], [(-1.0, 1.0, 0.2)], "full", "quiescent", "flattop", "impulse", 50),
 ]
 
 

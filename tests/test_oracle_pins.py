@@ -398,3 +398,27 @@ def test_field_identities():
     Ep = (kabs * kap)[:, None] * np.abs(npm - rho)
     assert np.allclose(rec["mag"][1] ** 2, rec["mag"][4] ** 2 + Ep ** 2, rtol=1e-12)
     assert np.allclose(rec["mag"][2], (kabs * kap)[:, None] * np.abs(rho), rtol=1e-14)
+
+
+def test_tsi_k0_exact_series_and_exponent():
+    """k = 0 (the two-stream instability of a wide beam, Sec. IV.A): only the
+    gamma^-3 coupling drives the mode.  The oracle converges at second order
+    to the exact k = 0 series (Gamma^2 = 0, eps = sum w^2 / gamma^2), and
+    the series grows with the exponent of Eq. (37),
+    (3 / 2^(2/3)) Gamma_TSI xi^(1/3) tau^(2/3), in the SVEA regime
+    xi >> Gamma_TSI tau (within 8 % at C >= 15)."""
+    gam, n0 = 5.0, 0.2
+    w2 = n0 / gam
+    eps = w2 / gam ** 2
+    xs = [2.0, 4.0, 6.0]
+    ex = np.array([cf.greens_full(60.0, x, 0.0, eps) for x in xs])
+    errs = []
+    for D in (0.1, 0.05):
+        v = _impulse_np(D, D, 60.0, 8.0, [(-1.0, 1.0, n0)], gam, 0.0, "full")
+        errs.append(np.max(np.abs(v[[int(round(x / D)) for x in xs]].real / ex - 1)))
+    assert errs[1] < 5e-4 and 3.5 < errs[0] / errs[1] < 4.5
+    G = cf.gamma_tsi(w2, gam)
+    xi, taus = 150.0, np.array([60.0, 80.0, 100.0, 120.0])
+    env = [max(abs(cf.greens_full(t, x, 0.0, eps)) for x in xi + np.linspace(0, 2 * np.pi, 13)) for t in taus]
+    slope = np.polyfit(taus ** (2 / 3), np.log(env), 1)[0]
+    assert slope / ((3 / 2 ** (2 / 3)) * G * xi ** (1 / 3)) == pytest.approx(1.0, rel=0.08)
