@@ -209,14 +209,24 @@ qs_status qs_modes(const qs_ctx *ctx, double *kx, double *ky);
 enum { QS_VARIANT_REGISTERS = 0,  /* thread per line, register prefetch       */
        QS_VARIANT_TMA = 1,        /* thread per line, warp-wide TMA tiles of
                                    * (cells x 32 modes) through shared memory */
-       QS_VARIANT_SCAN = 2 };     /* FP64 only, for few lines: the lanes of a
+       QS_VARIANT_SCAN = 2,       /* FP64 only, for few lines: the lanes of a
                                    * warp split xi into sub-chunks joined by a
                                    * shuffle scan of the cell propagators      */
+       QS_VARIANT_RESIDENT = 3 }; /* FP32 only: whole warps hold a line in
+                                   * registers for every step of a call (HBM
+                                   * is read once and written once per call);
+                                   * xi is joined by a block scan of the cell
+                                   * propagators.  Steps that record, and field
+                                   * passes, run the register kernel          */
 typedef struct {
-    int warps_per_cta;   /* REGISTERS: 1, 2, 4 or 8 (TMA: always 1)         */
+    int warps_per_cta;   /* REGISTERS: 1, 2, 4 or 8 (TMA: always 1);
+                          * RESIDENT: 1, 2, 4, 8 or 16 (CTA size; a line
+                          * takes ceil(ceil(n_xi / cells) / 32) warps and
+                          * must fit in one CTA)                            */
     int prefetch;        /* REGISTERS: cells per register batch (FP32 4|8,
                           * FP64 2|4); TMA: cells per tile (FP32 8|16,
-                          * FP64 4|8)                                       */
+                          * FP64 4|8); RESIDENT: cells per thread (8|16 for
+                          * one species, 8 for two)                         */
     int persistent;      /* 1: LPT-ordered work list pulled by atomic ticket */
     int ctas_per_sm;     /* persistent grid size = ctas_per_sm * SM count    */
     int variant;         /* QS_VARIANT_*                                    */

@@ -20,6 +20,7 @@
 
 #include "qs.h"
 #include "qs_kernels.cuh"
+#include "qs_resident.cuh"
 
 using qsk::InstDev;
 using qsk::SweepArgs;
@@ -55,6 +56,9 @@ struct qs_ctx {
     InstDev *inst_d = nullptr;
     int2 *items_d = nullptr;
     int n_items = 0;
+    int2 *res_items_d = nullptr;    // resident variant: one item per CTA's lines
+    int n_res_items = 0;
+    long long res_key = -1;
     double *kap_d = nullptr, *kapk2_d = nullptr, *kabs_d = nullptr, *held_d = nullptr;
     void *w_d = nullptr;
     double *shape_d = nullptr, *dens_d = nullptr;
@@ -218,7 +222,46 @@ bool same_kset(const qs_params &a, const qs_params &b) {
     return a.nkx == b.nkx && a.nky == b.nky && a.kmax == b.kmax && a.disc_mask == b.disc_mask;
 }
 
+int max_nxi(const qs_ctx *c) {
+    int mx = 0;
+    for (const auto &I : c->inst) mx = std::max(mx, I.n_xi);
+    return mx;
+}
+
+// threads holding one line in the resident variant (whole warps)
+int res_threads_per_line(int n_xi, int V) { return ((n_xi + V - 1) / V + 31) & ~31; }
+
+// Resident variant: an item is (instance, first mode) for the T / Tl
+// consecutive lines one CTA holds; instances longest first when persistent.
+qs_status build_res_items(qs_ctx *c) {
+    const int V = c->launch.prefetch, T = 32 * c->launch.warps_per_cta, P = c->launch.persistent;
+    const long long key = ((long long)V << 32) | ((long long)T << 1) | P;
+    if (c->res_key == key && c->res_items_d) return QS_OK;
+    std::vector<int> order(c->n_inst);
+    for (int i = 0; i < c->n_inst; ++i) order[i] = i;
+    if (P)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return c->inst[a].n_xi > c->inst[b].n_xi; });
+    std::vector<int2> items;
+    for (int i : order) {
+        const int L = T / res_threads_per_line(c->inst[i].n_xi, V);
+        if (L < 1) return fail(c, QS_ERR_ARG, "resident: a line of instance %d needs more than %d threads", i, T);
+        for (int m = 0; m < c->M; m += L) items.push_back(make_int2(i, m));
+    }
+    if (!c->res_items_d) {
+        qs_status s = dalloc_t(c, (size_t)c->n_inst * c->M * sizeof(int2), &c->res_items_d);
+        if (s) return s;
+    }
+    qs_status s = upload(c, c->res_items_d, items.data(), items.size() * sizeof(int2));
+    if (s) return s;
+    CU(c, cudaStreamSynchronize(c->stream));   // host vector dies at return
+    c->n_res_items = (int)items.size();
+    c->res_key = key;
+    return QS_OK;
+}
+
 qs_status build_items(qs_ctx *c) {
+    if (c->launch.variant == QS_VARIANT_RESIDENT) return build_res_items(c);
     // modes per work item: 32 x warps (thread per line), 32 (TMA), 32/S (scan)
     const int wpc = c->launch.variant == QS_VARIANT_TMA ? 1
                   : c->launch.variant == QS_VARIANT_SCAN ? -c->launch.prefetch
@@ -335,10 +378,8 @@ cudaError_t scan_dispatch(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads,
 // One launch of the sweep kernel for n_steps steps starting at global step
 // step0.  update = 0 runs the field pass only.  rec: record target (may be
 // null).
-qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
-                       double *rec, long long rec_g0, int rec_stride, long long rec_max_snap) {
-    qs_status s = build_items(c);
-    if (s) return s;
+SweepArgs sweep_args(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
+                     double *rec, long long rec_g0, int rec_stride, long long rec_max_snap) {
     SweepArgs a{};
     a.st = c->st; a.th = c->th; a.ex = c->ex;
     a.inst = c->inst_d; a.items = c->items_d; a.n_items = c->n_items;
@@ -361,6 +402,76 @@ qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int 
     a.scan_v = c->launch.scan_cells;
     a.spin_limit = c->spin_limit;
     a.tx_extra = c->tx_extra;
+    return a;
+}
+
+template <int NS, int V>
+cudaError_t launch_res_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) {
+    qsk::k_sweep_res<NS, V><<<grid, threads, (size_t)V * NS * threads * sizeof(float), c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
+                       double *rec, long long rec_g0, int rec_stride, long long rec_max_snap);
+
+// Resident variant: updating steps without records run on chip; a step that
+// records, and every field pass, runs the register kernel (same per-cell
+// arithmetic) on its own work list.
+qs_status launch_resident(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
+                          double *rec, long long rec_g0, int rec_stride, long long rec_max_snap) {
+    auto fallback = [&](long long s0, int n, int upd) {
+        const qs_launch keep = c->launch;
+        c->launch = qs_launch{1, 8, 0, 8, QS_VARIANT_REGISTERS, 8};
+        qs_status r = launch_sweep(c, s0, n, upd, rec_kinds, rec, rec_g0, rec_stride, rec_max_snap);
+        c->launch = keep;
+        return r;
+    };
+    if (!update) return fallback(step0, n_steps, 0);
+    const bool recording = rec && rec_kinds;
+    const long long end = step0 + n_steps;
+    long long cur = step0;
+    while (cur < end) {
+        long long r = end;   // next step that records
+        if (recording) {
+            const long long d = cur - rec_g0;
+            const long long cand = d <= 0 ? rec_g0 : rec_g0 + ((d + rec_stride - 1) / rec_stride) * rec_stride;
+            if (cand < end && (cand - rec_g0) / rec_stride < rec_max_snap) r = cand;
+        }
+        if (r > cur) {
+            qs_status s = build_res_items(c);
+            if (s) return s;
+            SweepArgs a = sweep_args(c, cur, (int)(r - cur), 1, 0, nullptr, 0, 1, 0);
+            a.items = c->res_items_d;
+            a.n_items = c->n_res_items;
+            const int T = 32 * c->launch.warps_per_cta;
+            dim3 grid(c->n_res_items);
+            if (a.persistent) {
+                CU(c, cudaMemsetAsync(c->ticket_d, 0, sizeof(int), c->stream));
+                const long long g = (long long)c->launch.ctas_per_sm * c->n_sm;
+                grid = dim3((unsigned)std::max<long long>(1, std::min<long long>(g, c->n_res_items)));
+            }
+            const int V = c->launch.prefetch;
+            cudaError_t e = c->NS == 1 ? (V >= 16 ? launch_res_t<1, 16>(c, a, grid, T) : launch_res_t<1, 8>(c, a, grid, T))
+                                       : launch_res_t<2, 8>(c, a, grid, T);
+            if (e != cudaSuccess) return fail(c, QS_ERR_CUDA, "resident sweep launch: %s", cudaGetErrorString(e));
+            ++c->n_launch;
+        }
+        if (r < end) {
+            qs_status s = fallback(r, 1, 1);
+            if (s) return s;
+        }
+        cur = r + 1;
+    }
+    return QS_OK;
+}
+
+qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
+                       double *rec, long long rec_g0, int rec_stride, long long rec_max_snap) {
+    if (c->launch.variant == QS_VARIANT_RESIDENT)
+        return launch_resident(c, step0, n_steps, update, rec_kinds, rec, rec_g0, rec_stride, rec_max_snap);
+    qs_status s = build_items(c);
+    if (s) return s;
+    SweepArgs a = sweep_args(c, step0, n_steps, update, rec_kinds, rec, rec_g0, rec_stride, rec_max_snap);
     const bool use_tma = c->launch.variant == QS_VARIANT_TMA && update && !rec_kinds;
     const bool use_scan = c->launch.variant == QS_VARIANT_SCAN && update && !rec_kinds && c->prec == QS_FP64;
     if (c->launch.variant == QS_VARIANT_SCAN && !use_scan) {
@@ -820,7 +931,22 @@ qs_status qs_modes(const qs_ctx *c, double *kx, double *ky) {
 qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
     if (!c || !l) return QS_ERR_ARG;
     const int w = l->warps_per_cta;
-    if (l->variant < QS_VARIANT_REGISTERS || l->variant > QS_VARIANT_SCAN) return fail(c, QS_ERR_ARG, "variant");
+    if (l->variant < QS_VARIANT_REGISTERS || l->variant > QS_VARIANT_RESIDENT) return fail(c, QS_ERR_ARG, "variant");
+    if (l->variant == QS_VARIANT_RESIDENT) {
+        if (c->prec != QS_FP32_RENORM) return fail(c, QS_ERR_UNSUPPORTED, "the resident variant is FP32 only");
+        const int V = l->prefetch;
+        if (!(V == 8 || (V == 16 && c->NS == 1)))
+            return fail(c, QS_ERR_ARG, "resident: cells per thread must be 8 or 16 (one species), 8 (two)");
+        if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16)) return fail(c, QS_ERR_ARG, "resident: warps_per_cta");
+        if (res_threads_per_line(max_nxi(c), V) > 32 * w)
+            return fail(c, QS_ERR_ARG, "resident: a line of %d cells needs %d threads, the CTA has %d", max_nxi(c),
+                        res_threads_per_line(max_nxi(c), V), 32 * w);
+        if (l->persistent && (l->ctas_per_sm < 1 || l->ctas_per_sm > 32)) return fail(c, QS_ERR_ARG, "ctas_per_sm");
+        c->launch = *l;
+        for (auto &g : c->graphs) cudaGraphExecDestroy(g.second);
+        c->graphs.clear();
+        return QS_OK;
+    }
     if (l->variant == QS_VARIANT_SCAN) {
         if (c->prec != QS_FP64) return fail(c, QS_ERR_UNSUPPORTED, "the scan variant is FP64 only");
         const int S = l->prefetch;

@@ -1,0 +1,170 @@
+"""GPU parity of the resident (on-chip) FP32 sweep against the FP64 oracle.
+
+The resident variant keeps every line in registers for all steps of a call
+and joins xi with a block scan of the cell propagators, so its rounding
+differs from the streaming kernels: it is held to the FP32 tolerance against
+the oracle, and bit for bit only where the arithmetic is the same by
+construction (graph replay, chunked calls, k/-k pairs).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from test_gpu_parity import FP32_LOG_TOL, SMALL, _log_err, _run_gpu, _run_oracle, _small_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2607_24234_b300 as m
+    return m
+
+
+def _res(V=8, w=4, pers=0, cps=2):
+    return dict(warps_per_cta=w, prefetch=V, persistent=pers, ctas_per_sm=cps, variant=3)
+
+
+def _fits(n_xi, V, w):
+    return ((-(-n_xi // V) + 31) // 32) * 32 <= 32 * w
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"nxi{c[0]}-m{len(c[1])}-s{len(c[2])}-{c[3]}-{c[4]}-{c[5]}-{c[6]}")
+@pytest.mark.parametrize("V", [8, 16])
+def test_small_cases_resident(qs, case, V):
+    p, held, user, sd, steps = _small_problem(case)
+    if V == 16 and len(p["species"]) == 2:
+        pytest.skip("16 cells per thread is for one species")
+    w = next(w for w in (1, 2, 4, 8, 16) if _fits(p["n_xi"], V, w))
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=sd, held=held, user=user, launch=_res(V, max(w, 2)))
+    nb_o, th_o = _run_oracle(p, steps, seed=sd, held=held, user=user)
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL
+    assert _log_err(th, th_o) <= FP32_LOG_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("n_xi,V,w,pers", [
+    (700, 8, 8, 0),      # 88 -> 96 threads per line: 2 lines per 256-thread CTA, 64 idle threads
+    (700, 8, 8, 1),
+    (1000, 16, 2, 1),    # 63 -> 64 threads, one line per CTA
+    (33, 16, 4, 0),      # 3 -> 32 threads: 4 lines per CTA, most threads without cells
+    (2048, 16, 4, 1),    # the benchmark's line length
+])
+def test_ragged_packing(qs, n_xi, V, w, pers):
+    """Lines per CTA, idle threads and a mode count that is not a multiple
+    of the lines per CTA."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=n_xi, dxi=0.05, length=n_xi * 0.05, k_list=list(np.linspace(0.3, 5.0, 37)),
+                     species=[(-1.0, 1.0, 0.05)], gamma_b=20.0, dt=1.5)
+    steps = 40
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=("noise", 5, 1e-6), launch=_res(V, w, pers))
+    nb_o, th_o = _run_oracle(p, steps, seed=("noise", 5, 1e-6))
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    s.close()
+
+
+def test_batched_instances_resident(qs):
+    """Instances of different length, density and gamma in one persistent
+    launch (LPT order); each against its own oracle run."""
+    insts = synth.batch_instances(6, param_seed=4, base=synth.scaled(synth.BATCH_BASE, nkx=8, nky=8), dxi=0.25)
+    s = qs.Solver(insts, prec="fp32")
+    mx = max(p["n_xi"] for p in insts)
+    w = next(w for w in (1, 2, 4, 8, 16) if _fits(mx, 8, w))
+    s.set_launch(**_res(8, w, 1, 2))
+    s.seed_noise(0, 1e-6)
+    s.step(30)
+    s.sync()
+    nb, th = s.state_arrays()
+    for i, p in enumerate(insts):
+        nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, inst=i)
+        oracle.sweep(p, nb_o, th_o, 0, 30)
+        assert _log_err(nb[i], nb_o) <= FP32_LOG_TOL, i
+        assert _log_err(th[i], th_o) <= FP32_LOG_TOL, i
+    s.close()
+
+
+def test_records_split_the_call(qs):
+    """A call that records every 7 steps: the recording steps run the
+    register kernel, the others stay on chip; snapshots and final state
+    against the oracle."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=300, dxi=0.05, length=15.0, k_list=[0.5, 1.5, 3.0, 6.0],
+                     species=[(-1.0, 1.0, 0.05)], gamma_b=20.0)
+    steps, stride = 50, 7
+    s = qs.Solver(p, prec="fp32")
+    s.set_launch(**_res(16, 2))
+    s.seed_noise(6, 1e-6)
+    n_snap = (steps - 1) // stride + 1
+    buf = s.record(qs.REC_MAG | qs.REC_NP, stride, n_snap)
+    s.step(steps)
+    s.sync()
+    rec = buf.cpu().numpy().reshape(n_snap, -1)
+    nb, th = s.state_arrays()
+    nb_o, th_o = oracle.seed_noise(p, 6, 1e-6)
+    ro = oracle.sweep(p, nb_o, th_o, 0, steps, rec_stride=stride)
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    for i in range(n_snap):
+        sn = s.split_snapshot(rec[i], qs.REC_MAG | qs.REC_NP)
+        mag = s.per_instance(sn["mag"], 0)
+        for k in range(5):
+            ref = ro["mag"][i, k]
+            m = ref >= 1e-3 * ref.max(axis=1, keepdims=True)
+            assert np.max(np.abs(mag[k][m] - np.log(ref[m]))) <= FP32_LOG_TOL, (i, k)
+        assert _log_err(s.per_instance(sn["np"], 0), ro["np"][i]) <= FP32_LOG_TOL
+    s.close()
+
+
+def test_extreme_growth_resident(qs):
+    """Growth to ~e^150, past the FP32 range: per-thread exponents."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=400, dxi=0.025, length=10.0, species=[(-1.0, 1.0, 0.1)],
+                     gamma_b=10.0, k_list=[1.0, 3.0, 6.0, 9.0], dt=2.0)
+    steps = 2000
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=("noise", 4, 1e-6), launch=_res(8, 2))
+    nb_o, th_o = _run_oracle(p, steps, seed=("noise", 4, 1e-6))
+    assert np.max(np.abs(nb_o)) > 1e40
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    s.close()
+
+
+def test_resident_bitwise_properties(qs):
+    """Chunked calls (exponents are powers of two, so re-entering a line at
+    another scale changes no bits), graph replay, and k/-k conjugate pairs."""
+    import torch
+    p = synth.scaled(synth.BEAM_3D, nkx=24, nky=24, kmax=5.0, n_xi=150, dxi=0.04, length=6.0)
+    L = _res(8, 4)
+    _, nb, th = _run_gpu(qs, p, "fp32", 13, seed=("noise", 2, 1e-6), launch=L)
+    _, nb2, th2 = _run_gpu(qs, p, "fp32", 13, seed=("noise", 2, 1e-6), launch=L, chunks=[6, 1, 6])
+    assert np.array_equal(nb, nb2) and np.array_equal(th, th2)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = qs.Solver(p, prec="fp32", stream=st)
+        s.set_launch(**L)
+        s.seed_noise(2, 1e-6)
+        for n in (5, 4, 4):
+            s.step_graph(n)
+        s.sync()
+        nb3, th3 = s.state_arrays()
+        s.close()
+    assert np.array_equal(nb, nb3) and np.array_equal(th, th3)
+    md = oracle.modes(p)
+    pos = {int(i): j for j, i in enumerate(md["mode_id"])}
+    for j, pi in enumerate(md["partner_id"]):
+        jj = pos[int(pi)]
+        assert np.array_equal(nb[j], np.conj(nb[jj])) and np.array_equal(th[j], np.conj(th[jj]))
+    nb_o, th_o = _run_oracle(p, 13, seed=("noise", 2, 1e-6))
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+
+
+def test_launch_validation(qs):
+    p = synth.scaled(synth.SLAB_2D, n_xi=2048, dxi=0.05, length=102.4, k_list=[1.0, 2.0])
+    s = qs.Solver(p, prec="fp32")
+    with pytest.raises(qs.QSError):
+        s.set_launch(**_res(8, 4))      # 256 threads per line, CTA of 128
+    s.set_launch(**_res(16, 4))
+    s.close()
+    s = qs.Solver(p, prec="fp64")
+    with pytest.raises(qs.QSError):
+        s.set_launch(**_res(16, 4))     # FP32 only
+    s.close()
