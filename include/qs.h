@@ -225,8 +225,9 @@ typedef struct {
                           * must fit in one CTA)                            */
     int prefetch;        /* REGISTERS: cells per register batch (FP32 4|8,
                           * FP64 2|4); TMA: cells per tile (FP32 8|16,
-                          * FP64 4|8); RESIDENT: cells per thread (8|16 for
-                          * one species, 8 for two)                         */
+                          * FP64 4|8); RESIDENT: cells per thread, 8|16 with
+                          * any CTA size, 32 (one species) with 2|4|8 warps,
+                          * 16 (two species) with 4|8|16 warps               */
     int persistent;      /* 1: LPT-ordered work list pulled by atomic ticket */
     int ctas_per_sm;     /* persistent grid size = ctas_per_sm * SM count    */
     int variant;         /* QS_VARIANT_*                                    */

@@ -29,7 +29,6 @@
 // On the way out the threads sharing a 32-cell group agree on one exponent
 // and write the usual (mantissa, exponent word) layout.
 #pragma once
-#include <type_traits>
 
 namespace qsk {
 
@@ -37,6 +36,7 @@ constexpr int RES_MAX_WARPS = 16;   // T <= 512
 constexpr int RES_SPAN = 96;
 constexpr int RES_HYST = 16;
 constexpr int RES_NONE = -(1 << 20);   // exponent of a thread that holds no value yet
+constexpr int RES_WSTRIDE = 512;       // shared-memory row of the cell weights (max threads)
 
 struct RotF { float c, s; };
 __device__ __forceinline__ RotF rotf(double ang) {
@@ -57,17 +57,30 @@ __device__ __forceinline__ int clamp_shift(int s) { return s < -126 ? -126 : (s 
 // 2^e for e in [-126, 127]; 0 below (branch free)
 __device__ __forceinline__ float p2(int e) { return __int_as_float((max(-127, min(e, 127)) + 127) << 23); }
 
-template <int NS, int V>
-__global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
+// TT > 0 keeps Theta in shared memory (float2 rows [v * NS + sp][thread],
+// read and written once per cell in pass 2, next to float rows of the
+// weights dt n_b0) so that 32 cells of one species, or 16 of two, fit the register
+// budget; the CTA then has exactly TT threads (compile-time row stride).
+// TT = 0 keeps Theta in registers and only the weights in shared memory.
+template <int NS, int V, int TT>
+__global__ void __launch_bounds__(TT > 0 ? TT : 512, 512 / (TT > 0 ? TT : 512)) k_sweep_res(const SweepArgs a) {
+    constexpr bool THS = TT > 0;
     static_assert(GRP % V == 0, "a thread's cells lie in one exponent group");
     constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ float sW[];             // dt n_bs0 per cell: [v * NS + sp][thread]
+    constexpr int CB = 4;                     // cells per shared-memory batch (THS)
+    static_assert(V % CB == 0, "whole batches");
+    extern __shared__ float4 sdyn[];          // THS: Theta then w, rows [v * NS + sp][T]; else w [v * NS + sp][RES_WSTRIDE]
     __shared__ float4 sZ[2][RES_MAX_WARPS];   // inclusive warp aggregate (lane 31)
     __shared__ int sE[2][RES_MAX_WARPS];      // its exponent
     __shared__ int sM[2][RES_MAX_WARPS];      // largest exponent in the warp
     __shared__ int s_item;
+    __shared__ float2 sRk[6];                 // R^(V 2^k), k = 0..4, and R^(32 V)
+    __shared__ float2 sRl[32];                // R^(V lane)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int T = blockDim.x, nw = T >> 5;
+    const int T = THS ? TT : (int)blockDim.x, nw = T >> 5;
+    float2 *sT = reinterpret_cast<float2 *>(sdyn) + tid;                      // THS: row stride T = TT
+    float *sWt = reinterpret_cast<float *>(reinterpret_cast<float2 *>(sdyn) + V * NS * (THS ? TT : 0)) + tid;
+    float *sWr = reinterpret_cast<float *>(sdyn) + tid;                       // !THS: row stride RES_WSTRIDE
     int item = blockIdx.x;
     int buf = 0;
     for (;;) {
@@ -91,7 +104,6 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
         const int wend = min(w0 + (Tl >> 5), nw);
         const int jb = t * V;
         const bool has = live && jb < N;
-        const bool full = live && jb + V <= N;         // no cell of the chunk past the end
         const bool front1 = a.front == 1 && live && t == 0;
 
         // per-line constants
@@ -99,22 +111,39 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
         float Af[NS], Bf[NS], q[NS];
 #pragma unroll
         for (int sp = 0; sp < NS; ++sp) {
+            // the chunk holds y_s = q_s n_bs and q_s Theta_s (exact for |q| a
+            // power of two), so rho = sum_s y_s and the kick carries q_s
             const double f1 = I.qm_g[sp] * kk2d, f2 = I.qm_g3[sp] * kapd;
-            Af[sp] = (float)(I.dt * (f1 + f2));
-            Bf[sp] = (float)(I.dt * f2);
+            Af[sp] = (float)(I.q[sp] * (I.dt * (f1 + f2)));
+            Bf[sp] = (float)(I.q[sp] * (I.dt * f2));
             q[sp] = (float)I.q[sp];
         }
         const float c = (float)I.c, s = (float)I.s, ch = (float)I.ch, sh = (float)I.sh;
-        RotF Rk[5];
+        // rotation tables: registers when Theta is in registers, else shared
+        // by the CTA's lines (one instance per item; visible after the first
+        // barrier below)
+        RotF Rk[THS ? 1 : 5], Rl{1.f, 0.f}, Rw{1.f, 0.f};
+        if constexpr (!THS) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) Rk[k] = rotf(I.dxi * (double)(V << k));
-        const RotF Rl = rotf(I.dxi * (double)(V * lane));
-        const RotF Rw = rotf(I.dxi * (double)(32 * V));
+            for (int k = 0; k < 5; ++k) Rk[k] = rotf(I.dxi * (double)(V << k));
+            Rl = rotf(I.dxi * (double)(V * lane));
+            Rw = rotf(I.dxi * (double)(32 * V));
+        }
+        if (THS && warp == 0) {
+            const RotF r = rotf(I.dxi * (double)(V * lane));
+            sRl[lane] = make_float2(r.c, r.s);
+            if (lane < 6) {
+                const RotF q6 = rotf(I.dxi * (double)(lane < 5 ? V << lane : 32 * V));
+                sRk[lane] = make_float2(q6.c, q6.s);
+            }
+        }
         const bool held = a.front == 2 && a.held != nullptr && live && t == 0;
         const double *hp = held ? a.held + ((long long)itx.x * a.Mp + mc) * 4 : nullptr;
 
-        // load the chunk: mantissas relative to e = W + s8 of its group
-        Cell<float> x[V][NS];
+        // load the chunk: mantissas relative to e = W + s8 of its group; cells
+        // past the end of the line hold zeros (state and weight)
+        float2 xn[V][NS];                      // q_s n_bs (re, im)
+        float2 xt[THS ? 1 : V][NS];            // q_s Theta_s when it stays in registers
         int e = RES_NONE;
         float fin = 1.0f;
         if (has) {
@@ -129,15 +158,22 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
 #pragma unroll
             for (int sp = 0; sp < NS; ++sp) {
                 float wv = 0.f;
+                Cell<float> y{0.f, 0.f, 0.f, 0.f};
                 if (has && j < N) {
                     const long long row = (I.cell_off + j) * NS + sp;
-                    ld_cell(a, row, mode, x[v][sp]);
-                    x[v][sp].nr *= fin; x[v][sp].ni *= fin; x[v][sp].tr *= fin; x[v][sp].ti *= fin;
+                    ld_cell(a, row, mode, y);
+                    const float f = fin * q[sp];
+                    y.nr *= f; y.ni *= f; y.tr *= f; y.ti *= f;
                     wv = __ldg(reinterpret_cast<const float *>(a.w) + row);
-                } else {
-                    x[v][sp] = Cell<float>{0.f, 0.f, 0.f, 0.f};
                 }
-                sW[(v * NS + sp) * T + tid] = wv;    // only this thread reads it back
+                xn[v][sp] = make_float2(y.nr, y.ni);
+                if constexpr (THS) {
+                    sT[(v * NS + sp) * T] = make_float2(y.tr, y.ti);
+                    sWt[(v * NS + sp) * T] = wv;
+                } else {
+                    xt[v][sp] = make_float2(y.tr, y.ti);
+                    sWr[(v * NS + sp) * RES_WSTRIDE] = wv;   // only this thread reads it back
+                }
             }
         }
         auto scale_chunk = [&](float f) {
@@ -145,7 +181,13 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
             for (int v = 0; v < V; ++v)
 #pragma unroll
                 for (int sp = 0; sp < NS; ++sp) {
-                    x[v][sp].nr *= f; x[v][sp].ni *= f; x[v][sp].tr *= f; x[v][sp].ti *= f;
+                    xn[v][sp].x *= f; xn[v][sp].y *= f;
+                    if constexpr (THS) {
+                        float2 &z = sT[(v * NS + sp) * T];
+                        z.x *= f; z.y *= f;
+                    } else {
+                        xt[v][sp].x *= f; xt[v][sp].y *= f;
+                    }
                 }
         };
         if (held) {   // the held front value enters thread 0's scale
@@ -167,8 +209,8 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
             buf ^= 1;
         }
         auto rho = [&](int v, float &rr, float &ri) {
-            rr = q[0] * x[v][0].nr; ri = q[0] * x[v][0].ni;
-            if (NS == 2) { rr = fmaf(q[NS - 1], x[v][NS - 1].nr, rr); ri = fmaf(q[NS - 1], x[v][NS - 1].ni, ri); }
+            rr = xn[v][0].x; ri = xn[v][0].y;
+            if (NS == 2) { rr += xn[v][NS - 1].x; ri += xn[v][NS - 1].y; }
         };
         // front: P entering cell 0 (thread 0 of the line), in this thread's scale
         auto front_state = [&](float &nr, float &ni, float &dr, float &di) {
@@ -179,11 +221,11 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
             }
             if (front1) rho(0, nr, ni);   // equilibrium front: n_p = rho, n_p' = 0 at xi = 0
         };
-        // pass 1: the chunk's response from the given entry state
-        auto pass1 = [&](auto chk, float &nr, float &ni, float &dr, float &di) {
+        // pass 1: the chunk's response from the given entry state (cells past
+        // the end propagate values nobody reads)
+        auto pass1 = [&](float &nr, float &ni, float &dr, float &di) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                if (decltype(chk)::value && jb + v >= N) break;
                 float rr, ri;
                 rho(v, rr, ri);
                 const float ur = nr - rr, ui = ni - ri;
@@ -193,35 +235,77 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
                 nr = xr; ni = xi;
             }
         };
+        // kick and drift of one species at one cell: Theta += A n_mid - B rho,
+        // n_b += dt n_b0 Theta; one species folds n_mid = ch u + sh n' + rho
+        // into the coefficients (Ach u + Ash n' + (A - B) rho)
+        auto kick = [&](float2 &y, float &tr, float &ti, const float wv, float ur, float ui, float dr, float di,
+                        float rr, float ri, float mr, float mi, float A, float B, float Ach, float Ash, float AB,
+                        float &gmax) {
+            if (NS == 1) {
+                tr = fmaf(Ach, ur, fmaf(Ash, dr, fmaf(AB, rr, tr)));
+                ti = fmaf(Ach, ui, fmaf(Ash, di, fmaf(AB, ri, ti)));
+            } else {
+                tr = fmaf(A, mr, fmaf(-B, rr, tr));
+                ti = fmaf(A, mi, fmaf(-B, ri, ti));
+            }
+            y.x = fmaf(wv, tr, y.x);
+            y.y = fmaf(wv, ti, y.y);
+            gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(tr), fabsf(ti))));
+        };
         // pass 2: fields at the cell centre and the push
-        auto pass2 = [&](auto chk, float nr, float ni, float dr, float di, const float *A, const float *B) {
+        auto pass2 = [&](float nr, float ni, float dr, float di, const float *A, const float *B) {
             float gmax = 0.f;
+            const float Ach = A[0] * ch, Ash = A[0] * sh, AB = A[0] - B[0];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if (decltype(chk)::value && jb + v >= N) break;
-                float rr, ri;
-                rho(v, rr, ri);
-                const float ur = nr - rr, ui = ni - ri;
-                const float mr = fmaf(ch, ur, fmaf(sh, dr, rr)), mi = fmaf(ch, ui, fmaf(sh, di, ri));
-                const float xr = fmaf(c, ur, fmaf(s, dr, rr)), xi = fmaf(c, ui, fmaf(s, di, ri));
-                dr = fmaf(-s, ur, c * dr);
-                di = fmaf(-s, ui, c * di);
-                nr = xr; ni = xi;
+            for (int vb = 0; vb < V; vb += CB) {
+                float4 z[THS ? CB : 1][NS];
+                if constexpr (THS) {
 #pragma unroll
-                for (int sp = 0; sp < NS; ++sp) {
-                    Cell<float> &y = x[v][sp];
-                    const float wv = sW[(v * NS + sp) * T + tid];
-                    y.tr = fmaf(A[sp], mr, fmaf(-B[sp], rr, y.tr));
-                    y.ti = fmaf(A[sp], mi, fmaf(-B[sp], ri, y.ti));
-                    y.nr = fmaf(wv, y.tr, y.nr);
-                    y.ni = fmaf(wv, y.ti, y.ni);
-                    gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(y.nr), fabsf(y.ni)), fmaxf(fabsf(y.tr), fabsf(y.ti))));
+                    for (int u = 0; u < CB; ++u)
+#pragma unroll
+                        for (int sp = 0; sp < NS; ++sp) {
+                            const float2 t2 = sT[((vb + u) * NS + sp) * T];
+                            z[u][sp] = make_float4(t2.x, t2.y, sWt[((vb + u) * NS + sp) * T], 0.f);
+                        }
+                }
+#pragma unroll
+                for (int u = 0; u < CB; ++u) {
+                    const int v = vb + u;
+                    float rr, ri;
+                    rho(v, rr, ri);
+                    const float ur = nr - rr, ui = ni - ri;
+                    float mr = 0.f, mi = 0.f;
+                    if (NS == 2) { mr = fmaf(ch, ur, fmaf(sh, dr, rr)); mi = fmaf(ch, ui, fmaf(sh, di, ri)); }
+#pragma unroll
+                    for (int sp = 0; sp < NS; ++sp) {
+                        float2 &y = xn[v][sp];
+                        if constexpr (THS) {
+                            float4 &zz = z[THS ? u : 0][sp];
+                            kick(y, zz.x, zz.y, zz.z, ur, ui, dr, di, rr, ri, mr, mi, A[sp], B[sp], Ach, Ash, AB, gmax);
+                        } else {
+                            const float wv = sWr[(v * NS + sp) * RES_WSTRIDE];
+                            float2 &tt = xt[THS ? 0 : v][sp];
+                            kick(y, tt.x, tt.y, wv, ur, ui, dr, di, rr, ri, mr, mi, A[sp], B[sp], Ach, Ash, AB, gmax);
+                        }
+                    }
+                    const float xr = fmaf(c, ur, fmaf(s, dr, rr)), xi = fmaf(c, ui, fmaf(s, di, ri));
+                    dr = fmaf(-s, ur, c * dr);
+                    di = fmaf(-s, ui, c * di);
+                    nr = xr; ni = xi;
+                }
+                if constexpr (THS) {
+#pragma unroll
+                    for (int u = 0; u < CB; ++u)
+#pragma unroll
+                        for (int sp = 0; sp < NS; ++sp)
+                            sT[((vb + u) * NS + sp) * T] = make_float2(z[u][sp].x, z[u][sp].y);
+                    // keep the next batch's loads after this point: hoisting all
+                    // of them would hold every cell's Theta in registers
+                    asm volatile("" ::: "memory");
                 }
             }
             return gmax;
         };
-        using Yes = std::integral_constant<bool, true>;
-        using No = std::integral_constant<bool, false>;
 
         for (int it = 0; it < a.n_steps; ++it) {
             const float hf = (a.step0 + it) == 0 ? 0.5f : 1.0f;
@@ -231,8 +315,7 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
             // ---- pass 1 (thread 0 starts from the front, the others from 0)
             float nr, ni, dr, di;
             front_state(nr, ni, dr, di);
-            if (full) pass1(No(), nr, ni, dr, di);
-            else if (has) pass1(Yes(), nr, ni, dr, di);
+            pass1(nr, ni, dr, di);
             // ---- inclusive scan over the warp's lanes
             float fk[5];
 #pragma unroll
@@ -242,7 +325,9 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
                 const int d = 1 << k;
                 const float ur = __shfl_up_sync(FULL, nr, d), ui = __shfl_up_sync(FULL, ni, d);
                 const float vr = __shfl_up_sync(FULL, dr, d), vi = __shfl_up_sync(FULL, di, d);
-                if (lane >= d) acc_rot(nr, ni, dr, di, Rk[k], fk[k], ur, ui, vr, vi);
+                RotF R;
+                if constexpr (THS) { const float2 r2 = sRk[k]; R = RotF{r2.x, r2.y}; } else { R = Rk[THS ? 0 : k]; }
+                if (lane >= d) acc_rot(nr, ni, dr, di, R, fk[k], ur, ui, vr, vi);
             }
             float Xr = __shfl_up_sync(FULL, nr, 1), Xi = __shfl_up_sync(FULL, ni, 1);
             float Xdr = __shfl_up_sync(FULL, dr, 1), Xdi = __shfl_up_sync(FULL, di, 1);
@@ -266,6 +351,7 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
             }
             // ---- entry state: earlier warps of the line, then this warp's lanes
             float Yr = 0.f, Yi = 0.f, Ydr = 0.f, Ydi = 0.f;
+            if constexpr (THS) { const float2 r2 = sRk[5]; Rw = RotF{r2.x, r2.y}; }
             for (int ww = w0; ww < warp; ++ww) {
                 const float4 z = sZ[buf][ww];
                 const float fz = p2(sE[buf][ww] - e);
@@ -278,12 +364,11 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
                 front_state(nr, ni, dr, di);
             } else {
                 nr = Xr; ni = Xi; dr = Xdr; di = Xdi;
+                if constexpr (THS) { const float2 r2 = sRl[lane]; Rl = RotF{r2.x, r2.y}; }
                 acc_rot(nr, ni, dr, di, Rl, 1.0f, Yr, Yi, Ydr, Ydi);
             }
             // ---- pass 2
-            float gmax = 0.f;
-            if (full) gmax = pass2(No(), nr, ni, dr, di, A, B);
-            else if (has) gmax = pass2(Yes(), nr, ni, dr, di, A, B);
+            const float gmax = pass2(nr, ni, dr, di, A, B);
             // ---- own renormalisation (hysteresis)
             if (gmax > 0.f) {
                 const int ex = expof(gmax);
@@ -294,6 +379,7 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
         }
 
         // write back: the threads of a 32-cell group agree on one exponent
+        const long long cell0 = a.inst[itx.x].cell_off, grp0 = a.inst[itx.x].grp_off;
         int Wg = e;
 #pragma unroll
         for (int o = 1; o < GRP / V; o <<= 1) Wg = max(Wg, __shfl_xor_sync(FULL, Wg, o));
@@ -304,13 +390,20 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
             const int j = jb + v;
 #pragma unroll
             for (int sp = 0; sp < NS; ++sp) {
-                Cell<float> &y = x[v][sp];
-                y.nr *= fo; y.ni *= fo; y.tr *= fo; y.ti *= fo;
+                Cell<float> y{xn[v][sp].x, xn[v][sp].y, 0.f, 0.f};
+                if constexpr (THS) {
+                    const float2 z = sT[(v * NS + sp) * T];
+                    y.tr = z.x; y.ti = z.y;
+                } else {
+                    y.tr = xt[THS ? 0 : v][sp].x; y.ti = xt[THS ? 0 : v][sp].y;
+                }
+                const float f = fo / q[sp];
+                y.nr *= f; y.ni *= f; y.tr *= f; y.ti *= f;
                 if (has && j < N) {
                     gm = fmaxf(gm, fmaxf(fmaxf(fabsf(y.nr), fabsf(y.ni)), fmaxf(fabsf(y.tr), fabsf(y.ti))));
                     gn = fmaf(y.nr + y.ti, 0.0f, gn);
                     gn = fmaf(y.ni + y.tr, 0.0f, gn);
-                    st_cell(a, (I.cell_off + j) * NS + sp, mode, y);
+                    st_cell(a, (cell0 + j) * NS + sp, mode, y);
                 }
             }
         }
@@ -321,13 +414,18 @@ __global__ void __launch_bounds__(512) k_sweep_res(const SweepArgs a) {
                 int s8 = gm > 0.0f ? expof(gm) : 0;
                 s8 = s8 < -100 ? -100 : (s8 > 100 ? 100 : s8);
                 const int Ws = gm > 0.0f ? Wg : 0;
-                __stcg(a.ex + (I.grp_off + jb / GRP) * a.Mp + mode, (Ws << 8) | (s8 & 0xff));
+                __stcg(a.ex + (grp0 + jb / GRP) * a.Mp + mode, (Ws << 8) | (s8 & 0xff));
             }
             if (!(gn == 0.0f) || !(gm <= 3.0e38f)) atomicOr(a.err, ERR_NONFINITE);
         }
         if (!a.persistent) break;
         __syncthreads();   // shared state of this item is done before the next ticket
     }
+}
+
+// dynamic shared memory of one CTA (TT > 0: TT threads)
+constexpr size_t res_smem_bytes(int NS, int V, int TT) {
+    return TT > 0 ? (size_t)V * NS * TT * (sizeof(float2) + sizeof(float)) : (size_t)V * NS * RES_WSTRIDE * sizeof(float);
 }
 
 }  // namespace qsk

@@ -405,10 +405,40 @@ SweepArgs sweep_args(qs_ctx *c, long long step0, int n_steps, int update, int re
     return a;
 }
 
-template <int NS, int V>
+template <int NS, int V, int TT>
 cudaError_t launch_res_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) {
-    qsk::k_sweep_res<NS, V><<<grid, threads, (size_t)V * NS * threads * sizeof(float), c->stream>>>(a);
+    const size_t smem = qsk::res_smem_bytes(NS, V, TT);
+    static int opted = 0;   // shared-memory opt-in (dynamic + static may pass 48 KiB), once per instantiation
+    if (!opted) {
+        cudaError_t e = cudaFuncSetAttribute(qsk::k_sweep_res<NS, V, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        opted = 1;
+    }
+    qsk::k_sweep_res<NS, V, TT><<<grid, threads, smem, c->stream>>>(a);
     return cudaGetLastError();
+}
+
+// resident instantiations: Theta in registers (any CTA size) for 8 | 16 cells
+// of one species and 8 of two; Theta in shared memory for 32 cells of one
+// species (CTA of 64 | 128 | 256) and 16 of two (CTA of 128 | 256 | 512)
+cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V) {
+    if (c->NS == 1) {
+        if (V == 32) return T == 64 ? launch_res_t<1, 32, 64>(c, a, grid, T)
+                          : T == 128 ? launch_res_t<1, 32, 128>(c, a, grid, T)
+                                     : launch_res_t<1, 32, 256>(c, a, grid, T);
+        return V == 16 ? launch_res_t<1, 16, 0>(c, a, grid, T) : launch_res_t<1, 8, 0>(c, a, grid, T);
+    }
+    if (V == 16) return T == 128 ? launch_res_t<2, 16, 128>(c, a, grid, T)
+                      : T == 256 ? launch_res_t<2, 16, 256>(c, a, grid, T)
+                                 : launch_res_t<2, 16, 512>(c, a, grid, T);
+    return launch_res_t<2, 8, 0>(c, a, grid, T);
+}
+
+bool res_shape_ok(int NS, int V, int w) {
+    if (NS == 1 && V == 32) return w == 2 || w == 4 || w == 8;
+    if (NS == 2 && V == 16) return w == 4 || w == 8 || w == 16;
+    return (V == 8 || (V == 16 && NS == 1)) && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16);
 }
 
 qs_status launch_sweep(qs_ctx *c, long long step0, int n_steps, int update, int rec_kinds,
@@ -450,9 +480,7 @@ qs_status launch_resident(qs_ctx *c, long long step0, int n_steps, int update, i
                 const long long g = (long long)c->launch.ctas_per_sm * c->n_sm;
                 grid = dim3((unsigned)std::max<long long>(1, std::min<long long>(g, c->n_res_items)));
             }
-            const int V = c->launch.prefetch;
-            cudaError_t e = c->NS == 1 ? (V >= 16 ? launch_res_t<1, 16>(c, a, grid, T) : launch_res_t<1, 8>(c, a, grid, T))
-                                       : launch_res_t<2, 8>(c, a, grid, T);
+            cudaError_t e = launch_res(c, a, grid, T, c->launch.prefetch);
             if (e != cudaSuccess) return fail(c, QS_ERR_CUDA, "resident sweep launch: %s", cudaGetErrorString(e));
             ++c->n_launch;
         }
@@ -935,9 +963,9 @@ qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
     if (l->variant == QS_VARIANT_RESIDENT) {
         if (c->prec != QS_FP32_RENORM) return fail(c, QS_ERR_UNSUPPORTED, "the resident variant is FP32 only");
         const int V = l->prefetch;
-        if (!(V == 8 || (V == 16 && c->NS == 1)))
-            return fail(c, QS_ERR_ARG, "resident: cells per thread must be 8 or 16 (one species), 8 (two)");
-        if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16)) return fail(c, QS_ERR_ARG, "resident: warps_per_cta");
+        if (!res_shape_ok(c->NS, V, w))
+            return fail(c, QS_ERR_ARG, "resident: cells per thread 8|16 (any CTA size) or 32 (one species, 2|4|8 "
+                                       "warps); two species: 8 (any) or 16 (4|8|16 warps)");
         if (res_threads_per_line(max_nxi(c), V) > 32 * w)
             return fail(c, QS_ERR_ARG, "resident: a line of %d cells needs %d threads, the CTA has %d", max_nxi(c),
                         res_threads_per_line(max_nxi(c), V), 32 * w);

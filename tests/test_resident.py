@@ -34,13 +34,15 @@ def _fits(n_xi, V, w):
 
 
 @pytest.mark.parametrize("case", SMALL, ids=lambda c: f"nxi{c[0]}-m{len(c[1])}-s{len(c[2])}-{c[3]}-{c[4]}-{c[5]}-{c[6]}")
-@pytest.mark.parametrize("V", [8, 16])
+@pytest.mark.parametrize("V", [8, 16, 32])
 def test_small_cases_resident(qs, case, V):
     p, held, user, sd, steps = _small_problem(case)
-    if V == 16 and len(p["species"]) == 2:
-        pytest.skip("16 cells per thread is for one species")
-    w = next(w for w in (1, 2, 4, 8, 16) if _fits(p["n_xi"], V, w))
-    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=sd, held=held, user=user, launch=_res(V, max(w, 2)))
+    ns = len(p["species"])
+    if V == 32 and ns == 2:
+        pytest.skip("32 cells per thread is for one species")
+    ok = (lambda w: w in (2, 4, 8)) if V == 32 else (lambda w: w in (4, 8, 16)) if (V == 16 and ns == 2) else (lambda w: True)
+    w = next(w for w in (1, 2, 4, 8, 16) if _fits(p["n_xi"], V, w) and ok(w) and w >= 2)
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=sd, held=held, user=user, launch=_res(V, w))
     nb_o, th_o = _run_oracle(p, steps, seed=sd, held=held, user=user)
     assert _log_err(nb, nb_o) <= FP32_LOG_TOL
     assert _log_err(th, th_o) <= FP32_LOG_TOL
@@ -53,6 +55,8 @@ def test_small_cases_resident(qs, case, V):
     (1000, 16, 2, 1),    # 63 -> 64 threads, one line per CTA
     (33, 16, 4, 0),      # 3 -> 32 threads: 4 lines per CTA, most threads without cells
     (2048, 16, 4, 1),    # the benchmark's line length
+    (2048, 32, 4, 1),    # Theta in shared memory, 2 lines per CTA
+    (1000, 32, 8, 0),    # 32 -> 32 threads: 4 lines per CTA
 ])
 def test_ragged_packing(qs, n_xi, V, w, pers):
     """Lines per CTA, idle threads and a mode count that is not a multiple
@@ -73,7 +77,7 @@ def test_batched_instances_resident(qs):
     s = qs.Solver(insts, prec="fp32")
     mx = max(p["n_xi"] for p in insts)
     w = next(w for w in (1, 2, 4, 8, 16) if _fits(mx, 8, w))
-    s.set_launch(**_res(8, w, 1, 2))
+    s.set_launch(**_res(16, max(w, 4), 1, 2))
     s.seed_noise(0, 1e-6)
     s.step(30)
     s.sync()
@@ -94,7 +98,7 @@ def test_records_split_the_call(qs):
                      species=[(-1.0, 1.0, 0.05)], gamma_b=20.0)
     steps, stride = 50, 7
     s = qs.Solver(p, prec="fp32")
-    s.set_launch(**_res(16, 2))
+    s.set_launch(**_res(32, 2))
     s.seed_noise(6, 1e-6)
     n_snap = (steps - 1) // stride + 1
     buf = s.record(qs.REC_MAG | qs.REC_NP, stride, n_snap)
@@ -121,7 +125,7 @@ def test_extreme_growth_resident(qs):
     p = synth.scaled(synth.SLAB_2D, n_xi=400, dxi=0.025, length=10.0, species=[(-1.0, 1.0, 0.1)],
                      gamma_b=10.0, k_list=[1.0, 3.0, 6.0, 9.0], dt=2.0)
     steps = 2000
-    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=("noise", 4, 1e-6), launch=_res(8, 2))
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=("noise", 4, 1e-6), launch=_res(32, 2))
     nb_o, th_o = _run_oracle(p, steps, seed=("noise", 4, 1e-6))
     assert np.max(np.abs(nb_o)) > 1e40
     assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
@@ -133,7 +137,7 @@ def test_resident_bitwise_properties(qs):
     another scale changes no bits), graph replay, and k/-k conjugate pairs."""
     import torch
     p = synth.scaled(synth.BEAM_3D, nkx=24, nky=24, kmax=5.0, n_xi=150, dxi=0.04, length=6.0)
-    L = _res(8, 4)
+    L = _res(32, 4)
     _, nb, th = _run_gpu(qs, p, "fp32", 13, seed=("noise", 2, 1e-6), launch=L)
     _, nb2, th2 = _run_gpu(qs, p, "fp32", 13, seed=("noise", 2, 1e-6), launch=L, chunks=[6, 1, 6])
     assert np.array_equal(nb, nb2) and np.array_equal(th, th2)
