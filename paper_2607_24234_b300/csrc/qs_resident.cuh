@@ -29,6 +29,7 @@
 // On the way out the threads sharing a 32-cell group agree on one exponent
 // and write the usual (mantissa, exponent word) layout.
 #pragma once
+#include <type_traits>
 
 namespace qsk {
 
@@ -52,6 +53,19 @@ __device__ __forceinline__ void acc_rot(float &nr, float &ni, float &dr, float &
     ni = fmaf(C, xi, fmaf(S, yi, ni));
     dr = fmaf(-S, xr, fmaf(C, yr, dr));
     di = fmaf(-S, xi, fmaf(C, yi, di));
+}
+// packed (re, im) arithmetic: one f32x2 instruction for both components,
+// each rounded as its scalar counterpart (__fmaf_rn, __fmul_rn, __fadd_rn)
+__device__ __forceinline__ float2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// (n, n') += f R^m (x, x') with both components of each in one register pair
+__device__ __forceinline__ void acc_rot2(float2 &n, float2 &d, const RotF R, const float f, const float2 x,
+                                         const float2 y) {
+    const float C = R.c * f, S = R.s * f;
+    n = pfma(F2(C), x, pfma(F2(S), y, n));
+    d = pfma(F2(-S), x, pfma(F2(C), y, d));
 }
 __device__ __forceinline__ int clamp_shift(int s) { return s < -126 ? -126 : (s > 126 ? 126 : s); }
 // 2^e for e in [-126, 127]; 0 below (branch free)
@@ -208,97 +222,78 @@ __global__ void __launch_bounds__(TT > 0 ? TT : 512, 512 / (TT > 0 ? TT : 512)) 
             if (e < lo) { scale_chunk(p2(e - lo)); e = lo; }
             buf ^= 1;
         }
-        auto rho = [&](int v, float &rr, float &ri) {
-            rr = xn[v][0].x; ri = xn[v][0].y;
-            if (NS == 2) { rr += xn[v][NS - 1].x; ri += xn[v][NS - 1].y; }
-        };
+        auto rho = [&](int v) -> float2 { return NS == 2 ? padd(xn[v][0], xn[v][NS - 1]) : xn[v][0]; };
         // front: P entering cell 0 (thread 0 of the line), in this thread's scale
-        auto front_state = [&](float &nr, float &ni, float &dr, float &di) {
-            nr = ni = dr = di = 0.f;
+        auto front_state = [&](float2 &n, float2 &d) {
+            n = d = F2(0.f);
             if (held) {
-                nr = (float)ldexp(hp[0], -e); ni = (float)ldexp(hp[1], -e);
-                dr = (float)ldexp(hp[2], -e); di = (float)ldexp(hp[3], -e);
+                n = make_float2((float)ldexp(hp[0], -e), (float)ldexp(hp[1], -e));
+                d = make_float2((float)ldexp(hp[2], -e), (float)ldexp(hp[3], -e));
             }
-            if (front1) rho(0, nr, ni);   // equilibrium front: n_p = rho, n_p' = 0 at xi = 0
+            if (front1) n = rho(0);   // equilibrium front: n_p = rho, n_p' = 0 at xi = 0
+        };
+        const float2 C2 = F2(c), S2 = F2(s), NS2 = F2(-s), M1 = F2(-1.f);
+        // exact cell propagator of Eq. (5): u = n - rho, n <- c u + s n' + rho,
+        // n' <- -s u + c n'
+        auto cross = [&](float2 &n, float2 &d, const float2 u, const float2 r) {
+            n = pfma(C2, u, pfma(S2, d, r));
+            d = pfma(NS2, u, pmul(C2, d));
         };
         // pass 1: the chunk's response from the given entry state (cells past
         // the end propagate values nobody reads)
-        auto pass1 = [&](float &nr, float &ni, float &dr, float &di) {
+        auto pass1 = [&](float2 &n, float2 &d) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                float rr, ri;
-                rho(v, rr, ri);
-                const float ur = nr - rr, ui = ni - ri;
-                const float xr = fmaf(c, ur, fmaf(s, dr, rr)), xi = fmaf(c, ui, fmaf(s, di, ri));
-                dr = fmaf(-s, ur, c * dr);
-                di = fmaf(-s, ui, c * di);
-                nr = xr; ni = xi;
+                const float2 r = rho(v);
+                cross(n, d, pfma(M1, r, n), r);
             }
         };
-        // kick and drift of one species at one cell: Theta += A n_mid - B rho,
-        // n_b += dt n_b0 Theta; one species folds n_mid = ch u + sh n' + rho
-        // into the coefficients (Ach u + Ash n' + (A - B) rho)
-        auto kick = [&](float2 &y, float &tr, float &ti, const float wv, float ur, float ui, float dr, float di,
-                        float rr, float ri, float mr, float mi, float A, float B, float Ach, float Ash, float AB,
-                        float &gmax) {
-            if (NS == 1) {
-                tr = fmaf(Ach, ur, fmaf(Ash, dr, fmaf(AB, rr, tr)));
-                ti = fmaf(Ach, ui, fmaf(Ash, di, fmaf(AB, ri, ti)));
-            } else {
-                tr = fmaf(A, mr, fmaf(-B, rr, tr));
-                ti = fmaf(A, mi, fmaf(-B, ri, ti));
-            }
-            y.x = fmaf(wv, tr, y.x);
-            y.y = fmaf(wv, ti, y.y);
-            gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(tr), fabsf(ti))));
-        };
-        // pass 2: fields at the cell centre and the push
-        auto pass2 = [&](float nr, float ni, float dr, float di, const float *A, const float *B) {
+        // pass 2: fields at the cell centre and the push, Theta += A n_mid -
+        // B rho, n_b += dt n_b0 Theta; one species folds n_mid = ch u + sh n' +
+        // rho into the coefficients (Ach u + Ash n' + (A - B) rho).  GM: track
+        // the chunk's largest magnitude for the renormalisation.
+        auto pass2 = [&](auto gm_tag, float2 n, float2 d, const float *A, const float *B) {
+            constexpr bool GM = decltype(gm_tag)::value;
             float gmax = 0.f;
-            const float Ach = A[0] * ch, Ash = A[0] * sh, AB = A[0] - B[0];
+            const float2 Ach = F2(A[0] * ch), Ash = F2(A[0] * sh), AB = F2(A[0] - B[0]);
+            const float2 CH2 = F2(ch), SH2 = F2(sh);
 #pragma unroll
             for (int vb = 0; vb < V; vb += CB) {
-                float4 z[THS ? CB : 1][NS];
+                float2 zt[THS ? CB : 1][NS];
+                float zw[THS ? CB : 1][NS];
                 if constexpr (THS) {
 #pragma unroll
                     for (int u = 0; u < CB; ++u)
 #pragma unroll
                         for (int sp = 0; sp < NS; ++sp) {
-                            const float2 t2 = sT[((vb + u) * NS + sp) * T];
-                            z[u][sp] = make_float4(t2.x, t2.y, sWt[((vb + u) * NS + sp) * T], 0.f);
+                            zt[u][sp] = sT[((vb + u) * NS + sp) * T];
+                            zw[u][sp] = sWt[((vb + u) * NS + sp) * T];
                         }
                 }
 #pragma unroll
                 for (int u = 0; u < CB; ++u) {
                     const int v = vb + u;
-                    float rr, ri;
-                    rho(v, rr, ri);
-                    const float ur = nr - rr, ui = ni - ri;
-                    float mr = 0.f, mi = 0.f;
-                    if (NS == 2) { mr = fmaf(ch, ur, fmaf(sh, dr, rr)); mi = fmaf(ch, ui, fmaf(sh, di, ri)); }
+                    const float2 r = rho(v);
+                    const float2 uu = pfma(M1, r, n);
+                    float2 m = F2(0.f);
+                    if (NS == 2) m = pfma(CH2, uu, pfma(SH2, d, r));
 #pragma unroll
                     for (int sp = 0; sp < NS; ++sp) {
                         float2 &y = xn[v][sp];
-                        if constexpr (THS) {
-                            float4 &zz = z[THS ? u : 0][sp];
-                            kick(y, zz.x, zz.y, zz.z, ur, ui, dr, di, rr, ri, mr, mi, A[sp], B[sp], Ach, Ash, AB, gmax);
-                        } else {
-                            const float wv = sWr[(v * NS + sp) * RES_WSTRIDE];
-                            float2 &tt = xt[THS ? 0 : v][sp];
-                            kick(y, tt.x, tt.y, wv, ur, ui, dr, di, rr, ri, mr, mi, A[sp], B[sp], Ach, Ash, AB, gmax);
-                        }
+                        float2 &th = THS ? zt[THS ? u : 0][sp] : xt[THS ? 0 : v][sp];
+                        const float wv = THS ? zw[THS ? u : 0][sp] : sWr[(v * NS + sp) * RES_WSTRIDE];
+                        if (NS == 1) th = pfma(Ach, uu, pfma(Ash, d, pfma(AB, r, th)));
+                        else th = pfma(F2(A[sp]), m, pfma(F2(-B[sp]), r, th));
+                        y = pfma(F2(wv), th, y);
+                        if (GM) gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(th.x), fabsf(th.y))));
                     }
-                    const float xr = fmaf(c, ur, fmaf(s, dr, rr)), xi = fmaf(c, ui, fmaf(s, di, ri));
-                    dr = fmaf(-s, ur, c * dr);
-                    di = fmaf(-s, ui, c * di);
-                    nr = xr; ni = xi;
+                    cross(n, d, uu, r);
                 }
                 if constexpr (THS) {
 #pragma unroll
                     for (int u = 0; u < CB; ++u)
 #pragma unroll
-                        for (int sp = 0; sp < NS; ++sp)
-                            sT[((vb + u) * NS + sp) * T] = make_float2(z[u][sp].x, z[u][sp].y);
+                        for (int sp = 0; sp < NS; ++sp) sT[((vb + u) * NS + sp) * T] = zt[u][sp];
                     // keep the next batch's loads after this point: hoisting all
                     // of them would hold every cell's Theta in registers
                     asm volatile("" ::: "memory");
@@ -313,27 +308,26 @@ __global__ void __launch_bounds__(TT > 0 ? TT : 512, 512 / (TT > 0 ? TT : 512)) 
 #pragma unroll
             for (int sp = 0; sp < NS; ++sp) { A[sp] = hf * Af[sp]; B[sp] = hf * Bf[sp]; }
             // ---- pass 1 (thread 0 starts from the front, the others from 0)
-            float nr, ni, dr, di;
-            front_state(nr, ni, dr, di);
-            pass1(nr, ni, dr, di);
+            float2 n, d;
+            front_state(n, d);
+            pass1(n, d);
             // ---- inclusive scan over the warp's lanes
             float fk[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) fk[k] = p2(__shfl_up_sync(FULL, e, 1 << k) - e);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                const int d = 1 << k;
-                const float ur = __shfl_up_sync(FULL, nr, d), ui = __shfl_up_sync(FULL, ni, d);
-                const float vr = __shfl_up_sync(FULL, dr, d), vi = __shfl_up_sync(FULL, di, d);
+                const int dl = 1 << k;
+                const float2 un = make_float2(__shfl_up_sync(FULL, n.x, dl), __shfl_up_sync(FULL, n.y, dl));
+                const float2 ud = make_float2(__shfl_up_sync(FULL, d.x, dl), __shfl_up_sync(FULL, d.y, dl));
                 RotF R;
                 if constexpr (THS) { const float2 r2 = sRk[k]; R = RotF{r2.x, r2.y}; } else { R = Rk[THS ? 0 : k]; }
-                if (lane >= d) acc_rot(nr, ni, dr, di, R, fk[k], ur, ui, vr, vi);
+                if (lane >= dl) acc_rot2(n, d, R, fk[k], un, ud);
             }
-            float Xr = __shfl_up_sync(FULL, nr, 1), Xi = __shfl_up_sync(FULL, ni, 1);
-            float Xdr = __shfl_up_sync(FULL, dr, 1), Xdi = __shfl_up_sync(FULL, di, 1);
             const float fx = lane == 0 ? 0.f : fk[0];
-            Xr *= fx; Xi *= fx; Xdr *= fx; Xdi *= fx;
-            if (lane == 31) { sZ[buf][warp] = make_float4(nr, ni, dr, di); sE[buf][warp] = e; }
+            float2 Xn = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, n.x, 1), __shfl_up_sync(FULL, n.y, 1)));
+            float2 Xd = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, d.x, 1), __shfl_up_sync(FULL, d.y, 1)));
+            if (lane == 31) { sZ[buf][warp] = make_float4(n.x, n.y, d.x, d.y); sE[buf][warp] = e; }
             const int wm = __reduce_max_sync(FULL, e);
             if (lane == 0) sM[buf][warp] = wm;
             __syncthreads();
@@ -345,35 +339,39 @@ __global__ void __launch_bounds__(TT > 0 ? TT : 512, 512 / (TT > 0 ? TT : 512)) 
                 if (e < lo) {
                     const float f = p2(e - lo);
                     scale_chunk(f);
-                    Xr *= f; Xi *= f; Xdr *= f; Xdi *= f;
+                    Xn = pmul(F2(f), Xn); Xd = pmul(F2(f), Xd);
                     e = lo;
                 }
             }
             // ---- entry state: earlier warps of the line, then this warp's lanes
-            float Yr = 0.f, Yi = 0.f, Ydr = 0.f, Ydi = 0.f;
+            float2 Yn = F2(0.f), Yd = F2(0.f);
             if constexpr (THS) { const float2 r2 = sRk[5]; Rw = RotF{r2.x, r2.y}; }
             for (int ww = w0; ww < warp; ++ww) {
                 const float4 z = sZ[buf][ww];
                 const float fz = p2(sE[buf][ww] - e);
-                const float yr = fmaf(Rw.c, Yr, Rw.s * Ydr), yi = fmaf(Rw.c, Yi, Rw.s * Ydi);
-                const float ydr = fmaf(-Rw.s, Yr, Rw.c * Ydr), ydi = fmaf(-Rw.s, Yi, Rw.c * Ydi);
-                Yr = fmaf(fz, z.x, yr); Yi = fmaf(fz, z.y, yi);
-                Ydr = fmaf(fz, z.z, ydr); Ydi = fmaf(fz, z.w, ydi);
+                const float2 yn = Yn, yd = Yd;
+                Yn = pmul(F2(fz), make_float2(z.x, z.y));
+                Yd = pmul(F2(fz), make_float2(z.z, z.w));
+                acc_rot2(Yn, Yd, Rw, 1.0f, yn, yd);
             }
             if (t == 0) {
-                front_state(nr, ni, dr, di);
+                front_state(n, d);
             } else {
-                nr = Xr; ni = Xi; dr = Xdr; di = Xdi;
+                n = Xn; d = Xd;
                 if constexpr (THS) { const float2 r2 = sRl[lane]; Rl = RotF{r2.x, r2.y}; }
-                acc_rot(nr, ni, dr, di, Rl, 1.0f, Yr, Yi, Ydr, Ydi);
+                acc_rot2(n, d, Rl, 1.0f, Yn, Yd);
             }
-            // ---- pass 2
-            const float gmax = pass2(nr, ni, dr, di, A, B);
-            // ---- own renormalisation (hysteresis)
-            if (gmax > 0.f) {
-                const int ex = expof(gmax);
-                const int sx = clamp_shift(ex == -200 ? -126 : ex);
-                if (sx > RES_HYST || sx < -RES_HYST) { scale_chunk(p2(-sx)); e += sx; }
+            // ---- pass 2; every 4th step also the renormalisation (growth over
+            // 4 steps stays far inside the 2^RES_SPAN headroom)
+            if ((it & 3) == 3) {
+                const float gmax = pass2(std::integral_constant<bool, true>(), n, d, A, B);
+                if (gmax > 0.f) {
+                    const int ex = expof(gmax);
+                    const int sx = clamp_shift(ex == -200 ? -126 : ex);
+                    if (sx > RES_HYST || sx < -RES_HYST) { scale_chunk(p2(-sx)); e += sx; }
+                }
+            } else {
+                pass2(std::integral_constant<bool, false>(), n, d, A, B);
             }
             buf ^= 1;
         }
