@@ -6,7 +6,9 @@ Workload (the 3D uniform-beam case): one electron-like species, n_b/n_p =
 cells, (kx, ky) grid 256 x 256 over |k| <= 6 (disc: 51,468 active modes),
 white-noise seed 1e-6 (seed 0), dt = 2.  One bench step = one whole job of
 2000 slow-time steps (one qs_step call, one kernel launch) on the FP32 +
-renormalisation path; the FP64 path is reported beside it on a shorter job.
+renormalisation path, in the launch shape the autotuner picks (the resident
+variant, which holds every line on chip for the whole job); the FP64 path
+is reported beside it on a shorter job.
 
 value  = updates / device time (state resident in HBM; the 1.7 GB state is
          larger than L2, so no flush is needed between launches).
@@ -39,7 +41,14 @@ UNIT = "updates/s"
 BYTES_PER_UPDATE_FP32 = 32.0 + 8.0 / 32.0   # read+write complex64 n_b and Theta, + exponents
 BYTES_PER_UPDATE_FP64 = 64.0
 KERNEL_SRC = os.path.join(ROOT, "paper_2607_24234_b300", "csrc", "qs_kernels.cuh")
+RESIDENT_SRC = os.path.join(ROOT, "paper_2607_24234_b300", "csrc", "qs_resident.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_fp32_beam3d_traffic.json")
+RES_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_resident_fp32_beam3d_traffic.json")
+# Algorithmic FP32 work of one cell update, one species (Line::cell): rho
+# 2 MUL, u = n_p - rho 2 ADD, centre value 4 FMA, cell exit 4 FMA + 2 MUL +
+# 2 FMA, kick 4 FMA, drift 2 FMA; an FMA counts as one instruction.
+FP32_INSTR_PER_UPDATE = 22.0
+VARIANT_RESIDENT = 3
 
 
 def peaks():
@@ -49,8 +58,39 @@ def peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def kernel_hash():
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+def kernel_hash(*paths):
+    h = hashlib.sha256()
+    for p in (paths or (KERNEL_SRC,)):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def fp32_alu_peak(pk):
+    """FP32 peak in lane-operations: 148 SMs x 128 FP32 lanes x max SM clock."""
+    return 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
+
+
+def sweep_roofline(launch, upd, launch_s, traffic, pk, pk_kind):
+    """Roofline of the FP32 sweep kernel that ran: ALU (FP32 lane-ops) for
+    the resident variant, HBM for the streaming ones."""
+    hbm_view = BYTES_PER_UPDATE_FP32 * upd / launch_s / 1e9
+    if launch.get("variant") == VARIANT_RESIDENT:
+        peak = fp32_alu_peak(pk)
+        ach = FP32_INSTR_PER_UPDATE * upd / launch_s
+        return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP32-ops/s",
+                "frac": ach / peak, "traffic": traffic,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (an FMA is one op; "
+                               "a packed f32x2 instruction is two)",
+                "algorithmic_fp32_ops_per_update": FP32_INSTR_PER_UPDATE,
+                "kernel": f"qsk::k_sweep_res<1,{launch.get('prefetch')},{32 * launch.get('warps_per_cta')}>",
+                "streaming_equivalent_gbs": hbm_view,
+                "streaming_equivalent_frac_of_hbm": hbm_view / pk["hbm_gbs"],
+                "note": "lines held on chip for the whole job: HBM is read and written once per launch"}
+    return {"bound": "hbm", "achieved": hbm_view, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": hbm_view / pk["hbm_gbs"], "traffic": traffic, "peak_source": pk_kind,
+            "algorithmic_bytes_per_update": BYTES_PER_UPDATE_FP32,
+            "kernel": ("qsk::k_sweep_tma<float,1,C,ST>" if launch.get("variant") == 1
+                       else "qsk::k_sweep<float,1,U,false>")}
 
 
 class Clocks:
@@ -168,7 +208,7 @@ def run_reference(args):
 def run_batch(args):
     """Batched workload: 512 instances (n_b/n_p 10^U(-3,-1), gamma 10^U(1,4),
     L U(5,200) at dxi = 0.025, seed 0), 64 x 64 disc grid (3,228 modes),
-    1000 steps per job, FP32, one persistent LPT-ordered launch per job."""
+    1000 steps per job, FP32, the autotuned launch shape (one launch per job)."""
     import torch
     import paper_2607_24234_b300 as qs
     insts = synth.batch_instances(args.batch_instances, param_seed=0)
@@ -179,10 +219,13 @@ def run_batch(args):
     cells = sum(p["n_xi"] for p in insts)
     upd_job = cells * s.n_modes * job
     s.seed_noise(0, 1e-6)
+    if args.tune:
+        s.tune(reps=args.tune_reps, cache_path=os.path.join(ROOT, "paper_2607_24234_b300", "tune_cache.json"))
     s.step(2)
     torch.cuda.synchronize()
     clk = Clocks(0)
     ms = []
+    n0 = s.launch_count()
     for _ in range(args.steps):
         s.seed_noise(0, 1e-6)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -194,16 +237,14 @@ def run_batch(args):
     clocks = clk.stop()
     pk, pk_kind = peaks()
     t = float(np.mean(ms)) / 1e3
-    achieved = BYTES_PER_UPDATE_FP32 * upd_job / t / 1e9
     print(json.dumps({
         "metric": METRIC, "value": upd_job / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batch_{len(insts)}inst_64sq_disc_{job}steps", "instances": len(insts),
                    "modes": s.n_modes, "total_cells": cells, "launch": s.get_launch()},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind},
-        "clocks": clocks, "gpu_launches": s.launch_count()}), flush=True)
+        "roofline": sweep_roofline(s.get_launch(), upd_job, t, None, pk, pk_kind),
+        "clocks": clocks, "gpu_launches": s.launch_count() - n0}), flush=True)
     s.close()
 
 
@@ -313,13 +354,20 @@ def run_ours(args):
     import paper_2607_24234_b300 as qs
 
     p = synth.scaled(synth.BEAM_3D)
+    if args.nk is not None:   # reduced k grid (profiling); named as such
+        p = synth.scaled(p, nkx=args.nk, nky=args.nk, name=f"beam3d_{args.nk}sq_disc_2048xi_profiling")
     job = args.job_steps
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = qs.Solver(p, prec="fp32", stream=stream)
     s.seed_noise(rank, p["amplitude"])
-    if args.tune:
-        s.tune(reps=2, cache_path=os.path.join(ROOT, "paper_2607_24234_b300", "tune_cache.json"))
+    if args.shape:
+        variant, prefetch, warps = (int(x) for x in args.shape.split(","))
+        s.set_launch(warps_per_cta=warps, prefetch=prefetch, persistent=0, ctas_per_sm=8, variant=variant)
+    elif args.tune:
+        # trials of tune_reps steps per call: long enough that the resident
+        # variant's one-off state load and store is amortised as in a job
+        s.tune(reps=args.tune_reps, cache_path=os.path.join(ROOT, "paper_2607_24234_b300", "tune_cache.json"))
     launch = s.get_launch()
     M, N = s.n_modes, p["n_xi"]
     upd_job = M * N * job
@@ -365,14 +413,21 @@ def run_ours(args):
     ms_per_step = 1e3 * total_s / args.steps
     avg_launch_s = float(np.mean(kern_ms)) / 1e3
     pk, pk_kind = peaks()
-    achieved = BYTES_PER_UPDATE_FP32 * upd_job / avg_launch_s / 1e9
+    resident = launch.get("variant") == VARIANT_RESIDENT
     traffic = None
     try:
-        tj = json.load(open(TRAFFIC_FILE))
-        if tj.get("kernel_sha256_16") == kernel_hash():
-            traffic = tj["dram_bytes_per_update"] * upd_job
+        if resident:
+            tj = json.load(open(RES_TRAFFIC_FILE))
+            if tj.get("kernel_sha256_16") == kernel_hash(KERNEL_SRC, RESIDENT_SRC):
+                # one load and one store of the state per launch, whatever the step count
+                traffic = tj["dram_bytes_per_line_cell"] * M * N
+        else:
+            tj = json.load(open(TRAFFIC_FILE))
+            if tj.get("kernel_sha256_16") == kernel_hash():
+                traffic = tj["dram_bytes_per_update"] * upd_job
     except Exception:
         pass
+    roofline = sweep_roofline(launch, upd_job, avg_launch_s, traffic, pk, pk_kind)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -445,12 +500,7 @@ def run_ours(args):
                        "l2": "state 1.7 GB > 126 MB L2 (no flush needed)",
                        "parallelism": f"replicas x{ws}", "launch": launch,
                        "error_vs_oracle": "<= 1e-3 in log-amplitude, fitted rates <= 0.5% (tests)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                         "peak_source": pk_kind,
-                         "algorithmic_bytes_per_update": BYTES_PER_UPDATE_FP32,
-                         "kernel": ("qsk::k_sweep_tma<float,1,C,ST>" if launch.get("variant") == 1
-                                    else "qsk::k_sweep<float,1,U,false>")},
+            "roofline": roofline,
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "fp64": fp64,
             "cpu_baseline": cpu, "wall_s": wall,
         }
@@ -473,6 +523,11 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (use the library's default launch shape)")
+    ap.add_argument("--tune-reps", type=int, default=64, help="slow-time steps per autotuner trial")
+    ap.add_argument("--shape", default=None,
+                    help="force the launch shape 'variant,prefetch,warps_per_cta' (no autotuner)")
+    ap.add_argument("--nk", type=int, default=None,
+                    help="k grid of nk x nk instead of 256 x 256 (small cases for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default="beam3d", choices=["beam3d", "batch", "surrogate", "narrow"])
     ap.add_argument("--narrow-steps", type=int, default=20)

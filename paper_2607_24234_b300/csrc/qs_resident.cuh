@@ -37,6 +37,10 @@ constexpr int RES_MAX_WARPS = 16;   // T <= 512
 constexpr int RES_SPAN = 96;
 constexpr int RES_HYST = 16;
 constexpr int RES_NONE = -(1 << 20);   // exponent of a thread that holds no value yet
+#ifndef QS_RES_REGS64
+#define QS_RES_REGS64 128
+#endif
+constexpr int RES_REGS64 = QS_RES_REGS64;   // register cap of the 64-thread shared-Theta kernel
 constexpr int RES_WSTRIDE = 512;       // shared-memory row of the cell weights (max threads)
 
 struct RotF { float c, s; };
@@ -77,7 +81,7 @@ __device__ __forceinline__ float p2(int e) { return __int_as_float((max(-127, mi
 // budget; the CTA then has exactly TT threads (compile-time row stride).
 // TT = 0 keeps Theta in registers and only the weights in shared memory.
 template <int NS, int V, int TT>
-__global__ void __launch_bounds__(TT > 0 ? TT : 512, 512 / (TT > 0 ? TT : 512)) k_sweep_res(const SweepArgs a) {
+__global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const SweepArgs a) {
     constexpr bool THS = TT > 0;
     static_assert(GRP % V == 0, "a thread's cells lie in one exponent group");
     constexpr unsigned FULL = 0xffffffffu;
