@@ -37,10 +37,7 @@ constexpr int RES_MAX_WARPS = 16;   // T <= 512
 constexpr int RES_SPAN = 96;
 constexpr int RES_HYST = 16;
 constexpr int RES_NONE = -(1 << 20);   // exponent of a thread that holds no value yet
-#ifndef QS_RES_REGS64
-#define QS_RES_REGS64 128
-#endif
-constexpr int RES_REGS64 = QS_RES_REGS64;   // register cap of the 64-thread shared-Theta kernel
+constexpr int RES_REGS64 = 128;       // register cap of the 64-thread shared-Theta kernel (96..224 measured: 128 best)
 constexpr int RES_WSTRIDE = 512;       // shared-memory row of the cell weights (max threads)
 
 struct RotF { float c, s; };
@@ -85,7 +82,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
     constexpr bool THS = TT > 0;
     static_assert(GRP % V == 0, "a thread's cells lie in one exponent group");
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int CB = 4;                     // cells per shared-memory batch (THS)
+    constexpr int CB = 4;                     // cells per shared-memory batch (THS; 2 and 8 measured slower)
     static_assert(V % CB == 0, "whole batches");
     extern __shared__ float4 sdyn[];          // THS: Theta then w, rows [v * NS + sp][T]; else w [v * NS + sp][RES_WSTRIDE]
     __shared__ float4 sZ[2][RES_MAX_WARPS];   // inclusive warp aggregate (lane 31)
@@ -237,6 +234,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
             if (front1) n = rho(0);   // equilibrium front: n_p = rho, n_p' = 0 at xi = 0
         };
         const float2 C2 = F2(c), S2 = F2(s), NS2 = F2(-s), M1 = F2(-1.f);
+
         // exact cell propagator of Eq. (5): u = n - rho, n <- c u + s n' + rho,
         // n' <- -s u + c n'
         auto cross = [&](float2 &n, float2 &d, const float2 u, const float2 r) {

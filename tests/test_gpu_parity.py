@@ -540,7 +540,7 @@ def test_beam3d_full_size_sampled(qs, prec):
     with torch.cuda.stream(st):
         s = qs.Solver(p, prec=prec, stream=st)
         s.seed_noise(0, 1e-6)
-        s.tune(reps=1)
+        s.tune(reps=64)          # the trial length bench.py tunes with
         s.step(p["n_steps"])
         s.sync()
         mm = s.split_snapshot(s.diag(qs.REC_MODEMAX), qs.REC_MODEMAX)["modemax"][:, 0, :s.n_modes]

@@ -172,3 +172,30 @@ def test_launch_validation(qs):
     with pytest.raises(qs.QSError):
         s.set_launch(**_res(16, 4))     # FP32 only
     s.close()
+
+
+def test_beam3d_full_size_sampled_resident(qs):
+    """The benchmark workload at full size (51,468 modes x 2048 cells x 2000
+    steps in one call) in the benchmark's tuned shape (32 cells per thread,
+    64-thread CTAs): sampled mode lines against the oracle, and every mode
+    through the k/-k pairing of the per-mode maxima (bitwise)."""
+    import torch
+    p = synth.BEAM_3D
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = qs.Solver(p, prec="fp32", stream=st)
+        s.set_launch(**_res(32, 2))
+        s.seed_noise(0, 1e-6)
+        s.step(p["n_steps"])
+        s.sync()
+        mm = s.split_snapshot(s.diag(qs.REC_MODEMAX), qs.REC_MODEMAX)["modemax"][:, 0, :s.n_modes]
+        md = oracle.modes(p)
+        sel = np.sort(np.random.default_rng(12).choice(s.n_modes, 12, replace=False))
+        nb, th = s.state_arrays(modes=sel)
+        s.close()
+    pos = {int(i): j for j, i in enumerate(md["mode_id"])}
+    partner = np.array([pos[int(q)] for q in md["partner_id"]])
+    assert np.array_equal(mm, mm[:, partner])
+    nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, mode_sel=sel)
+    oracle.sweep(p, nb_o, th_o, 0, p["n_steps"], k2=md["k2"][sel])
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
