@@ -429,6 +429,27 @@ def run_ours(args):
         pass
     roofline = sweep_roofline(launch, upd_job, avg_launch_s, traffic, pk, pk_kind)
 
+    # ---- diagnostics on: per-mode maxima recorded every diag_stride steps ----
+    diag_on = None
+    if args.diag_stride > 0 and args.steps > 0:
+        s.seed_noise(rank, p["amplitude"])
+        n_snap = (job - 1) // args.diag_stride + 1
+        s.record(qs.REC_MODEMAX, args.diag_stride, n_snap)
+        n1 = s.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        s.step(job)
+        e1.record(stream)
+        barrier()
+        d_s = e0.elapsed_time(e1) / 1e3
+        s.record(0, 1, 0)
+        dv, _ = aggregate(ws, upd_job, d_s, reduce_max)
+        diag_on = {"value": dv, "unit": UNIT, "ms_per_job": 1e3 * d_s,
+                   "record": f"per-mode maxima of |dn_b|, |dE|, |dB| every {args.diag_stride} steps "
+                             f"({n_snap} snapshots per job, written on the device)",
+                   "gpu_launches": s.launch_count() - n1}
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if args.e2e and args.steps > 0:
@@ -501,7 +522,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}", "launch": launch,
                        "error_vs_oracle": "<= 1e-3 in log-amplitude, fitted rates <= 0.5% (tests)"},
             "roofline": roofline,
-            "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "fp64": fp64,
+            "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "diag_on": diag_on, "fp64": fp64,
             "cpu_baseline": cpu, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
@@ -529,6 +550,8 @@ def main():
     ap.add_argument("--nk", type=int, default=None,
                     help="k grid of nk x nk instead of 256 x 256 (small cases for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--diag-stride", type=int, default=100,
+                    help="record cadence of the diag-on job (0: skip it)")
     ap.add_argument("--workload", default="beam3d", choices=["beam3d", "batch", "surrogate", "narrow"])
     ap.add_argument("--narrow-steps", type=int, default=20)
     ap.add_argument("--sur-train-inst", type=int, default=64)

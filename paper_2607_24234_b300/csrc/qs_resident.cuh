@@ -91,6 +91,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
     __shared__ int s_item;
     __shared__ float2 sRk[6];                 // R^(V 2^k), k = 0..4, and R^(32 V)
     __shared__ float2 sRl[32];                // R^(V lane)
+    __shared__ double sMM[RES_MAX_WARPS][3];  // per-warp log maxima of a recording step
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = THS ? TT : (int)blockDim.x, nw = T >> 5;
     float2 *sT = reinterpret_cast<float2 *>(sdyn) + tid;                      // THS: row stride T = TT
@@ -254,8 +255,15 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
         // B rho, n_b += dt n_b0 Theta; one species folds n_mid = ch u + sh n' +
         // rho into the coefficients (Ach u + Ash n' + (A - B) rho).  GM: track
         // the chunk's largest magnitude for the renormalisation.
-        auto pass2 = [&](auto gm_tag, float2 n, float2 d, const float *A, const float *B) {
+        // REC: also the per-mode maxima of |n_b|^2, |E|^2 = kappa^2 |n_p'|^2 +
+        // k^2 kappa^2 |n_p - rho|^2 and |B|^2 = k^2 kappa^2 |rho|^2 at the cell
+        // centres, before the push (the fields of Eq. 14).  UPD = false: fields
+        // only, the state is not changed.
+        auto pass2 = [&](auto gm_tag, auto rec_tag, auto upd_tag, float2 n, float2 d, const float *A,
+                         const float *B, float *mx, const float *rc) {
             constexpr bool GM = decltype(gm_tag)::value;
+            constexpr bool REC = decltype(rec_tag)::value;
+            constexpr bool UPD = decltype(upd_tag)::value;
             float gmax = 0.f;
             const float2 Ach = F2(A[0] * ch), Ash = F2(A[0] * sh), AB = F2(A[0] - B[0]);
             const float2 CH2 = F2(ch), SH2 = F2(sh);
@@ -278,9 +286,22 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                     const float2 r = rho(v);
                     const float2 uu = pfma(M1, r, n);
                     float2 m = F2(0.f);
-                    if (NS == 2) m = pfma(CH2, uu, pfma(SH2, d, r));
+                    if (NS == 2 || REC) m = pfma(CH2, uu, pfma(SH2, d, r));
+                    if (REC && jb + v < N) {   // cells past the end of the line do not count
+                        const float2 md = pfma(F2(-sh), uu, pmul(CH2, d));     // n_p' at the centre
+                        const float2 ep = pfma(M1, r, m);                      // n_p - rho
+                        // rc = (kappa^2, k^2 kappa^2, 1/q_s^2): registers hold q_s n_bs
+                        float nb2 = 0.f;
+#pragma unroll
+                        for (int sp = 0; sp < NS; ++sp)
+                            nb2 = fmaf(rc[2 + sp], fmaf(xn[v][sp].x, xn[v][sp].x, xn[v][sp].y * xn[v][sp].y), nb2);
+                        const float e2 = fmaf(rc[0], fmaf(md.x, md.x, md.y * md.y), rc[1] * fmaf(ep.x, ep.x, ep.y * ep.y));
+                        const float b2 = rc[1] * fmaf(r.x, r.x, r.y * r.y);
+                        mx[0] = fmaxf(mx[0], nb2); mx[1] = fmaxf(mx[1], e2); mx[2] = fmaxf(mx[2], b2);
+                    }
 #pragma unroll
                     for (int sp = 0; sp < NS; ++sp) {
+                        if constexpr (!UPD) continue;
                         float2 &y = xn[v][sp];
                         float2 &th = THS ? zt[THS ? u : 0][sp] : xt[THS ? 0 : v][sp];
                         const float wv = THS ? zw[THS ? u : 0][sp] : sWr[(v * NS + sp) * RES_WSTRIDE];
@@ -291,7 +312,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                     }
                     cross(n, d, uu, r);
                 }
-                if constexpr (THS) {
+                if constexpr (THS && UPD) {
 #pragma unroll
                     for (int u = 0; u < CB; ++u)
 #pragma unroll
@@ -365,17 +386,68 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
             }
             // ---- pass 2; every 4th step also the renormalisation (growth over
             // 4 steps stays far inside the 2^RES_SPAN headroom)
-            if ((it & 3) == 3) {
-                const float gmax = pass2(std::integral_constant<bool, true>(), n, d, A, B);
-                if (gmax > 0.f) {
-                    const int ex = expof(gmax);
-                    const int sx = clamp_shift(ex == -200 ? -126 : ex);
-                    if (sx > RES_HYST || sx < -RES_HYST) { scale_chunk(p2(-sx)); e += sx; }
+            using Y_ = std::integral_constant<bool, true>;
+            using N_ = std::integral_constant<bool, false>;
+            long long snap = -1;   // recording step (per-mode maxima), uniform over the CTA
+            if (a.rec_kinds & 4) {
+                const long long dg = a.step0 + it - a.rec_g0;
+                if (dg >= 0 && dg % a.rec_stride == 0 && dg / a.rec_stride < a.rec_max_snap) snap = dg / a.rec_stride;
+            }
+            float gmax = 0.f;
+            if (snap >= 0) {
+                float mx[3] = {0.f, 0.f, 0.f};
+                float rc[2 + NS];
+                {
+                    const int2 ix = a.items[item];
+                    const int mr = min(ix.y + slot, a.M - 1);
+                    const double kp = a.kap[mr], ka = a.kabs[mr];
+                    rc[0] = (float)(kp * kp);
+                    rc[1] = (float)(ka * ka * kp * kp);
+#pragma unroll
+                    for (int sp = 0; sp < NS; ++sp) {
+                        const double qq = a.inst[ix.x].q[sp];
+                        rc[2 + sp] = (float)(1.0 / (qq * qq));
+                    }
                 }
+                const int e_rec = e;
+                if (a.update) gmax = pass2(Y_(), Y_(), Y_(), n, d, A, B, mx, rc);
+                else pass2(N_(), Y_(), N_(), n, d, A, B, mx, rc);
+                // thread maxima as logs (mantissa log + exponent), then the line's maximum
+                double lg[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    lg[i] = (has && mx[i] > 0.f) ? 0.5 * log((double)mx[i]) + e_rec * 0.69314718055994530942 : -INFINITY;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) lg[i] = fmax(lg[i], __shfl_xor_sync(FULL, lg[i], o));
+                }
+                if (lane == 0) { sMM[warp][0] = lg[0]; sMM[warp][1] = lg[1]; sMM[warp][2] = lg[2]; }
+                __syncthreads();
+                if (live && t == 0) {
+                    double L0 = -INFINITY, L1 = -INFINITY, L2 = -INFINITY;
+                    for (int ww = w0; ww < wend; ++ww) {
+                        L0 = fmax(L0, sMM[ww][0]); L1 = fmax(L1, sMM[ww][1]); L2 = fmax(L2, sMM[ww][2]);
+                    }
+                    double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)itx.x * a.Mp + mode;
+                    const long long pl = (long long)a.n_inst * a.Mp;
+                    o[0] = L0; o[pl] = L1; o[2 * pl] = L2;
+                }
+                __syncthreads();   // sMM is reused at the next recording step
+            } else if ((it & 3) == 3) {
+                gmax = pass2(Y_(), N_(), Y_(), n, d, A, B, nullptr, nullptr);
             } else {
-                pass2(std::integral_constant<bool, false>(), n, d, A, B);
+                pass2(N_(), N_(), Y_(), n, d, A, B, nullptr, nullptr);
+            }
+            if (gmax > 0.f) {
+                const int ex = expof(gmax);
+                const int sx = clamp_shift(ex == -200 ? -126 : ex);
+                if (sx > RES_HYST || sx < -RES_HYST) { scale_chunk(p2(-sx)); e += sx; }
             }
             buf ^= 1;
+        }
+        if (!a.update) {   // field pass: nothing to write back
+            if (!a.persistent) break;
+            __syncthreads();
+            continue;
         }
 
         // write back: the threads of a 32-cell group agree on one exponent

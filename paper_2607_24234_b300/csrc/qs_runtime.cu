@@ -456,8 +456,10 @@ qs_status launch_resident(qs_ctx *c, long long step0, int n_steps, int update, i
         c->launch = keep;
         return r;
     };
-    if (!update) return fallback(step0, n_steps, 0);
-    const bool recording = rec && rec_kinds;
+    // the per-mode maxima are computed on chip; full field snapshots are not
+    const bool mm_only = rec && rec_kinds == QS_REC_MODEMAX;
+    if (!update && !mm_only) return fallback(step0, n_steps, 0);
+    const bool recording = rec && rec_kinds && !mm_only;
     const long long end = step0 + n_steps;
     long long cur = step0;
     while (cur < end) {
@@ -470,7 +472,9 @@ qs_status launch_resident(qs_ctx *c, long long step0, int n_steps, int update, i
         if (r > cur) {
             qs_status s = build_res_items(c);
             if (s) return s;
-            SweepArgs a = sweep_args(c, cur, (int)(r - cur), 1, 0, nullptr, 0, 1, 0);
+            SweepArgs a = mm_only ? sweep_args(c, cur, (int)(r - cur), update, rec_kinds, rec, rec_g0, rec_stride,
+                                               rec_max_snap)
+                                  : sweep_args(c, cur, (int)(r - cur), 1, 0, nullptr, 0, 1, 0);
             a.items = c->res_items_d;
             a.n_items = c->n_res_items;
             const int T = 32 * c->launch.warps_per_cta;

@@ -199,3 +199,39 @@ def test_beam3d_full_size_sampled_resident(qs):
     nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, mode_sel=sel)
     oracle.sweep(p, nb_o, th_o, 0, p["n_steps"], k2=md["k2"][sel])
     assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+
+
+@pytest.mark.parametrize("n_xi,V,w,species", [
+    (700, 32, 2, [(-1.0, 1.0, 0.05)]),                      # one warp per line, ragged tail
+    (2100, 32, 4, [(-1.0, 1.0, 0.05)]),                     # three warps per line (cross-warp maximum)
+    (300, 16, 4, [(-1.0, 1.0, 0.03), (1.0, 1836.0, 0.05)]),  # two species, Theta in shared memory
+])
+def test_modemax_on_chip(qs, n_xi, V, w, species):
+    """Per-mode maxima of |dn_b|, |dE|, |dB| recorded every 7 steps inside
+    the resident kernel, and a read-only maxima pass at the end, against the
+    oracle's fields (maxima over the real cells only)."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=n_xi, dxi=0.05, length=n_xi * 0.05, k_list=[0.5, 1.5, 3.0, 6.0],
+                     species=species, gamma_b=20.0, dt=1.5)
+    steps, stride = 40, 7
+    n_snap = (steps - 1) // stride + 1
+    s = qs.Solver(p, prec="fp32")
+    s.set_launch(**_res(V, w))
+    s.seed_noise(9, 1e-6)
+    buf = s.record(qs.REC_MODEMAX, stride, n_snap)
+    n0 = s.launch_count()
+    s.step(steps)
+    s.sync()
+    assert s.launch_count() - n0 == 1          # no split: the maxima are taken on chip
+    rec = buf.cpu().numpy().reshape(n_snap, -1)
+    s.record(0, 1, 0)
+    fin = s.split_snapshot(s.diag(qs.REC_MODEMAX), qs.REC_MODEMAX)["modemax"][:, 0, :s.n_modes]
+    mms = [s.split_snapshot(rec[i], qs.REC_MODEMAX)["modemax"][:, 0, :s.n_modes] for i in range(n_snap)]
+    s.close()
+    nb_o, th_o = oracle.seed_noise(p, 9, 1e-6)
+    ro = oracle.sweep(p, nb_o, th_o, 0, steps, rec_stride=stride)
+    fo = oracle.fields(p, nb_o)
+    for i, mm in enumerate(mms):
+        for k in range(3):
+            assert np.max(np.abs(mm[k] - np.log(ro["mag"][i, k].max(axis=1)))) <= FP32_LOG_TOL, (i, k)
+    for k in range(3):
+        assert np.max(np.abs(fin[k] - np.log(fo["mag"][k].max(axis=1)))) <= FP32_LOG_TOL, k
