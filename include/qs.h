@@ -249,6 +249,25 @@ qs_status qs_tune(qs_ctx *ctx, int reps, const char *cache_path);
  * launch it.  Semantics as qs_step.  The record target must be detached. */
 qs_status qs_step_graph(qs_ctx *ctx, int n_steps);
 
+/* Green's-function path: advance the state by n_steps slow-time steps as a
+ * causal convolution in xi (Sec. III.A's Green's-function picture, for the
+ * discrete scheme).  For a uniform profile (the same dt n_bs0 in every cell
+ * of an instance) and a quiescent front each step is linear, causal and
+ * shift-invariant in xi with real coefficients, so n steps map every mode by
+ * x_n(j) = sum_{l<=j} G_n(l) x_0(j - l), G_n the response to a unit impulse at
+ * cell 0, which depends on the mode only through k^2.  The library sweeps
+ * one impulse line per (k^2 class, input component) through the resident
+ * FP32 kernel (Theta impulses only when Theta is not identically zero, i.e.
+ * after any step or an impulse / checkpoint seed) and convolves every mode
+ * with its class's responses.  Results agree with qs_step to FP32 accuracy
+ * (not bitwise).  FP32 contexts only; QS_ERR_UNSUPPORTED for FP64, a
+ * non-uniform profile, a front other than QS_FRONT_QUIESCENT, lines too long
+ * for the resident kernel (> 8192 cells) or a convolution that does not fit
+ * shared memory; QS_ERR_ARG with a record target attached.  Allocates
+ * impulse-line buffers and a second state buffer on the first call (kept
+ * until qs_free). */
+qs_status qs_step_green(qs_ctx *ctx, int n_steps);
+
 /* Wait for the stream and report device-side errors. */
 qs_status qs_sync(qs_ctx *ctx);
 

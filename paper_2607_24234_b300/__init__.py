@@ -31,7 +31,7 @@ Q_N_MODES, Q_MODES_PADDED, Q_N_INST, Q_TOTAL_CELLS, Q_STEP, Q_STATE_BYTES, Q_SNA
     Q_CELL_OFFSET, Q_LAUNCH = range(9)
 
 EXPORTS = ["qs_init", "qs_seed", "qs_step", "qs_record", "qs_diag", "qs_query", "qs_modes",
-           "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_sync",
+           "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_step_green", "qs_sync",
            "qs_launch_count", "qs_last_error", "qs_free"]
 
 
@@ -90,6 +90,7 @@ def _load():
     L.qs_get_launch.argtypes = [vp, ctypes.POINTER(Launch)]
     L.qs_tune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p]
     L.qs_step_graph.argtypes = [vp, ctypes.c_int]
+    L.qs_step_green.argtypes = [vp, ctypes.c_int]
     L.qs_sync.argtypes = [vp]
     L.qs_debug_waits.argtypes = [vp, i64, ctypes.c_int]
     L.qs_debug_waits.restype = ctypes.c_int
@@ -103,7 +104,7 @@ def _load():
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
     L.qs_sweep_noalloc.restype = ctypes.c_int
     for name in ("qs_init", "qs_seed", "qs_step", "qs_record", "qs_diag", "qs_query", "qs_modes",
-                 "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_sync"):
+                 "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_step_green", "qs_sync"):
         getattr(L, name).restype = ctypes.c_int
     return L
 
@@ -265,6 +266,10 @@ class Solver:
 
     def step_graph(self, n: int = 1):
         self._chk(lib.qs_step_graph(self.ctx, int(n)))
+
+    def step_green(self, n: int = 1):
+        """n steps by the Green's-function path (uniform beams, quiescent front, FP32)."""
+        self._chk(lib.qs_step_green(self.ctx, int(n)))
 
     def sync(self):
         self._chk(lib.qs_sync(self.ctx))

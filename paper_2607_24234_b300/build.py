@@ -11,7 +11,7 @@ SO = os.path.join(HERE, "libqs.so")
 SRCS = [os.path.join(HERE, "csrc", "qs_runtime.cu"), os.path.join(HERE, "csrc", "qs_noalloc.cu"),
         os.path.join(HERE, "csrc", "qs_mlp.cu"),
         os.path.join(HERE, "csrc", "qs_real2.cu")]
-DEPS = SRCS + [os.path.join(HERE, "csrc", f) for f in ("qs_kernels.cuh", "qs_resident.cuh", "qs_tune.inc", "qs_surdata.inc")] + \
+DEPS = SRCS + [os.path.join(HERE, "csrc", f) for f in ("qs_kernels.cuh", "qs_resident.cuh", "qs_tune.inc", "qs_green.inc", "qs_surdata.inc")] + \
     [os.path.join(ROOT, "include", "qs.h"), os.path.abspath(__file__)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

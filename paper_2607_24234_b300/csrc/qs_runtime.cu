@@ -56,6 +56,15 @@ struct qs_ctx {
     InstDev *inst_d = nullptr;
     int2 *items_d = nullptr;
     int n_items = 0;
+    // Green's-function path (qs_green.inc)
+    bool uniform = false;           // every instance: the same dt n_bs0 in every cell
+    bool theta_zero = false;        // Theta == 0 everywhere (fresh noise or user seed)
+    std::vector<int> g_class_of, g_rep, g_mem_off, g_mem_mode;
+    void *g_st = nullptr, *g_out = nullptr;
+    int *g_ex = nullptr, *g_oex = nullptr, *g_mem_off_d = nullptr, *g_mem_mode_d = nullptr;
+    double *g_kap = nullptr, *g_kapk2 = nullptr, *g_kabs = nullptr;
+    int2 *g_items = nullptr;
+    int g_n_items = 0, g_cap = 0;
     int2 *res_items_d = nullptr;    // resident variant: one item per CTA's lines
     int n_res_items = 0;
     long long res_key = -1;
@@ -640,10 +649,13 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
                 I.q[s] = 0.0; I.qm_g[s] = 0.0; I.qm_g3[s] = 0.0;
             }
         }
+        bool uni = true;
         for (int j = 0; j < q.n_xi; ++j) {
             shape_all.push_back(shp[j]);
             for (int s = 0; s < c->NS; ++s) w_all.push_back(q.dt * q.species[s].density_ratio * shp[j]);
+            uni = uni && shp[j] == shp[0];
         }
+        c->uniform = (i == 0 || c->uniform) && uni;
         cell += q.n_xi;
         grp += I.n_grp;
     }
@@ -793,6 +805,7 @@ qs_status qs_seed(qs_ctx *c, uint64_t seed, double amplitude, int kind, const vo
     }
     CU(c, cudaMemsetAsync(c->err_d, 0, 4 * sizeof(int), c->stream));
     c->seeded = true;
+    c->theta_zero = kind == QS_SEED_NOISE || kind == QS_SEED_USER;   // these seeds leave Theta = 0
     c->poisoned = false;
     return QS_OK;
 }
@@ -818,6 +831,7 @@ qs_status qs_step(qs_ctx *c, int n_steps) {
                      static_cast<double *>(c->rec_buf), c->rec_g0, c->rec_stride, max_snap);
     if (s) return s;
     c->step += n_steps;
+    c->theta_zero = false;
     return QS_OK;
 }
 
@@ -1050,4 +1064,5 @@ void qs_free(qs_ctx *c) {
 }  // extern "C"
 
 #include "qs_tune.inc"
+#include "qs_green.inc"
 #include "qs_surdata.inc"
