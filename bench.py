@@ -82,7 +82,8 @@ def sweep_roofline(launch, upd, launch_s, traffic, pk, pk_kind):
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (an FMA is one op; "
                                "a packed f32x2 instruction is two)",
                 "algorithmic_fp32_ops_per_update": FP32_INSTR_PER_UPDATE,
-                "kernel": f"qsk::k_sweep_res<1,{launch.get('prefetch')},{32 * launch.get('warps_per_cta')}>",
+                "kernel": f"qsk::k_sweep_res<1,{launch.get('prefetch')},T> (CTA of T <= {32 * launch.get('warps_per_cta')} "
+                          "threads: a whole number of lines)",
                 "streaming_equivalent_gbs": hbm_view,
                 "streaming_equivalent_frac_of_hbm": hbm_view / pk["hbm_gbs"],
                 "note": "lines held on chip for the whole job: HBM is read and written once per launch"}

@@ -68,6 +68,8 @@ struct qs_ctx {
     int2 *res_items_d = nullptr;    // resident variant: one item per CTA's lines
     int n_res_items = 0;
     long long res_key = -1;
+    struct ResGroup { int threads, first, count; };
+    std::vector<ResGroup> res_groups;   // instances sharing one CTA size, one launch each
     double *kap_d = nullptr, *kapk2_d = nullptr, *kabs_d = nullptr, *held_d = nullptr;
     void *w_d = nullptr;
     double *shape_d = nullptr, *dens_d = nullptr;
@@ -240,22 +242,42 @@ int max_nxi(const qs_ctx *c) {
 // threads holding one line in the resident variant (whole warps)
 int res_threads_per_line(int n_xi, int V) { return ((n_xi + V - 1) / V + 31) & ~31; }
 
-// Resident variant: an item is (instance, first mode) for the T / Tl
-// consecutive lines one CTA holds; instances longest first when persistent.
+// CTA size of the resident variant for lines needing tl threads, at most
+// Tmax: a whole number of lines (so no thread idles beyond the warp rounding
+// of a line)
+int res_cta_threads(int tl, int Tmax) { return tl * std::max(1, Tmax / tl); }
+// exact CTA sizes exist for every variant but two species at 16 cells per
+// thread (Theta in shared memory, CTA of 128 | 256 | 512 threads only)
+bool res_exact_sizes(int NS, int V) { return !(NS == 2 && V == 16); }
+
+// Resident variant: an item is (instance, first mode) for the lines one CTA
+// holds.  Instances are grouped by CTA size (one launch per group), longest
+// lines first within a group when persistent.
 qs_status build_res_items(qs_ctx *c) {
-    const int V = c->launch.prefetch, T = 32 * c->launch.warps_per_cta, P = c->launch.persistent;
-    const long long key = ((long long)V << 32) | ((long long)T << 1) | P;
+    const int V = c->launch.prefetch, Tmax = 32 * c->launch.warps_per_cta, P = c->launch.persistent;
+    const long long key = ((long long)V << 32) | ((long long)Tmax << 1) | P;
     if (c->res_key == key && c->res_items_d) return QS_OK;
     std::vector<int> order(c->n_inst);
     for (int i = 0; i < c->n_inst; ++i) order[i] = i;
-    if (P)
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int a, int b) { return c->inst[a].n_xi > c->inst[b].n_xi; });
-    std::vector<int2> items;
+    std::map<int, std::vector<int>> by_t;   // CTA size -> instances
     for (int i : order) {
-        const int L = T / res_threads_per_line(c->inst[i].n_xi, V);
-        if (L < 1) return fail(c, QS_ERR_ARG, "resident: a line of instance %d needs more than %d threads", i, T);
-        for (int m = 0; m < c->M; m += L) items.push_back(make_int2(i, m));
+        const int tl = res_threads_per_line(c->inst[i].n_xi, V);
+        if (tl > Tmax) return fail(c, QS_ERR_ARG, "resident: a line of instance %d needs more than %d threads", i, Tmax);
+        by_t[res_exact_sizes(c->NS, V) ? res_cta_threads(tl, Tmax) : Tmax].push_back(i);
+    }
+    std::vector<int2> items;
+    c->res_groups.clear();
+    for (auto &g : by_t) {
+        std::vector<int> &inst = g.second;
+        if (P)
+            std::stable_sort(inst.begin(), inst.end(),
+                             [&](int a, int b) { return c->inst[a].n_xi > c->inst[b].n_xi; });
+        const int first = (int)items.size();
+        for (int i : inst) {
+            const int L = g.first / res_threads_per_line(c->inst[i].n_xi, V);
+            for (int m = 0; m < c->M; m += L) items.push_back(make_int2(i, m));
+        }
+        c->res_groups.push_back({g.first, first, (int)items.size() - first});
     }
     if (!c->res_items_d) {
         qs_status s = dalloc_t(c, (size_t)c->n_inst * c->M * sizeof(int2), &c->res_items_d);
@@ -433,14 +455,22 @@ cudaError_t launch_res_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) 
 // species (CTA of 64 | 128 | 256) and 16 of two (CTA of 128 | 256 | 512)
 cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V) {
     if (c->NS == 1) {
-        if (V == 32) return T == 64 ? launch_res_t<1, 32, 64>(c, a, grid, T)
-                          : T == 128 ? launch_res_t<1, 32, 128>(c, a, grid, T)
-                                     : launch_res_t<1, 32, 256>(c, a, grid, T);
+        if (V == 32) switch (T) {   // every whole number of 64-thread lines up to 4, and 96 .. 224 for 96-thread lines
+            case 64: return launch_res_t<1, 32, 64>(c, a, grid, T);
+            case 96: return launch_res_t<1, 32, 96>(c, a, grid, T);
+            case 128: return launch_res_t<1, 32, 128>(c, a, grid, T);
+            case 160: return launch_res_t<1, 32, 160>(c, a, grid, T);
+            case 192: return launch_res_t<1, 32, 192>(c, a, grid, T);
+            case 224: return launch_res_t<1, 32, 224>(c, a, grid, T);
+            case 256: return launch_res_t<1, 32, 256>(c, a, grid, T);
+            default: return cudaErrorInvalidValue;   // no kernel for this CTA size
+            }
         return V == 16 ? launch_res_t<1, 16, 0>(c, a, grid, T) : launch_res_t<1, 8, 0>(c, a, grid, T);
     }
     if (V == 16) return T == 128 ? launch_res_t<2, 16, 128>(c, a, grid, T)
                       : T == 256 ? launch_res_t<2, 16, 256>(c, a, grid, T)
-                                 : launch_res_t<2, 16, 512>(c, a, grid, T);
+                      : T == 512 ? launch_res_t<2, 16, 512>(c, a, grid, T)
+                                 : cudaErrorInvalidValue;
     return launch_res_t<2, 8, 0>(c, a, grid, T);
 }
 
@@ -484,18 +514,19 @@ qs_status launch_resident(qs_ctx *c, long long step0, int n_steps, int update, i
             SweepArgs a = mm_only ? sweep_args(c, cur, (int)(r - cur), update, rec_kinds, rec, rec_g0, rec_stride,
                                                rec_max_snap)
                                   : sweep_args(c, cur, (int)(r - cur), 1, 0, nullptr, 0, 1, 0);
-            a.items = c->res_items_d;
-            a.n_items = c->n_res_items;
-            const int T = 32 * c->launch.warps_per_cta;
-            dim3 grid(c->n_res_items);
-            if (a.persistent) {
-                CU(c, cudaMemsetAsync(c->ticket_d, 0, sizeof(int), c->stream));
-                const long long g = (long long)c->launch.ctas_per_sm * c->n_sm;
-                grid = dim3((unsigned)std::max<long long>(1, std::min<long long>(g, c->n_res_items)));
+            for (const auto &grp : c->res_groups) {   // one launch per CTA size
+                a.items = c->res_items_d + grp.first;
+                a.n_items = grp.count;
+                dim3 grid(grp.count);
+                if (a.persistent) {
+                    CU(c, cudaMemsetAsync(c->ticket_d, 0, sizeof(int), c->stream));
+                    const long long g = (long long)c->launch.ctas_per_sm * c->n_sm;
+                    grid = dim3((unsigned)std::max<long long>(1, std::min<long long>(g, grp.count)));
+                }
+                cudaError_t e = launch_res(c, a, grid, grp.threads, c->launch.prefetch);
+                if (e != cudaSuccess) return fail(c, QS_ERR_CUDA, "resident sweep launch: %s", cudaGetErrorString(e));
+                ++c->n_launch;
             }
-            cudaError_t e = launch_res(c, a, grid, T, c->launch.prefetch);
-            if (e != cudaSuccess) return fail(c, QS_ERR_CUDA, "resident sweep launch: %s", cudaGetErrorString(e));
-            ++c->n_launch;
         }
         if (r < end) {
             qs_status s = fallback(r, 1, 1);

@@ -235,3 +235,30 @@ def test_modemax_on_chip(qs, n_xi, V, w, species):
             assert np.max(np.abs(mm[k] - np.log(ro["mag"][i, k].max(axis=1)))) <= FP32_LOG_TOL, (i, k)
     for k in range(3):
         assert np.max(np.abs(fin[k] - np.log(fo["mag"][k].max(axis=1)))) <= FP32_LOG_TOL, k
+
+
+@pytest.mark.parametrize("pers", [0, 1])
+def test_batched_exact_cta_sizes(qs, pers):
+    """Instances whose lines need 1 .. 8 warps at 32 cells per thread: one
+    launch per CTA size (256: 8, 4 or 1 lines; 192: 2 or 1; 160; 224), each
+    CTA a whole number of lines; every instance against its own oracle run."""
+    lengths = [1000, 2000, 3000, 5000, 6000, 7000, 8000]
+    base = synth.scaled(synth.BATCH_BASE, nkx=8, nky=8, dxi=0.025)
+    insts = []
+    for i, n in enumerate(lengths):
+        insts.append(synth.scaled(base, n_xi=n, length=n * 0.025, inst_seed=i,
+                                  species=[(-1.0, 1.0, 0.02 + 0.01 * i)], gamma_b=30.0 + 10 * i))
+    s = qs.Solver(insts, prec="fp32")
+    s.set_launch(**_res(32, 8, pers, 2))
+    s.seed_noise(0, 1e-6)
+    n0 = s.launch_count()
+    s.step(8)
+    s.sync()
+    assert s.launch_count() - n0 == 4        # CTA sizes 160, 192, 224, 256
+    nb, th = s.state_arrays()
+    s.close()
+    for i, p in enumerate(insts):
+        nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, inst=i)
+        oracle.sweep(p, nb_o, th_o, 0, 8)
+        assert _log_err(nb[i], nb_o) <= FP32_LOG_TOL, i
+        assert _log_err(th[i], th_o) <= FP32_LOG_TOL, i
