@@ -36,7 +36,8 @@ __device__ __forceinline__ float ld_op(const __nv_bfloat16 *X, int ld, int r, in
 enum { EPI_STORE = 0,      // C fp32 = acc
        EPI_BIAS_GELU = 1,  // Z fp32 = acc + b; H bf16 = gelu(Z)
        EPI_BIAS = 2,       // C fp32 = acc + b
-       EPI_DGELU = 3 };    // G bf16 = acc * gelu'(Z)
+       EPI_DGELU = 3,      // G bf16 = acc * gelu'(Z)
+       EPI_ATOMIC = 4 };   // C fp32 += acc (atomically; C zeroed by the caller)
 
 struct GemmArgs {
     const __nv_bfloat16 *A, *B;
@@ -50,6 +51,10 @@ struct GemmArgs {
     int ldh;
     int epi;
     int accumulate;       // C += acc (EPI_STORE only)
+    int kchunks;          // tcgen05 path: K chunks per CTA (0 or 1: one); CTA z owns
+    int Ktot;             // K columns [z kchunks K, (z + 1) kchunks K) of Ktot (zero fill past it)
+    __nv_bfloat16 *Ht;    // tcgen05 path, optional: the bf16 output H transposed, Ht[n][m] (row stride ldht)
+    int ldht;
 };
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -218,52 +223,63 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    // stage both operands with asynchronous 16-byte copies (all in flight at
-    // once; rows past M or N are zero-filled)
+    // K chunks of this CTA (one unless the caller splits a long K over z)
+    const int nk = g.kchunks > 1 ? g.kchunks : 1;
+    const long long kz = (long long)blockIdx.z * nk * K;
+    const int ktot = g.kchunks > 0 ? g.Ktot : K;
+    uint32_t ok = 1;
+    uint32_t taddr = 0;
+    for (int kc = 0; kc < nk && ok; ++kc) {
+        const long long k0 = kz + (long long)kc * K;
+        // stage both operands with asynchronous 16-byte copies (all in flight
+        // at once; rows past M or N, and columns past Ktot, are zero-filled)
 #pragma unroll 4
-    for (int i = tid; i < 128 * (K / 8); i += 128) {
-        const int r = i / (K / 8), kc = i % (K / 8);
-        const bool in = m0 + r < g.M;
-        const __nv_bfloat16 *src = g.A + (long long)(in ? m0 + r : 0) * g.lda + kc * 8;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + kc * LBO + (r % 8) * 16)),
-                     "l"(src), "r"(in ? 16 : 0) : "memory");
-    }
-#pragma unroll 4
-    for (int i = tid; i < NT * (K / 8); i += 128) {
-        const int r = i / (K / 8), kc = i % (K / 8);
-        const bool in = n0 + r < g.N;
-        const __nv_bfloat16 *src = g.B + (long long)(in ? n0 + r : 0) * g.ldb + kc * 8;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + kc * LBO + (r % 8) * 16)),
-                     "l"(src), "r"(in ? 16 : 0) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t taddr = taddr_s;
-    if (tid == 0) {
-        constexpr uint32_t id = tc::idesc_bf16(128, NT);
-#pragma unroll
-        for (int kk = 0; kk < K / 16; ++kk) {
-            const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
-            const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
-            const uint32_t acc = kk > 0 ? 1u : 0u;
-            asm volatile(
-                "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
-                "l"(ad), "l"(bd), "r"(id), "r"(acc)
-                : "memory");
+        for (int i = tid; i < 128 * (K / 8); i += 128) {
+            const int r = i / (K / 8), c8 = i % (K / 8);
+            const bool in = m0 + r < g.M && k0 + c8 * 8 < ktot;
+            const __nv_bfloat16 *src = g.A + (in ? (long long)(m0 + r) * g.lda + k0 + c8 * 8 : 0);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+                         "l"(src), "r"(in ? 16 : 0) : "memory");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
-                     : "memory");
+#pragma unroll 4
+        for (int i = tid; i < NT * (K / 8); i += 128) {
+            const int r = i / (K / 8), c8 = i % (K / 8);
+            const bool in = n0 + r < g.N && k0 + c8 * 8 < ktot;
+            const __nv_bfloat16 *src = g.B + (in ? (long long)(n0 + r) * g.ldb + k0 + c8 * 8 : 0);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+                         "l"(src), "r"(in ? 16 : 0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        taddr = taddr_s;
+        if (tid == 0) {
+            constexpr uint32_t id = tc::idesc_bf16(128, NT);
+#pragma unroll
+            for (int kk = 0; kk < K / 16; ++kk) {
+                const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
+                const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
+                const uint32_t acc = (kk > 0 || kc > 0) ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
+                         : "memory");
+        }
+        // the chunk's MMAs are done (its shared-memory operands may be reused)
+        uint32_t done = 0;
+        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(tc::su32(&bar)), "r"((uint32_t)(kc & 1)) : "memory");
+        if (!done && lane == 0) atomicOr(err, 2);
+        ok = __syncthreads_and(done);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    uint32_t ok = 0;
-    for (long long spin = 0; spin < (1LL << 24) && !ok; ++spin)
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(ok) : "r"(tc::su32(&bar)) : "memory");
-    if (!ok && lane == 0) atomicOr(err, 2);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         const int m = m0 + warp * 32 + lane;
 #pragma unroll 1
@@ -293,9 +309,13 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
                         const float4 z = *reinterpret_cast<const float4 *>(g.Z + oc + j);
                         v[j] *= dgelu(z.x); v[j + 1] *= dgelu(z.y); v[j + 2] *= dgelu(z.z); v[j + 3] *= dgelu(z.w);
                     }
-                } else if (g.epi != EPI_STORE) {
+                } else if (g.epi != EPI_STORE && g.epi != EPI_ATOMIC) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] += g.bias[nb + j];
+                }
+                if (g.epi == EPI_ATOMIC) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) atomicAdd(g.C + oc + j, v[j]);
                 }
                 if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS || g.epi == EPI_STORE) {
 #pragma unroll
@@ -314,6 +334,13 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
                             q[t] = __floats2bfloat162_rn(a0, a1);
                         }
                         *reinterpret_cast<uint4 *>(h + j) = *reinterpret_cast<const uint4 *>(q);
+                        if (g.Ht) {   // K-major copy for the weight gradient: lanes write consecutive m
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                g.Ht[(long long)(nb + j + 2 * t) * g.ldht + m] = __low2bfloat16(q[t]);
+                                g.Ht[(long long)(nb + j + 2 * t + 1) * g.ldht + m] = __high2bfloat16(q[t]);
+                            }
+                        }
                     }
                 }
             }
@@ -364,6 +391,37 @@ __global__ void k_loss(const float *out, const float *y, int n, float ymean, flo
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, l / n);
+}
+
+// column sums of a bf16 [n][cols] matrix (cols even), 32 rows per block,
+// coalesced bf16x2 loads, accumulated into out[cols] (zeroed by the caller)
+__global__ void k_colsum_tiles(const __nv_bfloat16 *g, int n, int cols, float *out) {
+    const int c2 = threadIdx.x, r0 = blockIdx.x * 32;
+    if (2 * c2 >= cols) return;
+    float sx = 0.0f, sy = 0.0f;
+    const int r1 = min(n, r0 + 32);
+    for (int r = r0; r < r1; ++r) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(g + (long long)r * cols + 2 * c2);
+        sx += __low2float(v);
+        sy += __high2float(v);
+    }
+    atomicAdd(out + 2 * c2, sx);
+    atomicAdd(out + 2 * c2 + 1, sy);
+}
+
+// dst[c][r] = src[r][c] for a bf16 [rows][cols] matrix, 32 x 32 tiles
+__global__ void k_transpose_b16(const __nv_bfloat16 *src, int rows, int cols, __nv_bfloat16 *dst) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        tile[j][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * cols + c] : __float2bfloat16(0.0f);
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) dst[(long long)c * rows + r] = tile[threadIdx.x][j];
+    }
 }
 
 // column sums of a bf16 [n][cols] matrix into fp32 out[cols]
@@ -489,6 +547,9 @@ struct qs_mlp {
     float ymean = 0.0f, ystd = 1.0f;
     float *loss = nullptr;
     __nv_bfloat16 *PT = nullptr;         // [E][nparam]: W^T copies (bf16) for dX
+    __nv_bfloat16 *TDZ = nullptr, *TACT = nullptr;   // [width][B]: dZ^T and act^T (K-major operands of dW)
+    std::vector<__nv_bfloat16 *> HT;     // per hidden layer [width][B]: H^T written by the forward epilogue
+    std::vector<char> ht_valid;          // HT[l] holds this batch (the forward ran on the tcgen05 path)
     int *errw = nullptr;                 // device error word (bounded waits)
     bool use_tc = true;
     long long step = 0;
@@ -526,21 +587,28 @@ bool gemm_tc(qs_mlp *m, const mlp::GemmArgs &g) {
     if (!m->use_tc || g.N % 128 != 0 || !(g.K == 16 || g.K == 256) || (g.lda % 8) || (g.ldb % 8) ||
         (g.ldc % 8) || (g.epi != mlp::EPI_STORE && g.epi != mlp::EPI_BIAS && g.ldh % 8))
         return false;
-    const dim3 grid((g.M + 127) / 128, g.N / 128);
-    const size_t smem = (size_t)(128 + 128) * g.K * 2;
-    if (g.K == 16) mlp::k_gemm_tc<16, 128><<<grid, 128, smem, m->stream>>>(g, m->errw);
-    else mlp::k_gemm_tc<256, 128><<<grid, 128, smem, m->stream>>>(g, m->errw);
+    if (g.K == 16) {
+        mlp::k_gemm_tc<16, 128><<<dim3((g.M + 127) / 128, g.N / 128), 128, (size_t)(128 + 128) * 16 * 2, m->stream>>>(
+            g, m->errw);
+    } else {
+        // 128 x 64 output tiles: 96 KB of operands, two CTAs per SM overlap one
+        // CTA's loads and epilogue with the other's MMAs
+        mlp::k_gemm_tc<256, 64><<<dim3((g.M + 127) / 128, g.N / 64), 128, (size_t)(128 + 64) * 256 * 2, m->stream>>>(
+            g, m->errw);
+    }
     return true;
 }
 
-void gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g, int split = 1) {
-    if (TA == 0 && TB == 0 && split == 1 && gemm_tc(m, g)) return;
+// returns true when the tcgen05 path ran (only it writes the transposed copy Ht)
+bool gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g, int split = 1) {
+    if (TA == 0 && TB == 0 && split == 1 && gemm_tc(m, g)) return true;
     dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM, split);
     if (split > 1) cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.ldc, m->stream);
     if (TA == 0 && TB == 0) mlp::k_gemm<0, 0><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 0 && TB == 1) mlp::k_gemm<0, 1><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 1 && TB == 0) mlp::k_gemm<1, 0><<<grid, 128, 0, m->stream>>>(g);
     else mlp::k_gemm<1, 1><<<grid, 128, 0, m->stream>>>(g);
+    return false;
 }
 
 // bf16 W^T of every layer of member e (the K-major B operand of dX)
@@ -553,8 +621,9 @@ void refresh_wt(qs_mlp *m, int e) {
     }
 }
 
-// forward of member e on n rows of X0 (already standardised); fills OUT[e]
-void forward(qs_mlp *m, int e, int n) {
+// forward of member e on n rows of X0 (already standardised); fills OUT[e];
+// with want_ht the hidden activations are also written transposed (training)
+void forward(qs_mlp *m, int e, int n, bool want_ht = false) {
     const float *Pe = m->P + (long long)e * m->nparam;
     const __nv_bfloat16 *Pbe = m->Pb + (long long)e * m->nparam;
     for (int l = 0; l <= m->depth; ++l) {
@@ -568,7 +637,10 @@ void forward(qs_mlp *m, int e, int n) {
         if (l < m->depth) {
             g.C = m->Z[l]; g.ldc = m->width;
             g.H = m->H[l]; g.ldh = m->width;
+            g.Ht = want_ht ? m->HT[l] : nullptr; g.ldht = n;   // act^T for the weight gradient (tcgen05 path)
             g.epi = mlp::EPI_BIAS_GELU;
+            m->ht_valid[l] = gemm(m, 0, 0, g) && want_ht;
+            continue;
         } else {
             g.C = m->OUT + (long long)e * m->max_batch * m->n_out; g.ldc = m->n_out;
             g.epi = mlp::EPI_BIAS;
@@ -583,6 +655,7 @@ void backward(qs_mlp *m, int e, int n) {
     const __nv_bfloat16 *Pbe = m->Pb + (long long)e * m->nparam;
     const __nv_bfloat16 *dz = m->DOUT;   // dL/dz of the current layer, bf16 [n][lout]
     __nv_bfloat16 *ping[2] = {m->DG0, m->DG1};
+    bool dzt_ready = false;              // TDZ holds dz^T (written by the previous dX epilogue)
     for (int l = m->depth; l >= 0; --l) {
         const int in = m->lin[l], out = m->lout[l];
         const __nv_bfloat16 *act = l == 0 ? m->X0 : m->H[l - 1];
@@ -594,13 +667,40 @@ void backward(qs_mlp *m, int e, int n) {
         gw.M = out; gw.N = in; gw.K = n;
         gw.C = Ge + m->woff[l]; gw.ldc = in;
         gw.epi = mlp::EPI_STORE;
-        // the weight gradient reduces over the batch: split it so that the
-        // (out x in) output tiles fill the GPU
-        const int tiles = ((out + mlp::BM - 1) / mlp::BM) * ((in + mlp::BN - 1) / mlp::BN);
-        int split = std::max(1, std::min(64, 296 / std::max(1, tiles)));
-        split = std::min(split, std::max(1, n / 256));
-        gemm(m, 1, 1, gw, split);
-        mlp::k_colsum<<<out, 256, 0, m->stream>>>(dz, n, out, Ge + m->boff[l]);
+        if (m->use_tc && in % 128 == 0 && out >= 128 && n % 8 == 0) {
+            // tensor cores: transpose dz and act to K-major [width][batch], then
+            // one 128 x 128 tile per CTA over a slice of the batch, slices
+            // summed atomically into the (zeroed) fp32 gradient
+            const dim3 tb(32, 8);
+            if (!dzt_ready)
+                mlp::k_transpose_b16<<<dim3((out + 31) / 32, (n + 31) / 32), tb, 0, m->stream>>>(dz, n, out, m->TDZ);
+            const __nv_bfloat16 *actT = m->TACT;
+            if (l >= 1 && m->ht_valid[l - 1]) actT = m->HT[l - 1];
+            else mlp::k_transpose_b16<<<dim3((in + 31) / 32, (n + 31) / 32), tb, 0, m->stream>>>(act, n, in, m->TACT);
+            mlp::GemmArgs gt{};
+            gt.A = m->TDZ; gt.lda = n;        // A(m=o, k=b) = dz^T[o][b]
+            gt.B = actT; gt.ldb = n;          // B(n=i, k=b) = act^T[i][b]
+            gt.M = out; gt.N = in; gt.K = 256;
+            gt.C = Ge + m->woff[l]; gt.ldc = in;
+            gt.epi = mlp::EPI_ATOMIC;
+            const int S = std::max(1, std::min(32, (n + 255) / 256));
+            gt.kchunks = (n + 256 * S - 1) / (256 * S);
+            gt.Ktot = n;
+            cudaMemsetAsync(gt.C, 0, sizeof(float) * (size_t)out * in, m->stream);
+            mlp::k_gemm_tc<256, 128><<<dim3((out + 127) / 128, in / 128, S), 128, (size_t)(128 + 128) * 256 * 2,
+                                       m->stream>>>(gt, m->errw);
+        } else {
+            // the weight gradient reduces over the batch: split it so that the
+            // (out x in) output tiles fill the GPU
+            const int tiles = ((out + mlp::BM - 1) / mlp::BM) * ((in + mlp::BN - 1) / mlp::BN);
+            int split = std::max(1, std::min(64, 296 / std::max(1, tiles)));
+            split = std::min(split, std::max(1, n / 256));
+            gemm(m, 1, 1, gw, split);
+        }
+        // bias gradient: column sums of dz
+        cudaMemsetAsync(Ge + m->boff[l], 0, sizeof(float) * out, m->stream);
+        mlp::k_colsum_tiles<<<(n + 31) / 32, std::max(32, (out / 2 + 31) / 32 * 32), 0, m->stream>>>(
+            dz, n, out, Ge + m->boff[l]);
         if (l == 0) break;
         // dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * gelu'(Z[l-1][b][i])
         mlp::GemmArgs gx{};
@@ -611,8 +711,9 @@ void backward(qs_mlp *m, int e, int n) {
         gx.Z = m->Z[l - 1];
         __nv_bfloat16 *dst = ping[l & 1];
         gx.H = dst; gx.ldh = m->width;
+        gx.Ht = m->TDZ; gx.ldht = n;     // dz^T for the next weight gradient (tcgen05 path only)
         gx.epi = mlp::EPI_DGELU;
-        gemm(m, 0, 0, gx);
+        dzt_ready = gemm(m, 0, 0, gx);
         dz = dst;
     }
 }
@@ -654,7 +755,9 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG0)) ||
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG1)) ||
         (s = mdev(m, sizeof(float) * 64, &m->stats)) || (s = mdev(m, sizeof(float) * 4, &m->loss)) ||
-        (s = mdev(m, pb / 2, &m->PT)) || (s = mdev(m, sizeof(int) * 4, &m->errw))) {
+        (s = mdev(m, pb / 2, &m->PT)) || (s = mdev(m, sizeof(int) * 4, &m->errw)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->TDZ)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->TACT))) {
         qs_mlp_free(m);
         return s;
     }
@@ -665,8 +768,15 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
             qs_mlp_free(m);
             return s;
         }
+        __nv_bfloat16 *ht;
+        if ((s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &ht))) {
+            qs_mlp_free(m);
+            return s;
+        }
         m->Z.push_back(z);
         m->H.push_back(h);
+        m->HT.push_back(ht);
+        m->ht_valid.push_back(0);
     }
     // initialisation: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) over the real
     // inputs (padding columns zero), b = 0; per member seed
@@ -706,6 +816,7 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     for (int e = 0; e < ensemble; ++e) refresh_wt(m, e);
     cudaFuncSetAttribute(mlp::k_gemm_tc<256, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 256 * 2);
     cudaFuncSetAttribute(mlp::k_gemm_tc<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 16 * 2);
+    cudaFuncSetAttribute(mlp::k_gemm_tc<256, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 + 64) * 256 * 2);
     if (const char *v = getenv("QS_MLP_NO_TCGEN05")) m->use_tc = v[0] == '0';
     if (cudaGetLastError() != cudaSuccess) { qs_mlp_free(m); return QS_ERR_CUDA; }
     *out = m;
@@ -771,7 +882,7 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     for (int e = 0; e < m->E; ++e) {
-        forward(m, e, nb);
+        forward(m, e, nb, true);
         mlp::k_loss<<<(nb + 255) / 256, 256, 0, m->stream>>>(m->OUT + (long long)e * m->max_batch * 2, Y, nb,
                                                               m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss);
         backward(m, e, nb);
