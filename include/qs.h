@@ -368,6 +368,27 @@ qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float 
 const char *qs_mlp_last_error(const qs_mlp *m);
 void qs_mlp_free(qs_mlp *m);
 
+/* Whole-model surrogate: train the ensemble on n device rows X [n][7],
+ * Y [n][2] (fp32, as written by qs_sur_points) with the options of a flat
+ * JSON object (numbers; defaults in brackets): "epochs" [8], "batch"
+ * [16384], "lr" [0.002, cosine-decayed over the epochs], "ensemble" [4],
+ * "width" [256], "depth" [3], "seed" [3] (initial weights and the per-epoch
+ * shuffles), "var_threshold" [inf] (the fallback threshold of
+ * qs_sur_infer).  json_cfg may be NULL.  ctx (may be NULL) lends its stream
+ * and allocator.  Synchronises the stream every epoch (the shuffle is drawn
+ * on the host).  On success *out owns the model; free it with qs_sur_free. */
+typedef struct qs_sur qs_sur;
+qs_status qs_sur_train(qs_ctx *ctx, const void *X, const void *Y, int64_t n, const char *json_cfg, qs_sur **out);
+/* Ensemble inference on n device rows X [n][7]: y_mean, y_var [n][2] fp32
+ * device (output 0 in target units); fallback_mask (device, may be NULL):
+ * 1 where the output-0 variance exceeds the model's threshold, i.e. the
+ * rows to answer with the solver. */
+qs_status qs_sur_infer(qs_sur *s, const void *X, int64_t n, void *y_mean, void *y_var, uint8_t *fallback_mask);
+/* Mean loss of each epoch's first batch (host; *n_out = epochs). */
+qs_status qs_sur_losses(const qs_sur *s, float *host, int max_n, int *n_out);
+qs_status qs_sur_set_threshold(qs_sur *s, float var_threshold);
+void qs_sur_free(qs_sur *s);
+
 /* Training samples for the surrogate from one snapshot of ctx (the
  * device buffer `snap` written by qs_diag(QS_DIAG_MAG) at the current step;
  * snap_bytes its size).  n samples, cells drawn uniformly over all

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -933,6 +934,120 @@ qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float 
 }
 
 const char *qs_mlp_last_error(const qs_mlp *m) { return m ? m->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Whole-model surrogate entry points: training of the ensemble from a JSON
+// configuration, inference with the solver-fallback mask.
+// ---------------------------------------------------------------------------
+cudaStream_t qs_ctx_stream(const qs_ctx *c);
+const qs_allocator *qs_ctx_allocator(const qs_ctx *c);
+
+struct qs_sur {
+    qs_mlp *m = nullptr;
+    float var_threshold = INFINITY;
+    std::vector<float> losses;
+    std::string err;
+};
+
+namespace mlp {
+// Xb[i] = X[perm[b0 + i]], Yb[i] = Y[perm[b0 + i]] (rows of 7 and 2 floats)
+__global__ void k_gather_rows(const float *X, const float *Y, const int *perm, long long b0, int nb, int nx, int ny,
+                              float *Xb, float *Yb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const long long r = perm[b0 + i];
+    for (int c = 0; c < nx; ++c) Xb[(long long)i * nx + c] = X[r * nx + c];
+    for (int c = 0; c < ny; ++c) Yb[(long long)i * ny + c] = Y[r * ny + c];
+}
+}  // namespace mlp
+
+namespace {
+// number after "key": in a flat JSON object, else the default
+double cfg_num(const char *json, const char *key, double dflt) {
+    if (!json) return dflt;
+    const std::string pat = std::string("\"") + key + "\"";
+    const char *p = strstr(json, pat.c_str());
+    if (!p) return dflt;
+    p = strchr(p + pat.size(), ':');
+    if (!p) return dflt;
+    char *end = nullptr;
+    const double v = strtod(p + 1, &end);
+    return end == p + 1 ? dflt : v;
+}
+}  // namespace
+
+extern "C" {
+
+qs_status qs_sur_train(qs_ctx *ctx, const void *X_, const void *Y_, int64_t n, const char *json_cfg, qs_sur **out) {
+    if (!X_ || !Y_ || !out || n < 1) return QS_ERR_ARG;
+    const float *X = static_cast<const float *>(X_), *Y = static_cast<const float *>(Y_);
+    const int epochs = (int)cfg_num(json_cfg, "epochs", 8), ens = (int)cfg_num(json_cfg, "ensemble", 4);
+    const int width = (int)cfg_num(json_cfg, "width", 256), depth = (int)cfg_num(json_cfg, "depth", 3);
+    const double lr = cfg_num(json_cfg, "lr", 2e-3);
+    const uint64_t seed = (uint64_t)cfg_num(json_cfg, "seed", 3);
+    int batch = (int)cfg_num(json_cfg, "batch", 16384);
+    if (batch > n) batch = (int)n;
+    if (epochs < 1 || batch < 1 || !(lr > 0)) return QS_ERR_ARG;
+    cudaStream_t st = qs_ctx_stream(ctx);
+    const qs_allocator *al = qs_ctx_allocator(ctx);
+    qs_sur *s = new qs_sur();
+    s->var_threshold = (float)cfg_num(json_cfg, "var_threshold", INFINITY);
+    qs_status r = qs_mlp_create(7, width, depth, 2, ens, batch, seed, al, st, &s->m);
+    if (r) { delete s; return r; }
+    qs_mlp *m = s->m;
+    float *Xb = nullptr, *Yb = nullptr;
+    int *perm_d = nullptr;
+    if ((r = mdev(m, sizeof(float) * (size_t)batch * 7, &Xb)) || (r = mdev(m, sizeof(float) * (size_t)batch * 2, &Yb)) ||
+        (r = mdev(m, sizeof(int) * (size_t)n, &perm_d)) || (r = qs_mlp_set_norm(m, X, n, Y))) {
+        qs_sur_free(s);
+        return r;
+    }
+    std::vector<int> perm(n);
+    std::mt19937_64 rng(seed);
+    for (int ep = 0; ep < epochs && !r; ++ep) {
+        for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
+        for (int64_t i = n - 1; i > 0; --i) std::swap(perm[i], perm[rng() % (uint64_t)(i + 1)]);
+        if (cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { r = QS_ERR_CUDA; break; }
+        const float lr_ep = (float)(lr * 0.5 * (1.0 + std::cos(3.14159265358979323846 * ep / epochs)));
+        for (int64_t b0 = 0; b0 + batch <= n && !r; b0 += batch) {
+            mlp::k_gather_rows<<<(batch + 255) / 256, 256, 0, st>>>(X, Y, perm_d, b0, batch, 7, 2, Xb, Yb);
+            float loss = 0.0f;
+            r = qs_mlp_train_step(m, Xb, Yb, batch, lr_ep, 1, b0 == 0 ? &loss : nullptr);
+            if (b0 == 0) s->losses.push_back(loss);
+        }
+    }
+    if (r) { s->err = qs_mlp_last_error(m); qs_sur_free(s); return r; }
+    *out = s;
+    return QS_OK;
+}
+
+qs_status qs_sur_infer(qs_sur *s, const void *X, int64_t n, void *y_mean, void *y_var, uint8_t *fallback_mask) {
+    if (!s || !X || !y_mean || !y_var || n < 1) return QS_ERR_ARG;
+    return qs_mlp_infer(s->m, static_cast<const float *>(X), n, static_cast<float *>(y_mean),
+                        static_cast<float *>(y_var), fallback_mask, s->var_threshold);
+}
+
+qs_status qs_sur_losses(const qs_sur *s, float *host, int max_n, int *n_out) {
+    if (!s || !n_out) return QS_ERR_ARG;
+    *n_out = (int)s->losses.size();
+    for (int i = 0; host && i < max_n && i < *n_out; ++i) host[i] = s->losses[i];
+    return QS_OK;
+}
+
+qs_status qs_sur_set_threshold(qs_sur *s, float var_threshold) {
+    if (!s) return QS_ERR_ARG;
+    s->var_threshold = var_threshold;
+    return QS_OK;
+}
+
+void qs_sur_free(qs_sur *s) {
+    if (!s) return;
+    qs_mlp_free(s->m);
+    delete s;
+}
 
 void qs_mlp_free(qs_mlp *m) {
     if (!m) return;

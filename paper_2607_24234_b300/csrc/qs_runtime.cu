@@ -1082,6 +1082,15 @@ qs_status qs_debug_waits(qs_ctx *c, int64_t spin_limit, int unsatisfiable) {
 
 const char *qs_last_error(const qs_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 
+}  // extern "C"
+
+// internal (same library): the context's stream and allocator, for the
+// surrogate entry points of qs_mlp.cu
+cudaStream_t qs_ctx_stream(const qs_ctx *c) { return c ? c->stream : nullptr; }
+const qs_allocator *qs_ctx_allocator(const qs_ctx *c) { return c && c->has_alloc ? &c->alloc : nullptr; }
+
+extern "C" {
+
 void qs_free(qs_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();

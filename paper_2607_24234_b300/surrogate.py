@@ -41,8 +41,15 @@ def _setup():
     L.qs_mlp_free.argtypes = [_vp]
     L.qs_mlp_free.restype = None
     L.qs_sur_points.argtypes = [_vp, _vp, ctypes.c_size_t, ctypes.c_double, i64, ctypes.c_uint64, _vp, _vp]
+    L.qs_sur_train.argtypes = [_vp, _vp, _vp, i64, ctypes.c_char_p, ctypes.POINTER(_vp)]
+    L.qs_sur_infer.argtypes = [_vp, _vp, i64, _vp, _vp, _vp]
+    L.qs_sur_losses.argtypes = [_vp, _fp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.qs_sur_set_threshold.argtypes = [_vp, ctypes.c_float]
+    L.qs_sur_free.argtypes = [_vp]
+    L.qs_sur_free.restype = None
     for n in ("qs_mlp_create", "qs_mlp_set_norm", "qs_mlp_params", "qs_mlp_layout", "qs_mlp_train_step",
-              "qs_mlp_grads", "qs_mlp_infer", "qs_sur_points"):
+              "qs_mlp_grads", "qs_mlp_infer", "qs_sur_points", "qs_sur_train", "qs_sur_infer", "qs_sur_losses",
+              "qs_sur_set_threshold"):
         getattr(L, n).restype = ctypes.c_int
 
 
@@ -139,6 +146,52 @@ class MLP:
         self._chk(lib.qs_mlp_infer(self.h, _ptr(X), n, _ptr(mean), _ptr(var), _ptr(mask),
                                    float(min(var_threshold, 3e38))))
         return mean, var, mask
+
+
+class SurModel:
+    """A surrogate trained in one library call (qs_sur_train): the whole
+    training loop, shuffles included, runs behind the C ABI."""
+
+    def __init__(self, X, Y, solver=None, **cfg):
+        import json
+        self.h = _vp()
+        js = json.dumps({k: float(v) for k, v in cfg.items()}).encode()
+        st = lib.qs_sur_train(solver.ctx if solver is not None else None, _ptr(X), _ptr(Y), X.shape[0], js,
+                              ctypes.byref(self.h))
+        if st != 0:
+            raise QSError(st, "qs_sur_train failed")
+
+    def losses(self):
+        n = ctypes.c_int()
+        lib.qs_sur_losses(self.h, None, 0, ctypes.byref(n))
+        out = (ctypes.c_float * max(n.value, 1))()
+        lib.qs_sur_losses(self.h, out, n.value, ctypes.byref(n))
+        return list(out)[:n.value]
+
+    def set_threshold(self, thr):
+        lib.qs_sur_set_threshold(self.h, float(min(thr, 3e38)))
+
+    def infer(self, X):
+        import torch
+        n = X.shape[0]
+        mean = torch.empty((n, 2), dtype=torch.float32, device=X.device)
+        var = torch.empty_like(mean)
+        mask = torch.empty(n, dtype=torch.uint8, device=X.device)
+        st = lib.qs_sur_infer(self.h, _ptr(X), n, _ptr(mean), _ptr(var), _ptr(mask))
+        if st != 0:
+            raise QSError(st, "qs_sur_infer failed")
+        return mean, var, mask
+
+    def close(self):
+        if self.h:
+            lib.qs_sur_free(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def generate(problems, snapshot_steps, n_per_snapshot, seed=0, amplitude=1e-6, prec="fp32",

@@ -146,3 +146,32 @@ def test_surrogate_learns_and_screens_heldout(sg):
     assert infer_s < 0.1 * solver_s          # screening gain over running the solver
     assert math.isfinite(res["rmse"])
     m.close()
+
+
+def test_native_training_entry_points(sg):
+    """qs_sur_train / qs_sur_infer: the whole training loop behind the C ABI
+    (host-drawn shuffles, cosine learning rate) reaches the same quality
+    bars on held-out parameter sets; the fallback mask follows the
+    threshold."""
+    import torch
+    qs, sur = sg
+    base = synth.scaled(synth.BATCH_BASE, nkx=32, nky=32)
+    snaps = [200, 400, 600, 800, 1000]
+    tr = synth.batch_instances(16, param_seed=0, base=base, dxi=0.05)
+    ho = synth.batch_instances(8, param_seed=1, base=base, dxi=0.05)
+    Xtr, Ytr, _ = sur.generate(tr, snaps, 1 << 16, seed=1)
+    Xho, Yho, _ = sur.generate(ho, snaps, 1 << 14, seed=2, noise_seed=1)
+    m = sur.SurModel(Xtr, Ytr, epochs=12, batch=8192, lr=2e-3, ensemble=4, seed=3)
+    losses = m.losses()
+    assert len(losses) == 12 and losses[-1] < 0.5 * losses[0]
+    mu, var, mask = m.infer(Xho)
+    err = (mu[:, 0] - Yho[:, 0])
+    rmse = float(torch.sqrt(torch.mean(err * err)))
+    acc = float(((mu[:, 1] > 0).float() == Yho[:, 1]).float().mean())
+    assert rmse < 0.35 * float(Yho[:, 0].std()) and acc > 0.8
+    assert int(mask.sum()) == 0                       # default threshold: no fallback
+    m.set_threshold(float(torch.quantile(var[:, 0], 0.9)))
+    _, _, mask = m.infer(Xho)
+    frac = float(mask.float().mean())
+    assert 0.05 < frac < 0.15
+    m.close()
