@@ -476,30 +476,52 @@ def run_ours(args):
                            "per mode (qs_step_green); FP32 accuracy, not bitwise equal to qs_step"}
 
     # ---- end to end through the C ABI with host buffers ----
+    # Two contexts on two streams: while one sweeps job i, the other's state
+    # for job i + 1 is restored from pinned host memory (copy engine), and job
+    # i's per-mode maxima are read back after it ends.  Every job still pays
+    # its own H2D restore and D2H read inside the timed region.
     e2e = None
     if args.e2e and args.steps > 0:
         s.seed_noise(rank, p["amplitude"])
         ck = s.checkpoint()
         pinned = torch.from_numpy(ck).pin_memory()
         ck_np = pinned.numpy()
-        mm = np.empty(s.snapshot_doubles(qs.REC_MODEMAX), np.float64)
-        mm_t = torch.from_numpy(mm).pin_memory()
+        mm_t = torch.from_numpy(np.empty(s.snapshot_doubles(qs.REC_MODEMAX), np.float64)).pin_memory()
         mm_np = mm_t.numpy()
         import ctypes
+        stream2 = torch.cuda.Stream()
+        s2 = qs.Solver(p, prec="fp32", stream=stream2)
+        s2.set_launch(**launch)
+        ctxs = [s, s2]
+
+        def restore(sv):
+            st = qs.lib.qs_seed(sv.ctx, 0, 0.0, qs.SEED_STATE, ck_np.ctypes.data_as(ctypes.c_void_p), ck_np.nbytes, 1)
+            assert st == 0
+
+        def read_max(sv):
+            st = qs.lib.qs_diag(sv.ctx, qs.REC_MODEMAX, mm_np.ctypes.data_as(ctypes.c_void_p), mm_np.nbytes, 1)
+            assert st == 0
+
+        restore(s2)
+        s2.step(2)                  # warm the second context (work list, kernels)
+        read_max(s2)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            st = qs.lib.qs_seed(s.ctx, 0, 0.0, qs.SEED_STATE, ck_np.ctypes.data_as(ctypes.c_void_p),
-                                ck_np.nbytes, 1)
-            assert st == 0
-            s.step(job)
-            st = qs.lib.qs_diag(s.ctx, qs.REC_MODEMAX, mm_np.ctypes.data_as(ctypes.c_void_p),
-                                mm_np.nbytes, 1)
-            assert st == 0
+        prev = None
+        for i in range(args.steps):
+            sv = ctxs[i % 2]
+            restore(sv)             # overlaps the previous job's sweep on the other stream
+            sv.step(job)
+            if prev is not None:
+                read_max(prev)
+            prev = sv
+        read_max(prev)
         barrier()
         e2e_v, _ = aggregate(ws, upd_job * args.steps, time.perf_counter() - t0, reduce_max)
         e2e = {"value": e2e_v, "unit": UNIT,
-               "h2d_bytes_per_step": int(ck_np.nbytes), "d2h_bytes_per_step": int(mm_np.nbytes)}
+               "h2d_bytes_per_step": int(ck_np.nbytes), "d2h_bytes_per_step": int(mm_np.nbytes),
+               "pipeline": "two contexts / streams: job i+1's H2D restore overlaps job i's sweep"}
+        s2.close()
 
     # ---- FP64 path (shorter job, same workload) ----
     fp64 = None
