@@ -259,8 +259,11 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
         // k^2 kappa^2 |n_p - rho|^2 and |B|^2 = k^2 kappa^2 |rho|^2 at the cell
         // centres, before the push (the fields of Eq. 14).  UPD = false: fields
         // only, the state is not changed.
+        // UPD also extends the NEXT step's chunk aggregate (pass 1 of step k+1)
+        // cell by cell from the pushed rho: a second, independent march
+        // interleaved with this one, instead of a separate pass.
         auto pass2 = [&](auto gm_tag, auto rec_tag, auto upd_tag, float2 n, float2 d, const float *A,
-                         const float *B, float *mx, const float *rc) {
+                         const float *B, float *mx, const float *rc, float2 &an, float2 &ad) {
             constexpr bool GM = decltype(gm_tag)::value;
             constexpr bool REC = decltype(rec_tag)::value;
             constexpr bool UPD = decltype(upd_tag)::value;
@@ -310,6 +313,11 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                         y = pfma(F2(wv), th, y);
                         if (GM) gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(th.x), fabsf(th.y))));
                     }
+                    if constexpr (UPD) {
+                        const float2 r1 = rho(v);                     // rho after the push
+                        if (v == 0 && front1) { an = r1; ad = F2(0.f); }   // equilibrium front, next step
+                        cross(an, ad, pfma(M1, r1, an), r1);
+                    }
                     cross(n, d, uu, r);
                 }
                 if constexpr (THS && UPD) {
@@ -325,15 +333,17 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
             return gmax;
         };
 
+        // the first step's chunk aggregate (thread 0 starts from the front)
+        float2 An, Ad;
+        front_state(An, Ad);
+        pass1(An, Ad);
         for (int it = 0; it < a.n_steps; ++it) {
             const float hf = (a.step0 + it) == 0 ? 0.5f : 1.0f;
             float A[NS], B[NS];
 #pragma unroll
             for (int sp = 0; sp < NS; ++sp) { A[sp] = hf * Af[sp]; B[sp] = hf * Bf[sp]; }
-            // ---- pass 1 (thread 0 starts from the front, the others from 0)
-            float2 n, d;
-            front_state(n, d);
-            pass1(n, d);
+            // ---- this step's chunk aggregate (pass 1), formed by the previous pass 2
+            float2 n = An, d = Ad;
             // ---- inclusive scan over the warp's lanes
             float fk[5];
 #pragma unroll
@@ -384,6 +394,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 if constexpr (THS) { const float2 r2 = sRl[lane]; Rl = RotF{r2.x, r2.y}; }
                 acc_rot2(n, d, Rl, 1.0f, Yn, Yd);
             }
+            front_state(An, Ad);   // the next aggregate starts at the front (thread 0) or from 0
             // ---- pass 2; every 4th step also the renormalisation (growth over
             // 4 steps stays far inside the 2^RES_SPAN headroom)
             using Y_ = std::integral_constant<bool, true>;
@@ -410,8 +421,8 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                     }
                 }
                 const int e_rec = e;
-                if (a.update) gmax = pass2(Y_(), Y_(), Y_(), n, d, A, B, mx, rc);
-                else pass2(N_(), Y_(), N_(), n, d, A, B, mx, rc);
+                if (a.update) gmax = pass2(Y_(), Y_(), Y_(), n, d, A, B, mx, rc, An, Ad);
+                else pass2(N_(), Y_(), N_(), n, d, A, B, mx, rc, An, Ad);
                 // thread maxima as logs (mantissa log + exponent), then the line's maximum
                 double lg[3];
 #pragma unroll
@@ -433,14 +444,19 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 }
                 __syncthreads();   // sMM is reused at the next recording step
             } else if ((it & 3) == 3) {
-                gmax = pass2(Y_(), N_(), Y_(), n, d, A, B, nullptr, nullptr);
+                gmax = pass2(Y_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);
             } else {
-                pass2(N_(), N_(), Y_(), n, d, A, B, nullptr, nullptr);
+                pass2(N_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);
             }
             if (gmax > 0.f) {
                 const int ex = expof(gmax);
                 const int sx = clamp_shift(ex == -200 ? -126 : ex);
-                if (sx > RES_HYST || sx < -RES_HYST) { scale_chunk(p2(-sx)); e += sx; }
+                if (sx > RES_HYST || sx < -RES_HYST) {
+                    const float f = p2(-sx);
+                    scale_chunk(f);
+                    An = pmul(F2(f), An); Ad = pmul(F2(f), Ad);   // next aggregate, same scale
+                    e += sx;
+                }
             }
             buf ^= 1;
         }
