@@ -262,3 +262,54 @@ def test_batched_exact_cta_sizes(qs, pers):
         oracle.sweep(p, nb_o, th_o, 0, 8)
         assert _log_err(nb[i], nb_o) <= FP32_LOG_TOL, i
         assert _log_err(th[i], th_o) <= FP32_LOG_TOL, i
+
+
+@pytest.mark.parametrize("n_xi,V,ks", [
+    (1, 8, [1.3]),            # one cell, one mode: thread 0 alone, 31 idle lanes
+    (256, 8, [0.4, 2.2]),     # exactly one warp of 8-cell chunks
+    (257, 8, [0.4, 2.2]),     # one cell into a second warp
+    (1024, 32, [5.0]),        # one warp of 32-cell chunks, shared-memory Theta
+    (1025, 32, [5.0]),
+])
+def test_resident_edges(qs, n_xi, V, ks):
+    p = synth.scaled(synth.SLAB_2D, n_xi=n_xi, dxi=0.05, length=n_xi * 0.05, k_list=ks,
+                     species=[(-1.0, 1.0, 0.05)], gamma_b=20.0, dt=1.5)
+    w = next(w for w in (2, 4, 8) if _fits(n_xi, V, w))
+    s, nb, th = _run_gpu(qs, p, "fp32", 25, seed=("noise", 7, 1e-6), launch=_res(V, w))
+    nb_o, th_o = _run_oracle(p, 25, seed=("noise", 7, 1e-6))
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    s.close()
+
+
+def test_resident_held_front_on_zero_state(qs):
+    """A held front driving an all-zero state: the line starts without any
+    exponent except the front's (thread 0), the others take theirs from the
+    line maximum."""
+    ks = [0.6, 1.7, 3.1]
+    p = synth.scaled(synth.SLAB_2D, n_xi=600, dxi=0.05, length=30.0, k_list=ks, front="held",
+                     species=[(-1.0, 1.0, 0.05)], gamma_b=20.0, dt=1.5)
+    held = synth.user_seed(len(ks), 1, 2, 21, 1e-3).reshape(len(ks), 2)
+    held = np.stack([held.real, held.imag], axis=-1).reshape(len(ks), 4)
+    zero = np.zeros((len(ks), 1, 600), complex)
+    s, nb, th = _run_gpu(qs, p, "fp32", 30, seed=("user",), held=held, user=zero, launch=_res(32, 2))
+    nb_o, th_o = _run_oracle(p, 30, seed=("user",), held=held, user=zero)
+    assert np.max(np.abs(nb_o)) > 0
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    s.close()
+
+
+def test_resident_nonfinite_detected(qs):
+    p = synth.scaled(synth.SLAB_2D, n_xi=64, k_list=[1.0, 2.0])
+    s = qs.Solver(p, prec="fp32")
+    s.set_launch(**_res(16, 2))
+    bad = synth.user_seed(2, 1, 64, 1, 1e-6)
+    bad[1, 0, 40] = np.nan
+    s.seed_user(bad)
+    s.step(3)
+    with pytest.raises(qs.QSError) as e:
+        s.sync()
+    assert e.value.status == qs.QS_ERR_NONFINITE
+    s.seed_noise(1, 1e-6)
+    s.step(2)
+    s.sync()
+    s.close()
