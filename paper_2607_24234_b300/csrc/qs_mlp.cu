@@ -56,7 +56,27 @@ struct GemmArgs {
     int Ktot;             // K columns [z kchunks K, (z + 1) kchunks K) of Ktot (zero fill past it)
     __nv_bfloat16 *Ht;    // tcgen05 path, optional: the bf16 output H transposed, Ht[n][m] (row stride ldht)
     int ldht;
+    // ensemble members in one launch: member = blockIdx.z / zper (zper CTAs
+    // along z per member, its K slices); per-member strides in elements
+    int zper;
+    long long sA, sB, sC, sH, sHt, sZ, sBias;
 };
+
+// the arguments of this CTA's member, and its K slice zz of zn
+__device__ __forceinline__ GemmArgs for_member(const GemmArgs &g0, int &zz, int &zn) {
+    zn = g0.zper > 1 ? g0.zper : 1;
+    const int mem = blockIdx.z / zn;
+    zz = blockIdx.z - mem * zn;
+    GemmArgs g = g0;
+    g.A += mem * g0.sA;
+    g.B += mem * g0.sB;
+    if (g.C) g.C += mem * g0.sC;
+    if (g.H) g.H += mem * g0.sH;
+    if (g.Ht) g.Ht += mem * g0.sHt;
+    if (g.Z) g.Z += mem * g0.sZ;
+    if (g.bias) g.bias += mem * g0.sBias;
+    return g;
+}
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float dgelu(float z) {
@@ -69,7 +89,9 @@ __device__ __forceinline__ uint32_t pack2(const __nv_bfloat16 *p) {
 
 // C[M][N] = sum_k A(m,k) B(n,k), 4 warps (2 x 2), each 32 x 32 of the tile.
 template <int TA, int TB>
-__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g0) {
+    int zz, zn;
+    const GemmArgs g = for_member(g0, zz, zn);
     __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -83,9 +105,9 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-    // split-K over gridDim.z: this CTA reduces k in [kb, ke)
-    const int kchunk = ((g.K + gridDim.z * BK - 1) / (gridDim.z * BK)) * BK;
-    const int kb = blockIdx.z * kchunk, ke = min(g.K, kb + kchunk);
+    // split-K over the member's zn CTAs along z: this CTA reduces k in [kb, ke)
+    const int kchunk = ((g.K + zn * BK - 1) / (zn * BK)) * BK;
+    const int kb = zz * kchunk, ke = min(g.K, kb + kchunk);
     for (int k0 = kb; k0 < ke; k0 += BK) {
         // K-contiguous operands: 16-byte vectors of 8 bf16; transposed
         // operands: the fastest thread index runs along the contiguous rows
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
                 const long long oc = (long long)m * g.ldc + n;
                 switch (g.epi) {
                 case EPI_STORE:
-                    if (gridDim.z > 1) atomicAdd(g.C + oc, v);
+                    if (zn > 1) atomicAdd(g.C + oc, v);
                     else g.C[oc] = g.accumulate ? g.C[oc] + v : v;
                     break;
                 case EPI_BIAS: g.C[oc] = v + g.bias[n]; break;
@@ -208,7 +230,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }  // namespace tc
 
 template <int K, int NT>
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
+    int zz, zn;
+    const GemmArgs g = for_member(g0, zz, zn);
     extern __shared__ __align__(1024) unsigned char smtc[];
     unsigned char *As = smtc, *Bs = smtc + 128 * K * 2;
     __shared__ __align__(8) uint64_t bar;
@@ -226,7 +250,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
     }
     // K chunks of this CTA (one unless the caller splits a long K over z)
     const int nk = g.kchunks > 1 ? g.kchunks : 1;
-    const long long kz = (long long)blockIdx.z * nk * K;
+    const long long kz = (long long)zz * nk * K;
     const int ktot = g.kchunks > 0 ? g.Ktot : K;
     uint32_t ok = 1;
     uint32_t taddr = 0;
@@ -356,7 +380,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, int *err) {
 }
 
 // W [out][in] fp32 -> W^T [in][out] bf16 (K-major operand for dX = dz W)
-__global__ void k_transpose_bf16(const float *W, int out, int in, __nv_bfloat16 *WT) {
+__global__ void k_transpose_bf16(const float *W, int out, int in, __nv_bfloat16 *WT, long long s_member) {
+    W += blockIdx.y * s_member;  // ensemble member
+    WT += blockIdx.y * s_member;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)out * in) return;
     const int o = (int)(i / in), c = (int)(i % in);
@@ -375,7 +401,10 @@ __global__ void k_standardise(const float *x, int n, int n_in, int kpad, const f
 
 // loss and output gradient; out [n][2] = (regression, logit), y [n][2]
 __global__ void k_loss(const float *out, const float *y, int n, float ymean, float yinv, float *dout_f,
-                       __nv_bfloat16 *dout, float *loss_acc) {
+                       __nv_bfloat16 *dout, float *loss_acc, long long s_member) {
+    out += blockIdx.y * s_member;   // ensemble member (outputs and output gradients)
+    dout_f += blockIdx.y * s_member;
+    dout += blockIdx.y * s_member;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.0f;
     if (i < n) {
@@ -396,7 +425,9 @@ __global__ void k_loss(const float *out, const float *y, int n, float ymean, flo
 
 // column sums of a bf16 [n][cols] matrix (cols even), 32 rows per block,
 // coalesced bf16x2 loads, accumulated into out[cols] (zeroed by the caller)
-__global__ void k_colsum_tiles(const __nv_bfloat16 *g, int n, int cols, float *out) {
+__global__ void k_colsum_tiles(const __nv_bfloat16 *g, int n, int cols, float *out, long long s_g, long long s_out) {
+    g += blockIdx.y * s_g;       // ensemble member
+    out += blockIdx.y * s_out;
     const int c2 = threadIdx.x, r0 = blockIdx.x * 32;
     if (2 * c2 >= cols) return;
     float sx = 0.0f, sy = 0.0f;
@@ -411,9 +442,12 @@ __global__ void k_colsum_tiles(const __nv_bfloat16 *g, int n, int cols, float *o
 }
 
 // dst[c][r] = src[r][c] for a bf16 [rows][cols] matrix, 32 x 32 tiles
-__global__ void k_transpose_b16(const __nv_bfloat16 *src, int rows, int cols, __nv_bfloat16 *dst) {
+__global__ void k_transpose_b16(const __nv_bfloat16 *src, int rows, int cols, __nv_bfloat16 *dst, long long s_src,
+                                long long s_dst) {
     __shared__ __nv_bfloat16 tile[32][34];
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    src += blockIdx.z * s_src;   // ensemble member
+    dst += blockIdx.z * s_dst;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
         const int r = r0 + j, c = c0 + threadIdx.x;
         tile[j][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * cols + c] : __float2bfloat16(0.0f);
@@ -551,6 +585,7 @@ struct qs_mlp {
     __nv_bfloat16 *TDZ = nullptr, *TACT = nullptr;   // [width][B]: dZ^T and act^T (K-major operands of dW)
     std::vector<__nv_bfloat16 *> HT;     // per hidden layer [width][B]: H^T written by the forward epilogue
     std::vector<char> ht_valid;          // HT[l] holds this batch (the forward ran on the tcgen05 path)
+    long long astride = 0;               // per-member stride of the activation buffers (max_batch * width)
     int *errw = nullptr;                 // device error word (bounded waits)
     bool use_tc = true;
     long long step = 0;
@@ -584,27 +619,30 @@ qs_status mdev(qs_mlp *m, size_t bytes, P **p) {
     return s;
 }
 
-bool gemm_tc(qs_mlp *m, const mlp::GemmArgs &g) {
+bool gemm_tc(qs_mlp *m, const mlp::GemmArgs &g, int members) {
     if (!m->use_tc || g.N % 128 != 0 || !(g.K == 16 || g.K == 256) || (g.lda % 8) || (g.ldb % 8) ||
         (g.ldc % 8) || (g.epi != mlp::EPI_STORE && g.epi != mlp::EPI_BIAS && g.ldh % 8))
         return false;
     if (g.K == 16) {
-        mlp::k_gemm_tc<16, 128><<<dim3((g.M + 127) / 128, g.N / 128), 128, (size_t)(128 + 128) * 16 * 2, m->stream>>>(
-            g, m->errw);
+        mlp::k_gemm_tc<16, 128><<<dim3((g.M + 127) / 128, g.N / 128, members), 128, (size_t)(128 + 128) * 16 * 2,
+                                  m->stream>>>(g, m->errw);
     } else {
         // 128 x 64 output tiles: 96 KB of operands, two CTAs per SM overlap one
         // CTA's loads and epilogue with the other's MMAs
-        mlp::k_gemm_tc<256, 64><<<dim3((g.M + 127) / 128, g.N / 64), 128, (size_t)(128 + 64) * 256 * 2, m->stream>>>(
-            g, m->errw);
+        mlp::k_gemm_tc<256, 64><<<dim3((g.M + 127) / 128, g.N / 64, members), 128, (size_t)(128 + 64) * 256 * 2,
+                                  m->stream>>>(g, m->errw);
     }
     return true;
 }
 
-// returns true when the tcgen05 path ran (only it writes the transposed copy Ht)
-bool gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g, int split = 1) {
-    if (TA == 0 && TB == 0 && split == 1 && gemm_tc(m, g)) return true;
-    dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM, split);
-    if (split > 1) cudaMemsetAsync(g.C, 0, sizeof(float) * (size_t)g.M * g.ldc, m->stream);
+// All members of the ensemble in one launch (strides in g, z = member x
+// split).  Returns true when the tcgen05 path ran (only it writes the
+// transposed copy Ht).  Split-K accumulates atomically into a C zeroed by
+// the caller.
+bool gemm(qs_mlp *m, int TA, int TB, mlp::GemmArgs g, int split = 1) {
+    g.zper = split;
+    if (TA == 0 && TB == 0 && split == 1 && gemm_tc(m, g, m->E)) return true;
+    dim3 grid((g.N + mlp::BN - 1) / mlp::BN, (g.M + mlp::BM - 1) / mlp::BM, split * m->E);
     if (TA == 0 && TB == 0) mlp::k_gemm<0, 0><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 0 && TB == 1) mlp::k_gemm<0, 1><<<grid, 128, 0, m->stream>>>(g);
     else if (TA == 1 && TB == 0) mlp::k_gemm<1, 0><<<grid, 128, 0, m->stream>>>(g);
@@ -612,110 +650,114 @@ bool gemm(qs_mlp *m, int TA, int TB, const mlp::GemmArgs &g, int split = 1) {
     return false;
 }
 
-// bf16 W^T of every layer of member e (the K-major B operand of dX)
-void refresh_wt(qs_mlp *m, int e) {
+// bf16 W^T of every layer of every member (the K-major B operand of dX)
+void refresh_wt(qs_mlp *m) {
     for (int l = 1; l <= m->depth; ++l) {
         const long long nw = (long long)m->lin[l] * m->lout[l];
-        mlp::k_transpose_bf16<<<(unsigned)((nw + 255) / 256), 256, 0, m->stream>>>(
-            m->P + (long long)e * m->nparam + m->woff[l], m->lout[l], m->lin[l],
-            m->PT + (long long)e * m->nparam + m->woff[l]);
+        mlp::k_transpose_bf16<<<dim3((unsigned)((nw + 255) / 256), m->E), 256, 0, m->stream>>>(
+            m->P + m->woff[l], m->lout[l], m->lin[l], m->PT + m->woff[l], m->nparam);
     }
 }
 
-// forward of member e on n rows of X0 (already standardised); fills OUT[e];
-// with want_ht the hidden activations are also written transposed (training)
-void forward(qs_mlp *m, int e, int n, bool want_ht = false) {
-    const float *Pe = m->P + (long long)e * m->nparam;
-    const __nv_bfloat16 *Pbe = m->Pb + (long long)e * m->nparam;
+// forward of every member on n rows of X0 (already standardised); fills
+// OUT[e]; with want_ht the hidden activations are also written transposed
+// (training)
+void forward(qs_mlp *m, int n, bool want_ht = false) {
+    const long long as = m->astride;
     for (int l = 0; l <= m->depth; ++l) {
         mlp::GemmArgs g{};
         g.A = l == 0 ? m->X0 : m->H[l - 1];
+        g.sA = l == 0 ? 0 : as;              // the standardised input is shared
         g.lda = l == 0 ? m->kin : m->width;
-        g.B = Pbe + m->woff[l];
+        g.B = m->Pb + m->woff[l]; g.sB = m->nparam;
         g.ldb = m->lin[l];
         g.M = n; g.N = m->lout[l]; g.K = m->lin[l];
-        g.bias = Pe + m->boff[l];
+        g.bias = m->P + m->boff[l]; g.sBias = m->nparam;
         if (l < m->depth) {
-            g.C = m->Z[l]; g.ldc = m->width;
-            g.H = m->H[l]; g.ldh = m->width;
-            g.Ht = want_ht ? m->HT[l] : nullptr; g.ldht = n;   // act^T for the weight gradient (tcgen05 path)
+            g.C = m->Z[l]; g.sC = as; g.ldc = m->width;
+            g.H = m->H[l]; g.sH = as; g.ldh = m->width;
+            g.Ht = want_ht ? m->HT[l] : nullptr; g.sHt = as; g.ldht = n;   // act^T for the weight gradient
             g.epi = mlp::EPI_BIAS_GELU;
             m->ht_valid[l] = gemm(m, 0, 0, g) && want_ht;
-            continue;
         } else {
-            g.C = m->OUT + (long long)e * m->max_batch * m->n_out; g.ldc = m->n_out;
+            g.C = m->OUT; g.sC = (long long)m->max_batch * m->n_out; g.ldc = m->n_out;
             g.epi = mlp::EPI_BIAS;
+            gemm(m, 0, 0, g);
         }
-        gemm(m, 0, 0, g);
     }
 }
 
-// backward of member e (after forward + loss); gradients into G[e]
-void backward(qs_mlp *m, int e, int n) {
-    float *Ge = m->G + (long long)e * m->nparam;
-    const __nv_bfloat16 *Pbe = m->Pb + (long long)e * m->nparam;
-    const __nv_bfloat16 *dz = m->DOUT;   // dL/dz of the current layer, bf16 [n][lout]
+// backward of every member (after forward + loss); gradients into G
+void backward(qs_mlp *m, int n) {
+    const long long as = m->astride, os = (long long)m->max_batch * m->n_out;
+    float *G = m->G;
+    cudaMemsetAsync(G, 0, sizeof(float) * (size_t)m->nparam * m->E, m->stream);   // every path accumulates
+    const __nv_bfloat16 *dz = m->DOUT;   // dL/dz of the current layer, bf16 [n][lout] per member
+    long long sdz = os;
     __nv_bfloat16 *ping[2] = {m->DG0, m->DG1};
     bool dzt_ready = false;              // TDZ holds dz^T (written by the previous dX epilogue)
     for (int l = m->depth; l >= 0; --l) {
         const int in = m->lin[l], out = m->lout[l];
         const __nv_bfloat16 *act = l == 0 ? m->X0 : m->H[l - 1];
+        const long long sact = l == 0 ? 0 : as;
         const int lda_act = l == 0 ? m->kin : m->width;
         // dW[o][i] = sum_b dz[b][o] act[b][i]
-        mlp::GemmArgs gw{};
-        gw.A = dz; gw.lda = out;          // A(m=o, k=b) = dz[b*out + o]  (TA = 1)
-        gw.B = act; gw.ldb = lda_act;     // B(n=i, k=b) = act[b*ld + i]  (TB = 1)
-        gw.M = out; gw.N = in; gw.K = n;
-        gw.C = Ge + m->woff[l]; gw.ldc = in;
-        gw.epi = mlp::EPI_STORE;
         if (m->use_tc && in % 128 == 0 && out >= 128 && n % 8 == 0) {
-            // tensor cores: transpose dz and act to K-major [width][batch], then
-            // one 128 x 128 tile per CTA over a slice of the batch, slices
-            // summed atomically into the (zeroed) fp32 gradient
+            // tensor cores: dz and act K-major [width][batch], then one 128 x 128
+            // tile per CTA over a slice of the batch, slices summed atomically
             const dim3 tb(32, 8);
             if (!dzt_ready)
-                mlp::k_transpose_b16<<<dim3((out + 31) / 32, (n + 31) / 32), tb, 0, m->stream>>>(dz, n, out, m->TDZ);
+                mlp::k_transpose_b16<<<dim3((out + 31) / 32, (n + 31) / 32, m->E), tb, 0, m->stream>>>(
+                    dz, n, out, m->TDZ, sdz, as);
             const __nv_bfloat16 *actT = m->TACT;
             if (l >= 1 && m->ht_valid[l - 1]) actT = m->HT[l - 1];
-            else mlp::k_transpose_b16<<<dim3((in + 31) / 32, (n + 31) / 32), tb, 0, m->stream>>>(act, n, in, m->TACT);
+            else mlp::k_transpose_b16<<<dim3((in + 31) / 32, (n + 31) / 32, m->E), tb, 0, m->stream>>>(
+                     act, n, in, m->TACT, sact, as);
             mlp::GemmArgs gt{};
-            gt.A = m->TDZ; gt.lda = n;        // A(m=o, k=b) = dz^T[o][b]
-            gt.B = actT; gt.ldb = n;          // B(n=i, k=b) = act^T[i][b]
+            gt.A = m->TDZ; gt.sA = as; gt.lda = n;   // A(m=o, k=b) = dz^T[o][b]
+            gt.B = actT; gt.sB = as; gt.ldb = n;     // B(n=i, k=b) = act^T[i][b]
             gt.M = out; gt.N = in; gt.K = 256;
-            gt.C = Ge + m->woff[l]; gt.ldc = in;
+            gt.C = G + m->woff[l]; gt.sC = m->nparam; gt.ldc = in;
             gt.epi = mlp::EPI_ATOMIC;
             const int S = std::max(1, std::min(32, (n + 255) / 256));
             gt.kchunks = (n + 256 * S - 1) / (256 * S);
             gt.Ktot = n;
-            cudaMemsetAsync(gt.C, 0, sizeof(float) * (size_t)out * in, m->stream);
-            mlp::k_gemm_tc<256, 128><<<dim3((out + 127) / 128, in / 128, S), 128, (size_t)(128 + 128) * 256 * 2,
+            gt.zper = S;
+            mlp::k_gemm_tc<256, 128><<<dim3((out + 127) / 128, in / 128, S * m->E), 128, (size_t)(128 + 128) * 256 * 2,
                                        m->stream>>>(gt, m->errw);
         } else {
+            mlp::GemmArgs gw{};
+            gw.A = dz; gw.sA = sdz; gw.lda = out;        // A(m=o, k=b) = dz[b*out + o]  (TA = 1)
+            gw.B = act; gw.sB = sact; gw.ldb = lda_act;  // B(n=i, k=b) = act[b*ld + i]  (TB = 1)
+            gw.M = out; gw.N = in; gw.K = n;
+            gw.C = G + m->woff[l]; gw.sC = m->nparam; gw.ldc = in;
+            gw.epi = mlp::EPI_STORE;
             // the weight gradient reduces over the batch: split it so that the
-            // (out x in) output tiles fill the GPU
-            const int tiles = ((out + mlp::BM - 1) / mlp::BM) * ((in + mlp::BN - 1) / mlp::BN);
+            // (out x in) output tiles of all members fill the GPU
+            const int tiles = ((out + mlp::BM - 1) / mlp::BM) * ((in + mlp::BN - 1) / mlp::BN) * m->E;
             int split = std::max(1, std::min(64, 296 / std::max(1, tiles)));
             split = std::min(split, std::max(1, n / 256));
+            gw.accumulate = 1;
             gemm(m, 1, 1, gw, split);
         }
         // bias gradient: column sums of dz
-        cudaMemsetAsync(Ge + m->boff[l], 0, sizeof(float) * out, m->stream);
-        mlp::k_colsum_tiles<<<(n + 31) / 32, std::max(32, (out / 2 + 31) / 32 * 32), 0, m->stream>>>(
-            dz, n, out, Ge + m->boff[l]);
+        mlp::k_colsum_tiles<<<dim3((n + 31) / 32, m->E), std::max(32, (out / 2 + 31) / 32 * 32), 0, m->stream>>>(
+            dz, n, out, G + m->boff[l], sdz, m->nparam);
         if (l == 0) break;
         // dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * gelu'(Z[l-1][b][i])
         mlp::GemmArgs gx{};
-        gx.A = dz; gx.lda = out;                       // A(m=b, k=o), TA = 0
-        gx.B = m->PT + (long long)e * m->nparam + m->woff[l]; gx.ldb = out;   // B(n=i, k=o) = W^T[i*out + o]
+        gx.A = dz; gx.sA = sdz; gx.lda = out;                          // A(m=b, k=o), TA = 0
+        gx.B = m->PT + m->woff[l]; gx.sB = m->nparam; gx.ldb = out;    // B(n=i, k=o) = W^T[i*out + o]
         gx.M = n; gx.N = in; gx.K = out;
-        gx.C = m->Z[l - 1]; gx.ldc = m->width;         // read as Z in the epilogue
-        gx.Z = m->Z[l - 1];
+        gx.C = m->Z[l - 1]; gx.sC = as; gx.ldc = m->width;             // read as Z in the epilogue
+        gx.Z = m->Z[l - 1]; gx.sZ = as;
         __nv_bfloat16 *dst = ping[l & 1];
-        gx.H = dst; gx.ldh = m->width;
-        gx.Ht = m->TDZ; gx.ldht = n;     // dz^T for the next weight gradient (tcgen05 path only)
+        gx.H = dst; gx.sH = as; gx.ldh = m->width;
+        gx.Ht = m->TDZ; gx.sHt = as; gx.ldht = n;   // dz^T for the next weight gradient (tcgen05 path)
         gx.epi = mlp::EPI_DGELU;
         dzt_ready = gemm(m, 0, 0, gx);
         dz = dst;
+        sdz = as;
     }
 }
 
@@ -745,32 +787,33 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
         off = (off + 7) / 8 * 8;
     }
     m->nparam = off;
+    m->astride = (long long)max_batch * width;
     const size_t pb = sizeof(float) * (size_t)off * ensemble;
     qs_status s = QS_OK;
     if ((s = mdev(m, pb, &m->P)) || (s = mdev(m, pb, &m->Mm)) || (s = mdev(m, pb, &m->Vv)) ||
         (s = mdev(m, pb, &m->G)) || (s = mdev(m, pb / 2, &m->Pb)) ||
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * m->kin, &m->X0)) ||
         (s = mdev(m, sizeof(float) * (size_t)ensemble * max_batch * n_out, &m->OUT)) ||
-        (s = mdev(m, sizeof(float) * (size_t)max_batch * n_out, &m->DOUTF)) ||
-        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * n_out, &m->DOUT)) ||
-        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG0)) ||
-        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->DG1)) ||
+        (s = mdev(m, sizeof(float) * (size_t)ensemble * max_batch * n_out, &m->DOUTF)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * n_out, &m->DOUT)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &m->DG0)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &m->DG1)) ||
         (s = mdev(m, sizeof(float) * 64, &m->stats)) || (s = mdev(m, sizeof(float) * 4, &m->loss)) ||
         (s = mdev(m, pb / 2, &m->PT)) || (s = mdev(m, sizeof(int) * 4, &m->errw)) ||
-        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->TDZ)) ||
-        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &m->TACT))) {
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &m->TDZ)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &m->TACT))) {
         qs_mlp_free(m);
         return s;
     }
     for (int l = 0; l < depth; ++l) {
         float *z; __nv_bfloat16 *h;
-        if ((s = mdev(m, sizeof(float) * (size_t)max_batch * width, &z)) ||
-            (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &h))) {
+        if ((s = mdev(m, sizeof(float) * (size_t)ensemble * max_batch * width, &z)) ||
+            (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &h))) {
             qs_mlp_free(m);
             return s;
         }
         __nv_bfloat16 *ht;
-        if ((s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * width, &ht))) {
+        if ((s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &ht))) {
             qs_mlp_free(m);
             return s;
         }
@@ -814,7 +857,7 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     mlp::k_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, m->stream>>>(m->P, tot, m->Pb);
     cudaMemsetAsync(m->PT, 0, pb / 2, m->stream);
     cudaMemsetAsync(m->errw, 0, sizeof(int) * 4, m->stream);
-    for (int e = 0; e < ensemble; ++e) refresh_wt(m, e);
+    refresh_wt(m);
     cudaFuncSetAttribute(mlp::k_gemm_tc<256, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 256 * 2);
     cudaFuncSetAttribute(mlp::k_gemm_tc<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 16 * 2);
     cudaFuncSetAttribute(mlp::k_gemm_tc<256, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 + 64) * 256 * 2);
@@ -847,7 +890,7 @@ qs_status qs_mlp_params(qs_mlp *m, int member, float *host, int64_t n, int set) 
     if (set) {
         e = cudaMemcpyAsync(dst, host, n * sizeof(float), cudaMemcpyHostToDevice, m->stream);
         mlp::k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, m->stream>>>(dst, n, m->Pb + (long long)member * m->nparam);
-        refresh_wt(m, member);
+        refresh_wt(m);
     } else {
         e = cudaMemcpyAsync(host, dst, n * sizeof(float), cudaMemcpyDeviceToHost, m->stream);
     }
@@ -882,18 +925,16 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
     ++m->step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
-    for (int e = 0; e < m->E; ++e) {
-        forward(m, e, nb, true);
-        mlp::k_loss<<<(nb + 255) / 256, 256, 0, m->stream>>>(m->OUT + (long long)e * m->max_batch * 2, Y, nb,
-                                                              m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss);
-        backward(m, e, nb);
-        if (do_update) {
-            const long long off = (long long)e * m->nparam;
-            mlp::k_adam<<<(unsigned)((m->nparam + 255) / 256), 256, 0, m->stream>>>(
-                m->P + off, m->Mm + off, m->Vv + off, m->G + off, m->nparam, lr, b1, b2, 1e-8f, c1, c2,
-                m->Pb + off);
-            refresh_wt(m, e);
-        }
+    // every member in the same launches (member = the launch's z or y index)
+    forward(m, nb, true);
+    mlp::k_loss<<<dim3((nb + 255) / 256, m->E), 256, 0, m->stream>>>(
+        m->OUT, Y, nb, m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss, (long long)m->max_batch * 2);
+    backward(m, nb);
+    if (do_update) {
+        const long long np = m->nparam * m->E;   // members' parameters are contiguous
+        mlp::k_adam<<<(unsigned)((np + 255) / 256), 256, 0, m->stream>>>(m->P, m->Mm, m->Vv, m->G, np, lr, b1, b2,
+                                                                           1e-8f, c1, c2, m->Pb);
+        refresh_wt(m);
     }
     if (!do_update) --m->step;
     if (cudaGetLastError() != cudaSuccess) return mfail(m, QS_ERR_CUDA, "mlp launch failed");
@@ -925,7 +966,7 @@ qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float 
         const int nb = (int)std::min<int64_t>(m->max_batch, n - r0);
         mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(
             X + r0 * m->n_in, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0);
-        for (int e = 0; e < m->E; ++e) forward(m, e, nb);
+        forward(m, nb);
         mlp::k_ensemble<<<(nb + 255) / 256, 256, 0, m->stream>>>(
             m->OUT, (long long)m->max_batch * 2, m->E, nb, m->ymean, m->ystd, mean + r0 * 2, var + r0 * 2,
             mask ? mask + r0 : nullptr, var_threshold);
