@@ -155,10 +155,18 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
     make_tw256(tw);
     const float *src = np + slice * (long long)N * N;
+    // 4-byte asynchronous copies of the two real rows into the (re, im)
+    // halves of each packed complex row, all in flight at once
     for (int i = threadIdx.x; i < PR * N; i += blockDim.x) {
         const int pr = i >> 8, x = i & 255;
-        A[i] = make_float2(__ldcg(src + (long long)(r0 + 2 * pr) * N + x), __ldcg(src + (long long)(r0 + 2 * pr + 1) * N + x));
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(A + i);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + (long long)(r0 + 2 * pr) * N + x)
+                     : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4u), "l"(src + (long long)(r0 + 2 * pr + 1) * N + x)
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     fft256_team<false>(A + team * N, T + team * 272, tw, t);
     __syncthreads();
@@ -182,10 +190,16 @@ __global__ void __launch_bounds__(256) k_colfft256(const float2 *__restrict__ S1
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
     make_tw256(tw);
     const float2 *src = S1 + slice * (long long)N * NH;
+    // 8-byte asynchronous copies, all in flight at once (zero fill past the
+    // last spectral column)
     for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
         const int y = i >> 4, c = i & 15;
-        A[c * LD + y] = (c0 + c < NH) ? __ldcg(src + (long long)y * NH + c0 + c) : make_float2(0.0f, 0.0f);
+        const bool in = c0 + c < NH;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(A + c * LD + y)),
+                     "l"(src + (in ? (long long)y * NH + c0 + c : 0)), "r"(in ? 8 : 0) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     float2 *col = A + team * LD, *col2 = A2 + team * LD;
     fft256_team<false>(col, T + team * 272, tw, t);
@@ -416,11 +430,25 @@ __global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict
     }
     const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
     const float tz = 6.283185307179586f / a.lz;
+    // stage the raw half spectra of the CTA's rows (T1 and T2, RBn rows each)
+    // in the FFT scratch with 8-byte asynchronous copies, all in flight at once
+    float2 *S1s = T, *S2s = T + RBn * NH;        // 2 RBn NH <= 16 * 272 entries
+    for (int i = threadIdx.x; i < RBn * NH; i += blockDim.x) {
+        const int r = i / NH, k = i - r * NH;
+        const long long o = (long long)(r0 + r) * NH + k;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(S1s + i)),
+                     "l"(t1 + o) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(S2s + i)),
+                     "l"(t2 + o) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
     for (int i = threadIdx.x; i < RBn * N; i += blockDim.x) {
         const int r = i >> 8, k = i & 255;
         const bool lo = k <= 128;
         const int kk = lo ? k : N - k;
-        float2 X = __ldcg(t1 + (long long)(r0 + r) * NH + kk);
+        float2 X = S1s[r * NH + kk];
         if (!lo) X.y = -X.y;
         const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
         A[r * N + k] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
@@ -429,11 +457,11 @@ __global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict
         const int pr = i >> 8, k = i & 255;
         const bool lo = k <= 128;
         const int kk = lo ? k : N - k;
-        float2 U = __ldcg(t2 + (long long)(r0 + 2 * pr) * NH + kk), V = __ldcg(t2 + (long long)(r0 + 2 * pr + 1) * NH + kk);
+        float2 U = S2s[(2 * pr) * NH + kk], V = S2s[(2 * pr + 1) * NH + kk];
         if (!lo) { U.y = -U.y; V.y = -V.y; }
         A[(RBn + pr) * N + k] = make_float2(U.x - V.y, U.y + V.x);
     }
-    __syncthreads();
+    __syncthreads();   // the FFTs below reuse the scratch
     fft256_team<true>(A + team * N, T + team * 272, tw, t);
     if (team < 8) fft256_team<true>(A + (RBn + team) * N, T + team * 272, tw, t);
     __syncthreads();
