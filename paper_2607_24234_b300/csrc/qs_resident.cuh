@@ -92,6 +92,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
     __shared__ float2 sRk[6];                 // R^(V 2^k), k = 0..4, and R^(32 V)
     __shared__ float2 sRl[32];                // R^(V lane)
     __shared__ double sMM[RES_MAX_WARPS][3];  // per-warp log maxima of a recording step
+    __shared__ float4 sG[32];                 // R^(V-1-v) (1 - cos dxi, sin dxi), each component twice
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = THS ? TT : (int)blockDim.x, nw = T >> 5;
     float2 *sT = reinterpret_cast<float2 *>(sdyn) + tid;                      // THS: row stride T = TT
@@ -152,6 +153,15 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 const RotF q6 = rotf(I.dxi * (double)(lane < 5 ? V << lane : 32 * V));
                 sRk[lane] = make_float2(q6.c, q6.s);
             }
+        }
+        if (warp == 0 && lane < V) {
+            // a chunk's response from P = 0 is sum_v rho_v R^(V-1-v) g with
+            // g = (1 - cos dxi, sin dxi) (Eq. 5 unrolled over the chunk)
+            double sn, cs;
+            sincos(I.dxi * (double)(V - 1 - lane), &sn, &cs);
+            const double sh1 = sin(0.5 * I.dxi), g1 = 2.0 * sh1 * sh1, g2 = I.s;
+            const float ga = (float)(cs * g1 + sn * g2), gb = (float)(cs * g2 - sn * g1);
+            sG[lane] = make_float4(ga, ga, gb, gb);
         }
         const bool held = a.front == 2 && a.held != nullptr && live && t == 0;
         const double *hp = held ? a.held + ((long long)itx.x * a.Mp + mc) * 4 : nullptr;
@@ -242,14 +252,32 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
             n = pfma(C2, u, pfma(S2, d, r));
             d = pfma(NS2, u, pmul(C2, d));
         };
-        // pass 1: the chunk's response from the given entry state (cells past
-        // the end propagate values nobody reads)
-        auto pass1 = [&](float2 &n, float2 &d) {
+        // the front's share R^V P_front of a chunk aggregate (thread 0 of a
+        // line with an equilibrium or held front; P_front in this scale)
+        auto add_front = [&](float2 &an, float2 &ad) {
+            if (front1 || held) {
+                float2 pn, pd;
+                front_state(pn, pd);
+                RotF RV;
+                if constexpr (THS) { const float2 r2 = sRk[0]; RV = RotF{r2.x, r2.y}; } else { RV = Rk[0]; }
+                acc_rot2(an, ad, RV, 1.0f, pn, pd);
+            }
+        };
+        // pass 1: the chunk's response from its entry state, in closed form:
+        // sum_v rho_v G_v, then the front's share; the same operations, in the
+        // same order, as the aggregate that pass 2 forms for the next step, so
+        // that splitting a run into calls changes no bits (cells past the end
+        // hold rho = 0)
+        auto pass1 = [&](float2 &an, float2 &ad) {
+            an = ad = F2(0.f);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const float2 r = rho(v);
-                cross(n, d, pfma(M1, r, n), r);
+                const float4 g = sG[v];
+                an = pfma(make_float2(g.x, g.y), r, an);
+                ad = pfma(make_float2(g.z, g.w), r, ad);
             }
+            add_front(an, ad);
         };
         // pass 2: fields at the cell centre and the push, Theta += A n_mid -
         // B rho, n_b += dt n_b0 Theta; one species folds n_mid = ch u + sh n' +
@@ -259,9 +287,9 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
         // k^2 kappa^2 |n_p - rho|^2 and |B|^2 = k^2 kappa^2 |rho|^2 at the cell
         // centres, before the push (the fields of Eq. 14).  UPD = false: fields
         // only, the state is not changed.
-        // UPD also extends the NEXT step's chunk aggregate (pass 1 of step k+1)
-        // cell by cell from the pushed rho: a second, independent march
-        // interleaved with this one, instead of a separate pass.
+        // UPD also accumulates the NEXT step's chunk aggregate (pass 1 of step
+        // k+1) from the pushed rho in its closed form sum_v rho_v G_v (two
+        // packed FMAs per cell); the front's share is added after the pass.
         auto pass2 = [&](auto gm_tag, auto rec_tag, auto upd_tag, float2 n, float2 d, const float *A,
                          const float *B, float *mx, const float *rc, float2 &an, float2 &ad) {
             constexpr bool GM = decltype(gm_tag)::value;
@@ -315,8 +343,9 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                     }
                     if constexpr (UPD) {
                         const float2 r1 = rho(v);                     // rho after the push
-                        if (v == 0 && front1) { an = r1; ad = F2(0.f); }   // equilibrium front, next step
-                        cross(an, ad, pfma(M1, r1, an), r1);
+                        const float4 g = sG[v];
+                        an = pfma(make_float2(g.x, g.y), r1, an);
+                        ad = pfma(make_float2(g.z, g.w), r1, ad);
                     }
                     cross(n, d, uu, r);
                 }
@@ -335,7 +364,6 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
 
         // the first step's chunk aggregate (thread 0 starts from the front)
         float2 An, Ad;
-        front_state(An, Ad);
         pass1(An, Ad);
         for (int it = 0; it < a.n_steps; ++it) {
             const float hf = (a.step0 + it) == 0 ? 0.5f : 1.0f;
@@ -394,7 +422,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 if constexpr (THS) { const float2 r2 = sRl[lane]; Rl = RotF{r2.x, r2.y}; }
                 acc_rot2(n, d, Rl, 1.0f, Yn, Yd);
             }
-            front_state(An, Ad);   // the next aggregate starts at the front (thread 0) or from 0
+            if (a.update) An = Ad = F2(0.f);   // the next aggregate; unchanged by a field pass
             // ---- pass 2; every 4th step also the renormalisation (growth over
             // 4 steps stays far inside the 2^RES_SPAN headroom)
             using Y_ = std::integral_constant<bool, true>;
@@ -448,6 +476,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
             } else {
                 pass2(N_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);
             }
+            if (a.update) add_front(An, Ad);   // pushed rho (equilibrium front) or held value, scale e
             if (gmax > 0.f) {
                 const int ex = expof(gmax);
                 const int sx = clamp_shift(ex == -200 ? -126 : ex);
