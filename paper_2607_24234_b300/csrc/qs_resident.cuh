@@ -21,11 +21,15 @@
 //
 // FP32 range.  Each thread stores its chunk as mantissas times 2^e, one
 // exponent per thread; scan partials move between threads' scales by exact
-// powers of two.  A thread renormalises its chunk when the largest mantissa
-// leaves [2^-16, 2^16], and no exponent of a line may lie more than
-// RES_SPAN below the line's largest (checked every step), so no scale factor
-// in the scan exceeds about 2^(RES_SPAN + 17) and nothing overflows.  Only
-// values below ~2^-(RES_SPAN + 126) of the line maximum flush to zero.
+// powers of two.  Every RES_EVERY-th step a thread renormalises its chunk
+// when the largest mantissa has left [2^-16, 2^16], and no exponent of a
+// line may lie more than RES_SPAN below the line's largest (checked every
+// step).  A scan partial is then at most about 2^(16 + 5) G times
+// 2^RES_SPAN in any thread's scale, G the growth between two checks, so
+// nothing overflows while G < 2^(128 - 21 - RES_SPAN) = 2^27 over
+// RES_EVERY = 8 steps (e^2.3 per step; physical growth is below e^1 per
+// step at the time steps of the scheme).  Only values below
+// ~2^-(RES_SPAN + 126) of the line maximum flush to zero.
 // On the way out the threads sharing a 32-cell group agree on one exponent
 // and write the usual (mantissa, exponent word) layout.
 #pragma once
@@ -34,8 +38,9 @@
 namespace qsk {
 
 constexpr int RES_MAX_WARPS = 16;   // T <= 512
-constexpr int RES_SPAN = 96;
+constexpr int RES_SPAN = 80;
 constexpr int RES_HYST = 16;
+constexpr int RES_EVERY = 8;          // steps between renormalisation checks (a power of two)
 constexpr int RES_NONE = -(1 << 20);   // exponent of a thread that holds no value yet
 constexpr int RES_REGS64 = 128;       // register cap of the 64-thread shared-Theta kernel (96..224 measured: 128 best)
 constexpr int RES_WSTRIDE = 512;       // shared-memory row of the cell weights (max threads)
@@ -82,7 +87,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
     constexpr bool THS = TT > 0;
     static_assert(GRP % V == 0, "a thread's cells lie in one exponent group");
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int CB = 4;                     // cells per shared-memory batch (THS; 2 and 8 measured slower)
+    constexpr int CB = 2;                     // cells per shared-memory batch (THS; 4 and 8 measured 0.7 % and 0.3 % slower)
     static_assert(V % CB == 0, "whole batches");
     extern __shared__ float4 sdyn[];          // THS: Theta then w, rows [v * NS + sp][T]; else w [v * NS + sp][RES_WSTRIDE]
     __shared__ float4 sZ[2][RES_MAX_WARPS];   // inclusive warp aggregate (lane 31)
@@ -383,7 +388,8 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 const float2 ud = make_float2(__shfl_up_sync(FULL, d.x, dl), __shfl_up_sync(FULL, d.y, dl));
                 RotF R;
                 if constexpr (THS) { const float2 r2 = sRk[k]; R = RotF{r2.x, r2.y}; } else { R = Rk[THS ? 0 : k]; }
-                if (lane >= dl) acc_rot2(n, d, R, fk[k], un, ud);
+                // lanes below dl add 0 x (their own value): no divergent branch
+                acc_rot2(n, d, R, lane >= dl ? fk[k] : 0.f, un, ud);
             }
             const float fx = lane == 0 ? 0.f : fk[0];
             float2 Xn = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, n.x, 1), __shfl_up_sync(FULL, n.y, 1)));
@@ -423,8 +429,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 acc_rot2(n, d, Rl, 1.0f, Yn, Yd);
             }
             if (a.update) An = Ad = F2(0.f);   // the next aggregate; unchanged by a field pass
-            // ---- pass 2; every 4th step also the renormalisation (growth over
-            // 4 steps stays far inside the 2^RES_SPAN headroom)
+            // ---- pass 2; every RES_EVERY-th step also the renormalisation
             using Y_ = std::integral_constant<bool, true>;
             using N_ = std::integral_constant<bool, false>;
             long long snap = -1;   // recording step (per-mode maxima), uniform over the CTA
@@ -471,7 +476,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                     o[0] = L0; o[pl] = L1; o[2 * pl] = L2;
                 }
                 __syncthreads();   // sMM is reused at the next recording step
-            } else if ((it & 3) == 3) {
+            } else if ((it & (RES_EVERY - 1)) == RES_EVERY - 1) {
                 gmax = pass2(Y_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);
             } else {
                 pass2(N_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);
