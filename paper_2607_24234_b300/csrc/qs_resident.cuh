@@ -249,13 +249,13 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
             }
             if (front1) n = rho(0);   // equilibrium front: n_p = rho, n_p' = 0 at xi = 0
         };
-        const float2 C2 = F2(c), S2 = F2(s), NS2 = F2(-s), M1 = F2(-1.f);
+        const float2 C2 = F2(c), S2 = F2(s), M1 = F2(-1.f);
 
         // exact cell propagator of Eq. (5): u = n - rho, n <- c u + s n' + rho,
         // n' <- -s u + c n'
         auto cross = [&](float2 &n, float2 &d, const float2 u, const float2 r) {
             n = pfma(C2, u, pfma(S2, d, r));
-            d = pfma(NS2, u, pmul(C2, d));
+            d = pfma(S2, make_float2(-u.x, -u.y), pmul(C2, d));   // -s u, without a (-s, -s) register pair
         };
         // the front's share R^V P_front of a chunk aggregate (thread 0 of a
         // line with an equilibrium or held front; P_front in this scale)
@@ -320,7 +320,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                 for (int u = 0; u < CB; ++u) {
                     const int v = vb + u;
                     const float2 r = rho(v);
-                    const float2 uu = pfma(M1, r, n);
+                    const float2 uu = padd(n, make_float2(-r.x, -r.y));   // n - rho (the negation folds into the add)
                     float2 m = F2(0.f);
                     if (NS == 2 || REC) m = pfma(CH2, uu, pfma(SH2, d, r));
                     if (REC && jb + v < N) {   // cells past the end of the line do not count
