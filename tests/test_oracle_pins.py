@@ -422,3 +422,58 @@ def test_tsi_k0_exact_series_and_exponent():
     env = [max(abs(cf.greens_full(t, x, 0.0, eps)) for x in xi + np.linspace(0, 2 * np.pi, 13)) for t in taus]
     slope = np.polyfit(taus ** (2 / 3), np.log(env), 1)[0]
     assert slope / ((3 / 2 ** (2 / 3)) * G * xi ** (1 / 3)) == pytest.approx(1.0, rel=0.08)
+
+
+def test_held_front_free_oscillation():
+    """Held front (Sec. III.C: the plasma state at xi = 0 is imposed per mode).
+    With no beam charge (zero density) rho stays 0, so the plasma entering
+    from the held value (n0, n0') follows the free solution of n_p'' + n_p = 0
+    (Eq. 5 with a zero right-hand side): n_p = n0 cos xi + n0' sin xi, taken at
+    the cell centres xi_j + dxi/2. The kick then adds the same field every
+    step, half of it at the first step (leapfrog), so after n steps Theta is
+    (2n - 1) times its first-step value, and n_b stays 0."""
+    N, dxi = 300, 0.05
+    p = _slab(n_xi=N, dxi=dxi, length=N * dxi, k_list=[0.5, 2.0, 4.0], species=[(-1.0, 1.0, 0.0)],
+              gamma_b=30.0, dt=1.5, front="held")
+    M = 3
+    rng = np.random.default_rng(17)
+    held = rng.normal(size=(M, 4))
+    xc = (np.arange(N) + 0.5) * dxi
+    h_n = held[:, 0] + 1j * held[:, 1]
+    h_d = held[:, 2] + 1j * held[:, 3]
+    free = h_n[:, None] * np.cos(xc)[None, :] + h_d[:, None] * np.sin(xc)[None, :]
+    out = {}
+    for steps in (1, 5):
+        nb = np.zeros((M, 1, N), np.complex128)
+        th = np.zeros_like(nb)
+        oracle.sweep(p, nb, th, 0, steps, held=held)
+        assert np.all(nb == 0)
+        out[steps] = th[:, 0, :]
+    for m in range(M):
+        t1 = out[1][m]
+        c = np.vdot(free[m], t1).real / np.vdot(free[m], free[m]).real   # one real coefficient per mode
+        assert abs(c) > 0
+        assert np.max(np.abs(t1 - c * free[m])) <= 1e-12 * np.max(np.abs(t1))
+        assert np.max(np.abs(out[5][m] - 9.0 * t1)) <= 1e-12 * np.max(np.abs(out[5][m]))
+
+
+def test_held_front_enters_linearly():
+    """With a beam present, the response is linear in (held value, seed)
+    jointly (Eq. 14 is linear): held H with seed S equals held H with no seed
+    plus held 0 with seed S."""
+    N = 200
+    p = _slab(n_xi=N, dxi=0.05, length=10.0, k_list=[0.7, 3.0], gamma_b=20.0, dt=1.0, front="held")
+    rng = np.random.default_rng(5)
+    H = 1e-3 * rng.normal(size=(2, 4))
+    S = synth.user_seed(2, 1, N, 3, 1e-3)
+    res = []
+    for hv, sv in ((H, S), (H, 0.0 * S), (0.0 * H, S)):
+        nb = np.array(sv, dtype=np.complex128)
+        th = np.zeros_like(nb)
+        oracle.sweep(p, nb, th, 0, 40, held=hv)
+        res.append((nb, th))
+    for i in (0, 1):
+        lin = res[1][i] + res[2][i]
+        assert np.max(np.abs(res[0][i] - lin)) <= 1e-12 * np.max(np.abs(lin))
+    # the held value matters: without it the answer differs
+    assert np.max(np.abs(res[0][1] - res[2][1])) > 1e-3 * np.max(np.abs(res[0][1]))
