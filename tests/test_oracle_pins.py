@@ -477,3 +477,26 @@ def test_held_front_enters_linearly():
         assert np.max(np.abs(res[0][i] - lin)) <= 1e-12 * np.max(np.abs(lin))
     # the held value matters: without it the answer differs
     assert np.max(np.abs(res[0][1] - res[2][1])) > 1e-3 * np.max(np.abs(res[0][1]))
+
+
+def test_field_ex_is_xi_derivative_of_psi():
+    """E_x = -d Psi / d xi with Psi = kappa n_p (Sec. II; the longitudinal
+    field of the reading of the field diagnostics). The oracle forms it from
+    the half-cell propagation of (n_p, n_p'); here it is checked against a
+    central difference of the recorded cell-centre n_p instead: the gap is
+    truncation error, falling about 4x when dxi halves."""
+    ks = np.array([0.5, 2.0, 5.0])
+    kap = 1.0 / (1.0 + ks ** 2)
+    errs = []
+    for N in (400, 800):
+        dxi = 16.0 / N
+        p = _slab(n_xi=N, dxi=dxi, length=16.0, k_list=list(ks), gamma_b=10.0)
+        x = (np.arange(N) + 0.5) * dxi
+        env = 1e-2 * np.exp(-((x - 8.0) / 2.0) ** 2) * np.exp(0.7j * x)
+        nb = np.broadcast_to(env, (3, 1, N)).astype(np.complex128)
+        rec = oracle.fields(p, nb)
+        npm, ex = rec["np"], rec["mag"][4]
+        fd = kap[:, None] * np.abs((npm[:, 2:] - npm[:, :-2]) / (2.0 * dxi))
+        errs.append(np.max(np.abs(ex[:, 1:-1] - fd)) / np.max(ex))
+    assert errs[0] <= 5e-4 and errs[1] <= 1.5e-4
+    assert 3.0 <= errs[0] / errs[1] <= 5.0
