@@ -73,6 +73,7 @@ def lib():
         L.or_sweep.restype = ctypes.c_int
         L.or_fields.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp]
         L.or_wake0.argtypes = [ctypes.POINTER(_Cfg), dp, dp]
+        L.or_fields_vec.argtypes = [ctypes.POINTER(_Cfg), dp, dp]
         _lib = L
     return _lib
 
@@ -246,6 +247,20 @@ def fields(problem: dict, nb: np.ndarray, k2=None, held=None):
     rec_np = np.zeros((1, M, N, 2))
     lib().or_fields(ctypes.byref(b.cfg), _dp(nbv), _dp(rec_mag), _dp(rec_np))
     return {"mag": rec_mag[0], "np": rec_np.view(np.complex128)[0, ..., 0]}
+
+
+def fields_vec(problem: dict, nb: np.ndarray, k2=None, held=None):
+    """Complex field components at the cell centres of the current state:
+    dict of [M, N] complex arrays 'ex', 'eperp', 'b', 'fperp' (each the
+    coefficient along its transverse unit vector; 2D slab: E_y, B_z, F_y)
+    and 'rho' (the beam charge of the cell)."""
+    b = _Bound(problem, k2=k2, held=held)
+    M, N = b.cfg.n_modes, b.cfg.n_xi
+    nbv = _to_c(nb).copy()
+    out = np.zeros((M, N, 10))
+    lib().or_fields_vec(ctypes.byref(b.cfg), _dp(nbv), _dp(out))
+    z = out.view(np.complex128)
+    return {"ex": z[..., 0], "eperp": z[..., 1], "b": z[..., 2], "fperp": z[..., 3], "rho": z[..., 4]}
 
 
 def wake0(problem: dict):

@@ -216,16 +216,34 @@ void or_seed_noise(uint64_t seed, double amplitude, int inst, int n_modes,
 /*   B_perp magnitude |k| kappa |rho|,  F_perp = E_perp - (x x B) =    */
 /*   i k Psi.                                                          */
 /* ------------------------------------------------------------------ */
+/* Complex field components at a cell centre, each the coefficient along
+ * its transverse unit vector (2D slab: E_y, B_z, F_y), from the centre
+ * values n = n_p, d = n_p' and the cell's beam charge rho:
+ *   v[0..1] E_x    = -kappa d                        (E_x = -d_xi Psi)
+ *   v[2..3] E_perp = i |k| kappa (n - rho)
+ *   v[4..5] B      = -i |k| kappa rho                 (B_z in the slab)
+ *   v[6..7] F_perp = i |k| kappa n                     (= i k Psi, which
+ *                    equals E_perp - B: the force on a beam particle)    */
+static void field_vec(double kabs, double kap, double npr, double npi,
+                      double dpr, double dpi, double rr, double ri, double *v)
+{
+    double a = kabs * kap;
+    v[0] = -kap * dpr;           v[1] = -kap * dpi;
+    v[2] = -a * (npi - ri);      v[3] = a * (npr - rr);
+    v[4] = a * ri;               v[5] = -a * rr;
+    v[6] = -a * npi;             v[7] = a * npr;
+}
+
 static void field_mags(double kabs, double kap, double npr, double npi,
                        double dpr, double dpi, double rr, double ri,
                        double *E, double *B, double *F, double *Ex)
 {
-    double exr = -kap * dpr, exi = -kap * dpi;
-    double epr = kabs * kap * (npr - rr), epi = kabs * kap * (npi - ri);
-    double ex2 = exr * exr + exi * exi;
-    *E = sqrt(ex2 + epr * epr + epi * epi);
-    *B = kabs * kap * sqrt(rr * rr + ri * ri);
-    *F = kabs * kap * sqrt(npr * npr + npi * npi);
+    double v[8];
+    field_vec(kabs, kap, npr, npi, dpr, dpi, rr, ri, v);
+    double ex2 = v[0] * v[0] + v[1] * v[1];
+    *E = sqrt(ex2 + v[2] * v[2] + v[3] * v[3]);
+    *B = sqrt(v[4] * v[4] + v[5] * v[5]);
+    *F = sqrt(v[6] * v[6] + v[7] * v[7]);
     *Ex = sqrt(ex2);
 }
 
@@ -364,6 +382,53 @@ int or_wake0(const or_cfg *cfg, double *out_edge, double *out_mid)
         double y = -s * n + c * d + r * s;
         n = x; d = y;
         if (out_edge) out_edge[j] = n;
+    }
+    return 0;
+}
+
+/* Complex field components at the current state (no update), for the
+ * Maxwell-law pins of the field reading: out [mode][j][10] = E_x, E_perp,
+ * B, F_perp (as in field_vec) and rho, each (re, im) at the cell centre,
+ * with n_p at the centre from the same exact half-cell propagation.     */
+int or_fields_vec(const or_cfg *cfg, const double *nb, double *out)
+{
+    const int N = cfg->n_xi, S = cfg->n_species, M = cfg->n_modes;
+    const double D = cfg->dxi, c = cos(D), s = sin(D);
+    const double ch = cos(0.5 * D), sh = sin(0.5 * D);
+    for (int mo = 0; mo < M; ++mo) {
+        const double k2 = cfg->kperp2[mo];
+        const double kap = 1.0 / (1.0 + k2), kabs = sqrt(k2);
+        double nr = 0, ni = 0, dr = 0, di = 0;
+        if (cfg->front == 1) {
+            for (int sp = 0; sp < S; ++sp) {
+                size_t o = (((size_t)mo * S + sp) * N + 0) * 2;
+                nr += cfg->q[sp] * nb[o];
+                ni += cfg->q[sp] * nb[o + 1];
+            }
+        } else if (cfg->front == 2 && cfg->held) {
+            nr = cfg->held[4 * mo + 0]; ni = cfg->held[4 * mo + 1];
+            dr = cfg->held[4 * mo + 2]; di = cfg->held[4 * mo + 3];
+        }
+        for (int j = 0; j < N; ++j) {
+            double rr = 0, ri = 0;
+            for (int sp = 0; sp < S; ++sp) {
+                size_t o = (((size_t)mo * S + sp) * N + j) * 2;
+                rr += cfg->q[sp] * nb[o];
+                ri += cfg->q[sp] * nb[o + 1];
+            }
+            double mr = ch * nr + sh * dr + rr * (1.0 - ch);
+            double mi = ch * ni + sh * di + ri * (1.0 - ch);
+            double mdr = -sh * nr + ch * dr + rr * sh;
+            double mdi = -sh * ni + ch * di + ri * sh;
+            double *v = out + ((size_t)mo * N + j) * 10;
+            field_vec(kabs, kap, mr, mi, mdr, mdi, rr, ri, v);
+            v[8] = rr; v[9] = ri;
+            double xr = c * nr + s * dr + rr * (1.0 - c);
+            double xi = c * ni + s * di + ri * (1.0 - c);
+            double yr = -s * nr + c * dr + rr * s;
+            double yi = -s * ni + c * di + ri * s;
+            nr = xr; ni = xi; dr = yr; di = yi;
+        }
     }
     return 0;
 }

@@ -106,23 +106,141 @@ def test_kgrid_counts():
 # --------------------------------------------------------------------------
 # closed forms of the scheme
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("prof", ["flattop", "ramp"])
-def test_wake_step_exact(prof):
+def test_wake_step_exact():
     """Eq. (5) behind a sharp step of charge: rho0 (1 - cos xi), exact at cell
-    edges and centres; with a ramp the wake is the ramp's exact response."""
-    if prof == "flattop":
-        p = _slab(n_xi=800, dxi=0.05, length=40.0)
-        edge, mid = oracle.wake0(p)
-        xe = (np.arange(800) + 1) * 0.05
-        xm = (np.arange(800) + 0.5) * 0.05
-        assert np.max(np.abs(edge - cf.wake_step(xe, -0.01))) < 1e-15
-        assert np.max(np.abs(mid - cf.wake_step(xm, -0.01))) < 1e-15
-    else:
-        # two species of opposite charge and equal density: no net wake
-        p = _slab(species=[(-1.0, 1.0, 0.02), (1.0, 1.0, 0.02)], profile="ramp_flattop",
-                  ramp_len=2 * math.pi, n_xi=400, dxi=0.05, length=20.0)
-        edge, mid = oracle.wake0(p)
-        assert np.max(np.abs(edge)) < 1e-17 and np.max(np.abs(mid)) < 1e-17
+    edges and centres (the scheme integrates a cell-constant source exactly)."""
+    p = _slab(n_xi=800, dxi=0.05, length=40.0)
+    edge, mid = oracle.wake0(p)
+    xe = (np.arange(800) + 1) * 0.05
+    xm = (np.arange(800) + 0.5) * 0.05
+    assert np.max(np.abs(edge - cf.wake_step(xe, -0.01))) < 1e-15
+    assert np.max(np.abs(mid - cf.wake_step(xm, -0.01))) < 1e-15
+
+
+def _wake_error(prof_kw, exact_edge, D, X):
+    """Max error of the oracle's zeroth-order wake (cell edges) against an
+    exact solution of Eq. (5), one species, peak density 0.02."""
+    N = int(round(X / D))
+    p = _slab(species=[(-1.0, 1.0, 0.02)], n_xi=N, dxi=D, **prof_kw)
+    edge, _ = oracle.wake0(p)
+    xe = (np.arange(N) + 1) * D
+    return np.max(np.abs(edge - exact_edge(xe)))
+
+
+def test_wake_ramp_exact_second_order():
+    """Linear front ramp of length R = 2 pi, then a flat top (the profile of
+    Sec. IV.B's long beams).  Eq. (5) with rho = rho0 xi / R on the ramp and a
+    quiescent plasma ahead has the exact solution n_p = rho0 (xi - sin xi) / R
+    there; at xi = R it reaches (rho0, 0), the equilibrium of the flat top,
+    so behind the ramp n_p = rho0 exactly, with no oscillation.  The scheme
+    samples the profile at cell centres, so it converges at second order (a
+    half-cell shift of the ramp would make it first order; a ramp of the
+    wrong length leaves an O(1) oscillation behind it)."""
+    rho0, R = -0.02, 2 * math.pi
+
+    def exact(x):
+        return np.where(x < R, rho0 * (x - np.sin(x)) / R, rho0)
+
+    kw = dict(profile="ramp_flattop", ramp_len=R, length=30.0)
+    errs = [_wake_error(kw, exact, D, 30.0) for D in (0.1, 0.05, 0.025)]
+    assert errs[2] < 2e-5 * abs(rho0)
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_wake_gaussian_exact_second_order():
+    """Gaussian bunch n_b0 = exp(-(xi - xi_c)^2 / (2 sigma^2)) (Sec. III.C's
+    longitudinal profile).  Far behind it, Eq. (5) gives the free oscillation
+    n_p = rho0 sqrt(2 pi) sigma exp(-sigma^2/2) sin(xi - xi_c) (the Fourier
+    transform of the bunch at the plasma wavenumber).  sigma = 1, xi_c = 10:
+    the part of the bunch ahead of xi = 0 is below e^-50.  Taking sigma as an
+    FWHM, or shifting the centre by half a cell, fails it."""
+    rho0, sig, xc = -0.02, 1.0, 10.0
+    amp = rho0 * math.sqrt(2 * math.pi) * sig * math.exp(-0.5 * sig ** 2)
+
+    def exact(x):
+        return np.where(x > xc + 9 * sig, amp * np.sin(x - xc), np.nan)
+
+    kw = dict(profile="gaussian", sigma_xi=sig, center_xi=xc, length=40.0)
+    errs = []
+    for D in (0.1, 0.05, 0.025):
+        N = int(round(40.0 / D))
+        p = _slab(species=[(-1.0, 1.0, 0.02)], n_xi=N, dxi=D, **kw)
+        edge, _ = oracle.wake0(p)
+        xe = (np.arange(N) + 1) * D
+        ex = exact(xe)
+        m = ~np.isnan(ex)
+        errs.append(np.max(np.abs(edge[m] - ex[m])) / abs(amp))
+    assert errs[2] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def _smooth_seed(N, D, ks, ns=1):
+    x = (np.arange(N) + 0.5) * D
+    env = 1e-2 * np.exp(-((x - 8.0) / 2.0) ** 2) * np.exp(0.7j * x)
+    nb = np.zeros((len(ks), ns, N), np.complex128)
+    for i in range(len(ks)):
+        nb[i, 0] = env * (1.0 + 0.3 * i)
+        if ns == 2:
+            nb[i, 1] = 0.4j * env
+    return nb
+
+
+@pytest.mark.parametrize("ns", [1, 2])
+def test_fields_gauss_law_second_order(ns):
+    """Gauss's law for the field reading: with d_x -> -d_xi (fields depend on
+    xi = t - x) and d_perp -> i k, div E = rho_b - n_p reads
+    -d_xi E_x + i |k| E_perp = rho - n_p (charge: beam rho, plasma electrons
+    -n_p; Sec. II).  The oracle's complex E_x and E_perp at cell centres are
+    checked with a central difference in xi: the residual is truncation error,
+    second order in dxi.  A wrong sign or factor in E_perp (rho - n_p for
+    n_p - rho, a missing kappa or |k|) leaves an O(1) residual."""
+    ks = np.array([0.5, 2.0, 5.0])
+    sp = [(-1.0, 1.0, 0.01)] if ns == 1 else [(-1.0, 1.0, 0.01), (1.0, 1.0, 0.01)]
+    errs = []
+    for N in (400, 800, 1600):
+        D = 16.0 / N
+        p = _slab(species=sp, n_xi=N, dxi=D, length=16.0, k_list=list(ks), gamma_b=10.0)
+        f = oracle.fields_vec(p, _smooth_seed(N, D, ks, ns))
+        rec = oracle.fields(p, _smooth_seed(N, D, ks, ns))
+        npm = rec["np"]
+        lhs = -(f["ex"][:, 2:] - f["ex"][:, :-2]) / (2 * D) + 1j * ks[:, None] * f["eperp"][:, 1:-1]
+        rhs = f["rho"][:, 1:-1] - npm[:, 1:-1]
+        errs.append(np.max(np.abs(lhs - rhs)) / np.max(np.abs(rhs)))
+    assert errs[2] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_fields_faraday_law_second_order():
+    """Faraday's law in the 2D slab, z component: d_x E_y - d_y E_x = -d_t B_z
+    with d_x -> -d_xi, d_t -> d_xi, d_y -> i k gives
+    d_xi (E_y - B_z) = -i k E_x.  Checked with a central difference of the
+    oracle's complex E_perp - B at cell centres (second order).  With Gauss's
+    law fixing E_perp, this fixes B: a flipped sign of B (B_z = +i k kappa rho)
+    leaves an O(1) residual.  Also checks that the force combination
+    E_perp - B is the recorded F_perp = i k Psi and that the recorded
+    magnitudes are those of these components."""
+    ks = np.array([0.5, 2.0, 5.0])
+    kap = 1.0 / (1.0 + ks ** 2)
+    errs = []
+    for N in (400, 800, 1600):
+        D = 16.0 / N
+        p = _slab(n_xi=N, dxi=D, length=16.0, k_list=list(ks), gamma_b=10.0)
+        nb = _smooth_seed(N, D, ks)
+        f = oracle.fields_vec(p, nb)
+        rec = oracle.fields(p, nb)
+        d = f["eperp"] - f["b"]
+        lhs = (d[:, 2:] - d[:, :-2]) / (2 * D)
+        rhs = -1j * ks[:, None] * f["ex"][:, 1:-1]
+        errs.append(np.max(np.abs(lhs - rhs)) / np.max(np.abs(rhs)))
+        assert np.allclose(d, f["fperp"], rtol=0, atol=1e-15 * np.max(np.abs(d)))
+        assert np.allclose(f["fperp"], 1j * (ks * kap)[:, None] * rec["np"], rtol=1e-14, atol=0)
+        mag = rec["mag"]
+        assert np.allclose(mag[1], np.sqrt(np.abs(f["ex"]) ** 2 + np.abs(f["eperp"]) ** 2), rtol=1e-14, atol=0)
+        assert np.allclose(mag[2], np.abs(f["b"]), rtol=1e-14, atol=0)
+        assert np.allclose(mag[3], np.abs(f["fperp"]), rtol=1e-14, atol=0)
+        assert np.allclose(mag[4], np.abs(f["ex"]), rtol=1e-14, atol=0)
+    assert errs[2] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
 
 
 @pytest.mark.parametrize("species,model", [
