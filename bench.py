@@ -7,18 +7,28 @@ cells, (kx, ky) grid 256 x 256 over |k| <= 6 (disc: 51,468 active modes),
 white-noise seed 1e-6 (seed 0), dt = 2.  One bench step = one whole job of
 2000 slow-time steps (one qs_step call, one kernel launch) on the FP32 +
 renormalisation path, in the launch shape the autotuner picks (the resident
-variant, which holds every line on chip for the whole job); the FP64 path
-is reported beside it on a shorter job.
+variant, which holds every line on chip for the whole job).
 
 value  = updates / device time (state resident in HBM; the 1.7 GB state is
          larger than L2, so no flush is needed between launches).
 e2e    = the same metric through the C ABI with host buffers: each step
          restores the job's initial state from pinned host memory (H2D),
          runs the job and reads the per-mode maxima back (D2H).
+The same line carries, each with its own roofline and clocks:
+  hbm_streaming  the per-step HBM-streaming FP32 kernel (TMA tiles) on the
+                 same workload, against the measured HBM copy bandwidth;
+  fp64           the FP64 path on a 200-step job, against the measured FP64
+                 FMA rate;
+  batch          the batched workload (512 instances, 3,228 modes, 200..8000
+                 cells, 1000 steps), one job;
+  narrow         the finite-width narrow beam (256 x 256 x 16,000 cells),
+                 20 slow-time steps;
+  alu_peaks      the FP32 and FP64 FMA rates measured on this GPU by
+                 qs_probe_alu, which the ALU-bound rooflines divide by.
 Multi-GPU (torchrun): every rank runs an independent instance (seed = rank),
 no data-path collective; value = all ranks' updates / max rank time.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (rank 0 only).
+workload (rank 0 only), with the same sampling routine as cpu_baseline.
 """
 import argparse
 import hashlib
@@ -65,27 +75,30 @@ def kernel_hash(*paths):
     return h.hexdigest()[:16]
 
 
-def fp32_alu_peak(pk):
-    """FP32 peak in lane-operations: 148 SMs x 128 FP32 lanes x max SM clock."""
+def fp32_alu_peak_derived(pk):
+    """Nominal FP32 rate in lane-operations: 148 SMs x 128 FP32 lanes x max SM clock."""
     return 148 * 128 * pk.get("sm_max_mhz", 2032.0) * 1e6
 
 
-def sweep_roofline(launch, upd, launch_s, traffic, pk, pk_kind):
-    """Roofline of the FP32 sweep kernel that ran: ALU (FP32 lane-ops) for
+def sweep_roofline(launch, upd, launch_s, traffic, pk, pk_kind, alu=None):
+    """Roofline of the FP32 sweep kernel that ran: ALU (FP32 lane-ops,
+    against the FMA rate measured by qs_probe_alu when `alu` is given) for
     the resident variant, HBM for the streaming ones."""
     hbm_view = BYTES_PER_UPDATE_FP32 * upd / launch_s / 1e9
     if launch.get("variant") == VARIANT_RESIDENT:
-        peak = fp32_alu_peak(pk)
+        if alu and alu.get("fp32_lane_ops_per_s"):
+            peak = alu["fp32_lane_ops_per_s"]
+            src = (f"measured: qs_probe_alu, best of packed and scalar FP32 FMA chains "
+                   f"({alu['fp32_best']}) at {alu['fp32_sm_mhz']} MHz; an FMA is one op")
+        else:
+            peak = fp32_alu_peak_derived(pk)
+            src = "derived: 148 SMs x 128 FP32 lanes x max SM clock (an FMA is one op)"
         ach = FP32_INSTR_PER_UPDATE * upd / launch_s
         return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP32-ops/s",
-                "frac": ach / peak, "traffic": traffic,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (an FMA is one op; "
-                               "a packed f32x2 instruction is two)",
+                "frac": ach / peak, "traffic": traffic, "peak_source": src,
                 "algorithmic_fp32_ops_per_update": FP32_INSTR_PER_UPDATE,
                 "kernel": f"qsk::k_sweep_res<1,{launch.get('prefetch')},T> (CTA of T <= {32 * launch.get('warps_per_cta')} "
                           "threads: a whole number of lines)",
-                "streaming_equivalent_gbs": hbm_view,
-                "streaming_equivalent_frac_of_hbm": hbm_view / pk["hbm_gbs"],
                 "note": "lines held on chip for the whole job: HBM is read and written once per launch"}
     return {"bound": "hbm", "achieved": hbm_view, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": hbm_view / pk["hbm_gbs"], "traffic": traffic, "peak_source": pk_kind,
@@ -143,31 +156,60 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_rate(problem, target_s=10.0, modes_sample=None, steps_cap=None):
-    """Time the FP64 oracle on a bounded sample: `modes_sample` mode lines of
-    the workload (default 32 per host core, so OpenMP keeps every core busy)
-    for as many slow-time steps as fit ~target_s seconds."""
+def _pin_omp():
+    """Fix the oracle's OpenMP threads before its library (and libgomp) loads:
+    one thread per CPU this process may run on, bound in order."""
+    try:
+        ncpu = len(os.sched_getaffinity(0))
+    except Exception:
+        ncpu = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(ncpu))
+    os.environ.setdefault("OMP_PROC_BIND", "close")
+    os.environ.setdefault("OMP_PLACES", "threads")
+
+
+def cpu_oracle_rate(problem, target_s=10.0, lines=None, chunk_steps=100):
+    """Time the FP64 oracle on a bounded sample of the workload: `lines` mode
+    lines (default 32 per OpenMP thread) from the job's initial noise, advanced
+    in chunks of `chunk_steps` slow-time steps; after the job's own step count
+    the sample restarts from the initial state, so the values stay those of
+    the job.  Runs until ~target_s seconds of chunks have elapsed.  Both the
+    cpu_baseline leg and --impl reference use this routine."""
+    _pin_omp()
     import oracle
     oracle.build()
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle.threads()
     md = oracle.modes(problem)
-    if modes_sample is None:
-        modes_sample = min(len(md["k2"]), 32 * cores)
-    sel = np.linspace(0, len(md["k2"]) - 1, modes_sample).astype(int)
-    nb, th = oracle.seed_noise(problem, 0, problem["amplitude"], mode_sel=sel)
+    if lines is None:
+        lines = min(len(md["k2"]), 32 * threads)
+    sel = np.linspace(0, len(md["k2"]) - 1, lines).astype(int)
+    nb0, th0 = oracle.seed_noise(problem, 0, problem["amplitude"], mode_sel=sel)
     k2 = md["k2"][sel]
-    oracle.sweep(problem, nb, th, 0, 1, k2=k2)          # warm the thread pool
-    # run in chunks until ~target_s of CPU time has elapsed
-    steps, chunk, dt = 0, 4, 0.0
-    while dt < target_s and (steps_cap is None or steps < steps_cap):
+    nb, th = nb0.copy(), th0.copy()
+    oracle.sweep(problem, nb, th, 0, 2, k2=k2)            # warm the thread pool
+    nb, th = nb0.copy(), th0.copy()
+    job = int(problem.get("n_steps", 2000))
+    step, total_t, n_chunks = 0, 0.0, 0
+    rates = []
+    upd_chunk = lines * problem["n_xi"] * chunk_steps
+    while total_t < target_s:
+        if step + chunk_steps > job:
+            nb, th = nb0.copy(), th0.copy()
+            step = 0
         t0 = time.perf_counter()
-        oracle.sweep(problem, nb, th, 1 + steps, chunk, k2=k2)
-        dt += time.perf_counter() - t0
-        steps += chunk
-        chunk = min(chunk * 2, 256)
-    upd = modes_sample * problem["n_xi"] * steps
-    return upd / dt, cores, (f"{modes_sample} of {len(md['k2'])} mode lines x {problem['n_xi']} cells x "
-                             f"{steps} steps ({dt:.1f} s, FP64, OpenMP over lines)")
+        oracle.sweep(problem, nb, th, step, chunk_steps, k2=k2)
+        dt = time.perf_counter() - t0
+        step += chunk_steps
+        total_t += dt
+        n_chunks += 1
+        rates.append(upd_chunk / dt)
+    value = upd_chunk * n_chunks / total_t
+    q = np.percentile(rates, [0, 50, 100])
+    desc = (f"{lines} of {len(md['k2'])} mode lines x {problem['n_xi']} cells, {n_chunks} chunks of {chunk_steps} "
+            f"steps within the {job}-step job ({total_t:.1f} s, FP64, OpenMP over lines, {threads} threads, "
+            f"OMP_PROC_BIND={os.environ.get('OMP_PROC_BIND')}; chunk rates min/median/max "
+            f"{q[0]:.3g}/{q[1]:.3g}/{q[2]:.3g})")
+    return value, threads, desc
 
 
 def aggregate(ws, units_per_rank, local_seconds, reduce_max=None):
@@ -206,47 +248,154 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def measure_alu_peaks(stream, target_ms=1000.0):
+    """FMA rates of this GPU from qs_probe_alu: packed f32x2, scalar FP32 and
+    FP64 chains, each one launch of about target_ms, timed with CUDA events
+    on `stream`, SM clocks sampled during the launch."""
+    import torch
+    import paper_2607_24234_b300 as qs
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(4, dtype=torch.float64, device="cuda")
+    blocks, threads = 4 * n_sm, 256
+    out = {"launch": f"{blocks} CTAs x {threads} threads (4 per SM), 8 independent FMA chains per thread"}
+    for name, kind in (("ffma2", qs.PROBE_FFMA2), ("ffma", qs.PROBE_FFMA), ("dfma", qs.PROBE_DFMA)):
+        iters = 2000
+        for attempt in range(2):   # calibrate on a short launch, then one of ~target_ms
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            clk = Clocks(torch.cuda.current_device()) if attempt else None
+            e0.record(stream)
+            ops = qs.probe_alu(kind, blocks, threads, iters, sink, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            clocks = clk.stop() if clk else None
+            if attempt == 0:
+                iters = max(2000, int(iters * target_ms / max(ms, 1e-3)))
+        out[name] = {"lane_ops_per_s": ops / (ms / 1e3), "ms": ms, "iters": iters, "clocks": clocks}
+    f2, f1 = out["ffma2"], out["ffma"]
+    best = "ffma2" if f2["lane_ops_per_s"] >= f1["lane_ops_per_s"] else "ffma"
+    out["fp32_lane_ops_per_s"] = out[best]["lane_ops_per_s"]
+    out["fp32_best"] = best
+    out["fp32_sm_mhz"] = (out[best]["clocks"] or {}).get("sm_mhz")
+    out["fp64_fma_per_s"] = out["dfma"]["lane_ops_per_s"]
+    out["fp64_sm_mhz"] = (out["dfma"]["clocks"] or {}).get("sm_mhz")
+    return out
+
+
+def time_job(stream, fn, reps):
+    """Mean CUDA-event time (s) of fn() on `stream` over reps calls."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms)) / 1e3, ms
+
+
+def streaming_leg(s, p, stream, pk, pk_kind, job=200, reps=3, rank=0):
+    """The per-step HBM-streaming FP32 kernel (TMA-staged tiles, one thread
+    per line) on the benchmark workload: the shape is chosen among the
+    library's TMA candidates by 20-step trials, then `reps` jobs of `job`
+    steps are timed.  HBM roofline: 32.25 algorithmic bytes per update
+    against the measured copy bandwidth."""
+    keep = s.get_launch()
+    cands = [dict(warps_per_cta=1, prefetch=C, persistent=pp, ctas_per_sm=cps, variant=1)
+             for C in (8, 16) for (pp, cps) in ((0, 16), (1, 16), (1, 32))]
+    best, best_t = None, 1e30
+    for c in cands:
+        s.set_launch(**c)
+        s.seed_noise(rank, p["amplitude"])
+        s.step(1)
+        t, _ = time_job(stream, lambda: s.step(20), 1)
+        if t < best_t:
+            best, best_t = c, t
+    s.set_launch(**best)
+    n0 = s.launch_count()
+    clk = Clocks(0)
+    ts = []
+    for _ in range(reps):
+        s.seed_noise(rank, p["amplitude"])
+        t, _ = time_job(stream, lambda: s.step(job), 1)
+        ts.append(t)
+    clocks = clk.stop()
+    launches = s.launch_count() - n0
+    t = float(np.mean(ts))
+    upd = s.n_modes * p["n_xi"] * job
+    traffic = None
+    try:
+        tj = json.load(open(TRAFFIC_FILE))
+        if tj.get("kernel_sha256_16") == kernel_hash():
+            traffic = tj["dram_bytes_per_update"] * upd
+    except Exception:
+        pass
+    roof = sweep_roofline(best, upd, t, traffic, pk, pk_kind)
+    roof["kernel"] = f"qsk::k_sweep_tma<float,1,{8 if best['prefetch'] < 16 else 16},{4 if best['prefetch'] < 16 else 3}>"
+    s.set_launch(**keep)
+    return {"value": upd / t, "unit": UNIT, "ms_per_job": 1e3 * t, "slow_time_steps_per_job": job,
+            "jobs": reps, "launch": best, "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+            "config": {"workload": p["name"], "note": "same state, seed and updates as the headline; "
+                       "HBM read and written every slow-time step"},
+            "error_vs_oracle": "<= 1e-3 in log-amplitude, fitted rates <= 0.5% (tests)"}
+
+
+def batch_leg(args, pk, pk_kind, alu=None):
     """Batched workload: 512 instances (n_b/n_p 10^U(-3,-1), gamma 10^U(1,4),
     L U(5,200) at dxi = 0.025, seed 0), 64 x 64 disc grid (3,228 modes),
-    1000 steps per job, FP32, the autotuned launch shape (one launch per job)."""
+    one 1000-step job per timed call, FP32, resident launch shape (forced
+    with --batch-shape, or the autotuner's with --batch-tune)."""
     import torch
     import paper_2607_24234_b300 as qs
     insts = synth.batch_instances(args.batch_instances, param_seed=0)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
+    stream = torch.cuda.current_stream()
     s = qs.Solver(insts, prec="fp32", stream=stream)
     job = args.batch_job_steps
     cells = sum(p["n_xi"] for p in insts)
     upd_job = cells * s.n_modes * job
     s.seed_noise(0, 1e-6)
-    if args.tune:
+    if args.batch_tune:
         s.tune(reps=args.tune_reps, cache_path=os.path.join(ROOT, "paper_2607_24234_b300", "tune_cache.json"))
+    else:
+        v, V, w, pp, cps = (int(x) for x in args.batch_shape.split(","))
+        s.set_launch(warps_per_cta=w, prefetch=V, persistent=pp, ctas_per_sm=cps, variant=v)
     s.step(2)
     torch.cuda.synchronize()
     clk = Clocks(0)
-    ms = []
     n0 = s.launch_count()
-    for _ in range(args.steps):
+    ts = []
+    for _ in range(args.batch_jobs):
         s.seed_noise(0, 1e-6)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(job)
-        e1.record(stream)
-        s.sync()
-        ms.append(e0.elapsed_time(e1))
+        t, _ = time_job(stream, lambda: s.step(job), 1)
+        ts.append(t)
+    s.sync()
     clocks = clk.stop()
-    pk, pk_kind = peaks()
-    t = float(np.mean(ms)) / 1e3
-    print(json.dumps({
-        "metric": METRIC, "value": upd_job / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": 1, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch_{len(insts)}inst_64sq_disc_{job}steps", "instances": len(insts),
-                   "modes": s.n_modes, "total_cells": cells, "launch": s.get_launch()},
-        "roofline": sweep_roofline(s.get_launch(), upd_job, t, None, pk, pk_kind),
-        "clocks": clocks, "gpu_launches": s.launch_count() - n0}), flush=True)
+    t = float(np.mean(ts))
+    launch = s.get_launch()
+    out = {"value": upd_job / t, "unit": UNIT, "ms_per_job": 1e3 * t, "jobs": args.batch_jobs,
+           "config": {"workload": f"batch_{len(insts)}inst_64sq_disc_{job}steps", "instances": len(insts),
+                      "modes": s.n_modes, "total_cells": cells, "slow_time_steps_per_job": job,
+                      "state_bytes": int(s.query(qs.Q_STATE_BYTES)), "launch": launch},
+           "roofline": sweep_roofline(launch, upd_job, t, None, pk, pk_kind, alu),
+           "clocks": clocks, "gpu_launches": s.launch_count() - n0,
+           "error_vs_oracle": "<= 1e-3 in log-amplitude on sampled lines of all 512 instances (tests)"}
     s.close()
+    return out
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    pk, pk_kind = peaks()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    alu = measure_alu_peaks(stream) if args.alu else None
+    r = batch_leg(args, pk, pk_kind, alu)
+    print(json.dumps({"metric": METRIC, "n_gpus": 1, "steps": r["jobs"], "warmup": 1,
+                      "ms_per_step": r["ms_per_job"], "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f32", "data": "synthetic", **r}), flush=True)
 
 
 def run_surrogate(args):
@@ -301,14 +450,13 @@ def run_surrogate(args):
     m.close()
 
 
-def run_narrow(args):
+def narrow_leg(args, pk, pk_kind):
     """Finite-width narrow beam: 256 x 256 transverse grid over +-8 sigma_r,
-    16,000 xi cells, FP32; one bench step = --narrow-steps slow-time steps."""
+    16,000 xi cells, FP32; one timed call = --narrow-steps slow-time steps."""
     import torch
     from paper_2607_24234_b300.realspace import RealSpace
     p = synth.NARROW_BEAM
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
+    stream = torch.cuda.current_stream()
     g = RealSpace(p, stream=stream)
     g.seed(seed=0, amplitude=p["amplitude"], offset=p["offset"])
     g.step(2)
@@ -316,33 +464,37 @@ def run_narrow(args):
     n = args.narrow_steps
     cells = p["n_xi"] * p["ny"] * p["nz"]
     clk = Clocks(0)
-    ms = []
-    for _ in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.step(n)
-        e1.record(stream)
-        g.sync()
-        ms.append(e0.elapsed_time(e1))
+    n0 = g.launch_count()
+    t, _ = time_job(stream, lambda: g.step(n), args.narrow_reps)
+    g.sync()
     clocks = clk.stop()
-    t = float(np.mean(ms)) / 1e3
-    pk, pk_kind = peaks()
     # algorithmic bytes per transverse-point cell update: n_b read (phase A) +
     # n_p write, then n_p read twice, n_b and G read and written (phase B)
     bpu = 4 + 4 + 4 + 4 + 16
     achieved = bpu * cells * n / t / 1e9
-    print(json.dumps({
-        "metric": METRIC, "value": cells * n / t, "unit": "point·ξ-cell updates/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * t / n, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": p["name"], "transverse": "256 x 256", "n_xi": p["n_xi"],
-                   "slow_time_steps_per_bench_step": n},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
-                     "algorithmic_bytes_per_update": bpu,
-                     "note": "spectral intermediates (3 x 4.2 GB per step) counted as overhead, not algorithmic"},
-        "clocks": clocks, "gpu_launches": g.launch_count()}), flush=True)
+    out = {"value": cells * n / t, "unit": "point·ξ-cell updates/s", "ms_per_slow_time_step": 1e3 * t / n,
+           "slow_time_steps_per_call": n, "calls": args.narrow_reps,
+           "config": {"workload": p["name"], "transverse": "256 x 256", "n_xi": p["n_xi"]},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind,
+                        "algorithmic_bytes_per_update": bpu,
+                        "note": "spectral intermediates between the transform kernels are overhead, not algorithmic"},
+           "clocks": clocks, "gpu_launches": g.launch_count() - n0}
     g.close()
+    return out
+
+
+def run_narrow(args):
+    import torch
+    torch.cuda.set_device(0)
+    pk, pk_kind = peaks()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    r = narrow_leg(args, pk, pk_kind)
+    print(json.dumps({"metric": METRIC, "n_gpus": 1, "steps": r["calls"], "warmup": 1,
+                      "ms_per_step": r["ms_per_slow_time_step"] * r["slow_time_steps_per_call"],
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                      "data": "synthetic", **r}), flush=True)
 
 
 def run_ours(args):
@@ -410,6 +562,9 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
+    # FMA rates of this GPU, which the ALU-bound rooflines divide by
+    alu = measure_alu_peaks(stream) if args.alu else None
+
     value, total_s = aggregate(ws, upd_job * args.steps, float(np.sum(kern_ms)) / 1e3, reduce_max)
     ms_per_step = 1e3 * total_s / args.steps
     avg_launch_s = float(np.mean(kern_ms)) / 1e3
@@ -428,7 +583,7 @@ def run_ours(args):
                 traffic = tj["dram_bytes_per_update"] * upd_job
     except Exception:
         pass
-    roofline = sweep_roofline(launch, upd_job, avg_launch_s, traffic, pk, pk_kind)
+    roofline = sweep_roofline(launch, upd_job, avg_launch_s, traffic, pk, pk_kind, alu)
 
     # ---- diagnostics on: per-mode maxima recorded every diag_stride steps ----
     diag_on = None
@@ -538,19 +693,36 @@ def run_ours(args):
         ms64 = e0.elapsed_time(e1)
         upd64 = M * N * j64
         # FP64 is bound by the FP64 units: 22 DP instructions per update (per
-        # real part: 3 MUL/ADD + 8 FMA, Line::cell); peak = the nominal 1.25
-        # TFLOP/s FP64 of B300 as 2 DP instructions/clock/SM at the max SM clock
-        pk, _ = peaks()
-        dp_peak = 2.0 * 148 * pk.get("sm_max_mhz", 2032.0) * 1e6
+        # real part: 3 MUL/ADD + 8 FMA, Line::cell), against the FP64 FMA
+        # instruction rate measured by qs_probe_alu (a MUL or ADD issues like an FMA)
+        if alu:
+            dp_peak = alu["fp64_fma_per_s"]
+            dp_src = f"measured: qs_probe_alu FP64 FMA chains at {alu['fp64_sm_mhz']} MHz"
+        else:
+            dp_peak = 2.0 * 148 * pk.get("sm_max_mhz", 2032.0) * 1e6
+            dp_src = "derived: nominal 1.25 TFLOP/s FP64 = 2 DP instr/clk/SM x 148 SMs x max SM clock"
         dp_ach = 22.0 * upd64 / (ms64 / 1e3)
         fp64 = {"value": upd64 / (ms64 / 1e3), "unit": UNIT, "slow_time_steps": j64,
                 "ms": ms64, "launch": s64.get_launch(),
                 "hbm_gbs_algorithmic": BYTES_PER_UPDATE_FP64 * upd64 / (ms64 / 1e3) / 1e9,
                 "roofline": {"bound": "alu", "achieved": dp_ach / 1e12, "peak": dp_peak / 1e12,
-                             "unit": "T DP-instr/s", "frac": dp_ach / dp_peak,
-                             "peak_source": "derived: nominal 1.25 TFLOP/s FP64 = 2 DP instr/clk/SM x 148 SMs x max SM clock"},
+                             "unit": "T DP-instr/s", "frac": dp_ach / dp_peak, "peak_source": dp_src},
                 "error_vs_oracle": "<= 1e-9 relative per mode line (tests/test_gpu_parity.py)"}
         s64.close()
+
+    # ---- the per-step HBM-streaming kernel on the same workload ----
+    hbm_streaming = None
+    if rank == 0 and args.streaming and args.steps > 0:
+        hbm_streaming = streaming_leg(s, p, stream, pk, pk_kind, job=args.streaming_job_steps,
+                                      reps=args.streaming_jobs, rank=rank)
+    s.close()
+    torch.cuda.empty_cache()
+
+    # ---- the other workloads, full size (rank 0) ----
+    narrow = narrow_leg(args, pk, pk_kind) if (rank == 0 and args.narrow) else None
+    torch.cuda.empty_cache()
+    batch = batch_leg(args, pk, pk_kind, alu) if (rank == 0 and args.batch) else None
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu:
@@ -570,11 +742,11 @@ def run_ours(args):
                        "error_vs_oracle": "<= 1e-3 in log-amplitude, fitted rates <= 0.5% (tests)"},
             "roofline": roofline,
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "diag_on": diag_on,
-            "green_path": green, "fp64": fp64,
+            "green_path": green, "fp64": fp64, "hbm_streaming": hbm_streaming, "batch": batch,
+            "narrow": narrow, "alu_peaks": alu,
             "cpu_baseline": cpu, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
-    s.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
@@ -609,6 +781,19 @@ def main():
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-job-steps", type=int, default=1000)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-alu", dest="alu", action="store_false", help="skip the FMA-rate probes")
+    ap.add_argument("--no-streaming", dest="streaming", action="store_false",
+                    help="skip the HBM-streaming kernel leg")
+    ap.add_argument("--streaming-job-steps", type=int, default=200)
+    ap.add_argument("--streaming-jobs", type=int, default=3)
+    ap.add_argument("--no-narrow", dest="narrow", action="store_false", help="skip the narrow-beam leg")
+    ap.add_argument("--narrow-reps", type=int, default=2)
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-workload leg")
+    ap.add_argument("--batch-jobs", type=int, default=1)
+    ap.add_argument("--batch-shape", default="3,32,8,0,1",
+                    help="batched workload launch 'variant,prefetch,warps_per_cta,persistent,ctas_per_sm'")
+    ap.add_argument("--batch-tune", action="store_true",
+                    help="autotune the batched workload (copies its ~107 GB state; slow)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.job_steps == 2000:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

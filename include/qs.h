@@ -402,6 +402,24 @@ void qs_sur_free(qs_sur *s);
 qs_status qs_sur_points(qs_ctx *ctx, const double *snap, size_t snap_bytes, double amplitude,
                         int64_t n, uint64_t seed, float *X, float *Y);
 
+/* Arithmetic-rate probe (measurement aid; the paper has no counterpart).
+ * The resident and Green's-function FP32 sweeps and the FP64 sweep are
+ * bound by arithmetic rather than HBM, so their roofline fractions divide
+ * by the rate the GPU actually sustains.  This enqueues on `stream` one
+ * launch of `blocks` x `threads` (32..256, a multiple of 32) threads, each
+ * running 8 independent chains of `iters` dependent fused multiply-adds:
+ *   QS_PROBE_FFMA2  packed f32x2 FMA (__ffma2_rn, two lane-ops each),
+ *   QS_PROBE_FFMA   scalar FP32 FMA (16 chains),
+ *   QS_PROBE_DFMA   FP64 FMA.
+ * *lane_ops (may be NULL) receives the number of FMA lane-operations the
+ * launch performs; time it with CUDA events on `stream`.  dev_sink is a
+ * device buffer of at least 8 bytes that the kernel never writes in practice
+ * (it keeps the arithmetic from being optimised away).  QS_ERR_ARG for a bad
+ * shape; QS_ERR_CUDA if the launch fails. */
+enum { QS_PROBE_FFMA2 = 0, QS_PROBE_FFMA = 1, QS_PROBE_DFMA = 2 };
+qs_status qs_probe_alu(int kind, int blocks, int threads, int64_t iters, void *dev_sink, void *stream,
+                       double *lane_ops);
+
 /* Allocation-free sweep (the paper has no counterpart; this is a service to
  * callers that must not allocate device memory when they step the solver,
  * e.g. a host framework whose memory pool forbids driver allocations in its
@@ -438,7 +456,14 @@ qs_status qs_sur_points(qs_ctx *ctx, const double *snap, size_t snap_bytes, doub
  * before any stream capture.  Every call reuses the same array and leaves
  * its contents behind (the ticket and error word are cleared at the start
  * of each call), so calls whose work overlaps on the GPU, e.g. on two
- * streams, race on it. */
+ * streams, race on it.
+ *
+ * The tables are computed on the host and copied from ordinary (pageable)
+ * host memory, so the call may wait for `stream` before it returns; a call
+ * on a stream that is being captured returns QS_ERR_UNSUPPORTED with nothing
+ * enqueued.  The problem statement is checked as in qs_init (QS_ERR_ARG for
+ * non-finite or out-of-range values, QS_ERR_UNSUPPORTED for geometries this
+ * build does not serve). */
 qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *theta, int *exponents,
                            int64_t step0, int n_steps, int *dev_status, void *stream);
 

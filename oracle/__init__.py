@@ -74,6 +74,7 @@ def lib():
         L.or_fields.argtypes = [ctypes.POINTER(_Cfg), dp, dp, dp]
         L.or_wake0.argtypes = [ctypes.POINTER(_Cfg), dp, dp]
         L.or_fields_vec.argtypes = [ctypes.POINTER(_Cfg), dp, dp]
+        L.or_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -270,6 +271,11 @@ def wake0(problem: dict):
     edge, mid = np.zeros(N), np.zeros(N)
     lib().or_wake0(ctypes.byref(b.cfg), _dp(edge), _dp(mid))
     return edge, mid
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().or_threads())
 
 
 def philox4x32_10(ctr, key):

@@ -43,6 +43,7 @@
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -432,3 +433,7 @@ int or_fields_vec(const or_cfg *cfg, const double *nb, double *out)
     }
     return 0;
 }
+
+/* Threads an OpenMP parallel region of this library uses (for reporting
+ * the core count of a timed oracle run). */
+int or_threads(void) { return omp_get_max_threads(); }

@@ -103,6 +103,9 @@ def _load():
     L.qs_sweep_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, ctypes.POINTER(ctypes.c_int), i64,
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp]
     L.qs_sweep_noalloc.restype = ctypes.c_int
+    L.qs_probe_alu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp,
+                               ctypes.POINTER(ctypes.c_double)]
+    L.qs_probe_alu.restype = ctypes.c_int
     for name in ("qs_init", "qs_seed", "qs_step", "qs_record", "qs_diag", "qs_query", "qs_modes",
                  "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_step_green", "qs_sync"):
         getattr(L, name).restype = ctypes.c_int
@@ -110,6 +113,21 @@ def _load():
 
 
 lib = _load()
+
+
+PROBE_FFMA2, PROBE_FFMA, PROBE_DFMA = range(3)
+
+
+def probe_alu(kind: int, blocks: int, threads: int, iters: int, sink, stream) -> float:
+    """Enqueue one arithmetic-rate probe launch (qs_probe_alu) on `stream`;
+    returns the FMA lane-operations it performs.  `sink`: a device tensor of
+    at least 8 bytes."""
+    ops = ctypes.c_double()
+    st = lib.qs_probe_alu(int(kind), int(blocks), int(threads), int(iters), ctypes.c_void_p(sink.data_ptr()),
+                          ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ops))
+    if st != QS_OK:
+        raise QSError(st, "qs_probe_alu")
+    return ops.value
 
 
 def _dptr(a):

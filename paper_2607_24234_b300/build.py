@@ -9,6 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libqs.so")
 SRCS = [os.path.join(HERE, "csrc", "qs_runtime.cu"), os.path.join(HERE, "csrc", "qs_noalloc.cu"),
+        os.path.join(HERE, "csrc", "qs_probe.cu"),
         os.path.join(HERE, "csrc", "qs_mlp.cu"),
         os.path.join(HERE, "csrc", "qs_real2.cu")]
 DEPS = SRCS + [os.path.join(HERE, "csrc", f) for f in ("qs_kernels.cuh", "qs_resident.cuh", "qs_tune.inc", "qs_green.inc", "qs_surdata.inc")] + \

@@ -20,6 +20,11 @@
 //     ticket and error word are cleared at the start of each call.  Two
 //     calls whose work overlaps on the GPU (e.g. on different streams) race
 //     on the array.
+//   - The tables are built on the host and copied from ordinary (pageable)
+//     host memory, so a call may wait for the stream before it returns, and
+//     a call on a stream that is being captured is refused
+//     (QS_ERR_UNSUPPORTED) before anything is enqueued: a captured copy
+//     would read host memory that is gone when the graph runs.
 //   - No cudaMalloc, cudaFree or other allocating routine is called.
 #include <cuda_runtime.h>
 
@@ -30,6 +35,7 @@
 
 #include "qs.h"
 #include "qs_kernels.cuh"
+#include "qs_problem.h"
 
 namespace {
 
@@ -65,39 +71,27 @@ extern "C" qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *the
                                       int64_t step0, int n_steps, int *dev_status, void *stream) {
     // ---- host-side checks (nothing is enqueued on failure) ----
     if (!p || !state || n_steps < 1 || step0 < 0) return QS_ERR_ARG;
-    if (p->geom != QS_GEOM_KLIST && p->geom != QS_GEOM_KGRID2) return QS_ERR_ARG;
-    if (p->prec != QS_FP64 && p->prec != QS_FP32_RENORM) return QS_ERR_ARG;
+    char msg[256];
+    qs_status vs = qsp::validate(*p, 0, msg, sizeof msg);
+    if (vs) return vs;
+    if (p->front == QS_FRONT_HELD) return QS_ERR_UNSUPPORTED;
     if (p->prec == QS_FP32_RENORM && !exponents) return QS_ERR_ARG;
     if (p->prec == QS_FP64 && !theta) return QS_ERR_ARG;
-    if (p->front == QS_FRONT_HELD) return QS_ERR_UNSUPPORTED;
-    if (p->front < 0 || p->front > 2 || p->model < 0 || p->model > 1) return QS_ERR_ARG;
-    if (p->n_species < 1 || p->n_species > 2 || !(p->gamma_b > 1.0) || p->n_xi < 1 ||
-        !(p->dxi > 0.0) || !(p->dt > 0.0))
-        return QS_ERR_ARG;
-    for (int s = 0; s < p->n_species; ++s)
-        if (!(p->species[s].m > 0.0) || !(p->species[s].density_ratio >= 0.0)) return QS_ERR_ARG;
-    if (p->geom == QS_GEOM_KLIST && (p->n_k < 1 || !p->k_list)) return QS_ERR_ARG;
-    if (p->geom == QS_GEOM_KGRID2 && (p->nkx < 1 || p->nky < 1 || !(p->kmax > 0.0))) return QS_ERR_ARG;
-    if (p->profile == QS_PROF_USER && !p->user_profile) return QS_ERR_ARG;
-    if (p->profile == QS_PROF_GAUSSIAN && !(p->sigma_xi > 0.0)) return QS_ERR_ARG;
-    if (p->profile < 0 || p->profile > 3) return QS_ERR_ARG;
-
-    // ---- transverse modes (same definition as qs_init) ----
-    std::vector<double> k2;
-    if (p->geom == QS_GEOM_KLIST) {
-        for (int i = 0; i < p->n_k; ++i) k2.push_back(p->k_list[i] * p->k_list[i]);
-    } else {
-        const double dkx = 2.0 * p->kmax / p->nkx, dky = 2.0 * p->kmax / p->nky, lim = p->kmax * p->kmax;
-        for (int ix = 0; ix < p->nkx; ++ix) {
-            const double kx = (ix - 0.5 * (p->nkx - 1)) * dkx;
-            for (int iy = 0; iy < p->nky; ++iy) {
-                const double ky = (iy - 0.5 * (p->nky - 1)) * dky;
-                const double q2 = kx * kx + ky * ky;
-                if (p->disc_mask && !(q2 <= lim)) continue;
-                k2.push_back(q2);
-            }
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return QS_ERR_CUDA;
         }
+        if (cs != cudaStreamCaptureStatusNone) return QS_ERR_UNSUPPORTED;
     }
+
+    // ---- transverse modes and profile (the same definitions as qs_init) ----
+    qsp::ModeList modes;
+    qsp::build_modes(*p, modes);
+    const std::vector<double> &k2 = modes.k2;
+    std::vector<double> shape;
+    if (!qsp::profile_shape(*p, shape)) return QS_ERR_ARG;
     const int M = (int)k2.size();
     if (M < 1) return QS_ERR_ARG;
     const int Mp = (M + 31) / 32 * 32;
@@ -151,19 +145,8 @@ extern "C" qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *the
     std::vector<int2> items(n_items);
     for (int i = 0; i < n_items; ++i) items[i] = make_int2(0, i * per_item);
     std::vector<double> wd((size_t)p->n_xi * NS);
-    for (int j = 0; j < p->n_xi; ++j) {
-        const double xi = (j + 0.5) * p->dxi;
-        double v;
-        switch (p->profile) {
-        case QS_PROF_FLATTOP: v = xi <= p->length ? 1.0 : 0.0; break;
-        case QS_PROF_GAUSSIAN: { const double u = (xi - p->center_xi) / p->sigma_xi; v = std::exp(-0.5 * u * u); } break;
-        case QS_PROF_RAMP_FLATTOP:
-            v = xi > p->length ? 0.0 : (p->ramp_len > 0.0 && xi < p->ramp_len ? xi / p->ramp_len : 1.0);
-            break;
-        default: v = p->user_profile[j]; break;
-        }
-        for (int sp = 0; sp < NS; ++sp) wd[(size_t)j * NS + sp] = p->dt * p->species[sp].density_ratio * v;
-    }
+    for (int j = 0; j < p->n_xi; ++j)
+        for (int sp = 0; sp < NS; ++sp) wd[(size_t)j * NS + sp] = p->dt * p->species[sp].density_ratio * shape[j];
     std::vector<float> wf;
     if (f32) wf.assign(wd.begin(), wd.end());
 

@@ -20,6 +20,7 @@
 
 #include "qs.h"
 #include "qs_kernels.cuh"
+#include "qs_problem.h"
 #include "qs_resident.cuh"
 
 using qsk::InstDev;
@@ -145,81 +146,20 @@ qs_status upload(qs_ctx *c, void *dst, const void *src, size_t bytes) {
     return QS_OK;
 }
 
-// Longitudinal profile n_b0(xi_j)/peak at cell centres.
-bool profile_shape(const qs_params &p, std::vector<double> &out) {
-    out.resize(p.n_xi);
-    for (int j = 0; j < p.n_xi; ++j) {
-        const double xi = (j + 0.5) * p.dxi;
-        double v = 0.0;
-        switch (p.profile) {
-        case QS_PROF_FLATTOP: v = xi <= p.length ? 1.0 : 0.0; break;
-        case QS_PROF_GAUSSIAN: {
-            const double u = (xi - p.center_xi) / p.sigma_xi;
-            v = std::exp(-0.5 * u * u);
-        } break;
-        case QS_PROF_RAMP_FLATTOP:
-            v = xi > p.length ? 0.0 : (p.ramp_len > 0.0 && xi < p.ramp_len ? xi / p.ramp_len : 1.0);
-            break;
-        case QS_PROF_USER:
-            if (!p.user_profile) return false;
-            v = p.user_profile[j];
-            break;
-        default: return false;
-        }
-        out[j] = v;
-    }
-    return true;
-}
+bool profile_shape(const qs_params &p, std::vector<double> &out) { return qsp::profile_shape(p, out); }
 
 qs_status validate(const qs_params &p, int idx) {
-    if (p.geom != QS_GEOM_KLIST && p.geom != QS_GEOM_KGRID2)
-        return fail(nullptr, p.geom == 2 ? QS_ERR_UNSUPPORTED : QS_ERR_ARG, "instance %d: geom %d", idx, p.geom);
-    if (p.prec != QS_FP64 && p.prec != QS_FP32_RENORM) return fail(nullptr, QS_ERR_ARG, "instance %d: prec", idx);
-    if (p.model != QS_MODEL_FULL && p.model != QS_MODEL_REDUCED) return fail(nullptr, QS_ERR_ARG, "instance %d: model", idx);
-    if (p.front < 0 || p.front > 2) return fail(nullptr, QS_ERR_ARG, "instance %d: front", idx);
-    if (p.n_species < 1 || p.n_species > 2) return fail(nullptr, QS_ERR_ARG, "instance %d: n_species must be 1 or 2", idx);
-    for (int s = 0; s < p.n_species; ++s) {
-        const qs_species &sp = p.species[s];
-        if (!(sp.m > 0.0) || !(sp.density_ratio >= 0.0) || !std::isfinite(sp.q) || !std::isfinite(sp.density_ratio))
-            return fail(nullptr, QS_ERR_ARG, "instance %d: species %d needs m > 0, density >= 0", idx, s);
-    }
-    if (!(p.gamma_b > 1.0) || !std::isfinite(p.gamma_b)) return fail(nullptr, QS_ERR_ARG, "instance %d: gamma_b must be > 1", idx);
-    if (p.n_xi < 1) return fail(nullptr, QS_ERR_ARG, "instance %d: n_xi must be >= 1", idx);
-    if (!(p.dxi > 0.0) || !std::isfinite(p.dxi)) return fail(nullptr, QS_ERR_ARG, "instance %d: dxi must be > 0", idx);
-    if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return fail(nullptr, QS_ERR_ARG, "instance %d: dt must be > 0", idx);
-    if (p.profile < 0 || p.profile > 3) return fail(nullptr, QS_ERR_ARG, "instance %d: profile", idx);
-    if (p.profile == QS_PROF_GAUSSIAN && !(p.sigma_xi > 0.0)) return fail(nullptr, QS_ERR_ARG, "instance %d: sigma_xi", idx);
-    if (p.profile == QS_PROF_USER && !p.user_profile) return fail(nullptr, QS_ERR_ARG, "instance %d: user_profile", idx);
-    if (p.geom == QS_GEOM_KLIST && (p.n_k < 1 || !p.k_list)) return fail(nullptr, QS_ERR_ARG, "instance %d: k_list", idx);
-    if (p.geom == QS_GEOM_KGRID2 && (p.nkx < 1 || p.nky < 1 || !(p.kmax > 0.0)))
-        return fail(nullptr, QS_ERR_ARG, "instance %d: kgrid", idx);
-    if (p.front == QS_FRONT_HELD && !p.held_front) return fail(nullptr, QS_ERR_ARG, "instance %d: held_front", idx);
-    return QS_OK;
+    char msg[256];
+    qs_status st = qsp::validate(p, idx, msg, sizeof msg);
+    return st ? fail(nullptr, st, "%s", msg) : QS_OK;
 }
 
 // Transverse wavenumbers of the active modes (row-major over the grid).
 void build_modes(qs_ctx *c, const qs_params &p) {
-    c->kx.clear(); c->ky.clear(); c->k2.clear(); c->mode_id.clear(); c->partner_id.clear();
-    if (p.geom == QS_GEOM_KLIST) {
-        for (int i = 0; i < p.n_k; ++i) {
-            const double k = p.k_list[i];
-            c->kx.push_back(k); c->ky.push_back(0.0); c->k2.push_back(k * k);
-            c->mode_id.push_back(i); c->partner_id.push_back(i);
-        }
-        return;
-    }
-    const double dkx = 2.0 * p.kmax / p.nkx, dky = 2.0 * p.kmax / p.nky, lim = p.kmax * p.kmax;
-    for (int ix = 0; ix < p.nkx; ++ix) {
-        const double kx = (ix - 0.5 * (p.nkx - 1)) * dkx;
-        for (int iy = 0; iy < p.nky; ++iy) {
-            const double ky = (iy - 0.5 * (p.nky - 1)) * dky;
-            const double k2 = kx * kx + ky * ky;
-            if (p.disc_mask && !(k2 <= lim)) continue;
-            c->kx.push_back(kx); c->ky.push_back(ky); c->k2.push_back(k2);
-            c->mode_id.push_back(ix * p.nky + iy);
-            c->partner_id.push_back((p.nkx - 1 - ix) * p.nky + (p.nky - 1 - iy));
-        }
-    }
+    qsp::ModeList m;
+    qsp::build_modes(p, m);
+    c->kx = std::move(m.kx); c->ky = std::move(m.ky); c->k2 = std::move(m.k2);
+    c->mode_id = std::move(m.mode_id); c->partner_id = std::move(m.partner_id);
 }
 
 bool same_kset(const qs_params &a, const qs_params &b) {

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def qs():
-    from paper_2607_24234_b300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2607_24234_b300 as mod
     return mod
 
@@ -106,3 +106,24 @@ def test_null_context_calls(qs):
     assert qs.lib.qs_query(None, 0, 0, ctypes.byref(v)) == qs.QS_ERR_ARG
     assert qs.lib.qs_sync(None) == qs.QS_ERR_ARG
     qs.lib.qs_free(None)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("dt", float("nan")), ("dt", float("inf")), ("dxi", float("nan")), ("gamma_b", float("nan")),
+    ("gamma_b", float("inf")), ("species", [(float("nan"), 1.0, 0.01)]), ("species", [(-1.0, 1.0, float("inf"))]),
+    ("k_list", [1.0, float("nan")]),
+])
+def test_nonfinite_parameters_rejected_by_both_entry_points(qs, field, value):
+    """qs_init and the allocation-free qs_sweep_noalloc share one check of the
+    problem statement: a non-finite parameter is an argument error, returned
+    on the host before any CUDA call."""
+    p = synth.scaled(synth.SLAB_2D, **{field: value})
+    st, ctx = _init(qs, p)
+    assert st == qs.QS_ERR_ARG and ctx.value is None
+    keep = []
+    prm = qs.make_params(p, "fp32", keep)
+    dummy = ctypes.c_void_p(0x1000)   # never dereferenced: the call returns first
+    ex = ctypes.cast(dummy, ctypes.POINTER(ctypes.c_int))
+    assert qs.lib.qs_sweep_noalloc(ctypes.byref(prm), dummy, None, ex, 0, 1, None, None) == qs.QS_ERR_ARG
+    prm.geom = 2
+    assert qs.lib.qs_sweep_noalloc(ctypes.byref(prm), dummy, None, ex, 0, 1, None, None) == qs.QS_ERR_UNSUPPORTED

@@ -114,3 +114,41 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(qs):
                                  ctypes.cast(ctypes.c_void_p(exb.data_ptr()), ctypes.POINTER(ctypes.c_int)),
                                  0, 1, None, None)
     assert st == qs.QS_ERR_UNSUPPORTED
+
+
+def test_noalloc_refuses_a_capturing_stream(qs):
+    """The tables come from pageable host memory, so a call made while its
+    stream is being captured into a CUDA graph is refused with nothing
+    enqueued (a captured copy would read host memory that is gone when the
+    graph runs); the same call outside capture works."""
+    import torch
+    p = synth.scaled(synth.BEAM_3D, nkx=16, nky=16, kmax=6.0, n_xi=64, dxi=0.05, length=3.2)
+    keep = []
+    prm = qs.make_params(p, "fp32", keep)
+    ref = qs.Solver(p, prec="fp32")
+    ref.seed_noise(1, 1e-6)
+    ck = ref.checkpoint()
+    Mp = ref.Mp
+    ref.close()
+    body = ck[64:]
+    nst = p["n_xi"] * Mp * 16
+    st = torch.from_numpy(body[:nst].copy()).cuda()
+    ex = torch.from_numpy(body[nst:].copy()).cuda()
+    exp_ = ctypes.cast(ctypes.c_void_p(ex.data_ptr()), ctypes.POINTER(ctypes.c_int))
+    side = torch.cuda.Stream()
+
+    def call():
+        return qs.lib.qs_sweep_noalloc(ctypes.byref(prm), ctypes.c_void_p(st.data_ptr()), None, exp_, 0, 2,
+                                       None, ctypes.c_void_p(side.cuda_stream))
+
+    assert call() == qs.QS_OK          # the first call on the device sets up the scratch address
+    side.synchronize()
+    before = st.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        rc = call()
+    assert rc == qs.QS_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    assert torch.equal(st, before)     # nothing was enqueued
+    assert call() == qs.QS_OK
+    side.synchronize()
