@@ -391,7 +391,7 @@ def run_batch(args):
     pk, pk_kind = peaks()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    alu = measure_alu_peaks(stream) if args.alu else None
+    alu = measure_alu_peaks(stream, args.alu_ms) if args.alu else None
     r = batch_leg(args, pk, pk_kind, alu)
     print(json.dumps({"metric": METRIC, "n_gpus": 1, "steps": r["jobs"], "warmup": 1,
                       "ms_per_step": r["ms_per_job"], "higher_is_better": True, "scaling": "weak",
@@ -401,11 +401,14 @@ def run_batch(args):
 def run_surrogate(args):
     """Learned surrogate, full size: 2^22 training samples from solver
     sweeps of batched-workload parameter sets (64 x 64 disc grid, dxi =
-    0.025, snapshots every 100 of 1000 steps), a validation split that
-    sets the fallback threshold (10% of queries flagged), 64 held-out runs
-    (parameter seed 1), 1e7 inference queries."""
+    0.025, snapshots every 100 of 1000 steps), trained by qs_sur_train; a
+    validation split sets the fallback threshold (10% of queries flagged);
+    64 held-out runs (parameter seed 1) are screened by qs_sur_screen, whose
+    flagged queries are answered by solver runs of their parameter sets; 1e7
+    inference queries are timed."""
     import torch
     from paper_2607_24234_b300 import surrogate as sur
+    torch.cuda.set_device(0)
     base = synth.scaled(synth.BATCH_BASE)
     snaps = list(range(100, 1001, 100))
     n_train = 1 << 22
@@ -418,35 +421,63 @@ def run_surrogate(args):
     X, Y = X[:n_train].contiguous(), Y[:n_train].contiguous()
     Xh, Yh, solver_ho = sur.generate(ho, snaps, (1 << 20) // len(snaps), seed=2, noise_seed=1)
     torch.cuda.synchronize()
+    batch = 16384
     t0 = time.perf_counter()
-    m, losses = sur.train(X, Y, epochs=args.sur_epochs, batch=16384, lr=2e-3, ensemble=4, seed=3)
+    m = sur.SurModel(X, Y, epochs=args.sur_epochs, batch=batch, lr=2e-3, ensemble=4, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    losses = m.losses()
     _, var_v, _ = m.infer(Xv)
     thr = float(torch.quantile(var_v[:, 0].float(), 0.9))
-    res = sur.evaluate(m, Xh, Yh)
-    res_fb = sur.evaluate(m, Xh, Yh, var_threshold=thr)
-    q = Xh.repeat((10_000_000 + Xh.shape[0] - 1) // Xh.shape[0], 1)[:10_000_000].contiguous()
-    m.infer(q[:1 << 16])
+    m.set_threshold(thr)
+    mean_h, _, mask_h = m.infer(Xh)
+    res = sur.score(mean_h, Yh)
+    # screening with the solver as fallback: with the held-out runs' own noise
+    # the solver answers the flagged queries as the held-out labels do; with
+    # fresh noise the answers are another realisation of the same runs
+    screen = {}
+    for tag, nseed in (("same_noise", 1), ("fresh_noise", 7)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y, _, mask, ns = m.screen(ho, Xh, noise_seed=nseed)
+        torch.cuda.synchronize()
+        sc = time.perf_counter() - t0
+        r = sur.score(y, Yh)
+        fl = mask.bool()
+        r_fl = sur.score(y[fl], Yh[fl]) if ns else None
+        r_sur_fl = sur.score(mean_h[fl], Yh[fl]) if ns else None
+        screen[tag] = {"noise_seed": nseed, "seconds": sc, "solver_answered": ns,
+                       "all_queries": r, "flagged_solver": r_fl, "flagged_surrogate_alone": r_sur_fl}
+    hm = Xh.shape[0]
+    m.infer(Xh[:1 << 16])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m.infer(q, thr)
+    m.infer(Xh)
+    torch.cuda.synchronize()
+    inf_h = time.perf_counter() - t0
+    q = Xh.repeat((10_000_000 + hm - 1) // hm, 1)[:10_000_000].contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.infer(q)
     torch.cuda.synchronize()
     inf_s = time.perf_counter() - t0
-    steps_per_epoch = n_train // 16384
-    flops_step = 6.0 * m.nparam * 16384 * 4
+    steps_total = (n_train // batch) * args.sur_epochs
+    nparam = 7 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 2 + 2
+    flops_step = 6.0 * nparam * batch * 4
     print(json.dumps({
         "metric": "surrogate: held-out error and inference queries/s", "workload": "surrogate_2p22",
         "unit": "queries/s", "value": 1e7 / inf_s, "higher_is_better": True,
-        "train": {"samples": n_train, "epochs": args.sur_epochs, "seconds": train_s,
+        "train": {"entry_point": "qs_sur_train", "samples": n_train, "epochs": args.sur_epochs, "seconds": train_s,
+                  "ms_per_step": 1e3 * train_s / steps_total, "steps": steps_total,
                   "loss_first": losses[0], "loss_last": losses[-1],
-                  "tflops": flops_step * steps_per_epoch * args.sur_epochs / train_s / 1e12,
-                  "ensemble": 4, "width": 256, "depth": 3},
+                  "tflops": flops_step * steps_total / train_s / 1e12, "ensemble": 4, "width": 256, "depth": 3},
         "data": {"train_instances": len(tr), "snapshots": snaps, "generation_s": gen_s,
                  "solver_s_train": solver_tr, "heldout_runs": len(ho), "solver_s_heldout": solver_ho},
-        "heldout": res, "fallback": {"var_threshold": thr, "chosen_on": "validation split, 90% coverage",
-                                     **res_fb},
-        "inference": {"queries": 10_000_000, "seconds": inf_s}}), flush=True)
+        "heldout": res,
+        "fallback": {"var_threshold": thr, "chosen_on": "validation split, 90% coverage",
+                     "flagged_fraction": float(mask_h.float().mean()), **screen},
+        "inference": {"queries": 10_000_000, "seconds": inf_s, "heldout_queries": hm, "heldout_seconds": inf_h}}),
+        flush=True)
     m.close()
 
 
@@ -563,7 +594,7 @@ def run_ours(args):
         return float(t.item())
 
     # FMA rates of this GPU, which the ALU-bound rooflines divide by
-    alu = measure_alu_peaks(stream) if args.alu else None
+    alu = measure_alu_peaks(stream, args.alu_ms) if args.alu else None
 
     value, total_s = aggregate(ws, upd_job * args.steps, float(np.sum(kern_ms)) / 1e3, reduce_max)
     ms_per_step = 1e3 * total_s / args.steps
@@ -782,6 +813,7 @@ def main():
     ap.add_argument("--batch-job-steps", type=int, default=1000)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-alu", dest="alu", action="store_false", help="skip the FMA-rate probes")
+    ap.add_argument("--alu-ms", type=float, default=1000.0, help="duration of each FMA-rate probe launch")
     ap.add_argument("--no-streaming", dest="streaming", action="store_false",
                     help="skip the HBM-streaming kernel leg")
     ap.add_argument("--streaming-job-steps", type=int, default=200)

@@ -389,6 +389,31 @@ qs_status qs_sur_losses(const qs_sur *s, float *host, int max_n, int *n_out);
 qs_status qs_sur_set_threshold(qs_sur *s, float var_threshold);
 void qs_sur_free(qs_sur *s);
 
+/* Parameter screening with the solver as fallback and judge.  X [n][7]
+ * fp32 device: queries as written by qs_sur_points (columns 0..2 name a
+ * parameter set, 3..6 the point (xi, t, |k|, angle)).  The ensemble answers
+ * every query (y, y_var [n][2] fp32 device, as qs_sur_infer); queries whose
+ * output-0 variance exceeds the model's threshold are answered by the solver
+ * instead: each is matched to the entry of sets[0..n_sets) (host; same k set,
+ * precision, model, front and species count) whose (ln n_b0/n_p, ln gamma_b,
+ * length) equal its columns 0..2 to fp32 rounding; the sets that have such
+ * queries run in solver contexts (instance counter of the noise = the set's
+ * index, so set i draws the noise it would draw as instance i of one context
+ * holding every set; seeded with noise_seed and amplitude), are stepped to
+ * each queried t (a whole number of steps), and the targets of
+ * qs_sur_points are evaluated at the queried cell and mode.  Those rows get
+ * y0 = the solver's log envelope, y1 = +-30 (the class as a saturated
+ * logit), zero variance, and mask = 1; the other rows keep the ensemble's
+ * answer and mask = 0.  *n_solved (may be NULL) receives the number of
+ * solver-answered rows.  The solver contexts use lend's stream and allocator
+ * (lend may be NULL: default stream, cudaMalloc), hold at most ~16 GiB each
+ * (sets are split across contexts beyond that), and are freed before the
+ * call returns.  Synchronises the device.  QS_ERR_ARG if a flagged query
+ * matches no set, lies outside its line, or names an inactive mode. */
+qs_status qs_sur_screen(qs_sur *s, qs_ctx *lend, const qs_params *sets, int n_sets, uint64_t noise_seed,
+                        double amplitude, const void *X, int64_t n, void *y, void *y_var, uint8_t *mask,
+                        int64_t *n_solved);
+
 /* Training samples for the surrogate from one snapshot of ctx (the
  * device buffer `snap` written by qs_diag(QS_DIAG_MAG) at the current step;
  * snap_bytes its size).  n samples, cells drawn uniformly over all

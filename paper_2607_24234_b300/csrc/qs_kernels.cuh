@@ -34,6 +34,7 @@ struct InstDev {
     double q[2];
     double qm_g[2];       // (q/m)/gamma
     double qm_g3[2];      // (q/m)/gamma^3, 0 for the reduced model
+    int noise_inst;       // instance word of the noise seed's Philox counter
 };
 
 struct SweepArgs {
@@ -730,7 +731,8 @@ __global__ void k_seed(const SeedArgs a) {
                     const int id = a.mode_id[mode], pid = a.partner_id[mode];
                     const bool cj = pid < id;
                     double g1, g2;
-                    normal2(a.seed, (uint32_t)j, (uint32_t)(cj ? pid : id), (uint32_t)inst, (uint32_t)sp, g1, g2);
+                    normal2(a.seed, (uint32_t)j, (uint32_t)(cj ? pid : id), (uint32_t)I.noise_inst, (uint32_t)sp, g1,
+                            g2);
                     const double am = a.amp * a.shape[I.cell_off + j] * 0.70710678118654752440;
                     nr = am * g1;
                     ni = cj ? -am * g2 : am * g2;

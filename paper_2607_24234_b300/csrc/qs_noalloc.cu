@@ -71,10 +71,10 @@ extern "C" qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *the
                                       int64_t step0, int n_steps, int *dev_status, void *stream) {
     // ---- host-side checks (nothing is enqueued on failure) ----
     if (!p || !state || n_steps < 1 || step0 < 0) return QS_ERR_ARG;
+    if (p->front == QS_FRONT_HELD) return QS_ERR_UNSUPPORTED;   // held values need a table of their own
     char msg[256];
     qs_status vs = qsp::validate(*p, 0, msg, sizeof msg);
     if (vs) return vs;
-    if (p->front == QS_FRONT_HELD) return QS_ERR_UNSUPPORTED;
     if (p->prec == QS_FP32_RENORM && !exponents) return QS_ERR_ARG;
     if (p->prec == QS_FP64 && !theta) return QS_ERR_ARG;
     {

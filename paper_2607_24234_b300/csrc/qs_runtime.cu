@@ -10,6 +10,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -605,6 +606,7 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
         I.n_grp = (q.n_xi + qsk::GRP - 1) / qsk::GRP;
         I.cell_off = cell;
         I.grp_off = grp;
+        I.noise_inst = i;
         I.c = std::cos(q.dxi); I.s = std::sin(q.dxi);
         I.ch = std::cos(0.5 * q.dxi); I.sh = std::sin(0.5 * q.dxi);
         I.dt = q.dt; I.dxi = q.dxi;

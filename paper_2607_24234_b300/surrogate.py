@@ -18,7 +18,7 @@ import time
 
 import numpy as np
 
-from . import lib, QSError, Solver, REC_MAG, Allocator
+from . import lib, QSError, Solver, REC_MAG, Allocator, Params, make_params
 
 _vp = ctypes.c_void_p
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -47,6 +47,9 @@ def _setup():
     L.qs_sur_set_threshold.argtypes = [_vp, ctypes.c_float]
     L.qs_sur_free.argtypes = [_vp]
     L.qs_sur_free.restype = None
+    L.qs_sur_screen.argtypes = [_vp, _vp, ctypes.POINTER(Params), ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
+                                _vp, i64, _vp, _vp, _vp, ctypes.POINTER(i64)]
+    L.qs_sur_screen.restype = ctypes.c_int
     for n in ("qs_mlp_create", "qs_mlp_set_norm", "qs_mlp_params", "qs_mlp_layout", "qs_mlp_train_step",
               "qs_mlp_grads", "qs_mlp_infer", "qs_sur_points", "qs_sur_train", "qs_sur_infer", "qs_sur_losses",
               "qs_sur_set_threshold"):
@@ -182,6 +185,27 @@ class SurModel:
             raise QSError(st, "qs_sur_infer failed")
         return mean, var, mask
 
+    def screen(self, problems, X, noise_seed, amplitude=1e-6, prec="fp32", lend=None):
+        """Screening with the solver as fallback (qs_sur_screen): the ensemble
+        answers every query of X; queries above the variance threshold are
+        answered by solver runs of their parameter sets (`problems`, the sets
+        the queries may name).  Returns (y, var, mask, n_solved): mask = 1
+        where the solver answered (y[:, 1] is then a saturated logit)."""
+        import torch
+        n = X.shape[0]
+        keep = []
+        arr = (Params * len(problems))(*[make_params(q, prec, keep) for q in problems])
+        y = torch.empty((n, 2), dtype=torch.float32, device=X.device)
+        var = torch.empty_like(y)
+        mask = torch.empty(n, dtype=torch.uint8, device=X.device)
+        ns = ctypes.c_int64()
+        st = lib.qs_sur_screen(self.h, lend.ctx if lend is not None else None, arr, len(problems),
+                               int(noise_seed) & 0xFFFFFFFFFFFFFFFF, float(amplitude), _ptr(X), n, _ptr(y),
+                               _ptr(var), _ptr(mask), ctypes.byref(ns))
+        if st != 0:
+            raise QSError(st, lib.qs_last_error(lend.ctx if lend is not None else None).decode())
+        return y, var, mask, ns.value
+
     def close(self):
         if self.h:
             lib.qs_sur_free(self.h)
@@ -249,24 +273,21 @@ def train(X, Y, epochs=20, batch=8192, lr=1e-3, ensemble=4, width=256, depth=3, 
     return m, losses
 
 
-def evaluate(m, X, Y, var_threshold=float("inf")):
-    """Held-out errors: RMSE of the envelope, class accuracy, and the same
-    after answering flagged queries with the solver's own values."""
-    mean, var, mask = m.infer(X, var_threshold)
+def score(mean, Y):
+    """Envelope RMSE / MAE and class accuracy of outputs `mean` [n][2] (target
+    units, class logit) against labels Y [n][2]."""
     yt = Y[:, 0]
     err = (mean[:, 0] - yt)
     cls = (mean[:, 1] > 0).float()
-    flagged = mask.bool()
-    err_fb = err.clone()
-    err_fb[flagged] = 0.0
-    cls_fb = cls.clone()
-    cls_fb[flagged] = Y[flagged, 1]
     return {
         "rmse": float(err.pow(2).mean().sqrt()),
         "mae": float(err.abs().mean()),
         "target_std": float(yt.std()),
         "accuracy": float((cls == Y[:, 1]).float().mean()),
-        "flagged_fraction": float(flagged.float().mean()),
-        "rmse_with_fallback": float(err_fb.pow(2).mean().sqrt()),
-        "accuracy_with_fallback": float((cls_fb == Y[:, 1]).float().mean()),
     }
+
+
+def evaluate(m, X, Y):
+    """Held-out errors of the ensemble alone (no fallback)."""
+    mean, _, _ = m.infer(X)
+    return score(mean, Y)
