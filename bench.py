@@ -256,8 +256,8 @@ def measure_alu_peaks(stream, target_ms=1000.0):
     import paper_2607_24234_b300 as qs
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     sink = torch.zeros(4, dtype=torch.float64, device="cuda")
-    blocks, threads = 4 * n_sm, 256
-    out = {"launch": f"{blocks} CTAs x {threads} threads (4 per SM), 8 independent FMA chains per thread"}
+    blocks, threads = 8 * n_sm, 256
+    out = {"launch": f"{blocks} CTAs x {threads} threads (8 per SM, 64 warps), 8 independent FMA chains per thread"}
     for name, kind in (("ffma2", qs.PROBE_FFMA2), ("ffma", qs.PROBE_FFMA), ("dfma", qs.PROBE_DFMA)):
         iters = 2000
         for attempt in range(2):   # calibrate on a short launch, then one of ~target_ms
@@ -359,8 +359,10 @@ def batch_leg(args, pk, pk_kind, alu=None):
     if args.batch_tune:
         s.tune(reps=args.tune_reps, cache_path=os.path.join(ROOT, "paper_2607_24234_b300", "tune_cache.json"))
     else:
-        v, V, w, pp, cps = (int(x) for x in args.batch_shape.split(","))
-        s.set_launch(warps_per_cta=w, prefetch=V, persistent=pp, ctas_per_sm=cps, variant=v)
+        f = [int(x) for x in args.batch_shape.split(",")]
+        v, V, w, pp, cps = f[:5]
+        s.set_launch(warps_per_cta=w, prefetch=V, persistent=pp, ctas_per_sm=cps, variant=v,
+                     scan_cells=f[5] if len(f) > 5 else 8)
     s.step(2)
     torch.cuda.synchronize()
     clk = Clocks(0)
@@ -546,8 +548,10 @@ def run_ours(args):
     s = qs.Solver(p, prec="fp32", stream=stream)
     s.seed_noise(rank, p["amplitude"])
     if args.shape:
-        variant, prefetch, warps = (int(x) for x in args.shape.split(","))
-        s.set_launch(warps_per_cta=warps, prefetch=prefetch, persistent=0, ctas_per_sm=8, variant=variant)
+        f = [int(x) for x in args.shape.split(",")]
+        variant, prefetch, warps = f[:3]
+        s.set_launch(warps_per_cta=warps, prefetch=prefetch, persistent=0, ctas_per_sm=8, variant=variant,
+                     scan_cells=f[3] if len(f) > 3 else 8)
     elif args.tune:
         # trials of tune_reps steps per call: long enough that the resident
         # variant's one-off state load and store is amortised as in a job
@@ -797,7 +801,8 @@ def main():
                     help="skip the autotuner (use the library's default launch shape)")
     ap.add_argument("--tune-reps", type=int, default=64, help="slow-time steps per autotuner trial")
     ap.add_argument("--shape", default=None,
-                    help="force the launch shape 'variant,prefetch,warps_per_cta' (no autotuner)")
+                    help="force the launch shape 'variant,prefetch,warps_per_cta[,scan_cells]' (no autotuner; "
+                         "resident: scan_cells 1 keeps Theta in registers)")
     ap.add_argument("--nk", type=int, default=None,
                     help="k grid of nk x nk instead of 256 x 256 (small cases for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -823,7 +828,7 @@ def main():
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-workload leg")
     ap.add_argument("--batch-jobs", type=int, default=1)
     ap.add_argument("--batch-shape", default="3,32,8,0,1",
-                    help="batched workload launch 'variant,prefetch,warps_per_cta,persistent,ctas_per_sm'")
+                    help="batched workload launch 'variant,prefetch,warps_per_cta,persistent,ctas_per_sm[,scan_cells]'")
     ap.add_argument("--batch-tune", action="store_true",
                     help="autotune the batched workload (copies its ~107 GB state; slow)")
     args = ap.parse_args()

@@ -232,8 +232,13 @@ typedef struct {
     int ctas_per_sm;     /* persistent grid size = ctas_per_sm * SM count    */
     int variant;         /* QS_VARIANT_*                                    */
     int scan_cells;      /* SCAN: cells per lane per sub-chunk (1..64); the
-                          * lanes per mode along xi are `prefetch` (2..32)  */
+                          * lanes per mode along xi are `prefetch` (2..32).
+                          * RESIDENT: QS_RES_THETA_REGS keeps Theta in
+                          * registers at 32 cells of one species or 16 of
+                          * two (1|2|4|8 warps); any other value keeps it in
+                          * shared memory there                             */
 } qs_launch;
+enum { QS_RES_THETA_REGS = 1 };
 
 qs_status qs_set_launch(qs_ctx *ctx, const qs_launch *l);
 qs_status qs_get_launch(const qs_ctx *ctx, qs_launch *l);

@@ -43,7 +43,11 @@ constexpr int RES_HYST = 16;
 constexpr int RES_EVERY = 16;         // steps between renormalisation checks (a power of two; 8 measured 1.7 % slower)
 constexpr int RES_NONE = -(1 << 20);   // exponent of a thread that holds no value yet
 constexpr int RES_REGS64 = 128;       // register cap of the 64-thread shared-Theta kernel (96..224 measured: 128 best)
-constexpr int RES_WSTRIDE = 512;       // shared-memory row of the cell weights (max threads)
+
+// register cap per instantiation: 32 cells of state per thread with Theta in
+// registers (V NS = 32, TT = 0) need the whole file (no spills at 255; the
+// CTA then has at most 256 threads)
+constexpr int res_maxnreg(int NS, int V, int TT) { return TT == 64 ? RES_REGS64 : (TT == 0 && V * NS == 32 ? 255 : 128); }
 
 struct RotF { float c, s; };
 __device__ __forceinline__ RotF rotf(double ang) {
@@ -79,17 +83,19 @@ __device__ __forceinline__ float p2(int e) { return __int_as_float((max(-127, mi
 
 // TT > 0 keeps Theta in shared memory (float2 rows [v * NS + sp][thread],
 // read and written once per cell in pass 2, next to float rows of the
-// weights dt n_b0) so that 32 cells of one species, or 16 of two, fit the register
-// budget; the CTA then has exactly TT threads (compile-time row stride).
-// TT = 0 keeps Theta in registers and only the weights in shared memory.
+// weights dt n_b0) so that 32 cells of one species, or 16 of two, fit a
+// 128-register budget; the CTA then has exactly TT threads (compile-time row
+// stride).  TT = 0 keeps Theta in registers and only the weights in shared
+// memory, as (w, w) pairs in rows [v * NS + sp][thread] of the CTA's size,
+// so that each cell's weight is one 8-byte load already in the packed form.
 template <int NS, int V, int TT>
-__global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const SweepArgs a) {
+__global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs a) {
     constexpr bool THS = TT > 0;
     static_assert(GRP % V == 0, "a thread's cells lie in one exponent group");
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int CB = 2;                     // cells per shared-memory batch (THS; 4 and 8 measured 0.7 % and 0.3 % slower)
     static_assert(V % CB == 0, "whole batches");
-    extern __shared__ float4 sdyn[];          // THS: Theta then w, rows [v * NS + sp][T]; else w [v * NS + sp][RES_WSTRIDE]
+    extern __shared__ float4 sdyn[];          // THS: Theta then w, rows [v * NS + sp][T]; else (w, w) [v * NS + sp][T]
     __shared__ float4 sZ[2][RES_MAX_WARPS];   // inclusive warp aggregate (lane 31)
     __shared__ int sE[2][RES_MAX_WARPS];      // its exponent
     __shared__ int sM[2][RES_MAX_WARPS];      // largest exponent in the warp
@@ -102,7 +108,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
     const int T = THS ? TT : (int)blockDim.x, nw = T >> 5;
     float2 *sT = reinterpret_cast<float2 *>(sdyn) + tid;                      // THS: row stride T = TT
     float *sWt = reinterpret_cast<float *>(reinterpret_cast<float2 *>(sdyn) + V * NS * (THS ? TT : 0)) + tid;
-    float *sWr = reinterpret_cast<float *>(sdyn) + tid;                       // !THS: row stride RES_WSTRIDE
+    float2 *sWr = reinterpret_cast<float2 *>(sdyn) + tid;                     // !THS: row stride T
     int item = blockIdx.x;
     int buf = 0;
     for (;;) {
@@ -203,7 +209,7 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                     sWt[(v * NS + sp) * T] = wv;
                 } else {
                     xt[v][sp] = make_float2(y.tr, y.ti);
-                    sWr[(v * NS + sp) * RES_WSTRIDE] = wv;   // only this thread reads it back
+                    sWr[(v * NS + sp) * T] = make_float2(wv, wv);   // only this thread reads it back
                 }
             }
         }
@@ -340,10 +346,12 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
                         if constexpr (!UPD) continue;
                         float2 &y = xn[v][sp];
                         float2 &th = THS ? zt[THS ? u : 0][sp] : xt[THS ? 0 : v][sp];
-                        const float wv = THS ? zw[THS ? u : 0][sp] : sWr[(v * NS + sp) * RES_WSTRIDE];
+                        float2 wv2;
+                        if constexpr (THS) wv2 = F2(zw[THS ? u : 0][sp]);
+                        else wv2 = sWr[(v * NS + sp) * T];
                         if (NS == 1) th = pfma(Ach, uu, pfma(Ash, d, pfma(AB, r, th)));
                         else th = pfma(F2(A[sp]), m, pfma(F2(-B[sp]), r, th));
-                        y = pfma(F2(wv), th, y);
+                        y = pfma(wv2, th, y);
                         if (GM) gmax = fmaxf(gmax, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(th.x), fabsf(th.y))));
                     }
                     if constexpr (UPD) {
@@ -545,9 +553,9 @@ __global__ void __maxnreg__(TT == 64 ? RES_REGS64 : 128) k_sweep_res(const Sweep
     }
 }
 
-// dynamic shared memory of one CTA (TT > 0: TT threads)
-constexpr size_t res_smem_bytes(int NS, int V, int TT) {
-    return TT > 0 ? (size_t)V * NS * TT * (sizeof(float2) + sizeof(float)) : (size_t)V * NS * RES_WSTRIDE * sizeof(float);
+// dynamic shared memory of one CTA of T threads (TT > 0: T = TT)
+constexpr size_t res_smem_bytes(int NS, int V, int TT, int T) {
+    return TT > 0 ? (size_t)V * NS * TT * (sizeof(float2) + sizeof(float)) : (size_t)V * NS * T * sizeof(float2);
 }
 
 }  // namespace qsk

@@ -187,16 +187,22 @@ int res_threads_per_line(int n_xi, int V) { return ((n_xi + V - 1) / V + 31) & ~
 // Tmax: a whole number of lines (so no thread idles beyond the warp rounding
 // of a line)
 int res_cta_threads(int tl, int Tmax) { return tl * std::max(1, Tmax / tl); }
+// Theta in registers at the largest cells per thread (launch.scan_cells)
+bool res_regs(int NS, int V, int scan_cells) {
+    return scan_cells == QS_RES_THETA_REGS && ((NS == 1 && V == 32) || (NS == 2 && V == 16));
+}
+
 // exact CTA sizes exist for every variant but two species at 16 cells per
 // thread (Theta in shared memory, CTA of 128 | 256 | 512 threads only)
-bool res_exact_sizes(int NS, int V) { return !(NS == 2 && V == 16); }
+bool res_exact_sizes(int NS, int V, bool regs) { return regs || !(NS == 2 && V == 16); }
 
 // Resident variant: an item is (instance, first mode) for the lines one CTA
 // holds.  Instances are grouped by CTA size (one launch per group), longest
 // lines first within a group when persistent.
 qs_status build_res_items(qs_ctx *c) {
     const int V = c->launch.prefetch, Tmax = 32 * c->launch.warps_per_cta, P = c->launch.persistent;
-    const long long key = ((long long)V << 32) | ((long long)Tmax << 1) | P;
+    const bool regs = res_regs(c->NS, V, c->launch.scan_cells);
+    const long long key = ((long long)V << 32) | ((long long)regs << 20) | ((long long)Tmax << 1) | P;
     if (c->res_key == key && c->res_items_d) return QS_OK;
     std::vector<int> order(c->n_inst);
     for (int i = 0; i < c->n_inst; ++i) order[i] = i;
@@ -204,7 +210,7 @@ qs_status build_res_items(qs_ctx *c) {
     for (int i : order) {
         const int tl = res_threads_per_line(c->inst[i].n_xi, V);
         if (tl > Tmax) return fail(c, QS_ERR_ARG, "resident: a line of instance %d needs more than %d threads", i, Tmax);
-        by_t[res_exact_sizes(c->NS, V) ? res_cta_threads(tl, Tmax) : Tmax].push_back(i);
+        by_t[res_exact_sizes(c->NS, V, regs) ? res_cta_threads(tl, Tmax) : Tmax].push_back(i);
     }
     std::vector<int2> items;
     c->res_groups.clear();
@@ -379,13 +385,14 @@ SweepArgs sweep_args(qs_ctx *c, long long step0, int n_steps, int update, int re
 
 template <int NS, int V, int TT>
 cudaError_t launch_res_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) {
-    const size_t smem = qsk::res_smem_bytes(NS, V, TT);
-    static int opted = 0;   // shared-memory opt-in (dynamic + static may pass 48 KiB), once per instantiation
-    if (!opted) {
+    const size_t smem = qsk::res_smem_bytes(NS, V, TT, threads);
+    // shared-memory opt-in (dynamic + static may pass 48 KiB), raised as larger CTAs appear
+    static size_t opted = 0;
+    if (smem > opted) {
         cudaError_t e = cudaFuncSetAttribute(qsk::k_sweep_res<NS, V, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        opted = 1;
+        opted = smem;
     }
     qsk::k_sweep_res<NS, V, TT><<<grid, threads, smem, c->stream>>>(a);
     return cudaGetLastError();
@@ -393,8 +400,11 @@ cudaError_t launch_res_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) 
 
 // resident instantiations: Theta in registers (any CTA size) for 8 | 16 cells
 // of one species and 8 of two; Theta in shared memory for 32 cells of one
-// species (CTA of 64 | 128 | 256) and 16 of two (CTA of 128 | 256 | 512)
-cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V) {
+// species (CTA of 64 | 128 | 256) and 16 of two (CTA of 128 | 256 | 512), or,
+// with `regs`, in registers there too (255 registers, CTA of at most 256)
+cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V, bool regs) {
+    if (regs && c->NS == 1 && V == 32) return T <= 256 ? launch_res_t<1, 32, 0>(c, a, grid, T) : cudaErrorInvalidValue;
+    if (regs && c->NS == 2 && V == 16) return T <= 256 ? launch_res_t<2, 16, 0>(c, a, grid, T) : cudaErrorInvalidValue;
     if (c->NS == 1) {
         if (V == 32) switch (T) {   // every whole number of 64-thread lines up to 4, and 96 .. 224 for 96-thread lines
             case 64: return launch_res_t<1, 32, 64>(c, a, grid, T);
@@ -415,7 +425,8 @@ cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V) {
     return launch_res_t<2, 8, 0>(c, a, grid, T);
 }
 
-bool res_shape_ok(int NS, int V, int w) {
+bool res_shape_ok(int NS, int V, int w, bool regs = false) {
+    if (regs) return res_regs(NS, V, QS_RES_THETA_REGS) && (w == 1 || w == 2 || w == 4 || w == 8);
     if (NS == 1 && V == 32) return w == 2 || w == 4 || w == 8;
     if (NS == 2 && V == 16) return w == 4 || w == 8 || w == 16;
     return (V == 8 || (V == 16 && NS == 1)) && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16);
@@ -464,7 +475,8 @@ qs_status launch_resident(qs_ctx *c, long long step0, int n_steps, int update, i
                     const long long g = (long long)c->launch.ctas_per_sm * c->n_sm;
                     grid = dim3((unsigned)std::max<long long>(1, std::min<long long>(g, grp.count)));
                 }
-                cudaError_t e = launch_res(c, a, grid, grp.threads, c->launch.prefetch);
+                cudaError_t e = launch_res(c, a, grid, grp.threads, c->launch.prefetch,
+                                           res_regs(c->NS, c->launch.prefetch, c->launch.scan_cells));
                 if (e != cudaSuccess) return fail(c, QS_ERR_CUDA, "resident sweep launch: %s", cudaGetErrorString(e));
                 ++c->n_launch;
             }
@@ -954,9 +966,10 @@ qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
     if (l->variant == QS_VARIANT_RESIDENT) {
         if (c->prec != QS_FP32_RENORM) return fail(c, QS_ERR_UNSUPPORTED, "the resident variant is FP32 only");
         const int V = l->prefetch;
-        if (!res_shape_ok(c->NS, V, w))
+        if (!res_shape_ok(c->NS, V, w, res_regs(c->NS, V, l->scan_cells)))
             return fail(c, QS_ERR_ARG, "resident: cells per thread 8|16 (any CTA size) or 32 (one species, 2|4|8 "
-                                       "warps); two species: 8 (any) or 16 (4|8|16 warps)");
+                                       "warps; Theta in registers: 1|2|4|8); two species: 8 (any) or 16 (4|8|16 "
+                                       "warps; Theta in registers: 1|2|4|8)");
         if (res_threads_per_line(max_nxi(c), V) > 32 * w)
             return fail(c, QS_ERR_ARG, "resident: a line of %d cells needs %d threads, the CTA has %d", max_nxi(c),
                         res_threads_per_line(max_nxi(c), V), 32 * w);

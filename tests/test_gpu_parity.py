@@ -212,6 +212,39 @@ def test_fitted_growth_rates_fp32(qs):
     s.close()
 
 
+GROWTH_CASE = dict(n_xi=256, dxi=0.05, length=12.8, k_list=[1.0, 2.5, 4.0], species=[(-1.0, 1.0, 0.05)],
+                   gamma_b=20.0)
+
+
+def fitted_rates_match(advance, state_nb, steps=400, stride=10, seed=8, tol=5e-3):
+    """Fitted growth rates of a GPU path against the FP64 oracle: the path
+    advances by `stride` steps per call (advance(stride)) and its state is
+    read after every call (state_nb() -> n_b [mode][species][xi]); the oracle
+    runs the same chunks.  Least-squares slope of ln|n_b| against tau over the
+    last 25 % of the snapshots at fixed (k, xi), relative difference <= tol
+    (0.5 %, the FP32 bar)."""
+    p = synth.scaled(synth.SLAB_2D, **GROWTH_CASE)
+    nb_o, th_o = oracle.seed_noise(p, seed, 1e-6)
+    n = steps // stride
+    g, o = [], []
+    for i in range(n):
+        advance(stride)
+        oracle.sweep(p, nb_o, th_o, i * stride, stride)
+        g.append(np.log(np.abs(state_nb()[:, 0, :])))
+        o.append(np.log(np.abs(nb_o[:, 0, :])))
+    g, o = np.array(g), np.array(o)
+    sel = slice(n - n // 4, n)
+    tau = (np.arange(n)[sel] + 1) * stride * p["dt"]
+    worst = 0.0
+    for mo in range(3):
+        for j in (40, 120, 250):
+            rg = np.polyfit(tau, g[sel, mo, j], 1)[0]
+            ro_ = np.polyfit(tau, o[sel, mo, j], 1)[0]
+            worst = max(worst, abs(rg / ro_ - 1))
+    assert worst <= tol, worst
+    return worst
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_kgrid_pairs_conjugate_bitwise(qs, prec):
     p = synth.scaled(synth.BEAM_3D, nkx=16, nky=16, kmax=4.0, n_xi=96, dxi=0.05, length=4.8)

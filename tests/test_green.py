@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from test_gpu_parity import FP32_LOG_TOL, _log_err, _run_oracle
+from test_gpu_parity import FP32_LOG_TOL, GROWTH_CASE, _log_err, _run_oracle, fitted_rates_match
 
 pytestmark = pytest.mark.gpu
 
@@ -136,3 +136,14 @@ def test_green_beam3d_full_size_sampled(qs):
     nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, mode_sel=sel)
     oracle.sweep(p, nb_o, th_o, 0, p["n_steps"], k2=md["k2"][sel])
     assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+
+
+def test_fitted_growth_rates_green(qs):
+    """Fitted growth rates of the Green's-function path: 40 chained
+    qs_step_green calls of 10 steps (after the first, Theta is non-zero, so
+    the Theta impulse responses enter too); within 0.5 % of the FP64 oracle."""
+    p = synth.scaled(synth.SLAB_2D, **GROWTH_CASE)
+    s = qs.Solver(p, prec="fp32")
+    s.seed_noise(8, 1e-6)
+    fitted_rates_match(lambda k: s.step_green(k), lambda: s.state_arrays()[0])
+    s.close()

@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 import synth
-from test_gpu_parity import FP32_LOG_TOL, SMALL, _log_err, _run_gpu, _run_oracle, _small_problem
+from test_gpu_parity import (FP32_LOG_TOL, GROWTH_CASE, SMALL, _log_err, _run_gpu, _run_oracle, _small_problem,
+                             fitted_rates_match)
 
 pytestmark = pytest.mark.gpu
 
@@ -25,8 +26,8 @@ def qs():
     return m
 
 
-def _res(V=8, w=4, pers=0, cps=2):
-    return dict(warps_per_cta=w, prefetch=V, persistent=pers, ctas_per_sm=cps, variant=3)
+def _res(V=8, w=4, pers=0, cps=2, regs=False):
+    return dict(warps_per_cta=w, prefetch=V, persistent=pers, ctas_per_sm=cps, variant=3, scan_cells=1 if regs else 8)
 
 
 def _fits(n_xi, V, w):
@@ -313,3 +314,59 @@ def test_resident_nonfinite_detected(qs):
     s.step(2)
     s.sync()
     s.close()
+
+
+@pytest.mark.parametrize("V,w", [(32, 2), (8, 1)])
+def test_fitted_growth_rates_resident(qs, V, w):
+    """Fitted growth rates (last 25 % of 40 snapshots over 400 steps) of the
+    resident kernel itself: every 10-step call is one on-chip launch, the
+    state is read back between calls; within 0.5 % of the FP64 oracle."""
+    p = synth.scaled(synth.SLAB_2D, **GROWTH_CASE)
+    s = qs.Solver(p, prec="fp32")
+    s.set_launch(**_res(V, w))
+    s.seed_noise(8, 1e-6)
+    n0 = s.launch_count()
+    fitted_rates_match(lambda k: s.step(k), lambda: s.state_arrays()[0])
+    assert s.launch_count() - n0 == 40          # one resident launch per call, nothing else
+    s.close()
+
+
+# Theta in registers at the largest cells per thread (32 of one species, 16 of
+# two): the same arithmetic as the shared-memory form, in another storage
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"nxi{c[0]}-m{len(c[1])}-s{len(c[2])}-{c[3]}-{c[4]}-{c[5]}-{c[6]}")
+def test_small_cases_resident_theta_registers(qs, case):
+    p, held, user, sd, steps = _small_problem(case)
+    V = 32 if len(p["species"]) == 1 else 16
+    w = next(w for w in (1, 2, 4, 8) if _fits(p["n_xi"], V, w))
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=sd, held=held, user=user, launch=_res(V, w, regs=True))
+    nb_o, th_o = _run_oracle(p, steps, seed=sd, held=held, user=user)
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL
+    assert _log_err(th, th_o) <= FP32_LOG_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("n_xi,V,w,pers,species", [
+    (700, 32, 8, 0, None),      # 22 -> 32 threads per line: 8 lines per 256-thread CTA
+    (2048, 32, 2, 1, None),     # the benchmark's line length, one line per CTA
+    (2100, 32, 4, 0, None),     # 66 -> 96 threads: 3 warps, cross-warp prefix
+    (1000, 16, 4, 1, [(-1.0, 1.0, 0.03), (1.0, 1836.0, 0.05)]),
+])
+def test_theta_registers_packing_and_bitwise(qs, n_xi, V, w, pers, species):
+    """Ragged packing, and bit-identity with the shared-memory form (same
+    operations in the same order) and across chunked calls."""
+    sp = species or [(-1.0, 1.0, 0.05)]
+    p = synth.scaled(synth.SLAB_2D, n_xi=n_xi, dxi=0.05, length=n_xi * 0.05, k_list=list(np.linspace(0.3, 5.0, 37)),
+                     species=sp, gamma_b=20.0, dt=1.5)
+    steps = 40
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=("noise", 5, 1e-6), launch=_res(V, w, pers, regs=True))
+    s.close()
+    nb_o, th_o = _run_oracle(p, steps, seed=("noise", 5, 1e-6))
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    ws = next(x for x in (2, 4, 8, 16) if _fits(n_xi, V, x) and (x >= 4 or len(sp) == 1))
+    s2, nb2, th2 = _run_gpu(qs, p, "fp32", steps, seed=("noise", 5, 1e-6), launch=_res(V, ws, pers))
+    s2.close()
+    assert np.array_equal(nb, nb2) and np.array_equal(th, th2)
+    s3, nb3, th3 = _run_gpu(qs, p, "fp32", steps, seed=("noise", 5, 1e-6), launch=_res(V, w, pers, regs=True),
+                            chunks=[17, 1, 22])
+    s3.close()
+    assert np.array_equal(nb, nb3) and np.array_equal(th, th3)
