@@ -489,6 +489,8 @@ def narrow_leg(args, pk, pk_kind):
     import torch
     from paper_2607_24234_b300.realspace import RealSpace
     p = synth.NARROW_BEAM
+    if args.narrow_nxi:   # fewer xi slices (profiling); named as such
+        p = synth.scaled(p, n_xi=args.narrow_nxi, name=f"narrow_beam_256sq_{args.narrow_nxi}xi_profiling")
     stream = torch.cuda.current_stream()
     g = RealSpace(p, stream=stream)
     g.seed(seed=0, amplitude=p["amplitude"], offset=p["offset"])
@@ -825,6 +827,7 @@ def main():
     ap.add_argument("--streaming-jobs", type=int, default=3)
     ap.add_argument("--no-narrow", dest="narrow", action="store_false", help="skip the narrow-beam leg")
     ap.add_argument("--narrow-reps", type=int, default=2)
+    ap.add_argument("--narrow-nxi", type=int, default=None, help="xi slices of the narrow beam (profiling)")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-workload leg")
     ap.add_argument("--batch-jobs", type=int, default=1)
     ap.add_argument("--batch-shape", default="3,32,8,0,1",

@@ -195,7 +195,10 @@ enum { QS_Q_N_MODES = 0,      /* active modes                              */
        QS_Q_STATE_BYTES = 5,  /* size of a QS_DIAG_STATE checkpoint        */
        QS_Q_SNAPSHOT_BYTES = 6, /* bytes of one snapshot for kinds = arg  */
        QS_Q_CELL_OFFSET = 7,  /* first cell of instance arg                */
-       QS_Q_LAUNCH = 8 };     /* packed launch shape in use (see qs_launch) */
+       QS_Q_LAUNCH = 8,       /* packed launch shape in use (see qs_launch) */
+       QS_Q_RES_EVERY = 9 };  /* resident variant's renormalisation interval
+                               * (steps; 0: the variant is refused, see
+                               * qs_growth_bound)                          */
 
 /* Query a size or counter; `arg` is used by QS_Q_SNAPSHOT_BYTES (kinds)
  * and QS_Q_CELL_OFFSET (instance). */
@@ -285,6 +288,23 @@ qs_status qs_sync(qs_ctx *ctx);
  * QS_ERR_TIMEOUT.  The context is usable again after qs_debug_waits(ctx,
  * limit, 0) and a reseed.  Other kernels have no device-side waits. */
 qs_status qs_debug_waits(qs_ctx *ctx, int64_t spin_limit, int unsatisfiable);
+
+/* Upper bound of the scheme's growth per slow-time step for a problem
+ * statement (host only, no CUDA call).  One step maps (n_b, Theta) by the
+ * kick of Eqs. (8)-(9) and the drift, with |n_p| <= L max|rho| over a line
+ * of length L (Eq. 5) and kappa k^2, kappa <= 1 (Eq. 14); with
+ *   a = dt max|q/m| (1/gamma + 1/gamma^3) sum_s |q_s| (2 + L),
+ *   b = dt max_s n_bs0 (peak of the profile),
+ * the step is bounded, in suitably weighted max norms, by a symmetric 2 x 2
+ * matrix whose spectral radius 1 + ab/2 + sqrt(ab + (ab)^2/4) gives
+ * *efolds_per_step (its log).  *res_every: the renormalisation interval the
+ * resident FP32 sweep uses for this problem, the largest power of two up to
+ * 16 steps over which the bound (plus the one-time weight factor) stays
+ * below e^28, or 0 when none does; a context refuses the resident variant
+ * and the Green's-function path (QS_ERR_UNSUPPORTED) when any instance has
+ * 0.  The bound is loose (the instabilities of Sec. III grow far slower),
+ * it only guards the FP32 range.  Either pointer may be NULL. */
+qs_status qs_growth_bound(const qs_params *p, double *efolds_per_step, int *res_every);
 
 /* Number of sweep-kernel launches enqueued by this context so far. */
 int64_t qs_launch_count(const qs_ctx *ctx);

@@ -28,7 +28,7 @@ SEED_NOISE, SEED_IMPULSE, SEED_USER, SEED_STATE = range(4)
 REC_MAG, REC_NP, REC_MODEMAX = 1, 2, 4
 DIAG_XIMAX, DIAG_STATE, DIAG_WAKE0 = 8, 16, 32
 Q_N_MODES, Q_MODES_PADDED, Q_N_INST, Q_TOTAL_CELLS, Q_STEP, Q_STATE_BYTES, Q_SNAPSHOT_BYTES, \
-    Q_CELL_OFFSET, Q_LAUNCH = range(9)
+    Q_CELL_OFFSET, Q_LAUNCH, Q_RES_EVERY = range(10)
 
 EXPORTS = ["qs_init", "qs_seed", "qs_step", "qs_record", "qs_diag", "qs_query", "qs_modes",
            "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_step_green", "qs_sync",
@@ -106,6 +106,8 @@ def _load():
     L.qs_probe_alu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp,
                                ctypes.POINTER(ctypes.c_double)]
     L.qs_probe_alu.restype = ctypes.c_int
+    L.qs_growth_bound.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    L.qs_growth_bound.restype = ctypes.c_int
     for name in ("qs_init", "qs_seed", "qs_step", "qs_record", "qs_diag", "qs_query", "qs_modes",
                  "qs_set_launch", "qs_get_launch", "qs_tune", "qs_step_graph", "qs_step_green", "qs_sync"):
         getattr(L, name).restype = ctypes.c_int
@@ -128,6 +130,18 @@ def probe_alu(kind: int, blocks: int, threads: int, iters: int, sink, stream) ->
     if st != QS_OK:
         raise QSError(st, "qs_probe_alu")
     return ops.value
+
+
+def growth_bound(problem: dict, prec: str = "fp32"):
+    """(e-folds per step bound, resident renormalisation interval) of a
+    problem (qs_growth_bound; host only)."""
+    keep = []
+    prm = make_params(problem, prec, keep)
+    g, ev = ctypes.c_double(), ctypes.c_int()
+    st = lib.qs_growth_bound(ctypes.byref(prm), ctypes.byref(g), ctypes.byref(ev))
+    if st != QS_OK:
+        raise QSError(st, lib.qs_last_error(None).decode())
+    return g.value, ev.value
 
 
 def _dptr(a):

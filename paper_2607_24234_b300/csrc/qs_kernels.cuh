@@ -24,6 +24,7 @@ namespace qsk {
 constexpr int GRP = 32;          // renormalisation group length (cells)
 constexpr int ERR_NONFINITE = 1; // bits of the sticky device error word
 constexpr int ERR_TIMEOUT = 2;
+constexpr int ERR_BOUNDS = 4;    // bounds-checked build: an index left its buffer (access skipped)
 
 struct InstDev {
     int n_xi, n_grp;
@@ -66,7 +67,30 @@ struct SweepArgs {
     int scan_v;           // scan variant: cells per lane per sub-chunk
     long long spin_limit; // TMA variant: bound on every mbarrier wait (iterations)
     int tx_extra;         // test hook: extra bytes each tile barrier expects (0)
+    int res_every;        // resident variant: steps between renormalisation checks (power of two <= 16)
+    // extents the bounds-checked build tests every global index against
+    long long rows_total;   // state rows: cells_total * NS
+    long long groups_total; // exponent-group rows
+    long long rec_cap;      // doubles in the record target
 };
+
+// Bounds-checked build (QS_CHECK_BOUNDS): chk(a, i, n) is true when 0 <= i <
+// n; otherwise it sets ERR_BOUNDS in the error word, keeps the first bad
+// index + 1 in words 2..3 of it, and the caller skips the access.  The
+// ordinary build compiles every check to `true`.
+#ifdef QS_CHECK_BOUNDS
+__device__ __noinline__ bool chk_fail(int *err, long long i) {
+    atomicOr(err, ERR_BOUNDS);
+    atomicCAS(reinterpret_cast<unsigned long long *>(err + 2), 0ull, (unsigned long long)(i + 1));
+    return false;
+}
+__device__ __forceinline__ bool chk(int *err, long long i, long long n) {
+    return (i >= 0 && i < n) ? true : chk_fail(err, i);
+}
+#define QS_CHK(a, i, n) qsk::chk((a).err, (long long)(i), (long long)(n))
+#else
+#define QS_CHK(a, i, n) true
+#endif
 
 template <typename T> struct Cell { T nr, ni, tr, ti; };
 
@@ -80,21 +104,35 @@ __device__ __forceinline__ int expof(float x) {   // floor(log2 |x|); -200 for 0
     return b ? b - 127 : -200;
 }
 
+__device__ __forceinline__ bool cell_ok(const SweepArgs &a, long long row, int mode) {
+    return QS_CHK(a, row * a.Mp + mode, a.rows_total * a.Mp) && QS_CHK(a, mode, a.Mp);
+}
 __device__ __forceinline__ void ld_cell(const SweepArgs &a, long long row, int mode, Cell<float> &c) {
+    if (!cell_ok(a, row, mode)) { c.nr = c.ni = c.tr = c.ti = 0.f; return; }
     float4 v = __ldcg(reinterpret_cast<const float4 *>(a.st) + row * a.Mp + mode);
     c.nr = v.x; c.ni = v.y; c.tr = v.z; c.ti = v.w;
 }
 __device__ __forceinline__ void ld_cell(const SweepArgs &a, long long row, int mode, Cell<double> &c) {
+    if (!cell_ok(a, row, mode)) { c.nr = c.ni = c.tr = c.ti = 0.0; return; }
     double2 x = __ldcg(reinterpret_cast<const double2 *>(a.st) + row * a.Mp + mode);
     double2 y = __ldcg(reinterpret_cast<const double2 *>(a.th) + row * a.Mp + mode);
     c.nr = x.x; c.ni = x.y; c.tr = y.x; c.ti = y.y;
 }
 __device__ __forceinline__ void st_cell(const SweepArgs &a, long long row, int mode, const Cell<float> &c) {
+    if (!cell_ok(a, row, mode)) return;
     __stcg(reinterpret_cast<float4 *>(a.st) + row * a.Mp + mode, make_float4(c.nr, c.ni, c.tr, c.ti));
 }
 __device__ __forceinline__ void st_cell(const SweepArgs &a, long long row, int mode, const Cell<double> &c) {
+    if (!cell_ok(a, row, mode)) return;
     __stcg(reinterpret_cast<double2 *>(a.st) + row * a.Mp + mode, make_double2(c.nr, c.ni));
     __stcg(reinterpret_cast<double2 *>(a.th) + row * a.Mp + mode, make_double2(c.tr, c.ti));
+}
+// exponent word of group row g (FP32 state)
+__device__ __forceinline__ int ld_ex(const SweepArgs &a, long long g, int mode) {
+    return QS_CHK(a, g * a.Mp + mode, a.groups_total * a.Mp) ? __ldcg(a.ex + g * a.Mp + mode) : 0;
+}
+__device__ __forceinline__ void st_ex(const SweepArgs &a, long long g, int mode, int v) {
+    if (QS_CHK(a, g * a.Mp + mode, a.groups_total * a.Mp)) __stcg(a.ex + g * a.Mp + mode, v);
 }
 
 template <typename T> __device__ __forceinline__ double lnabs2(T re2) {  // ln sqrt(re2)
@@ -140,11 +178,11 @@ struct Line {
 #pragma unroll
                 for (int sp = 0; sp < NS; ++sp) {
                     ld_cell(a, row + sp, mode, b.x[u][sp]);
-                    b.w[u][sp] = __ldg(reinterpret_cast<const T *>(a.w) + row + sp);
+                    b.w[u][sp] = QS_CHK(a, row + sp, a.rows_total) ? __ldg(reinterpret_cast<const T *>(a.w) + row + sp) : T(0);
                 }
             }
         }
-        if (RN && (j0 % GRP) == 0) b.exw = __ldcg(a.ex + (I.grp_off + j0 / GRP) * a.Mp + mode);
+        if (RN && (j0 % GRP) == 0) b.exw = ld_ex(a, I.grp_off + j0 / GRP, mode);
     }
 
     __device__ __forceinline__ void group_begin(int exw) {
@@ -169,7 +207,7 @@ struct Line {
                 int s8 = gmax > 0.0f ? expof(gmax) : 0;
                 s8 = s8 < -100 ? -100 : (s8 > 100 ? 100 : s8);
                 if (!(gnan == 0.0f) || !(gmax <= 3.0e38f)) atomicOr(a.err, ERR_NONFINITE);
-                __stcg(a.ex + (I.grp_off + g) * a.Mp + mode, (W << 8) | (s8 & 0xff));
+                st_ex(a, I.grp_off + g, mode, (W << 8) | (s8 & 0xff));
             }
         }
     }
@@ -478,7 +516,7 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
                 for (int k = 0; k < ST && k < nch; ++k) issue(k);
             for (int k = 0; k < ST && k < nch; ++k) pending |= 1u << k;
             int exn = 0;
-            if (F32 && live) exn = __ldcg(a.ex + I.grp_off * a.Mp + mode);
+            if (F32 && live) exn = ld_ex(a, I.grp_off, mode);
             for (int k = 0; k < nch; ++k) {
                 const int stg = k % ST;
                 const uint32_t par = (phase >> stg) & 1u;
@@ -492,7 +530,7 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
                 if (live) {
                     if (F32 && (j0 % GRP) == 0) {
                         L.group_begin(exn);
-                        if (j0 + GRP < N) exn = __ldcg(a.ex + (I.grp_off + (j0 + GRP) / GRP) * a.Mp + mode);
+                        if (j0 + GRP < N) exn = ld_ex(a, I.grp_off + (j0 + GRP) / GRP, mode);
                     }
 #pragma unroll
                     for (int cc = 0; cc < C; ++cc) {

@@ -119,4 +119,57 @@ inline void build_modes(const qs_params &p, ModeList &m) {
     }
 }
 
+// Upper bound (e-folds per slow-time step) of the growth of the scheme's
+// state, in the max norm, from the problem statement alone.  One step maps
+// (n_b, Theta) by Theta' = Theta + h F[n_b], n_b' = n_b + dt n_b0 Theta' with
+// h <= dt, |F[n_b]| <= a |n_b| / dt and |dt n_b0| <= b, where the kick is
+// (q/m)[kappa k^2 / gamma n_p - kappa / gamma^3 (rho - n_p)] (Eqs. 8-9, 14)
+// with kappa k^2 <= 1, kappa <= 1, and the plasma response of Eq. (5) over a
+// line of length L obeys |n_p| <= L max|rho|:
+//   a = dt max_s |q_s/m_s| (1/gamma + 1/gamma^3) sum_s |q_s| (2 + L),
+//   b = dt max_s n_bs0,peak max_j shape_j.
+// The max norms then obey (|n_b'|, |Theta'|) <= [[1 + ab, b], [a, 1]]
+// (|n_b|, |Theta|) componentwise.  In the weights (|n_b|, sqrt(b/a)
+// |Theta|) that matrix is symmetric, [[1 + ab, sqrt(ab)], [sqrt(ab), 1]],
+// so after k steps the weighted pair is at most rho^k times its 2-norm,
+// rho = 1 + ab/2 + sqrt(ab + (ab)^2 / 4) its spectral radius: ln rho bounds
+// the growth per step, and the change of weights and of norms costs a
+// one-time factor sqrt(2 max(a, b) / min(a, b)) (its log in *log_cond).
+// Both are 0 when a b = 0 (no coupling).
+inline double growth_bound(const qs_params &p, const std::vector<double> &shape, double *log_cond) {
+    double qm = 0.0, qs = 0.0, dmax = 0.0, smax = 0.0;
+    for (int s = 0; s < p.n_species; ++s) {
+        qm = std::max(qm, std::fabs(p.species[s].q / p.species[s].m));
+        qs += std::fabs(p.species[s].q);
+        dmax = std::max(dmax, p.species[s].density_ratio);
+    }
+    for (double v : shape) smax = std::max(smax, std::fabs(v));
+    const double g = p.gamma_b, L = p.n_xi * p.dxi;
+    const double a = p.dt * qm * (1.0 / g + 1.0 / (g * g * g)) * qs * (2.0 + L);
+    const double b = p.dt * dmax * smax;
+    const double ab = a * b;
+    if (!(ab > 0.0)) {
+        if (log_cond) *log_cond = 0.0;
+        return 0.0;
+    }
+    if (log_cond) *log_cond = 0.5 * std::fabs(std::log(a / b)) + 0.5 * std::log(2.0);
+    return std::log(1.0 + 0.5 * ab + std::sqrt(ab + 0.25 * ab * ab));
+}
+
+// Renormalisation interval of the resident FP32 sweep for a growth bound g
+// (e-folds per step), one-time factor lc and line length L: the largest power
+// of two up to 16 steps over which the state's growth stays inside the FP32
+// headroom between checks.  After a check a thread's mantissas are below
+// 2^16, other threads' values reach it at most 2^64 (RES_SPAN) larger, and
+// the plasma partials sum at most 2 L of those, so the growth G between two
+// checks must keep 2^(16 + 64) 2L G below 2^128 (half a bit to spare); 0
+// when even a check every step cannot.
+inline int res_every_for(double g, double lc, double L) {
+    const double bits = 128.0 - 16.0 - 64.0 - std::log2(std::max(32.0, 2.0 * L)) - 0.5;
+    const double budget = bits * std::log(2.0);
+    for (int every = 16; every >= 1; every >>= 1)
+        if (every * g + lc <= budget) return every;
+    return 0;
+}
+
 }  // namespace qsp

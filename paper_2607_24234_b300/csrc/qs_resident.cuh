@@ -21,15 +21,17 @@
 //
 // FP32 range.  Each thread stores its chunk as mantissas times 2^e, one
 // exponent per thread; scan partials move between threads' scales by exact
-// powers of two.  Every RES_EVERY-th step a thread renormalises its chunk
+// powers of two.  Every a.res_every-th step a thread renormalises its chunk
 // when the largest mantissa has left [2^-16, 2^16], and no exponent of a
 // line may lie more than RES_SPAN below the line's largest (checked every
 // step).  A scan partial is then at most about 2^(16 + 5) G times
 // 2^RES_SPAN in any thread's scale, G the growth between two checks, so
-// nothing overflows while G < 2^(128 - 21 - RES_SPAN) = 2^43 over
-// RES_EVERY = 16 steps (e^1.86 per step; physical growth is below e^1 per
-// step at the time steps of the scheme).  Only values below
-// ~2^-(RES_SPAN + 126) of the line maximum flush to zero.
+// nothing overflows while G < 2^(128 - 21 - RES_SPAN) = 2^43.  The host
+// picks res_every (a power of two up to 16) from a bound of the scheme's
+// growth per step derived from the problem statement (qsp::growth_bound),
+// so that G stays below e^28; problems whose bound leaves no interval are
+// not run by this kernel.  Only values below ~2^-(RES_SPAN + 126) of the
+// line maximum flush to zero.
 // On the way out the threads sharing a 32-cell group agree on one exponent
 // and write the usual (mantissa, exponent word) layout.
 #pragma once
@@ -40,7 +42,6 @@ namespace qsk {
 constexpr int RES_MAX_WARPS = 16;   // T <= 512
 constexpr int RES_SPAN = 64;
 constexpr int RES_HYST = 16;
-constexpr int RES_EVERY = 16;         // steps between renormalisation checks (a power of two; 8 measured 1.7 % slower)
 constexpr int RES_NONE = -(1 << 20);   // exponent of a thread that holds no value yet
 constexpr int RES_REGS64 = 128;       // register cap of the 64-thread shared-Theta kernel (96..224 measured: 128 best)
 
@@ -437,7 +438,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                 acc_rot2(n, d, Rl, 1.0f, Yn, Yd);
             }
             if (a.update) An = Ad = F2(0.f);   // the next aggregate; unchanged by a field pass
-            // ---- pass 2; every RES_EVERY-th step also the renormalisation
+            // ---- pass 2; every res_every-th step also the renormalisation
             using Y_ = std::integral_constant<bool, true>;
             using N_ = std::integral_constant<bool, false>;
             long long snap = -1;   // recording step (per-mode maxima), uniform over the CTA
@@ -484,7 +485,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     o[0] = L0; o[pl] = L1; o[2 * pl] = L2;
                 }
                 __syncthreads();   // sMM is reused at the next recording step
-            } else if ((it & (RES_EVERY - 1)) == RES_EVERY - 1) {
+            } else if ((it & (a.res_every - 1)) == a.res_every - 1) {
                 gmax = pass2(Y_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);
             } else {
                 pass2(N_(), N_(), Y_(), n, d, A, B, nullptr, nullptr, An, Ad);

@@ -94,6 +94,8 @@ struct qs_ctx {
     long long n_launch = 0;
     long long spin_limit = 1LL << 24;
     int tx_extra = 0;
+    int res_every = 16;             // resident variant's renormalisation interval (0: variant refused)
+    double growth = 0.0;            // largest per-step growth bound of the instances (e-folds)
     std::string err;
 };
 
@@ -380,6 +382,7 @@ SweepArgs sweep_args(qs_ctx *c, long long step0, int n_steps, int update, int re
     a.scan_v = c->launch.scan_cells;
     a.spin_limit = c->spin_limit;
     a.tx_extra = c->tx_extra;
+    a.res_every = c->res_every > 0 ? c->res_every : 1;
     return a;
 }
 
@@ -641,6 +644,13 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
             uni = uni && shp[j] == shp[0];
         }
         c->uniform = (i == 0 || c->uniform) && uni;
+        {
+            double lc = 0.0;
+            const double gb = qsp::growth_bound(q, shp, &lc);
+            c->growth = std::max(c->growth, gb);
+            const int ev = qsp::res_every_for(gb, lc, q.n_xi * q.dxi);
+            c->res_every = i == 0 ? ev : std::min(c->res_every, ev);
+        }
         cell += q.n_xi;
         grp += I.n_grp;
     }
@@ -948,6 +958,7 @@ qs_status qs_query(const qs_ctx *c, int what, int64_t arg, int64_t *value) {
                  ((int64_t)c->launch.ctas_per_sm << 24) | ((int64_t)c->launch.variant << 32) |
                  ((int64_t)c->launch.scan_cells << 40);
         break;
+    case QS_Q_RES_EVERY: *value = c->res_every; break;
     default: return QS_ERR_ARG;
     }
     return QS_OK;
@@ -965,6 +976,9 @@ qs_status qs_set_launch(qs_ctx *c, const qs_launch *l) {
     if (l->variant < QS_VARIANT_REGISTERS || l->variant > QS_VARIANT_RESIDENT) return fail(c, QS_ERR_ARG, "variant");
     if (l->variant == QS_VARIANT_RESIDENT) {
         if (c->prec != QS_FP32_RENORM) return fail(c, QS_ERR_UNSUPPORTED, "the resident variant is FP32 only");
+        if (c->res_every < 1)
+            return fail(c, QS_ERR_UNSUPPORTED, "resident: the state may grow by e^%.3g per step, beyond the range "
+                        "its FP32 scan partials keep between renormalisations; use a streaming variant", c->growth);
         const int V = l->prefetch;
         if (!res_shape_ok(c->NS, V, w, res_regs(c->NS, V, l->scan_cells)))
             return fail(c, QS_ERR_ARG, "resident: cells per thread 8|16 (any CTA size) or 32 (one species, 2|4|8 "
@@ -1025,6 +1039,19 @@ qs_status qs_sync(qs_ctx *c) {
 }
 
 int64_t qs_launch_count(const qs_ctx *c) { return c ? c->n_launch : -1; }
+
+qs_status qs_growth_bound(const qs_params *p, double *efolds_per_step, int *res_every) {
+    if (!p) return QS_ERR_ARG;
+    qs_status st = validate(*p, 0);
+    if (st) return st;
+    std::vector<double> shp;
+    if (!profile_shape(*p, shp)) return fail(nullptr, QS_ERR_ARG, "profile");
+    double lc = 0.0;
+    const double g = qsp::growth_bound(*p, shp, &lc);
+    if (efolds_per_step) *efolds_per_step = g;
+    if (res_every) *res_every = qsp::res_every_for(g, lc, p->n_xi * p->dxi);
+    return QS_OK;
+}
 
 qs_status qs_debug_waits(qs_ctx *c, int64_t spin_limit, int unsatisfiable) {
     if (!c || spin_limit < 1) return QS_ERR_ARG;

@@ -127,3 +127,56 @@ def test_nonfinite_parameters_rejected_by_both_entry_points(qs, field, value):
     assert qs.lib.qs_sweep_noalloc(ctypes.byref(prm), dummy, None, ex, 0, 1, None, None) == qs.QS_ERR_ARG
     prm.geom = 2
     assert qs.lib.qs_sweep_noalloc(ctypes.byref(prm), dummy, None, ex, 0, 1, None, None) == qs.QS_ERR_UNSUPPORTED
+
+
+def test_growth_bound_and_renormalisation_interval(qs):
+    """qs_growth_bound (host only): the benchmark beam keeps the resident
+    sweep's 16-step renormalisation interval, every instance of the batched
+    workload gets an interval, and an extreme problem is refused (0)."""
+    g, ev = qs.growth_bound(synth.BEAM_3D)
+    assert 0.0 < g < 0.1 and ev == 16
+    evs = [qs.growth_bound(p)[1] for p in synth.batch_instances(512, param_seed=0)]
+    assert min(evs) >= 4 and max(evs) == 16
+    assert sorted(evs)[:3] == [8, 8, 16]      # the two densest, slowest beams check every 8 steps
+    # the interval shrinks as the bound grows, down to refusal
+    prev = 16
+    for dens, dt in ((1.0, 20.0), (10.0, 100.0), (100.0, 1000.0)):
+        extreme = synth.scaled(synth.SLAB_2D, species=[(-1.0, 1.0, dens)], gamma_b=1.1, dt=dt, n_xi=4000, dxi=0.25,
+                               length=1000.0)
+        g, ev = qs.growth_bound(extreme)
+        assert ev <= prev
+        prev = ev
+    assert ev == 0 and g > 20.0
+    with pytest.raises(qs.QSError):
+        qs.growth_bound(synth.scaled(synth.SLAB_2D, dt=float("nan")))
+
+
+@pytest.mark.parametrize("species,gamma,dt,L", [
+    ([(-1.0, 1.0, 0.1)], 10.0, 2.0, 20.0),
+    ([(-1.0, 1.0, 0.3)], 2.0, 4.0, 10.0),
+    ([(-1.0, 1.0, 0.05), (1.0, 1.0, 0.05)], 3.0, 2.0, 15.0),
+])
+def test_growth_bound_bounds_the_oracle(qs, species, gamma, dt, L):
+    """The bound is an upper bound of the scheme's growth: from random states
+    (n_b and Theta both non-zero), the FP64 oracle's max norm over n_b and
+    Theta after k steps never exceeds e^(k g) times the one-time factor
+    sqrt(2 max(a, b) / min(a, b)) times the initial one."""
+    import math
+    import oracle
+    n_xi, D = int(round(L / 0.05)), 0.05
+    p = synth.scaled(synth.SLAB_2D, species=species, gamma_b=gamma, dt=dt, n_xi=n_xi, dxi=D, length=n_xi * D,
+                     k_list=[0.0, 0.7, 2.0, 6.0])
+    g, ev = qs.growth_bound(p)
+    qm = max(abs(q / m) for q, m, _ in species)
+    a = dt * qm * (1 / gamma + 1 / gamma ** 3) * sum(abs(q) for q, _, _ in species) * (2 + n_xi * D)
+    b = dt * max(d for _, _, d in species)
+    lc = 0.5 * abs(math.log(a / b)) + 0.5 * math.log(2.0)
+    rng = np.random.default_rng(3)
+    for trial in range(3):
+        nb = rng.standard_normal((4, len(species), n_xi)) + 1j * rng.standard_normal((4, len(species), n_xi))
+        th = (rng.standard_normal(nb.shape) + 1j * rng.standard_normal(nb.shape)) * 10.0 ** (trial - 1)
+        m0 = max(np.max(np.abs(nb)), np.max(np.abs(th)))
+        for k in range(1, 13):
+            oracle.sweep(p, nb, th, k, 1)
+            mk = max(np.max(np.abs(nb)), np.max(np.abs(th)))
+            assert math.log(mk / m0) <= k * g + lc + 1e-9, (trial, k)

@@ -370,3 +370,34 @@ def test_theta_registers_packing_and_bitwise(qs, n_xi, V, w, pers, species):
                             chunks=[17, 1, 22])
     s3.close()
     assert np.array_equal(nb, nb3) and np.array_equal(th, th3)
+
+
+def test_renormalisation_interval_from_growth_bound(qs):
+    """The context takes the resident sweep's renormalisation interval from
+    qs_growth_bound: a dense, slow beam checks every 8 steps (and still
+    matches the oracle over a fast-growing run); a problem whose bound leaves
+    no interval refuses the resident variant and the Green's-function path."""
+    p = synth.scaled(synth.SLAB_2D, species=[(-1.0, 1.0, 0.1)], gamma_b=10.0, dt=2.0, n_xi=4000, dxi=0.05,
+                     length=200.0, k_list=[0.5, 2.0, 6.0])
+    g, ev = qs.growth_bound(p)
+    assert ev == 8
+    steps = 120
+    s, nb, th = _run_gpu(qs, p, "fp32", steps, seed=("noise", 6, 1e-6), launch=_res(32, 4))
+    assert s.query(qs.Q_RES_EVERY) == 8
+    s.close()
+    nb_o, th_o = _run_oracle(p, steps, seed=("noise", 6, 1e-6))
+    assert np.max(np.abs(nb_o)) > 1e6 * 1e-6            # the run grows
+    assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+    bad = synth.scaled(synth.SLAB_2D, species=[(-1.0, 1.0, 100.0)], gamma_b=1.1, dt=1000.0, n_xi=4000, dxi=0.25,
+                       length=1000.0, k_list=[1.0])
+    assert qs.growth_bound(bad)[1] == 0
+    s = qs.Solver(bad, prec="fp32")
+    assert s.query(qs.Q_RES_EVERY) == 0
+    with pytest.raises(qs.QSError) as e:
+        s.set_launch(**_res(32, 8))
+    assert e.value.status == qs.QS_ERR_UNSUPPORTED
+    s.seed_noise(1, 1e-6)
+    with pytest.raises(qs.QSError) as e:
+        s.step_green(1)
+    assert e.value.status == qs.QS_ERR_UNSUPPORTED
+    s.close()
