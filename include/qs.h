@@ -52,7 +52,9 @@ typedef enum {
     QS_ERR_TIMEOUT = 4,      /* a bounded device wait ran out             */
     QS_ERR_NONFINITE = 5,    /* NaN/Inf appeared in the state             */
     QS_ERR_STATE = 6,        /* context poisoned by an earlier error      */
-    QS_ERR_UNSUPPORTED = 7   /* valid request this build does not serve   */
+    QS_ERR_UNSUPPORTED = 7,  /* valid request this build does not serve   */
+    QS_ERR_BOUNDS = 8        /* bounds-checked build: a device index left
+                              * its buffer (the access was skipped)       */
 } qs_status;
 
 enum { QS_GEOM_KLIST = 0,    /* explicit list of k (2D slab, k along y)   */
@@ -306,6 +308,29 @@ qs_status qs_debug_waits(qs_ctx *ctx, int64_t spin_limit, int unsatisfiable);
  * it only guards the FP32 range.  Either pointer may be NULL. */
 qs_status qs_growth_bound(const qs_params *p, double *efolds_per_step, int *res_every);
 
+/* Build variants.  The library built with -DQS_CHECK_BOUNDS (libqs_checked.so)
+ * tests every global-memory index of the sweep kernels against the extent of
+ * its buffer; an index outside it sets a device error bit, the first bad index
+ * is kept, the access is skipped (no trap, no fault), and the next qs_sync
+ * returns QS_ERR_BOUNDS.  qs_build_flags() reports the variant. */
+enum { QS_BUILD_CHECK_BOUNDS = 1 };
+int qs_build_flags(void);
+
+/* Test hook for the bounds checks (failure detection without a bad access):
+ * the checked build is told that the last rows_cut rows of the state
+ * (cells x species) are missing, so the sweep reports QS_ERR_BOUNDS at the
+ * first access to them and skips it; the memory is there, nothing strays.
+ * rows_cut = 0 restores the true extent.  No effect in the ordinary build. */
+qs_status qs_debug_bounds(qs_ctx *ctx, int64_t rows_cut);
+
+/* Guards: every context buffer is allocated 256 bytes longer, the tail is
+ * filled with a fixed byte, and qs_sync (and host-pointer qs_diag) check the
+ * tails; an overwritten one is reported as QS_ERR_BOUNDS ("the guard after
+ * buffer i was overwritten").  Test hook: qs_debug_canary overwrites one
+ * byte of buffer `buffer`'s guard (inside the allocation) so that the
+ * detection can be tested without a stray write. */
+qs_status qs_debug_canary(qs_ctx *ctx, int buffer);
+
 /* Number of sweep-kernel launches enqueued by this context so far. */
 int64_t qs_launch_count(const qs_ctx *ctx);
 
@@ -460,13 +485,15 @@ qs_status qs_sur_points(qs_ctx *ctx, const double *snap, size_t snap_bytes, doub
  * running 8 independent chains of `iters` dependent fused multiply-adds:
  *   QS_PROBE_FFMA2  packed f32x2 FMA (__ffma2_rn, two lane-ops each),
  *   QS_PROBE_FFMA   scalar FP32 FMA (16 chains),
- *   QS_PROBE_DFMA   FP64 FMA.
+ *   QS_PROBE_DFMA   FP64 FMA; QS_PROBE_DADD, QS_PROBE_DMUL FP64 add, multiply.
  * *lane_ops (may be NULL) receives the number of FMA lane-operations the
  * launch performs; time it with CUDA events on `stream`.  dev_sink is a
  * device buffer of at least 8 bytes that the kernel never writes in practice
  * (it keeps the arithmetic from being optimised away).  QS_ERR_ARG for a bad
  * shape; QS_ERR_CUDA if the launch fails. */
-enum { QS_PROBE_FFMA2 = 0, QS_PROBE_FFMA = 1, QS_PROBE_DFMA = 2 };
+enum { QS_PROBE_FFMA2 = 0, QS_PROBE_FFMA = 1, QS_PROBE_DFMA = 2,
+       QS_PROBE_DADD = 3,   /* FP64 add (one lane-op each)                 */
+       QS_PROBE_DMUL = 4 }; /* FP64 multiply (one lane-op each)            */
 qs_status qs_probe_alu(int kind, int blocks, int threads, int64_t iters, void *dev_sink, void *stream,
                        double *lane_ops);
 

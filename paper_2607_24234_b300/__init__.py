@@ -14,11 +14,14 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libqs.so")
+# QS_LIBRARY selects another build of the library (the bounds-checked
+# libqs_checked.so); the default is the ordinary build in this directory
+LIB_PATH = os.environ.get("QS_LIBRARY") or os.path.join(_HERE, "libqs.so")
 
 # --- enums (qs.h) ------------------------------------------------------------
 QS_OK, QS_ERR_ARG, QS_ERR_OOM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_NONFINITE, QS_ERR_STATE, \
-    QS_ERR_UNSUPPORTED = range(8)
+    QS_ERR_UNSUPPORTED, QS_ERR_BOUNDS = range(9)
+BUILD_CHECK_BOUNDS = 1
 GEOM = {"klist": 0, "kgrid2": 1, "real2": 2}
 PREC = {"fp64": 0, "fp32": 1}
 MODEL = {"full": 0, "reduced": 1}
@@ -94,6 +97,12 @@ def _load():
     L.qs_sync.argtypes = [vp]
     L.qs_debug_waits.argtypes = [vp, i64, ctypes.c_int]
     L.qs_debug_waits.restype = ctypes.c_int
+    L.qs_debug_bounds.argtypes = [vp, i64]
+    L.qs_debug_bounds.restype = ctypes.c_int
+    L.qs_debug_canary.argtypes = [vp, ctypes.c_int]
+    L.qs_debug_canary.restype = ctypes.c_int
+    L.qs_build_flags.argtypes = []
+    L.qs_build_flags.restype = ctypes.c_int
     L.qs_launch_count.argtypes = [vp]
     L.qs_launch_count.restype = i64
     L.qs_last_error.argtypes = [vp]
@@ -117,7 +126,7 @@ def _load():
 lib = _load()
 
 
-PROBE_FFMA2, PROBE_FFMA, PROBE_DFMA = range(3)
+PROBE_FFMA2, PROBE_FFMA, PROBE_DFMA, PROBE_DADD, PROBE_DMUL = range(5)
 
 
 def probe_alu(kind: int, blocks: int, threads: int, iters: int, sink, stream) -> float:
@@ -312,6 +321,9 @@ class Solver:
 
     def launch_count(self):
         return int(lib.qs_launch_count(self.ctx))
+
+    def debug_bounds(self, rows_cut: int):
+        self._chk(lib.qs_debug_bounds(self.ctx, int(rows_cut)))
 
     def debug_waits(self, spin_limit=1 << 24, unsatisfiable=False):
         self._chk(lib.qs_debug_waits(self.ctx, int(spin_limit), 1 if unsatisfiable else 0))

@@ -25,6 +25,7 @@ constexpr int GRP = 32;          // renormalisation group length (cells)
 constexpr int ERR_NONFINITE = 1; // bits of the sticky device error word
 constexpr int ERR_TIMEOUT = 2;
 constexpr int ERR_BOUNDS = 4;    // bounds-checked build: an index left its buffer (access skipped)
+constexpr int ERR_CANARY = 8;    // the guard after a buffer was overwritten
 
 struct InstDev {
     int n_xi, n_grp;
@@ -79,7 +80,7 @@ struct SweepArgs {
 // index + 1 in words 2..3 of it, and the caller skips the access.  The
 // ordinary build compiles every check to `true`.
 #ifdef QS_CHECK_BOUNDS
-__device__ __noinline__ bool chk_fail(int *err, long long i) {
+static __device__ __noinline__ bool chk_fail(int *err, long long i) {
     atomicOr(err, ERR_BOUNDS);
     atomicCAS(reinterpret_cast<unsigned long long *>(err + 2), 0ull, (unsigned long long)(i + 1));
     return false;
@@ -229,7 +230,8 @@ struct Line {
             const double sc = RN ? (double)W * 0.69314718055994530942 : 0.0;
             double *base = a.rec + snap * a.rec_snap_doubles;
             const long long cm = (I.cell_off + j) * a.Mp + mode;
-            if (a.rec_kinds & 1) {
+            if ((a.rec_kinds & 1) && QS_CHK(a, cm, a.cells_total * a.Mp) &&
+                QS_CHK(a, snap * a.rec_snap_doubles + a.rec_off_mag + cm + 4 * a.cells_total * a.Mp, a.rec_cap)) {
                 const long long pl = a.cells_total * a.Mp;
                 double *o = base + a.rec_off_mag + cm;
                 __stcs(o, 0.5 * log(nb2) + sc);
@@ -238,7 +240,7 @@ struct Line {
                 __stcs(o + 3 * pl, 0.5 * log(kk * ((double)mr * mr + (double)mi * mi)) + sc);
                 __stcs(o + 4 * pl, 0.5 * log(ex2) + sc);
             }
-            if (a.rec_kinds & 2) {
+            if ((a.rec_kinds & 2) && QS_CHK(a, snap * a.rec_snap_doubles + a.rec_off_np + 2 * cm + 1, a.rec_cap)) {
                 const double f = RN ? ldexp(1.0, W) : 1.0;
                 __stcs(reinterpret_cast<double2 *>(base + a.rec_off_np) + cm,
                        make_double2((double)mr * f, (double)mi * f));
@@ -325,7 +327,8 @@ struct Line {
     __device__ __forceinline__ void step_begin(int it) {
         const long long g = a.step0 + it;
         const double h = (g == 0) ? 0.5 * I.dt : I.dt;
-        const double kapd = a.kap[mode], kk2d = a.kapk2[mode];
+        const int mk = QS_CHK(a, mode, a.Mp) ? mode : 0;
+        const double kapd = a.kap[mk], kk2d = a.kapk2[mk];
 #pragma unroll
         for (int sp = 0; sp < NS; ++sp) {
             const double f1 = I.qm_g[sp] * kk2d, f2 = I.qm_g3[sp] * kapd;
@@ -345,7 +348,7 @@ struct Line {
         }
         nr = ni = dr = di = 0;
         W = 0;
-        if (a.front == 2 && a.held) {
+        if (a.front == 2 && a.held && QS_CHK(a, ((long long)inst * a.Mp + mode) * 4 + 3, (long long)a.n_inst * a.Mp * 4)) {
             const double *hp = a.held + ((long long)inst * a.Mp + mode) * 4;
             if constexpr (RN) {
                 double hm = fmax(fmax(fabs(hp[0]), fabs(hp[1])), fmax(fabs(hp[2]), fabs(hp[3])));
@@ -363,7 +366,9 @@ struct Line {
         if (!RN) fold_max();
         if (!(fabs((double)nr) + fabs((double)ni) + fabs((double)dr) + fabs((double)di) <= 1.0e300))
             atomicOr(a.err, ERR_NONFINITE);
-        if (REC && rec && (a.rec_kinds & 4)) {
+        if (REC && rec && (a.rec_kinds & 4) &&
+            QS_CHK(a, snap * a.rec_snap_doubles + a.rec_off_mm + ((long long)inst + 2LL * a.n_inst) * a.Mp + mode,
+                   a.rec_cap)) {
             double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)inst * a.Mp + mode;
             long long pl = (long long)a.n_inst * a.Mp;
             o[0] = mm0; o[pl] = mm1; o[2 * pl] = mm2;
@@ -372,9 +377,10 @@ struct Line {
 
     __device__ __forceinline__ void line_begin() {
         c = (T)I.c; s = (T)I.s; ch = (T)I.ch; sh = (T)I.sh;
-        const double kapd = a.kap[mode];
+        const int mk = QS_CHK(a, mode, a.Mp) ? mode : 0;
+        const double kapd = a.kap[mk];
         kap = (T)kapd;
-        kabsk = (T)(a.kabs[mode] * kapd);
+        kabsk = (T)(a.kabs[mk] * kapd);
         upd = a.update != 0;
     }
 
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(256) k_sweep(const SweepArgs a) {
         const int2 it = a.items[item];
         const int mode = it.y + threadIdx.x;
         if (mode < a.M) {
-            const InstDev I = a.inst[it.x];
+            const InstDev I = a.inst[QS_CHK(a, it.x, a.n_inst) ? it.x : 0];
             Line<T, NS, U, REC> L(a, I, it.x, mode);
             L.run();
         }
@@ -495,7 +501,7 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
         const int2 itx = a.items[item];
         const int mode = itx.y + lane;
         const bool live = mode < a.M;
-        const InstDev I = a.inst[itx.x];
+        const InstDev I = a.inst[QS_CHK(a, itx.x, a.n_inst) ? itx.x : 0];
         Line<T, NS, 1, false> L(a, I, itx.x, live ? mode : itx.y);
         L.line_begin();
         const int N = I.n_xi, nch = (N + C - 1) / C;
@@ -549,7 +555,8 @@ __global__ void __launch_bounds__(32) k_sweep_tma(const SweepArgs a, const __gri
                                     const double2 v = reinterpret_cast<const double2 *>(buf[stg] + TILE_A)[row * 32 + lane];
                                     x[sp].nr = u.x; x[sp].ni = u.y; x[sp].tr = v.x; x[sp].ti = v.y;
                                 }
-                                w[sp] = __ldg(wt + (long long)j * NS + sp);
+                                w[sp] = QS_CHK(a, (I.cell_off + j) * NS + sp, a.rows_total) ? __ldg(wt + (long long)j * NS + sp)
+                                                                                           : T(0);
                             }
                             L.cell(x, w, j, N);
                         }
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(128) k_sweep_scan(const SweepArgs a) {
     const int2 itx = a.items[item];
     const int mode = itx.y + mm;
     const bool live = mode < a.M;
-    const InstDev I = a.inst[itx.x];
+    const InstDev I = a.inst[QS_CHK(a, itx.x, a.n_inst) ? itx.x : 0];
     Line<double, NS, 1, false> L(a, I, itx.x, live ? mode : itx.y);
     L.line_begin();
     const int N = I.n_xi, V = a.scan_v, C = S * V;
@@ -646,8 +653,10 @@ __global__ void __launch_bounds__(128) k_sweep_scan(const SweepArgs a) {
                 if (j >= N || !live) break;
                 double rr = 0, ri = 0;
                 for (int sp = 0; sp < NS; ++sp) {
-                    const double2 x = __ldcg(reinterpret_cast<const double2 *>(a.st) +
-                                             ((I.cell_off + j) * NS + sp) * a.Mp + mode);
+                    const long long cix = ((I.cell_off + j) * NS + sp) * a.Mp + mode;
+                    const double2 x = QS_CHK(a, cix, a.rows_total * a.Mp)
+                                          ? __ldcg(reinterpret_cast<const double2 *>(a.st) + cix)
+                                          : make_double2(0.0, 0.0);
                     rr = fma(q[sp], x.x, rr);
                     ri = fma(q[sp], x.y, ri);
                 }
@@ -687,7 +696,7 @@ __global__ void __launch_bounds__(128) k_sweep_scan(const SweepArgs a) {
                 double w[NS];
                 for (int sp = 0; sp < NS; ++sp) {
                     ld_cell(a, (I.cell_off + j) * NS + sp, mode, x[sp]);
-                    w[sp] = __ldg(wt + (long long)j * NS + sp);
+                    w[sp] = QS_CHK(a, (I.cell_off + j) * NS + sp, a.rows_total) ? __ldg(wt + (long long)j * NS + sp) : 0.0;
                 }
                 L.cell(x, w, j, N);
             }

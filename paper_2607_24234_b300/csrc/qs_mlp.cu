@@ -21,6 +21,7 @@
 #include <cstdlib>
 
 #include "qs.h"
+#include "qs_nvtx.h"
 
 namespace mlp {
 
@@ -917,6 +918,7 @@ qs_status qs_mlp_layout(const qs_mlp *m, int64_t *nparam, int64_t *offsets, floa
 // do_update = 0 computes gradients only (member `member`, or all if < 0).
 qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n, float lr, int do_update,
                             float *loss_host) {
+    QS_RANGE("qs_mlp_train_step");
     if (!m || !X || !Y || n < 1 || n > m->max_batch) return QS_ERR_ARG;
     const int nb = (int)n;
     mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(
@@ -961,6 +963,7 @@ qs_status qs_mlp_grads(qs_mlp *m, int member, float *host_grad, int64_t n) {
 // the ensemble variance of output 0 exceeds var_threshold (solver fallback).
 qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float *var, uint8_t *mask,
                        float var_threshold) {
+    QS_RANGE("qs_mlp_infer");
     if (!m || !X || !mean || !var || n < 1) return QS_ERR_ARG;
     for (int64_t r0 = 0; r0 < n; r0 += m->max_batch) {
         const int nb = (int)std::min<int64_t>(m->max_batch, n - r0);
@@ -1022,6 +1025,7 @@ double cfg_num(const char *json, const char *key, double dflt) {
 extern "C" {
 
 qs_status qs_sur_train(qs_ctx *ctx, const void *X_, const void *Y_, int64_t n, const char *json_cfg, qs_sur **out) {
+    QS_RANGE("qs_sur_train");
     if (!X_ || !Y_ || !out || n < 1) return QS_ERR_ARG;
     const float *X = static_cast<const float *>(X_), *Y = static_cast<const float *>(Y_);
     const int epochs = (int)cfg_num(json_cfg, "epochs", 8), ens = (int)cfg_num(json_cfg, "ensemble", 4);
@@ -1066,6 +1070,7 @@ qs_status qs_sur_train(qs_ctx *ctx, const void *X_, const void *Y_, int64_t n, c
 }
 
 qs_status qs_sur_infer(qs_sur *s, const void *X, int64_t n, void *y_mean, void *y_var, uint8_t *fallback_mask) {
+    QS_RANGE("qs_sur_infer");
     if (!s || !X || !y_mean || !y_var || n < 1) return QS_ERR_ARG;
     return qs_mlp_infer(s->m, static_cast<const float *>(X), n, static_cast<float *>(y_mean),
                         static_cast<float *>(y_var), fallback_mask, s->var_threshold);

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "qs.h"
+#include "qs_nvtx.h"
 #include "qs_kernels.cuh"
 #include "qs_problem.h"
 
@@ -69,6 +70,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 extern "C" qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *theta, int *exponents,
                                       int64_t step0, int n_steps, int *dev_status, void *stream) {
+    QS_RANGE("qs_sweep_noalloc");
     // ---- host-side checks (nothing is enqueued on failure) ----
     if (!p || !state || n_steps < 1 || step0 < 0) return QS_ERR_ARG;
     if (p->front == QS_FRONT_HELD) return QS_ERR_UNSUPPORTED;   // held values need a table of their own
@@ -181,6 +183,10 @@ extern "C" qs_status qs_sweep_noalloc(const qs_params *p, void *state, void *the
     a.step0 = step0; a.n_steps = n_steps; a.update = 1;
     a.persistent = 1;
     a.rec_kinds = 0; a.rec = nullptr;
+    a.rows_total = (long long)p->n_xi * NS;
+    a.groups_total = I.n_grp;
+    a.rec_cap = 0;
+    a.res_every = 16;
     a.ticket = reinterpret_cast<int *>(sc + off_ctrl);
     a.err = reinterpret_cast<int *>(sc + off_ctrl) + 4;
     int nsm = 148, dev = 0;

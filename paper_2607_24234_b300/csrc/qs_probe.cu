@@ -71,11 +71,45 @@ __global__ void __launch_bounds__(256) k_probe_dfma(long long iters, double *sin
     if (__double_as_longlong(s) == 0x7ff8deaddeadbeefLL) sink[0] = s;
 }
 
+// FP64 add and multiply chains (the FP64 sweep issues 16 FMA, 4 MUL and 2
+// ADD per update; these show whether the latter issue at the FMA rate)
+__global__ void __launch_bounds__(256) k_probe_dadd(long long iters, double *sink) {
+    double x[NC];
+    const double t = 1e-3 * (double)(threadIdx.x + 1);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) x[k] = t + k;
+    const double c = 1e-12;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) x[k] = __dadd_rn(x[k], c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) s += x[k];
+    if (__double_as_longlong(s) == 0x7ff8deaddeadbeefLL) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(256) k_probe_dmul(long long iters, double *sink) {
+    double x[NC];
+    const double t = 1e-3 * (double)(threadIdx.x + 1);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) x[k] = t + k;
+    const double b = 0.9999999999;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) x[k] = __dmul_rn(x[k], b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) s += x[k];
+    if (__double_as_longlong(s) == 0x7ff8deaddeadbeefLL) sink[0] = s;
+}
+
 }  // namespace
 
 extern "C" qs_status qs_probe_alu(int kind, int blocks, int threads, int64_t iters, void *dev_sink,
                                   void *stream, double *lane_ops) {
-    if (kind < 0 || kind > 2 || blocks < 1 || threads < 32 || threads > 256 || threads % 32 || iters < 1 ||
+    if (kind < 0 || kind > 4 || blocks < 1 || threads < 32 || threads > 256 || threads % 32 || iters < 1 ||
         !dev_sink)
         return QS_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -84,8 +118,12 @@ extern "C" qs_status qs_probe_alu(int kind, int blocks, int threads, int64_t ite
         k_probe_ffma2<<<blocks, threads, 0, s>>>(iters, static_cast<float *>(dev_sink));
     else if (kind == QS_PROBE_FFMA)
         k_probe_ffma<<<blocks, threads, 0, s>>>(iters, static_cast<float *>(dev_sink));
-    else
+    else if (kind == QS_PROBE_DFMA)
         k_probe_dfma<<<blocks, threads, 0, s>>>(iters, static_cast<double *>(dev_sink));
+    else if (kind == QS_PROBE_DADD)
+        k_probe_dadd<<<blocks, threads, 0, s>>>(iters, static_cast<double *>(dev_sink));
+    else
+        k_probe_dmul<<<blocks, threads, 0, s>>>(iters, static_cast<double *>(dev_sink));
     if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
     if (lane_ops) *lane_ops = per_iter * (double)iters * (double)blocks * (double)threads;
     return QS_OK;

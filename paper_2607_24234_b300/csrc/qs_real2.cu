@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "qs.h"
+#include "qs_nvtx.h"
 
 namespace r2 {
 
@@ -620,6 +621,7 @@ qs_status r2_alloc_t(qs_r2 *c, size_t bytes, T **out) {
 extern "C" {
 
 qs_status qs_r2_init(const qs_r2_params *p, const qs_allocator *alloc, void *stream, qs_r2 **out) {
+    QS_RANGE("qs_r2_init");
     if (!p || !out) return QS_ERR_ARG;
     *out = nullptr;
     const int N = p->n_perp;
@@ -672,6 +674,7 @@ qs_status qs_r2_init(const qs_r2_params *p, const qs_allocator *alloc, void *str
 
 qs_status qs_r2_seed(qs_r2 *c, uint64_t seed, double amplitude, double centroid_offset, const float *user,
                      size_t user_bytes, int user_on_host) {
+    QS_RANGE("qs_r2_seed");
     if (!c) return QS_ERR_ARG;
     const qs_r2_params &p = c->p;
     const int N = c->N;
@@ -716,6 +719,7 @@ qs_status qs_r2_seed(qs_r2 *c, uint64_t seed, double amplitude, double centroid_
 }
 
 qs_status qs_r2_step(qs_r2 *c, int n_steps) {
+    QS_RANGE("qs_r2_step");
     if (!c || n_steps < 1) return QS_ERR_ARG;
     for (int i = 0; i < n_steps; ++i) {
         const float h = (float)(c->step == 0 ? 0.5 * c->p.dt : c->p.dt);

@@ -121,7 +121,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
         }
         if (item >= a.n_items) break;                  // uniform over the CTA
         const int2 itx = a.items[item];
-        const InstDev I = a.inst[itx.x];
+        const InstDev I = a.inst[QS_CHK(a, itx.x, a.n_inst) ? itx.x : 0];
         const int N = I.n_xi;
         const int Tl = (((N + V - 1) / V) + 31) & ~31;  // threads per line (whole warps)
         const int L = T / Tl;                          // lines per CTA (host: >= 1)
@@ -136,7 +136,8 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
         const bool front1 = a.front == 1 && live && t == 0;
 
         // per-line constants
-        const double kapd = a.kap[mc], kk2d = a.kapk2[mc];
+        const int mk = QS_CHK(a, mc, a.Mp) ? mc : 0;
+        const double kapd = a.kap[mk], kk2d = a.kapk2[mk];
         float Af[NS], Bf[NS], q[NS];
 #pragma unroll
         for (int sp = 0; sp < NS; ++sp) {
@@ -175,7 +176,8 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
             const float ga = (float)(cs * g1 + sn * g2), gb = (float)(cs * g2 - sn * g1);
             sG[lane] = make_float4(ga, ga, gb, gb);
         }
-        const bool held = a.front == 2 && a.held != nullptr && live && t == 0;
+        const bool held = a.front == 2 && a.held != nullptr && live && t == 0 &&
+                          QS_CHK(a, ((long long)itx.x * a.Mp + mc) * 4 + 3, (long long)a.n_inst * a.Mp * 4);
         const double *hp = held ? a.held + ((long long)itx.x * a.Mp + mc) * 4 : nullptr;
 
         // load the chunk: mantissas relative to e = W + s8 of its group; cells
@@ -185,7 +187,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
         int e = RES_NONE;
         float fin = 1.0f;
         if (has) {
-            const int exw = __ldcg(a.ex + (I.grp_off + jb / GRP) * a.Mp + mode);
+            const int exw = ld_ex(a, I.grp_off + jb / GRP, mode);
             const int s8 = (int)(signed char)(exw & 0xff);
             e = (exw >> 8) + s8;
             fin = p2(-s8);
@@ -202,7 +204,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     ld_cell(a, row, mode, y);
                     const float f = fin * q[sp];
                     y.nr *= f; y.ni *= f; y.tr *= f; y.ti *= f;
-                    wv = __ldg(reinterpret_cast<const float *>(a.w) + row);
+                    wv = QS_CHK(a, row, a.rows_total) ? __ldg(reinterpret_cast<const float *>(a.w) + row) : 0.f;
                 }
                 xn[v][sp] = make_float2(y.nr, y.ni);
                 if constexpr (THS) {
@@ -313,7 +315,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
 #pragma unroll
             for (int vb = 0; vb < V; vb += CB) {
                 float2 zt[THS ? CB : 1][NS];
-                float zw[THS ? CB : 1][NS];
+                [[maybe_unused]] float zw[THS ? CB : 1][NS];
                 if constexpr (THS) {
 #pragma unroll
                     for (int u = 0; u < CB; ++u)
@@ -458,7 +460,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     rc[1] = (float)(ka * ka * kp * kp);
 #pragma unroll
                     for (int sp = 0; sp < NS; ++sp) {
-                        const double qq = a.inst[ix.x].q[sp];
+                        const double qq = I.q[sp];
                         rc[2 + sp] = (float)(1.0 / (qq * qq));
                     }
                 }
@@ -480,9 +482,12 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     for (int ww = w0; ww < wend; ++ww) {
                         L0 = fmax(L0, sMM[ww][0]); L1 = fmax(L1, sMM[ww][1]); L2 = fmax(L2, sMM[ww][2]);
                     }
-                    double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)itx.x * a.Mp + mode;
-                    const long long pl = (long long)a.n_inst * a.Mp;
-                    o[0] = L0; o[pl] = L1; o[2 * pl] = L2;
+                    if (QS_CHK(a, snap * a.rec_snap_doubles + a.rec_off_mm + ((long long)itx.x + 2LL * a.n_inst) * a.Mp + mode,
+                               a.rec_cap)) {
+                        double *o = a.rec + snap * a.rec_snap_doubles + a.rec_off_mm + (long long)itx.x * a.Mp + mode;
+                        const long long pl = (long long)a.n_inst * a.Mp;
+                        o[0] = L0; o[pl] = L1; o[2 * pl] = L2;
+                    }
                 }
                 __syncthreads();   // sMM is reused at the next recording step
             } else if ((it & (a.res_every - 1)) == a.res_every - 1) {
@@ -510,7 +515,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
         }
 
         // write back: the threads of a 32-cell group agree on one exponent
-        const long long cell0 = a.inst[itx.x].cell_off, grp0 = a.inst[itx.x].grp_off;
+        const long long cell0 = I.cell_off, grp0 = I.grp_off;
         int Wg = e;
 #pragma unroll
         for (int o = 1; o < GRP / V; o <<= 1) Wg = max(Wg, __shfl_xor_sync(FULL, Wg, o));
@@ -545,7 +550,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                 int s8 = gm > 0.0f ? expof(gm) : 0;
                 s8 = s8 < -100 ? -100 : (s8 > 100 ? 100 : s8);
                 const int Ws = gm > 0.0f ? Wg : 0;
-                __stcg(a.ex + (grp0 + jb / GRP) * a.Mp + mode, (Ws << 8) | (s8 & 0xff));
+                st_ex(a, grp0 + jb / GRP, mode, (Ws << 8) | (s8 & 0xff));
             }
             if (!(gn == 0.0f) || !(gm <= 3.0e38f)) atomicOr(a.err, ERR_NONFINITE);
         }

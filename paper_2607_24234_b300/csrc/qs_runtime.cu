@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "qs.h"
+#include "qs_nvtx.h"
 #include "qs_kernels.cuh"
 #include "qs_problem.h"
 #include "qs_resident.cuh"
@@ -31,9 +32,18 @@ namespace {
 
 thread_local std::string g_init_err;
 
+// Every context buffer carries a guard of CANARY_BYTES after its payload
+// (at the payload size rounded up to 16 bytes), filled with CANARY_BYTE when
+// it is allocated; qs_sync and host-pointer qs_diag check the guards, so a
+// stray write past a buffer's end is reported (QS_ERR_BOUNDS) at the next
+// synchronisation instead of corrupting a neighbour silently.
+constexpr size_t CANARY_BYTES = 256;
+constexpr unsigned char CANARY_BYTE = 0xA5;
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    size_t canary = 0;   // offset of the guard
 };
 
 }  // namespace
@@ -95,6 +105,7 @@ struct qs_ctx {
     long long spin_limit = 1LL << 24;
     int tx_extra = 0;
     int res_every = 16;             // resident variant's renormalisation interval (0: variant refused)
+    long long dbg_rows_cut = 0;     // test hook: state rows the bounds checker is told are missing
     double growth = 0.0;            // largest per-step growth bound of the instances (e-folds)
     std::string err;
 };
@@ -120,6 +131,8 @@ qs_status fail(qs_ctx *c, qs_status st, const char *fmt, ...) {
 qs_status dalloc(qs_ctx *c, size_t bytes, void **out) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    const size_t guard = (bytes + 15) & ~size_t(15);
+    bytes = guard + CANARY_BYTES;
     if (c->has_alloc) {
         p = c->alloc.alloc(bytes, c->alloc.user);
         if (!p) return fail(c, QS_ERR_OOM, "allocator returned NULL for %zu bytes", bytes);
@@ -131,7 +144,11 @@ qs_status dalloc(qs_ctx *c, size_t bytes, void **out) {
                         "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
         }
     }
-    c->bufs.push_back({p, bytes});
+    c->bufs.push_back({p, bytes, guard});
+    if (cudaMemsetAsync(static_cast<char *>(p) + guard, CANARY_BYTE, CANARY_BYTES, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QS_ERR_CUDA, "canary fill failed");
+    }
     *out = p;
     return QS_OK;
 }
@@ -383,6 +400,9 @@ SweepArgs sweep_args(qs_ctx *c, long long step0, int n_steps, int update, int re
     a.spin_limit = c->spin_limit;
     a.tx_extra = c->tx_extra;
     a.res_every = c->res_every > 0 ? c->res_every : 1;
+    a.rows_total = c->cells_total * c->NS - c->dbg_rows_cut;
+    a.groups_total = c->groups_total;
+    a.rec_cap = rec ? rec_max_snap * off : 0;
     return a;
 }
 
@@ -563,6 +583,38 @@ long long snapshot_doubles(const qs_ctx *c, int kinds) {
     return d;
 }
 
+// guard check: one CTA per buffer compares its CANARY_BYTES with the fill;
+// a mismatch sets ERR_CANARY and keeps the buffer index + 1 in word 1
+struct CanaryArgs {
+    const uint4 *p[32];
+    int n, first;
+    int *err;
+};
+__global__ void k_canary(const CanaryArgs a) {
+    const int b = blockIdx.x;
+    if (b >= a.n) return;
+    const uint4 v = a.p[b][threadIdx.x];
+    const unsigned f = 0x01010101u * CANARY_BYTE;
+    if (v.x != f || v.y != f || v.z != f || v.w != f) {
+        atomicOr(a.err, qsk::ERR_CANARY);
+        atomicCAS(a.err + 1, 0, a.first + b + 1);
+    }
+}
+
+qs_status check_canaries(qs_ctx *c) {
+    for (size_t b0 = 0; b0 < c->bufs.size(); b0 += 32) {
+        CanaryArgs a{};
+        a.n = (int)std::min<size_t>(32, c->bufs.size() - b0);
+        a.first = (int)b0;
+        a.err = c->err_d;
+        for (int i = 0; i < a.n; ++i)
+            a.p[i] = reinterpret_cast<const uint4 *>(static_cast<const char *>(c->bufs[b0 + i].p) + c->bufs[b0 + i].canary);
+        k_canary<<<a.n, CANARY_BYTES / 16, 0, c->stream>>>(a);
+        CU(c, cudaGetLastError());
+    }
+    return QS_OK;
+}
+
 qs_status check_ready(qs_ctx *c) {
     if (!c) return QS_ERR_ARG;
     if (c->poisoned) return fail(c, QS_ERR_STATE, "context poisoned by an earlier device error; reseed");
@@ -576,6 +628,7 @@ extern "C" {
 
 qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
                   const qs_allocator *alloc, void *stream, qs_ctx **out) {
+    QS_RANGE("qs_init");
     if (!p || !out) return fail(nullptr, QS_ERR_ARG, "null params or out");
     *out = nullptr;
     if (n_inst < 1) return fail(nullptr, QS_ERR_ARG, "n_inst must be >= 1");
@@ -734,6 +787,7 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
 
 qs_status qs_seed(qs_ctx *c, uint64_t seed, double amplitude, int kind, const void *user,
                   size_t user_bytes, int user_on_host) {
+    QS_RANGE("qs_seed");
     if (!c) return QS_ERR_ARG;
     if (kind < 0 || kind > 3) return fail(c, QS_ERR_ARG, "seed kind %d", kind);
     if (kind == QS_SEED_STATE) {
@@ -806,6 +860,7 @@ qs_status qs_seed(qs_ctx *c, uint64_t seed, double amplitude, int kind, const vo
 }
 
 qs_status qs_step(qs_ctx *c, int n_steps) {
+    QS_RANGE("qs_step");
     qs_status s = check_ready(c);
     if (s) return s;
     if (n_steps < 1) return fail(c, QS_ERR_ARG, "n_steps must be >= 1");
@@ -831,6 +886,7 @@ qs_status qs_step(qs_ctx *c, int n_steps) {
 }
 
 qs_status qs_record(qs_ctx *c, int kinds, int stride, void *dev_out, size_t out_bytes) {
+    QS_RANGE("qs_record");
     if (!c) return QS_ERR_ARG;
     if (kinds == 0 || !dev_out) {
         c->rec_buf = nullptr; c->rec_kinds = 0; c->rec_bytes = 0;
@@ -845,6 +901,7 @@ qs_status qs_record(qs_ctx *c, int kinds, int stride, void *dev_out, size_t out_
 }
 
 qs_status qs_diag(qs_ctx *c, int kind, void *out, size_t out_bytes, int out_on_host) {
+    QS_RANGE("qs_diag");
     if (!c || !out) return c ? fail(c, QS_ERR_ARG, "null out") : QS_ERR_ARG;
     if (kind == QS_DIAG_STATE) {
         if (!c->seeded) return fail(c, QS_ERR_STATE, "not seeded");
@@ -1026,13 +1083,24 @@ qs_status qs_get_launch(const qs_ctx *c, qs_launch *l) {
 }
 
 qs_status qs_sync(qs_ctx *c) {
+    QS_RANGE("qs_sync");
     if (!c) return QS_ERR_ARG;
+    qs_status cs = check_canaries(c);
+    if (cs) return cs;
     CU(c, cudaStreamSynchronize(c->stream));
-    int e = 0;
-    CU(c, cudaMemcpy(&e, c->err_d, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
+    int e[4] = {0, 0, 0, 0};
+    CU(c, cudaMemcpy(e, c->err_d, sizeof e, cudaMemcpyDeviceToHost));
+    if (e[0]) {
         c->poisoned = true;
-        if (e & qsk::ERR_TIMEOUT) return fail(c, QS_ERR_TIMEOUT, "a bounded device wait ran out");
+        if (e[0] & qsk::ERR_CANARY)
+            return fail(c, QS_ERR_BOUNDS, "the guard after buffer %d was overwritten (a write past its end)", e[1] - 1);
+        if (e[0] & qsk::ERR_BOUNDS) {
+            long long bad = 0;
+            memcpy(&bad, e + 2, sizeof bad);
+            return fail(c, QS_ERR_BOUNDS, "an index left its buffer (bounds-checked build): first bad index %lld",
+                        bad - 1);
+        }
+        if (e[0] & qsk::ERR_TIMEOUT) return fail(c, QS_ERR_TIMEOUT, "a bounded device wait ran out");
         return fail(c, QS_ERR_NONFINITE, "non-finite value in the state");
     }
     return QS_OK;
@@ -1041,6 +1109,7 @@ qs_status qs_sync(qs_ctx *c) {
 int64_t qs_launch_count(const qs_ctx *c) { return c ? c->n_launch : -1; }
 
 qs_status qs_growth_bound(const qs_params *p, double *efolds_per_step, int *res_every) {
+    QS_RANGE("qs_growth_bound");
     if (!p) return QS_ERR_ARG;
     qs_status st = validate(*p, 0);
     if (st) return st;
@@ -1051,6 +1120,26 @@ qs_status qs_growth_bound(const qs_params *p, double *efolds_per_step, int *res_
     if (efolds_per_step) *efolds_per_step = g;
     if (res_every) *res_every = qsp::res_every_for(g, lc, p->n_xi * p->dxi);
     return QS_OK;
+}
+
+qs_status qs_debug_canary(qs_ctx *c, int buffer) {
+    if (!c || buffer < 0 || buffer >= (int)c->bufs.size()) return QS_ERR_ARG;
+    CU(c, cudaMemsetAsync(static_cast<char *>(c->bufs[buffer].p) + c->bufs[buffer].canary + 7, 0, 1, c->stream));
+    return QS_OK;
+}
+
+qs_status qs_debug_bounds(qs_ctx *c, int64_t rows_cut) {
+    if (!c || rows_cut < 0 || rows_cut > c->cells_total * c->NS) return QS_ERR_ARG;
+    c->dbg_rows_cut = rows_cut;
+    return QS_OK;
+}
+
+int qs_build_flags(void) {
+#ifdef QS_CHECK_BOUNDS
+    return QS_BUILD_CHECK_BOUNDS;
+#else
+    return 0;
+#endif
 }
 
 qs_status qs_debug_waits(qs_ctx *c, int64_t spin_limit, int unsatisfiable) {

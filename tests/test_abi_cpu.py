@@ -96,7 +96,7 @@ def test_allocator_failure_reports_oom(qs):
     al = qs.Allocator(qs.Allocator._fields_[0][1](_a), qs.Allocator._fields_[1][1](_f), None)
     st, ctx = _init(qs, synth.SLAB_2D, alloc=ctypes.byref(al))
     assert st == qs.QS_ERR_OOM
-    assert calls and calls[0] == 512 * 64 * 16   # first request: the FP32 state
+    assert calls and calls[0] == 512 * 64 * 16 + 256   # first request: the FP32 state and its 256-byte guard
     assert ctx.value is None
 
 
@@ -180,3 +180,17 @@ def test_growth_bound_bounds_the_oracle(qs, species, gamma, dt, L):
             oracle.sweep(p, nb, th, k, 1)
             mk = max(np.max(np.abs(nb)), np.max(np.abs(th)))
             assert math.log(mk / m0) <= k * g + lc + 1e-9, (trial, k)
+
+
+def test_bounds_checked_build(qs):
+    """The bounds-checked variant (libqs_checked.so, -DQS_CHECK_BOUNDS) is
+    built beside the ordinary one, reports itself through qs_build_flags and
+    exports every symbol the header declares."""
+    hdr = open(os.path.join(ROOT, "include", "qs.h")).read()
+    names = sorted(set(re.findall(r"\b(qs_[a-z_0-9]+)\s*\(", hdr)))
+    path = os.path.join(ROOT, "paper_2607_24234_b300", "libqs_checked.so")
+    L = ctypes.CDLL(path)
+    assert L.qs_build_flags() == qs.BUILD_CHECK_BOUNDS
+    assert qs.lib.qs_build_flags() == 0
+    for n in names:
+        assert hasattr(L, n), n
