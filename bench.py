@@ -488,6 +488,40 @@ def run_surrogate(args):
     m.close()
 
 
+def run_mlp(args):
+    """The surrogate network alone on seeded random rows: --mlp-steps training
+    steps of 16,384 rows x 4 members (16 -> 256 x 3 -> 2, BF16 on tcgen05)
+    and ensemble inference of --mlp-rows rows, each timed with CUDA events."""
+    import torch
+    from paper_2607_24234_b300 import surrogate as sur
+    torch.cuda.set_device(0)
+    pk, _ = peaks()
+    rng = np.random.default_rng(0)
+    n = 16384
+    X = torch.from_numpy((rng.standard_normal((args.mlp_rows, 7)) * 3).astype(np.float32)).cuda()
+    Y = torch.from_numpy(np.stack([rng.standard_normal(args.mlp_rows) * 10,
+                                   rng.random(args.mlp_rows) > 0.5], 1).astype(np.float32)).cuda()
+    m = sur.MLP(width=256, depth=3, ensemble=4, max_batch=n, seed=1)
+    m.set_norm(X[:n], Y[:n])
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        m.train_step(X[:n], Y[:n], 1e-3)
+    t_step, _ = time_job(stream, lambda: [m.train_step(X[i * n % (args.mlp_rows - n):][:n], Y[:n], 1e-3)
+                                          for i in range(args.mlp_steps)], 1)
+    m.infer(X[:n])
+    t_inf, _ = time_job(stream, lambda: m.infer(X), 3)
+    nparam = 7 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 2 + 2
+    flops_step = 6.0 * nparam * n * 4
+    ms = 1e3 * t_step / args.mlp_steps
+    print(json.dumps({"metric": "surrogate MLP: training step time and inference queries/s", "workload": "mlp_16384x4",
+                      "train_ms_per_step": ms, "train_tflops": flops_step / (ms / 1e3) / 1e12,
+                      "train_frac_of_bf16_peak": flops_step / (ms / 1e3) / 1e12 / pk.get("bf16_tflops", 1800.0),
+                      "infer_rows": args.mlp_rows, "infer_queries_per_s": args.mlp_rows / t_inf,
+                      "infer_tflops": 2.0 * nparam * 4 * args.mlp_rows / t_inf / 1e12,
+                      "gelu_per_query": 3 * 256 * 4}), flush=True)
+    m.close()
+
+
 def narrow_leg(args, pk, pk_kind):
     """Finite-width narrow beam: 256 x 256 transverse grid over +-8 sigma_r,
     16,000 xi cells, FP32; one timed call = --narrow-steps slow-time steps."""
@@ -818,7 +852,9 @@ def main():
                     help="skip the Green's-function path job")
     ap.add_argument("--diag-stride", type=int, default=100,
                     help="record cadence of the diag-on job (0: skip it)")
-    ap.add_argument("--workload", default="beam3d", choices=["beam3d", "batch", "surrogate", "narrow"])
+    ap.add_argument("--workload", default="beam3d", choices=["beam3d", "batch", "surrogate", "narrow", "mlp"])
+    ap.add_argument("--mlp-steps", type=int, default=20)
+    ap.add_argument("--mlp-rows", type=int, default=1 << 20)
     ap.add_argument("--narrow-steps", type=int, default=20)
     ap.add_argument("--sur-train-inst", type=int, default=64)
     ap.add_argument("--sur-epochs", type=int, default=8)
@@ -851,6 +887,8 @@ def main():
         run_surrogate(args)
     elif args.workload == "narrow":
         run_narrow(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     else:
         run_ours(args)
 

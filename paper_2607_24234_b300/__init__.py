@@ -74,10 +74,27 @@ class Launch(ctypes.Structure):
                 ("scan_cells", ctypes.c_int)]
 
 
+def _source_hash():
+    """The build script's hash of the library sources (loaded by path: the
+    build script imports nothing from this package)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("qs_build_hash", os.path.join(_HERE, "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.source_hash()
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
                           f"`python paper_2607_24234_b300/build.py` (nvcc, sm_103a)")
+    try:
+        built = open(LIB_PATH + ".srchash").read().strip()
+    except OSError:
+        built = None
+    if built != _source_hash():
+        raise ImportError(f"{LIB_PATH} was not built from the current sources: rebuild it with "
+                          f"`python paper_2607_24234_b300/build.py`")
     L = ctypes.CDLL(LIB_PATH)
     vp, i64 = ctypes.c_void_p, ctypes.c_int64
     L.qs_init.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(Params),

@@ -31,8 +31,19 @@ def link_cmd(objs, out: str):
     return ["nvcc", "-shared", *ARCH, *objs, "-o", out, "-cudart", "static"]
 
 
+def source_hash() -> str:
+    """Hash of every source the library is built from (written beside each
+    built library; the binding refuses a library whose sources changed)."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in DEPS[:-1]:   # the sources and headers (not this script)
+        with open(d, "rb") as f:
+            h.update(os.path.basename(d).encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
 def _fresh(target: str) -> bool:
-    if not os.path.exists(target):
+    if not os.path.exists(target) or not os.path.exists(target + ".srchash"):
         return False
     t = os.path.getmtime(target)
     return all(os.path.getmtime(d) <= t for d in DEPS if os.path.exists(d))
@@ -53,10 +64,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         for f in [ex.submit(subprocess.check_call, cmd) for _, _, cmd in jobs]:
             f.result()
+    digest = source_hash()
     for so in todo:
         tmp = so + f".tmp{os.getpid()}"
         subprocess.check_call(link_cmd([o for s, o, _ in jobs if s == so], tmp))
         os.replace(tmp, so)
+        with open(so + ".srchash", "w") as f:
+            f.write(digest + "\n")
     return SO
 
 

@@ -380,6 +380,232 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused ensemble inference for the 16 -> 256 -> 256 -> 256 -> 2 network (the
+// surrogate's shape).  A persistent CTA of 8 warps takes 128-row tiles; for
+// every member it runs the three hidden layers on tcgen05 (M = 128, N = 256,
+// accumulator in 256 TMEM columns), with the activations kept on chip: each
+// epilogue reads the accumulator with tcgen05.ld, adds the bias, applies GELU
+// and writes the bf16 activations straight into the next layer's shared-
+// memory A operand.  The next layer's 128 KB of weights (L2-resident: every
+// CTA reads the same ones) are copied with cp.async while the epilogue runs.
+// The last epilogue also forms the 2 outputs (dot products with W3 in FP32)
+// and the ensemble's mean, variance and fallback mask per row, so nothing but
+// the inputs and the final statistics touches global memory.
+// ---------------------------------------------------------------------------
+struct FusedArgs {
+    const float *X;                  // [n][n_in] raw inputs
+    long long n;
+    int n_in;
+    const float *stats;              // input mean[32], inverse std[32]
+    const __nv_bfloat16 *Pb;         // [E][nparam] bf16 parameters
+    const float *P;                  // [E][nparam] fp32 parameters (biases)
+    long long nparam;
+    long long w0, w1, w2, w3, b0, b1, b2, b3;   // offsets within a member's block
+    int E;
+    float ymean, ystd, thr;
+    float *mean, *var;
+    unsigned char *mask;
+    int *err;
+};
+
+namespace fz {
+constexpr int W = 256, KIN = 16;
+constexpr uint32_t SBO_W = (W / 8) * 128, SBO_I = (KIN / 8) * 128, LBO = 128;
+constexpr size_t OFF_WB = 0, OFF_AB = OFF_WB + (size_t)W * W * 2, OFF_W0 = OFF_AB + (size_t)128 * W * 2,
+                 OFF_A0 = OFF_W0 + (size_t)W * KIN * 2, OFF_BIAS = OFF_A0 + (size_t)128 * KIN * 2,
+                 OFF_W3 = OFF_BIAS + 3 * W * 4, OFF_PART = OFF_W3 + 2 * W * 4 + 16, SMEM = OFF_PART + 128 * 2 * 4;
+
+// 16-byte asynchronous copies of a [rows][K] bf16 row-major matrix into the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix)
+template <int K>
+__device__ __forceinline__ void stage(unsigned char *dst, const __nv_bfloat16 *src, int rows, int tid, int nthr) {
+    constexpr uint32_t SBO = (K / 8) * 128;
+    for (int i = tid; i < rows * (K / 8); i += nthr) {
+        const int r = i / (K / 8), c8 = i % (K / 8);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+                     "l"(src + (long long)r * K + c8 * 8) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+        "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+}  // namespace fz
+
+__global__ void __launch_bounds__(256, 1) k_mlp_infer_fused(const FusedArgs a) {
+    using namespace fz;
+    extern __shared__ __align__(1024) unsigned char sf[];
+    unsigned char *Wb = sf + OFF_WB, *Ab = sf + OFF_AB, *W0s = sf + OFF_W0, *A0 = sf + OFF_A0;
+    float *bias = reinterpret_cast<float *>(sf + OFF_BIAS), *w3 = reinterpret_cast<float *>(sf + OFF_W3);
+    float *part = reinterpret_cast<float *>(sf + OFF_PART);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t taddr_s;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hc = warp >> 2;    // TMEM lane quarter, column half
+    const int row = 32 * q + lane;             // the tile row this thread's TMEM lane holds
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&taddr_s)), "r"(W));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_bad = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    uint32_t phase = 0;
+    bool ok = true;
+    // make generic-proxy shared writes and finished copies visible to the MMA
+    // and order TMEM use around the barrier
+    auto sync_for_mma = [&]() {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    // one thread issues the layer's MMAs and commits; everyone waits (bounded)
+    auto mma_layer = [&](const unsigned char *A, const unsigned char *B, int ksteps, uint32_t sbo) {
+        if (tid == 0) {
+            constexpr uint32_t id = tc::idesc_bf16(128, W);
+            for (int kk = 0; kk < ksteps; ++kk) {
+                const uint64_t ad = tc::sdesc(tc::su32(A) + kk * 2 * LBO, LBO, sbo);
+                const uint64_t bd = tc::sdesc(tc::su32(B) + kk * 2 * LBO, LBO, sbo);
+                const uint32_t acc = kk > 0 ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
+                         : "memory");
+        }
+        uint32_t done = 0;
+        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(tc::su32(&bar)), "r"(phase & 1u) : "memory");
+        ++phase;
+        if (!done) atomicOr(&s_bad, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    };
+    // accumulator -> bias + GELU -> bf16 activations in the A operand layout
+    auto epilogue_hidden = [&](const float *b) {
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            const int c0 = 128 * hc + 32 * c;
+            float v[32];
+            tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                __nv_bfloat162 h2[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    h2[t] = __floats2bfloat162_rn(gelu(v[j + 2 * t] + b[c0 + j + 2 * t]),
+                                                  gelu(v[j + 2 * t + 1] + b[c0 + j + 2 * t + 1]));
+                *reinterpret_cast<uint4 *>(Ab + (row / 8) * SBO_W + ((c0 + j) / 8) * LBO + (row % 8) * 16) =
+                    *reinterpret_cast<const uint4 *>(h2);
+            }
+        }
+    };
+    const long long ntiles = (a.n + 127) / 128;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long r0 = tile * 128;
+        // standardised bf16 inputs of the tile (zero-padded to 16 columns and past n)
+        if (tid < 128) {
+            const long long gr = r0 + tid;
+            __nv_bfloat16 x16[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float v = (gr < a.n && k < a.n_in) ? (a.X[gr * a.n_in + k] - a.stats[k]) * a.stats[32 + k] : 0.0f;
+                x16[k] = __float2bfloat16(v);
+            }
+            *reinterpret_cast<uint4 *>(A0 + (tid / 8) * SBO_I + 0 * LBO + (tid % 8) * 16) = *reinterpret_cast<const uint4 *>(x16);
+            *reinterpret_cast<uint4 *>(A0 + (tid / 8) * SBO_I + 1 * LBO + (tid % 8) * 16) = *reinterpret_cast<const uint4 *>(x16 + 8);
+        }
+        float s0 = 0.f, q0 = 0.f, s1 = 0.f, q1 = 0.f;   // ensemble sums of the row (warps 0..3)
+        for (int e = 0; e < a.E && ok; ++e) {
+            const __nv_bfloat16 *Pm = a.Pb + (long long)e * a.nparam;
+            const float *Pf = a.P + (long long)e * a.nparam;
+            stage<KIN>(W0s, Pm + a.w0, W, tid, 256);
+            for (int i = tid; i < W; i += 256) {
+                bias[i] = Pf[a.b0 + i]; bias[W + i] = Pf[a.b1 + i]; bias[2 * W + i] = Pf[a.b2 + i];
+                w3[i] = __bfloat162float(Pm[a.w3 + i]); w3[W + i] = __bfloat162float(Pm[a.w3 + W + i]);
+            }
+            if (tid < 2) w3[2 * W + tid] = Pf[a.b3 + tid];
+            sync_for_mma();
+            mma_layer(A0, W0s, 1, SBO_I);                       // layer 0: K = 16
+            stage<W>(Wb, Pm + a.w1, W, tid, 256);               // W1 lands during the epilogue
+            epilogue_hidden(bias);
+            sync_for_mma();
+            mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 1
+            stage<W>(Wb, Pm + a.w2, W, tid, 256);               // W2 lands during the epilogue
+            epilogue_hidden(bias + W);
+            sync_for_mma();
+            mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 2
+            // output layer: GELU activations (rounded to bf16 as the operand of
+            // the unfused path) dotted with W3 in FP32
+            float o0 = 0.f, o1 = 0.f;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                const int c0 = 128 * hc + 32 * c;
+                float v[32];
+                tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float h = __bfloat162float(__float2bfloat16(gelu(v[j] + bias[2 * W + c0 + j])));
+                    o0 = fmaf(h, w3[c0 + j], o0);
+                    o1 = fmaf(h, w3[W + c0 + j], o1);
+                }
+            }
+            if (hc == 1) { part[2 * row] = o0; part[2 * row + 1] = o1; }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (hc == 0) {
+                const float y0 = (o0 + part[2 * row] + w3[2 * W]) * a.ystd + a.ymean;
+                const float y1 = o1 + part[2 * row + 1] + w3[2 * W + 1];
+                s0 += y0; q0 += y0 * y0; s1 += y1; q1 += y1 * y1;
+            }
+            ok = s_bad == 0;
+        }
+        if (hc == 0 && ok) {
+            const long long gr = r0 + row;
+            if (gr < a.n) {
+                const float inv = 1.0f / a.E;
+                const float m0 = s0 * inv, m1 = s1 * inv;
+                const float v0 = fmaxf(q0 * inv - m0 * m0, 0.f), v1 = fmaxf(q1 * inv - m1 * m1, 0.f);
+                a.mean[2 * gr] = m0; a.mean[2 * gr + 1] = m1;
+                a.var[2 * gr] = v0; a.var[2 * gr + 1] = v1;
+                if (a.mask) a.mask[gr] = v0 > a.thr ? 1 : 0;
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(a.err, 2);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(W));
+    }
+}
+
 // W [out][in] fp32 -> W^T [in][out] bf16 (K-major operand for dX = dz W)
 __global__ void k_transpose_bf16(const float *W, int out, int in, __nv_bfloat16 *WT, long long s_member) {
     W += blockIdx.y * s_member;  // ensemble member
@@ -589,6 +815,7 @@ struct qs_mlp {
     long long astride = 0;               // per-member stride of the activation buffers (max_batch * width)
     int *errw = nullptr;                 // device error word (bounded waits)
     bool use_tc = true;
+    bool fused_ok = false;               // 16 -> 256 x 3 (GELU) -> 2: fused inference kernel applies
     long long step = 0;
     std::string err;
 };
@@ -863,6 +1090,10 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     cudaFuncSetAttribute(mlp::k_gemm_tc<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 16 * 2);
     cudaFuncSetAttribute(mlp::k_gemm_tc<256, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 + 64) * 256 * 2);
     if (const char *v = getenv("QS_MLP_NO_TCGEN05")) m->use_tc = v[0] == '0';
+    // the fused inference kernel serves the surrogate's shape; QS_MLP_NO_FUSED=1
+    // selects the layer-by-layer path (used to compare the two)
+    m->fused_ok = m->kin == 16 && width == 256 && depth == 3 && n_out == 2;
+    if (const char *v = getenv("QS_MLP_NO_FUSED")) m->fused_ok = m->fused_ok && v[0] == '0';
     if (cudaGetLastError() != cudaSuccess) { qs_mlp_free(m); return QS_ERR_CUDA; }
     *out = m;
     return QS_OK;
@@ -965,6 +1196,30 @@ qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float 
                        float var_threshold) {
     QS_RANGE("qs_mlp_infer");
     if (!m || !X || !mean || !var || n < 1) return QS_ERR_ARG;
+    if (m->use_tc && m->fused_ok) {
+        // the surrogate's shape: one persistent launch over all rows, every
+        // member's layers on chip, the ensemble statistics in the epilogue
+        static bool attr = false;
+        if (!attr) {
+            if (cudaFuncSetAttribute(mlp::k_mlp_infer_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)mlp::fz::SMEM) != cudaSuccess)
+                return mfail(m, QS_ERR_CUDA, "fused inference: shared-memory opt-in failed");
+            attr = true;
+        }
+        mlp::FusedArgs fa{};
+        fa.X = X; fa.n = n; fa.n_in = m->n_in; fa.stats = m->stats;
+        fa.Pb = m->Pb; fa.P = m->P; fa.nparam = m->nparam;
+        fa.w0 = m->woff[0]; fa.w1 = m->woff[1]; fa.w2 = m->woff[2]; fa.w3 = m->woff[3];
+        fa.b0 = m->boff[0]; fa.b1 = m->boff[1]; fa.b2 = m->boff[2]; fa.b3 = m->boff[3];
+        fa.E = m->E; fa.ymean = m->ymean; fa.ystd = m->ystd; fa.thr = var_threshold;
+        fa.mean = mean; fa.var = var; fa.mask = mask; fa.err = m->errw;
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long tiles = (n + 127) / 128;
+        mlp::k_mlp_infer_fused<<<(unsigned)std::min<long long>(nsm, tiles), 256, mlp::fz::SMEM, m->stream>>>(fa);
+        return cudaGetLastError() == cudaSuccess ? QS_OK : mfail(m, QS_ERR_CUDA, "fused inference launch failed");
+    }
     for (int64_t r0 = 0; r0 < n; r0 += m->max_batch) {
         const int nb = (int)std::min<int64_t>(m->max_batch, n - r0);
         mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(

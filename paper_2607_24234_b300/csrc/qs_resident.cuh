@@ -312,6 +312,20 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
             float gmax = 0.f;
             const float2 Ach = F2(A[0] * ch), Ash = F2(A[0] * sh), AB = F2(A[0] - B[0]);
             const float2 CH2 = F2(ch), SH2 = F2(sh);
+            // THS: the Theta and w rows of a batch are loaded one batch ahead
+            // (software pipelining), so a batch's shared-memory latency is
+            // covered by the previous batch's arithmetic
+            [[maybe_unused]] float2 pt[THS ? CB : 1][NS];
+            [[maybe_unused]] float pw[THS ? CB : 1][NS];
+            if constexpr (THS) {
+#pragma unroll
+                for (int u = 0; u < CB; ++u)
+#pragma unroll
+                    for (int sp = 0; sp < NS; ++sp) {
+                        pt[u][sp] = sT[(u * NS + sp) * T];
+                        pw[u][sp] = sWt[(u * NS + sp) * T];
+                    }
+            }
 #pragma unroll
             for (int vb = 0; vb < V; vb += CB) {
                 float2 zt[THS ? CB : 1][NS];
@@ -321,9 +335,18 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     for (int u = 0; u < CB; ++u)
 #pragma unroll
                         for (int sp = 0; sp < NS; ++sp) {
-                            zt[u][sp] = sT[((vb + u) * NS + sp) * T];
-                            zw[u][sp] = sWt[((vb + u) * NS + sp) * T];
+                            zt[u][sp] = pt[u][sp];
+                            zw[u][sp] = pw[u][sp];
                         }
+                    if (vb + CB < V) {
+#pragma unroll
+                        for (int u = 0; u < CB; ++u)
+#pragma unroll
+                            for (int sp = 0; sp < NS; ++sp) {
+                                pt[u][sp] = sT[((vb + CB + u) * NS + sp) * T];
+                                pw[u][sp] = sWt[((vb + CB + u) * NS + sp) * T];
+                            }
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < CB; ++u) {
@@ -370,7 +393,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     for (int u = 0; u < CB; ++u)
 #pragma unroll
                         for (int sp = 0; sp < NS; ++sp) sT[((vb + u) * NS + sp) * T] = zt[u][sp];
-                    // keep the next batch's loads after this point: hoisting all
+                    // keep later batches' loads after this point: hoisting all
                     // of them would hold every cell's Theta in registers
                     asm volatile("" ::: "memory");
                 }
@@ -381,6 +404,8 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
         // the first step's chunk aggregate (thread 0 starts from the front)
         float2 An, Ad;
         pass1(An, Ad);
+        float fkm[5];        // scan scale factors (see the scan below)
+        bool echg = true;    // this thread's exponent changed since fkm was formed
         for (int it = 0; it < a.n_steps; ++it) {
             const float hf = (a.step0 + it) == 0 ? 0.5f : 1.0f;
             float A[NS], B[NS];
@@ -389,9 +414,16 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
             // ---- this step's chunk aggregate (pass 1), formed by the previous pass 2
             float2 n = An, d = Ad;
             // ---- inclusive scan over the warp's lanes
-            float fk[5];
+            // scale factors 2^(e_{lane - 2^k} - e), 0 for lanes below 2^k (they
+            // add 0 x their own value: no divergent branch); formed again only
+            // after an exponent of the warp changed (renormalisation, clamp)
+            if (__any_sync(FULL, echg)) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) fk[k] = p2(__shfl_up_sync(FULL, e, 1 << k) - e);
+                for (int k = 0; k < 5; ++k) {
+                    const float f = p2(__shfl_up_sync(FULL, e, 1 << k) - e);
+                    fkm[k] = lane >= (1 << k) ? f : 0.f;
+                }
+            }
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const int dl = 1 << k;
@@ -399,18 +431,20 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                 const float2 ud = make_float2(__shfl_up_sync(FULL, d.x, dl), __shfl_up_sync(FULL, d.y, dl));
                 RotF R;
                 if constexpr (THS) { const float2 r2 = sRk[k]; R = RotF{r2.x, r2.y}; } else { R = Rk[THS ? 0 : k]; }
-                // lanes below dl add 0 x (their own value): no divergent branch
-                acc_rot2(n, d, R, lane >= dl ? fk[k] : 0.f, un, ud);
+                acc_rot2(n, d, R, fkm[k], un, ud);
             }
-            const float fx = lane == 0 ? 0.f : fk[0];
+            const float fx = fkm[0];
             float2 Xn = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, n.x, 1), __shfl_up_sync(FULL, n.y, 1)));
             float2 Xd = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, d.x, 1), __shfl_up_sync(FULL, d.y, 1)));
             if (lane == 31) { sZ[buf][warp] = make_float4(n.x, n.y, d.x, d.y); sE[buf][warp] = e; }
             const int wm = __reduce_max_sync(FULL, e);
             if (lane == 0) sM[buf][warp] = wm;
-            __syncthreads();
+            // the barrier also tells whether any exponent of the CTA changed
+            // since the last clamp; if none did, every one is still in range
+            const int chg = __syncthreads_or(echg ? 1 : 0);
+            echg = false;
             // ---- keep within RES_SPAN of the line maximum
-            {
+            if (chg) {
                 int Em = RES_NONE;
                 for (int ww = w0; ww < wend; ++ww) Em = max(Em, sM[buf][ww]);
                 const int lo = Em - RES_SPAN;
@@ -419,6 +453,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     scale_chunk(f);
                     Xn = pmul(F2(f), Xn); Xd = pmul(F2(f), Xd);
                     e = lo;
+                    echg = true;
                 }
             }
             // ---- entry state: earlier warps of the line, then this warp's lanes
@@ -504,6 +539,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     scale_chunk(f);
                     An = pmul(F2(f), An); Ad = pmul(F2(f), Ad);   // next aggregate, same scale
                     e += sx;
+                    echg = true;
                 }
             }
             buf ^= 1;

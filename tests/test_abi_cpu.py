@@ -194,3 +194,20 @@ def test_bounds_checked_build(qs):
     assert qs.lib.qs_build_flags() == 0
     for n in names:
         assert hasattr(L, n), n
+
+
+def test_stale_library_is_refused(qs, tmp_path):
+    """The binding loads a library only if the hash of its sources, written
+    beside it by the build, matches the current sources: a library built from
+    other sources is refused at import, not run."""
+    import shutil
+    import subprocess
+    import sys
+    lib = os.path.join(ROOT, "paper_2607_24234_b300", "libqs.so")
+    assert open(lib + ".srchash").read().strip() == qs._source_hash()
+    stale = tmp_path / "libqs.so"
+    shutil.copy(lib, stale)
+    (tmp_path / "libqs.so.srchash").write_text("0" * 64 + "\n")
+    r = subprocess.run([sys.executable, "-c", "import paper_2607_24234_b300"], cwd=ROOT, capture_output=True,
+                       text=True, env=dict(os.environ, QS_LIBRARY=str(stale)))
+    assert r.returncode != 0 and "not built from the current sources" in r.stderr

@@ -57,3 +57,52 @@ def test_gaussian_beam_conserves_slice_charge_and_symmetry():
     assert np.max(np.abs(nb.sum(axis=(1, 2)) - q0)) <= 1e-7 * max(scale, np.max(np.abs(q0)))
     assert np.max(np.abs(nb - nb[:, :, ::-1])) <= 1e-12 * np.max(np.abs(nb))
     assert np.max(np.abs(G)) > 0
+
+
+def _nbi_exponent(sigma, mode, ny=256, dens=0.05, gam=10.0, xi0=150.0, dxi=0.05, dt=2.0, steps=50):
+    """Fitted growth exponent of the hosing (centroid) or self-modulation
+    (radius) moment of a slab beam (Gaussian in y, uniform in z: nz = 1) at
+    xi0, over the second half of the run, against tau^(2/3)."""
+    N = int(round((xi0 + 10.0) / dxi))
+    p = dict(species=[(-1.0, 1.0, dens)], gamma_b=gam, n_xi=N, dxi=dxi, dt=dt, ny=ny, nz=1, Ly=8.0, Lz=8.0,
+             sigma_r=sigma, transverse="gaussian")
+    nb0, _, _ = rs.profile(p)
+    Y, _ = rs.grid(p)
+    y = Y[:, 0]
+    if mode == "hosing":
+        nb, G = rs.seed(p, 0.0, 1e-3 * sigma)               # centroid offset
+        moment = y
+    else:
+        nb, G = rs.seed(p, 0.0, 0.0)
+        base = dens * np.exp(-(y * 1.001) ** 2 / (2 * sigma ** 2)) - nb0[:, 0]   # radius perturbation
+        nb[:, :, 0] = base[None, :]
+        moment = y * y
+    j0, w = int(xi0 / dxi), int(2 * np.pi / dxi)
+    taus, env = [], []
+    for k in range(steps):
+        rs.sweep(p, nb, G, k, 1)
+        D = (nb[:, :, 0] * moment[None, :]).sum(axis=1)
+        taus.append((k + 1) * dt)
+        env.append(np.max(np.abs(D[j0:j0 + w])))
+    taus, env = np.array(taus), np.array(env)
+    sel = taus >= 0.5 * taus[-1]
+    slope = np.polyfit(taus[sel] ** (2 / 3), np.log(env[sel]), 1)[0]
+    g_nbi = np.sqrt(3) / 2 ** (4 / 3) * (dens / gam) ** (1 / 3)     # Sec. IV.B, one species of |q| = m = 1
+    return slope / ((3 / 2 ** (2 / 3)) * g_nbi * xi0 ** (1 / 3))
+
+
+def test_narrow_beam_instabilities_follow_the_nbi_law():
+    """Sec. IV.B: for a narrow beam (k_p sigma_y << 1) the envelope obeys
+    (d_tau^2 d_xi - (8i / 3^(3/2)) Gamma_NBI^3) n = 0, whose growth exponent is
+    (3 / 2^(2/3)) Gamma_NBI tau^(2/3) xi^(1/3), Gamma_NBI = (sqrt3 / 2^(4/3))
+    (sum w^2)^(1/3), for both the centroid (hosing) and the radius (self-
+    modulation) moments, up to a geometrical factor that tends to 1 as
+    k_p sigma_y -> 0.  The finite-width oracle (a slab beam, Gaussian in y)
+    at xi = 150 >> Gamma tau (C = 12.8, growth ~e^18): the fitted exponent is
+    within 5 % of the law at k_p sigma_y = 0.2 for both modes, and closer to
+    it than at k_p sigma_y = 0.4."""
+    r_h2 = _nbi_exponent(0.2, "hosing")
+    r_h4 = _nbi_exponent(0.4, "hosing")
+    r_s2 = _nbi_exponent(0.2, "smi")
+    assert abs(r_h2 - 1) < 0.05 and abs(r_s2 - 1) < 0.05, (r_h2, r_s2)
+    assert abs(r_h2 - 1) < abs(r_h4 - 1), (r_h2, r_h4)

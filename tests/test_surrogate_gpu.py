@@ -232,3 +232,57 @@ def test_screen_answers_flagged_queries_with_the_solver(sg):
     assert bad0 == 0
     assert bad1 <= max(1, len(Xf) // 100)
     m.close()
+
+
+def test_fused_inference_matches_layer_path_and_fp64(sg, monkeypatch):
+    """The fused ensemble inference (one launch; every member's layers on
+    chip, outputs and ensemble statistics in the last epilogue) against the
+    layer-by-layer path and the FP64 forward of the CPU oracle on the same
+    BF16-rounded weights and inputs, on a ragged row count: mean within
+    rel. L2 1e-3 of the layer path and 1e-2 of FP64, variance within 2e-2
+    of the layer path, and the same fallback mask away from the threshold."""
+    import torch
+    qs, sur = sg
+    rng = np.random.default_rng(4)
+    n = 5003                                   # 39 full 128-row tiles and a ragged one
+    X = (rng.standard_normal((n, 7)) * np.array([1.0, 2.0, 50.0, 30.0, 500.0, 2.0, 1.5])
+         + np.array([-4.0, 6.0, 100.0, 40.0, 900.0, 3.0, 0.0])).astype(np.float32)
+    Y = np.stack([10 * rng.standard_normal(n) + 20, (rng.random(n) > 0.4)], axis=1).astype(np.float32)
+    Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    models = {}
+    for tag, env in (("fused", "0"), ("layers", "1")):
+        monkeypatch.setenv("QS_MLP_NO_FUSED", env)
+        m = sur.MLP(width=256, depth=3, ensemble=4, max_batch=2048, seed=9)
+        m.set_norm(Xt, Yt)
+        models[tag] = m
+    flats = []
+    for e in range(4):
+        flat = models["fused"].params(e)
+        for W, b in models["fused"].layers(flat):
+            b[:] = 0.2 * rng.standard_normal(b.shape)
+        flats.append(flat)
+        for m in models.values():
+            m.set_params(flat, e)
+    thr = 0.05
+    res = {tag: [t.cpu().numpy() for t in m.infer(Xt, thr)] for tag, m in models.items()}
+    torch.cuda.synchronize()
+    (mf, vf, kf), (ml, vl, kl) = res["fused"], res["layers"]
+    for o in range(2):
+        assert _rel(mf[:, o], ml[:, o]) <= 1e-3, o
+        assert _rel(vf[:, o], vl[:, o]) <= 2e-2, o
+    clear = np.abs(vl[:, 0] - thr) > 0.05 * thr
+    assert np.array_equal(kf[clear], kl[clear]) and kf.sum() > 0
+    # FP64 forward of every member (oracle/mlp.py) on the same BF16 weights and inputs
+    mean, inv_std, ymean, ystd = models["fused"].norm()
+    xs = np.zeros((n, 16))
+    xs[:, :7] = omlp.bf16((X - mean[:7].astype(np.float32)) * inv_std[:7].astype(np.float32))
+    outs = []
+    for e in range(4):
+        layers = [(omlp.bf16(W), b.astype(np.float64)) for W, b in models["fused"].layers(flats[e])]
+        _, _, out = omlp.loss_and_grads(layers, xs, Y.astype(np.float64), ymean, ystd)
+        outs.append(np.stack([out[:, 0] * ystd + ymean, out[:, 1]], axis=1))
+    ref = np.mean(outs, axis=0)
+    for o in range(2):
+        assert _rel(mf[:, o], ref[:, o]) <= 1e-2, o
+    for m in models.values():
+        m.close()
