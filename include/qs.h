@@ -222,7 +222,14 @@ enum { QS_VARIANT_REGISTERS = 0,  /* thread per line, register prefetch       */
                                    * is read once and written once per call);
                                    * xi is joined by a block scan of the cell
                                    * propagators.  Steps that record, and field
-                                   * passes, run the register kernel          */
+                                   * passes, run the register kernel.  Range:
+                                   * a line keeps 2^190 (e^131) below its
+                                   * largest value, smaller cells flush to 0
+                                   * (the streaming variants keep every 32-cell
+                                   * group at full FP32 precision); a front
+                                   * that grows far slower than the back of a
+                                   * long beam over thousands of steps can fall
+                                   * that far behind                          */
 typedef struct {
     int warps_per_cta;   /* REGISTERS: 1, 2, 4 or 8 (TMA: always 1);
                           * RESIDENT: 1, 2, 4, 8 or 16 (CTA size; a line

@@ -286,3 +286,27 @@ def test_fused_inference_matches_layer_path_and_fp64(sg, monkeypatch):
         assert _rel(mf[:, o], ref[:, o]) <= 1e-2, o
     for m in models.values():
         m.close()
+
+
+def test_screen_keeps_slow_growing_cells(sg):
+    """A dense, slow beam (n_b/n_p = 0.087, gamma = 10.4, L = 81.5) grows by
+    ~e^180 at its back over 1000 steps but only ~e^11 near its front: the
+    solver fallback answers queries at the front with the labels' values
+    (finite, equal to the labels drawn by qs_sur_points), not zeros."""
+    import torch
+    qs, sur = sg
+    p = synth.scaled(synth.BATCH_BASE, nkx=12, nky=12, species=[(-1.0, 1.0, 0.0870664478545601)],
+                     gamma_b=10.410552660460878, n_xi=3261, dxi=0.025, length=81.525)
+    Xq, Yq, _ = sur.generate([p], [1000], 4000, seed=2, noise_seed=1)
+    front = Xq[:, 3] < 10.0
+    assert int(front.sum()) > 100 and bool(torch.isfinite(Yq).all())
+    Xtr, Ytr, _ = sur.generate([p], [500, 1000], 4096, seed=1)
+    m = sur.SurModel(Xtr, Ytr, epochs=1, batch=2048, ensemble=2, seed=3)
+    m.set_threshold(-1.0)                       # every query goes to the solver
+    y, v, mask, ns = m.screen([p], Xq, noise_seed=1)
+    torch.cuda.synchronize()
+    assert ns == Xq.shape[0] and bool(torch.isfinite(y).all())
+    d = (y[:, 0] - Yq[:, 0]).abs()
+    assert float(d.max()) <= 1e-3, float(d.max())
+    assert float(Yq[front, 0].max()) < float(Yq[~front, 0].max()) - 50.0   # the dynamic range in play
+    m.close()
