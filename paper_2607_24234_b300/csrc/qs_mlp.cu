@@ -407,6 +407,13 @@ struct FusedArgs {
     float *mean, *var;
     unsigned char *mask;
     int *err;
+    // training forward (TRAIN): per hidden layer the pre-activation Z (fp32
+    // [n][256]), the activation H (bf16 [n][256]) and H^T (bf16 [256][n]),
+    // per member strides `as`; the raw outputs OUT (fp32 [n][2], stride os)
+    float *Z[3];
+    __nv_bfloat16 *H[3], *HT[3];
+    long long as, os;
+    float *OUT;
 };
 
 namespace fz {
@@ -445,7 +452,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&v)[32]) {
 }
 }  // namespace fz
 
-__global__ void __launch_bounds__(256, 1) k_mlp_infer_fused(const FusedArgs a) {
+template <bool TRAIN>
+__global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
     using namespace fz;
     extern __shared__ __align__(1024) unsigned char sf[];
     unsigned char *Wb = sf + OFF_WB, *Ab = sf + OFF_AB, *W0s = sf + OFF_W0, *A0 = sf + OFF_A0;
@@ -505,27 +513,49 @@ __global__ void __launch_bounds__(256, 1) k_mlp_infer_fused(const FusedArgs a) {
         if (!done) atomicOr(&s_bad, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
-    // accumulator -> bias + GELU -> bf16 activations in the A operand layout
-    auto epilogue_hidden = [&](const float *b) {
+    // accumulator -> bias + GELU -> bf16 activations in the A operand layout;
+    // training also stores Z, H and H^T of rows inside the batch
+    auto epilogue_hidden = [&](const float *b, int layer, long long r0, int e) {
+        const long long gr = r0 + row;
+        const bool keep = TRAIN && gr < a.n;
 #pragma unroll 1
         for (int c = 0; c < 4; ++c) {
             const int c0 = 128 * hc + 32 * c;
             float v[32];
             tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
 #pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += b[c0 + j];
+            if (keep) {
+                float *z = a.Z[layer] + e * a.as + gr * W + c0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4 *>(z + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            }
+#pragma unroll
             for (int j = 0; j < 32; j += 8) {
                 __nv_bfloat162 h2[4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    h2[t] = __floats2bfloat162_rn(gelu(v[j + 2 * t] + b[c0 + j + 2 * t]),
-                                                  gelu(v[j + 2 * t + 1] + b[c0 + j + 2 * t + 1]));
+                for (int t = 0; t < 4; ++t) h2[t] = __floats2bfloat162_rn(gelu(v[j + 2 * t]), gelu(v[j + 2 * t + 1]));
                 *reinterpret_cast<uint4 *>(Ab + (row / 8) * SBO_W + ((c0 + j) / 8) * LBO + (row % 8) * 16) =
                     *reinterpret_cast<const uint4 *>(h2);
+                if (keep) {
+                    *reinterpret_cast<uint4 *>(a.H[layer] + e * a.as + gr * W + c0 + j) = *reinterpret_cast<const uint4 *>(h2);
+                    __nv_bfloat16 *ht = a.HT[layer] + e * a.as + (long long)(c0 + j) * a.n + gr;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        ht[(long long)(2 * t) * a.n] = __low2bfloat16(h2[t]);
+                        ht[(long long)(2 * t + 1) * a.n] = __high2bfloat16(h2[t]);
+                    }
+                }
             }
         }
     };
     const long long ntiles = (a.n + 127) / 128;
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    // inference: one item per tile, members inside (the ensemble statistics);
+    // training: one item per (tile, member)
+    const long long nitems = TRAIN ? ntiles * a.E : ntiles;
+    for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        const long long tile = TRAIN ? item / a.E : item;
+        const int e_lo = TRAIN ? (int)(item % a.E) : 0, e_hi = TRAIN ? e_lo + 1 : a.E;
         const long long r0 = tile * 128;
         // standardised bf16 inputs of the tile (zero-padded to 16 columns and past n)
         if (tid < 128) {
@@ -540,7 +570,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_infer_fused(const FusedArgs a) {
             *reinterpret_cast<uint4 *>(A0 + (tid / 8) * SBO_I + 1 * LBO + (tid % 8) * 16) = *reinterpret_cast<const uint4 *>(x16 + 8);
         }
         float s0 = 0.f, q0 = 0.f, s1 = 0.f, q1 = 0.f;   // ensemble sums of the row (warps 0..3)
-        for (int e = 0; e < a.E && ok; ++e) {
+        for (int e = e_lo; e < e_hi && ok; ++e) {
             const __nv_bfloat16 *Pm = a.Pb + (long long)e * a.nparam;
             const float *Pf = a.P + (long long)e * a.nparam;
             stage<KIN>(W0s, Pm + a.w0, W, tid, 256);
@@ -552,26 +582,52 @@ __global__ void __launch_bounds__(256, 1) k_mlp_infer_fused(const FusedArgs a) {
             sync_for_mma();
             mma_layer(A0, W0s, 1, SBO_I);                       // layer 0: K = 16
             stage<W>(Wb, Pm + a.w1, W, tid, 256);               // W1 lands during the epilogue
-            epilogue_hidden(bias);
+            epilogue_hidden(bias, 0, r0, e);
             sync_for_mma();
             mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 1
             stage<W>(Wb, Pm + a.w2, W, tid, 256);               // W2 lands during the epilogue
-            epilogue_hidden(bias + W);
+            epilogue_hidden(bias + W, 1, r0, e);
             sync_for_mma();
             mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 2
             // output layer: GELU activations (rounded to bf16 as the operand of
             // the unfused path) dotted with W3 in FP32
             float o0 = 0.f, o1 = 0.f;
+            const long long gr = r0 + row;
+            const bool keep = TRAIN && gr < a.n;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int c0 = 128 * hc + 32 * c;
                 float v[32];
                 tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float h = __bfloat162float(__float2bfloat16(gelu(v[j] + bias[2 * W + c0 + j])));
-                    o0 = fmaf(h, w3[c0 + j], o0);
-                    o1 = fmaf(h, w3[W + c0 + j], o1);
+                for (int j = 0; j < 32; ++j) v[j] += bias[2 * W + c0 + j];
+                if (keep) {
+                    float *z = a.Z[2] + e * a.as + gr * W + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4 *>(z + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    __nv_bfloat162 h2[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) h2[t] = __floats2bfloat162_rn(gelu(v[j + 2 * t]), gelu(v[j + 2 * t + 1]));
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float h0 = __low2float(h2[t]), h1 = __high2float(h2[t]);
+                        o0 = fmaf(h0, w3[c0 + j + 2 * t], o0);
+                        o1 = fmaf(h0, w3[W + c0 + j + 2 * t], o1);
+                        o0 = fmaf(h1, w3[c0 + j + 2 * t + 1], o0);
+                        o1 = fmaf(h1, w3[W + c0 + j + 2 * t + 1], o1);
+                    }
+                    if (keep) {
+                        *reinterpret_cast<uint4 *>(a.H[2] + e * a.as + gr * W + c0 + j) = *reinterpret_cast<const uint4 *>(h2);
+                        __nv_bfloat16 *ht = a.HT[2] + e * a.as + (long long)(c0 + j) * a.n + gr;
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            ht[(long long)(2 * t) * a.n] = __low2bfloat16(h2[t]);
+                            ht[(long long)(2 * t + 1) * a.n] = __high2bfloat16(h2[t]);
+                        }
+                    }
                 }
             }
             if (hc == 1) { part[2 * row] = o0; part[2 * row + 1] = o1; }
@@ -579,13 +635,18 @@ __global__ void __launch_bounds__(256, 1) k_mlp_infer_fused(const FusedArgs a) {
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (hc == 0) {
-                const float y0 = (o0 + part[2 * row] + w3[2 * W]) * a.ystd + a.ymean;
+                const float r0u = o0 + part[2 * row] + w3[2 * W];    // raw outputs (standardised units)
                 const float y1 = o1 + part[2 * row + 1] + w3[2 * W + 1];
-                s0 += y0; q0 += y0 * y0; s1 += y1; q1 += y1 * y1;
+                if (TRAIN) {
+                    if (gr < a.n) { a.OUT[e * a.os + 2 * gr] = r0u; a.OUT[e * a.os + 2 * gr + 1] = y1; }
+                } else {
+                    const float y0 = r0u * a.ystd + a.ymean;
+                    s0 += y0; q0 += y0 * y0; s1 += y1; q1 += y1 * y1;
+                }
             }
             ok = s_bad == 0;
         }
-        if (hc == 0 && ok) {
+        if (!TRAIN && hc == 0 && ok) {
             const long long gr = r0 + row;
             if (gr < a.n) {
                 const float inv = 1.0f / a.E;
@@ -666,6 +727,40 @@ __global__ void k_colsum_tiles(const __nv_bfloat16 *g, int n, int cols, float *o
     }
     atomicAdd(out + 2 * c2, sx);
     atomicAdd(out + 2 * c2 + 1, sy);
+}
+
+// Weight gradient of a thin layer (the first, width x n_in, and the last,
+// 2 x width): C[o][i] += sum_b dz[b][o] act[b][i] over the batch, where one
+// of the two sides is narrow (R columns).  Thread w owns one column of the
+// wide side and keeps the R products with the narrow side in registers; a
+// block sums RB rows (coalesced loads of the wide row, broadcast loads of the
+// narrow one) and adds its partial sums to C with atomics.  NARROW_IN: the
+// narrow side is the layer input (C index w R + r), else the output (r W + w).
+template <int R, bool NARROW_IN>
+__global__ void __launch_bounds__(256) k_dw_thin(const __nv_bfloat16 *wide, int ldw, const __nv_bfloat16 *narrow, int ldn,
+                                                 int n, int W, int rb, float *C, long long s_wide, long long s_narrow,
+                                                 long long s_C) {
+    wide += blockIdx.y * s_wide;       // ensemble member
+    narrow += blockIdx.y * s_narrow;
+    C += blockIdx.y * s_C;
+    const int b0 = blockIdx.x * rb, b1 = min(n, b0 + rb);
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+        for (int b = b0; b < b1; ++b) {
+            const float x = __bfloat162float(wide[(long long)b * ldw + w]);
+            const __nv_bfloat16 *nr = narrow + (long long)b * ldn;
+#pragma unroll
+            for (int r = 0; r < R; r += 2) {
+                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(nr + r);
+                acc[r] = fmaf(x, __low2float(v), acc[r]);
+                acc[r + 1] = fmaf(x, __high2float(v), acc[r + 1]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) atomicAdd(C + (NARROW_IN ? (long long)w * R + r : (long long)r * W + w), acc[r]);
+    }
 }
 
 // dst[c][r] = src[r][c] for a bf16 [rows][cols] matrix, 32 x 32 tiles
@@ -887,6 +982,37 @@ void refresh_wt(qs_mlp *m) {
     }
 }
 
+// fused forward (k_mlp_fused): the common arguments
+mlp::FusedArgs fused_args(qs_mlp *m, const float *X, long long n) {
+    mlp::FusedArgs fa{};
+    fa.X = X; fa.n = n; fa.n_in = m->n_in; fa.stats = m->stats;
+    fa.Pb = m->Pb; fa.P = m->P; fa.nparam = m->nparam;
+    fa.w0 = m->woff[0]; fa.w1 = m->woff[1]; fa.w2 = m->woff[2]; fa.w3 = m->woff[3];
+    fa.b0 = m->boff[0]; fa.b1 = m->boff[1]; fa.b2 = m->boff[2]; fa.b3 = m->boff[3];
+    fa.E = m->E; fa.ymean = m->ymean; fa.ystd = m->ystd; fa.err = m->errw;
+    return fa;
+}
+
+bool fused_launch(qs_mlp *m, const mlp::FusedArgs &fa, bool train) {
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(mlp::k_mlp_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp::fz::SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(mlp::k_mlp_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp::fz::SMEM) != cudaSuccess)
+            return false;
+        attr = true;
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long items = (fa.n + 127) / 128 * (train ? fa.E : 1);
+    const unsigned grid = (unsigned)std::min<long long>(nsm, items);
+    if (train) mlp::k_mlp_fused<true><<<grid, 256, mlp::fz::SMEM, m->stream>>>(fa);
+    else mlp::k_mlp_fused<false><<<grid, 256, mlp::fz::SMEM, m->stream>>>(fa);
+    return cudaGetLastError() == cudaSuccess;
+}
+
 // forward of every member on n rows of X0 (already standardised); fills
 // OUT[e]; with want_ht the hidden activations are also written transposed
 // (training)
@@ -953,6 +1079,20 @@ void backward(qs_mlp *m, int n) {
             gt.zper = S;
             mlp::k_gemm_tc<256, 128><<<dim3((out + 127) / 128, in / 128, S * m->E), 128, (size_t)(128 + 128) * 256 * 2,
                                        m->stream>>>(gt, m->errw);
+        } else if ((in == 16 || in == 32) || out == 2) {
+            // a thin layer: one pass over the batch, the narrow side in registers
+            const int rb = 256;
+            const dim3 grid((unsigned)((n + rb - 1) / rb), m->E);
+            float *C = G + m->woff[l];
+            if (out == 2)
+                mlp::k_dw_thin<2, false><<<grid, 256, 0, m->stream>>>(act, lda_act, dz, out, n, in, rb, C, sact, sdz,
+                                                                       m->nparam);
+            else if (in == 16)
+                mlp::k_dw_thin<16, true><<<grid, 256, 0, m->stream>>>(dz, out, act, lda_act, n, out, rb, C, sdz, sact,
+                                                                       m->nparam);
+            else
+                mlp::k_dw_thin<32, true><<<grid, 256, 0, m->stream>>>(dz, out, act, lda_act, n, out, rb, C, sdz, sact,
+                                                                       m->nparam);
         } else {
             mlp::GemmArgs gw{};
             gw.A = dz; gw.sA = sdz; gw.lda = out;        // A(m=o, k=b) = dz[b*out + o]  (TA = 1)
@@ -1159,7 +1299,17 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     // every member in the same launches (member = the launch's z or y index)
-    forward(m, nb, true);
+    if (m->use_tc && m->fused_ok) {
+        // one fused launch: Z, H, H^T of every hidden layer and the outputs
+        mlp::FusedArgs fa = fused_args(m, X, nb);
+        for (int l = 0; l < 3; ++l) { fa.Z[l] = m->Z[l]; fa.H[l] = m->H[l]; fa.HT[l] = m->HT[l]; m->ht_valid[l] = 1; }
+        fa.as = m->astride;
+        fa.OUT = m->OUT;
+        fa.os = (long long)m->max_batch * m->n_out;
+        if (!fused_launch(m, fa, true)) return mfail(m, QS_ERR_CUDA, "fused forward launch failed");
+    } else {
+        forward(m, nb, true);
+    }
     mlp::k_loss<<<dim3((nb + 255) / 256, m->E), 256, 0, m->stream>>>(
         m->OUT, Y, nb, m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss, (long long)m->max_batch * 2);
     backward(m, nb);
@@ -1199,26 +1349,10 @@ qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float 
     if (m->use_tc && m->fused_ok) {
         // the surrogate's shape: one persistent launch over all rows, every
         // member's layers on chip, the ensemble statistics in the epilogue
-        static bool attr = false;
-        if (!attr) {
-            if (cudaFuncSetAttribute(mlp::k_mlp_infer_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)mlp::fz::SMEM) != cudaSuccess)
-                return mfail(m, QS_ERR_CUDA, "fused inference: shared-memory opt-in failed");
-            attr = true;
-        }
-        mlp::FusedArgs fa{};
-        fa.X = X; fa.n = n; fa.n_in = m->n_in; fa.stats = m->stats;
-        fa.Pb = m->Pb; fa.P = m->P; fa.nparam = m->nparam;
-        fa.w0 = m->woff[0]; fa.w1 = m->woff[1]; fa.w2 = m->woff[2]; fa.w3 = m->woff[3];
-        fa.b0 = m->boff[0]; fa.b1 = m->boff[1]; fa.b2 = m->boff[2]; fa.b3 = m->boff[3];
-        fa.E = m->E; fa.ymean = m->ymean; fa.ystd = m->ystd; fa.thr = var_threshold;
-        fa.mean = mean; fa.var = var; fa.mask = mask; fa.err = m->errw;
-        int dev = 0, nsm = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long tiles = (n + 127) / 128;
-        mlp::k_mlp_infer_fused<<<(unsigned)std::min<long long>(nsm, tiles), 256, mlp::fz::SMEM, m->stream>>>(fa);
-        return cudaGetLastError() == cudaSuccess ? QS_OK : mfail(m, QS_ERR_CUDA, "fused inference launch failed");
+        mlp::FusedArgs fa = fused_args(m, X, n);
+        fa.thr = var_threshold;
+        fa.mean = mean; fa.var = var; fa.mask = mask;
+        return fused_launch(m, fa, false) ? QS_OK : mfail(m, QS_ERR_CUDA, "fused inference launch failed");
     }
     for (int64_t r0 = 0; r0 < n; r0 += m->max_batch) {
         const int nb = (int)std::min<int64_t>(m->max_batch, n - r0);
