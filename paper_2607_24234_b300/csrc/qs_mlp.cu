@@ -38,8 +38,7 @@ __device__ __forceinline__ float ld_op(const __nv_bfloat16 *X, int ld, int r, in
 enum { EPI_STORE = 0,      // C fp32 = acc
        EPI_BIAS_GELU = 1,  // Z fp32 = acc + b; H bf16 = gelu(Z)
        EPI_BIAS = 2,       // C fp32 = acc + b
-       EPI_DGELU = 3,      // G bf16 = acc * gelu'(Z)
-       EPI_ATOMIC = 4 };   // C fp32 += acc (atomically; C zeroed by the caller)
+       EPI_DGELU = 3 };    // G bf16 = acc * gelu'(Z)
 
 struct GemmArgs {
     const __nv_bfloat16 *A, *B;
@@ -53,8 +52,6 @@ struct GemmArgs {
     int ldh;
     int epi;
     int accumulate;       // C += acc (EPI_STORE only)
-    int kchunks;          // tcgen05 path: K chunks per CTA (0 or 1: one); CTA z owns
-    int Ktot;             // K columns [z kchunks K, (z + 1) kchunks K) of Ktot (zero fill past it)
     __nv_bfloat16 *Ht;    // tcgen05 path, optional: the bf16 output H transposed, Ht[n][m] (row stride ldht)
     int ldht;
     // ensemble members in one launch: member = blockIdx.z / zper (zper CTAs
@@ -80,8 +77,51 @@ __device__ __forceinline__ GemmArgs for_member(const GemmArgs &g0, int &zz, int 
 }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU with erf from Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^(-x^2),
+// t = 1 / (1 + p x) for x >= 0, odd in x, |error| <= 1.5e-7 on the real line.
+// Used by the fused kernel, whose activations are rounded to bf16 next (the
+// GELU's relative error, <= 4e-6, is far below bf16's 2^-8).
+__device__ __forceinline__ float gelu_as(float z) {
+    const float x = z * 0.70710678118654752f, ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float e = 1.0f - poly * __expf(-ax * ax);
+    return 0.5f * z * (1.0f + copysignf(e, x));
+}
 __device__ __forceinline__ float dgelu(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// GELU and its derivative from one exponential (Abramowitz & Stegun 7.1.26
+// as in gelu_as): gelu'(z) = Phi(z) + z phi(z), phi(z) = e^(-z^2/2)/sqrt(2 pi)
+__device__ __forceinline__ void gelu_dgelu_as(float z, float &g, float &dg) {
+    const float x = z * 0.70710678118654752f, ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float ex = __expf(-ax * ax);
+    const float Phi = 0.5f * (1.0f + copysignf(1.0f - poly * ex, x));
+    g = z * Phi;
+    dg = fmaf(z * 0.39894228040143268f, ex, Phi);
+}
+
+// Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j):
+// a butterfly of 31 shuffles; on return v[0] of lane l holds the sum of
+// column l over the 32 rows (v is overwritten).
+__device__ __forceinline__ float colsum32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const float send = up ? v[j] : v[j + s];
+            const float keep = up ? v[j + s] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
 }
 
 __device__ __forceinline__ uint32_t pack2(const __nv_bfloat16 *p) {
@@ -230,6 +270,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }
 }  // namespace tc
 
+// 32 consecutive fp32 accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void fz_tmem_ld32(uint32_t ta, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+        "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 template <int K, int NT>
 __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
     int zz, zn;
@@ -249,65 +305,56 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    // K chunks of this CTA (one unless the caller splits a long K over z)
-    const int nk = g.kchunks > 1 ? g.kchunks : 1;
-    const long long kz = (long long)zz * nk * K;
-    const int ktot = g.kchunks > 0 ? g.Ktot : K;
-    uint32_t ok = 1;
-    uint32_t taddr = 0;
-    for (int kc = 0; kc < nk && ok; ++kc) {
-        const long long k0 = kz + (long long)kc * K;
-        // stage both operands with asynchronous 16-byte copies (all in flight
-        // at once; rows past M or N, and columns past Ktot, are zero-filled)
+    // stage both operands with asynchronous 16-byte copies (all in flight at
+    // once; rows past M or N are zero-filled)
 #pragma unroll 4
-        for (int i = tid; i < 128 * (K / 8); i += 128) {
-            const int r = i / (K / 8), c8 = i % (K / 8);
-            const bool in = m0 + r < g.M && k0 + c8 * 8 < ktot;
-            const __nv_bfloat16 *src = g.A + (in ? (long long)(m0 + r) * g.lda + k0 + c8 * 8 : 0);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
-                         "l"(src), "r"(in ? 16 : 0) : "memory");
-        }
-#pragma unroll 4
-        for (int i = tid; i < NT * (K / 8); i += 128) {
-            const int r = i / (K / 8), c8 = i % (K / 8);
-            const bool in = n0 + r < g.N && k0 + c8 * 8 < ktot;
-            const __nv_bfloat16 *src = g.B + (in ? (long long)(n0 + r) * g.ldb + k0 + c8 * 8 : 0);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
-                         "l"(src), "r"(in ? 16 : 0) : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        taddr = taddr_s;
-        if (tid == 0) {
-            constexpr uint32_t id = tc::idesc_bf16(128, NT);
-#pragma unroll
-            for (int kk = 0; kk < K / 16; ++kk) {
-                const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
-                const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
-                const uint32_t acc = (kk > 0 || kc > 0) ? 1u : 0u;
-                asm volatile(
-                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
-                    "l"(ad), "l"(bd), "r"(id), "r"(acc)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
-                         : "memory");
-        }
-        // the chunk's MMAs are done (its shared-memory operands may be reused)
-        uint32_t done = 0;
-        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
-            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                         : "=r"(done) : "r"(tc::su32(&bar)), "r"((uint32_t)(kc & 1)) : "memory");
-        if (!done && lane == 0) atomicOr(err, 2);
-        ok = __syncthreads_and(done);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int i = tid; i < 128 * (K / 8); i += 128) {
+        const int r = i / (K / 8), c8 = i % (K / 8);
+        const bool in = m0 + r < g.M;
+        const __nv_bfloat16 *src = g.A + (in ? (long long)(m0 + r) * g.lda + c8 * 8 : 0);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+                     "l"(src), "r"(in ? 16 : 0) : "memory");
     }
+#pragma unroll 4
+    for (int i = tid; i < NT * (K / 8); i += 128) {
+        const int r = i / (K / 8), c8 = i % (K / 8);
+        const bool in = n0 + r < g.N;
+        const __nv_bfloat16 *src = g.B + (in ? (long long)(n0 + r) * g.ldb + c8 * 8 : 0);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+                     "l"(src), "r"(in ? 16 : 0) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    if (tid == 0) {
+        constexpr uint32_t id = tc::idesc_bf16(128, NT);
+#pragma unroll
+        for (int kk = 0; kk < K / 16; ++kk) {
+            const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
+            const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
+            const uint32_t acc = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
+                     : "memory");
+    }
+    uint32_t done = 0;
+    for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(tc::su32(&bar)), "r"(0u) : "memory");
+    if (!done && lane == 0) atomicOr(err, 2);
+    const uint32_t ok = __syncthreads_and(done);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         const int m = m0 + warp * 32 + lane;
+        const bool inrow = m < g.M;
 #pragma unroll 1
         for (int c0 = 0; c0 < NT; c0 += 32) {
             uint32_t r[32];
@@ -322,26 +369,22 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             // the host routes only N % 128 == 0 and ldc, ldh % 8 == 0 here, so
-            // every 32-column chunk is in range and vector stores are aligned
-            if (m < g.M) {
-                const int nb = n0 + c0;
-                const long long oc = (long long)m * g.ldc + nb;
-                float v[32];
+            // every 32-column chunk is in range and vector accesses are aligned
+            const int nb = n0 + c0;
+            const long long oc = (long long)m * g.ldc + nb;
+            float v[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+            if (inrow) {
                 if (g.epi == EPI_DGELU) {
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
                         const float4 z = *reinterpret_cast<const float4 *>(g.Z + oc + j);
                         v[j] *= dgelu(z.x); v[j + 1] *= dgelu(z.y); v[j + 2] *= dgelu(z.z); v[j + 3] *= dgelu(z.w);
                     }
-                } else if (g.epi != EPI_STORE && g.epi != EPI_ATOMIC) {
+                } else if (g.epi != EPI_STORE) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] += g.bias[nb + j];
-                }
-                if (g.epi == EPI_ATOMIC) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) atomicAdd(g.C + oc + j, v[j]);
                 }
                 if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS || g.epi == EPI_STORE) {
 #pragma unroll
@@ -381,6 +424,158 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
 }
 
 // ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores: C[o][i] += sum_b A[o][b] B[i][b] over
+// this CTA's slice of the batch, A = dz^T and B = act^T, both K-major (the
+// batch contiguous, row stride ld).  One 128 x 128 output tile per CTA, the
+// accumulator in 128 TMEM columns.  The slice streams through a ring of NST
+// shared-memory stages of KC batch columns: the copies of chunk k + PD are
+// issued before the MMAs of chunk k, so copies and MMAs overlap.  A stage is
+// refilled only after the MMAs that read it have committed (bounded mbarrier
+// waits); with PD = NST - 2 that is chunk k - 2, issued two chunks earlier,
+// so the wait rarely stalls.  The partial tile is added to C with vector
+// atomics.
+// ---------------------------------------------------------------------------
+namespace wg {
+constexpr int KC = 64, NST = 6, PD = NST - 2;   // stages, prefetch distance
+constexpr uint32_t SBO = (KC / 8) * 128, LBO = 128;   // 8-row groups 1 KB apart
+constexpr size_t TILE = (size_t)128 * KC * 2;          // one operand tile, 16 KB
+constexpr size_t SMEM = (size_t)NST * 2 * TILE;        // 192 KB
+}  // namespace wg
+
+__global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int ld, int rowsA,
+                                                     int rowsB, int n, int cpc, float *C, int ldc, long long sA,
+                                                     long long sB, long long sC, int zper, int *err) {
+    using namespace wg;
+    extern __shared__ __align__(1024) unsigned char sw[];
+    __shared__ __align__(8) uint64_t bars[NST];
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mem = blockIdx.z / zper, sl = blockIdx.z - mem * zper;
+    A += mem * sA;
+    B += mem * sB;
+    C += mem * sC;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&taddr_s)), "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bars[i])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    const int nkt = (n + KC - 1) / KC;
+    const int kb = sl * cpc, nk = max(0, min(nkt, kb + cpc) - kb);
+    // chunk kc of the slice -> stage kc % NST.  Thread t copies the 16-byte
+    // column t % 8 of rows t / 8 + 16 it of both operands, so its source and
+    // shared-memory addresses are fixed up to the chunk offset.  Batch columns
+    // past n read as zero; operand rows past rowsA / rowsB are not loaded
+    // (they only reach accumulator rows / columns that are never stored).
+    const int ra = min(128, rowsA - m0), rbr = min(128, rowsB - n0);
+    const int c8 = tid & 7, rr = tid >> 3;
+    const __nv_bfloat16 *pa = A + (long long)(m0 + min(rr, ra - 1)) * ld + c8 * 8;
+    const __nv_bfloat16 *pb = B + (long long)(n0 + min(rr, rbr - 1)) * ld + c8 * 8;
+    const long long step16 = 16LL * ld;
+    const uint32_t sbase = tc::su32(sw) + (rr / 8) * SBO + c8 * LBO + (rr % 8) * 16;
+    auto load = [&](int kc) {
+        const uint32_t st = sbase + (uint32_t)(kc % NST) * (uint32_t)(2 * TILE);
+        const long long k0 = (long long)(kb + kc) * KC;
+        const bool in = k0 + c8 * 8 < n;
+        const long long off = in ? k0 : 0;
+        const uint32_t sz = in ? 16u : 0u;
+#pragma unroll
+        for (int it = 0; it < 8; ++it)
+            if (rr + 16 * it < ra)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + it * 2 * SBO), "l"(pa + it * step16 + off),
+                             "r"(sz) : "memory");
+#pragma unroll
+        for (int it = 0; it < 8; ++it)
+            if (rr + 16 * it < rbr)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + (uint32_t)TILE + it * 2 * SBO),
+                             "l"(pb + it * step16 + off), "r"(sz) : "memory");
+    };
+    auto wait_bar = [&](int kc) -> uint32_t {
+        uint32_t done = 0;
+        const uint32_t par = (uint32_t)((kc / NST) & 1);
+        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(tc::su32(&bars[kc % NST])), "r"(par) : "memory");
+        return done;
+    };
+#pragma unroll 1
+    for (int kc = 0; kc < PD; ++kc) {
+        if (kc < nk) load(kc);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int kc = 0; kc < nk; ++kc) {
+        const int pre = kc + PD;
+        uint32_t done = 1;
+        if (pre < nk) {
+            // the stage of chunk pre last held chunk pre - NST = kc - 2: its
+            // MMAs must be done
+            if (pre >= NST) done = wait_bar(pre - NST);
+            if (done) load(pre);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(PD) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        ok = __syncthreads_and(done) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+        if (tid == 0) {
+            constexpr uint32_t id = tc::idesc_bf16(128, 128);
+            const unsigned char *st = sw + (size_t)(kc % NST) * 2 * TILE;
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+                const uint64_t ad = tc::sdesc(tc::su32(st) + kk * 2 * LBO, LBO, SBO);
+                const uint64_t bd = tc::sdesc(tc::su32(st + TILE) + kk * 2 * LBO, LBO, SBO);
+                const uint32_t acc = (kk > 0 || kc > 0) ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bars[kc % NST]))
+                         : "memory");
+        }
+    }
+    if (ok && nk > 0) {
+        ok = __syncthreads_and(wait_bar(nk - 1)) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!ok && tid == 0) atomicOr(err, 2);
+    if (ok && nk > 0) {
+        const int o = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            float v[32];
+            fz_tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + c0, v);
+            if (o < rowsA && n0 + c0 < rowsB) {
+                float *dst = C + (long long)o * ldc + n0 + c0;
+                const int nc = min(32, rowsB - n0 - c0);   // rowsB % 4 == 0
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)
+                    if (j < nc)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(128));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Fused ensemble inference for the 16 -> 256 -> 256 -> 256 -> 2 network (the
 // surrogate's shape).  A persistent CTA of 8 warps takes 128-row tiles; for
 // every member it runs the three hidden layers on tcgen05 (M = 128, N = 256,
@@ -407,13 +602,18 @@ struct FusedArgs {
     float *mean, *var;
     unsigned char *mask;
     int *err;
-    // training forward (TRAIN): per hidden layer the pre-activation Z (fp32
-    // [n][256]), the activation H (bf16 [n][256]) and H^T (bf16 [256][n]),
-    // per member strides `as`; the raw outputs OUT (fp32 [n][2], stride os)
-    float *Z[3];
-    __nv_bfloat16 *H[3], *HT[3];
-    long long as, os;
-    float *OUT;
+    // training (TRAIN): per (tile, member) item the forward stores what the
+    // backward GEMMs read: H^T of the first two hidden layers (bf16 [256][n])
+    // and D = gelu'(Z) of the same layers (bf16 [n][256]), member stride
+    // `as`.  The output layer's backward runs in the last epilogue: the loss
+    // (summed into *loss), dL/dz of the last hidden layer (DZ bf16 [n][256]
+    // and its transpose DZT [256][n]), and the gradients of W3, b3 and b2,
+    // added to G (fp32, member stride nparam, zeroed by the caller).
+    __nv_bfloat16 *HT[2], *D[2], *DZ, *DZT;
+    long long as;
+    const float *Y;                  // [n][2] targets (regression, class)
+    float yinv;                      // 1 / ystd
+    float *loss, *G;
 };
 
 namespace fz {
@@ -421,7 +621,9 @@ constexpr int W = 256, KIN = 16;
 constexpr uint32_t SBO_W = (W / 8) * 128, SBO_I = (KIN / 8) * 128, LBO = 128;
 constexpr size_t OFF_WB = 0, OFF_AB = OFF_WB + (size_t)W * W * 2, OFF_W0 = OFF_AB + (size_t)128 * W * 2,
                  OFF_A0 = OFF_W0 + (size_t)W * KIN * 2, OFF_BIAS = OFF_A0 + (size_t)128 * KIN * 2,
-                 OFF_W3 = OFF_BIAS + 3 * W * 4, OFF_PART = OFF_W3 + 2 * W * 4 + 16, SMEM = OFF_PART + 128 * 2 * 4;
+                 OFF_W3 = OFF_BIAS + 3 * W * 4, OFF_PART = OFF_W3 + 2 * W * 4 + 16, OFF_RED = OFF_PART + 128 * 2 * 4,
+                 SMEM = OFF_RED + 3 * W * 4;
+static_assert(SMEM <= 227 * 1024, "fused kernel shared memory");
 
 // 16-byte asynchronous copies of a [rows][K] bf16 row-major matrix into the
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix)
@@ -436,20 +638,6 @@ __device__ __forceinline__ void stage(unsigned char *dst, const __nv_bfloat16 *s
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
-        "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(ta));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
 }  // namespace fz
 
 template <bool TRAIN>
@@ -459,6 +647,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
     unsigned char *Wb = sf + OFF_WB, *Ab = sf + OFF_AB, *W0s = sf + OFF_W0, *A0 = sf + OFF_A0;
     float *bias = reinterpret_cast<float *>(sf + OFF_BIAS), *w3 = reinterpret_cast<float *>(sf + OFF_W3);
     float *part = reinterpret_cast<float *>(sf + OFF_PART);
+    float *red = reinterpret_cast<float *>(sf + OFF_RED);   // training: per-item partial gradients
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t taddr_s;
     __shared__ int s_bad;
@@ -474,6 +663,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_bad = 0;
     }
+    if (TRAIN)
+        for (int i = tid; i < 3 * W; i += 256) red[i] = 0.0f;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -514,7 +705,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
     // accumulator -> bias + GELU -> bf16 activations in the A operand layout;
-    // training also stores Z, H and H^T of rows inside the batch
+    // training also stores H^T and D = gelu'(Z) of rows inside the batch
     auto epilogue_hidden = [&](const float *b, int layer, long long r0, int e) {
         const long long gr = r0 + row;
         const bool keep = TRAIN && gr < a.n;
@@ -522,23 +713,28 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
         for (int c = 0; c < 4; ++c) {
             const int c0 = 128 * hc + 32 * c;
             float v[32];
-            tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
+            fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j) v[j] += b[c0 + j];
-            if (keep) {
-                float *z = a.Z[layer] + e * a.as + gr * W + c0;
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4 *>(z + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            }
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
-                __nv_bfloat162 h2[4];
+                __nv_bfloat162 h2[4], d2[4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) h2[t] = __floats2bfloat162_rn(gelu(v[j + 2 * t]), gelu(v[j + 2 * t + 1]));
+                for (int t = 0; t < 4; ++t) {
+                    if (TRAIN) {
+                        float g0, g1, dg0, dg1;
+                        gelu_dgelu_as(v[j + 2 * t], g0, dg0);
+                        gelu_dgelu_as(v[j + 2 * t + 1], g1, dg1);
+                        h2[t] = __floats2bfloat162_rn(g0, g1);
+                        d2[t] = __floats2bfloat162_rn(dg0, dg1);
+                    } else {
+                        h2[t] = __floats2bfloat162_rn(gelu_as(v[j + 2 * t]), gelu_as(v[j + 2 * t + 1]));
+                    }
+                }
                 *reinterpret_cast<uint4 *>(Ab + (row / 8) * SBO_W + ((c0 + j) / 8) * LBO + (row % 8) * 16) =
                     *reinterpret_cast<const uint4 *>(h2);
                 if (keep) {
-                    *reinterpret_cast<uint4 *>(a.H[layer] + e * a.as + gr * W + c0 + j) = *reinterpret_cast<const uint4 *>(h2);
+                    *reinterpret_cast<uint4 *>(a.D[layer] + e * a.as + gr * W + c0 + j) = *reinterpret_cast<const uint4 *>(d2);
                     __nv_bfloat16 *ht = a.HT[layer] + e * a.as + (long long)(c0 + j) * a.n + gr;
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
@@ -593,41 +789,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
             // the unfused path) dotted with W3 in FP32
             float o0 = 0.f, o1 = 0.f;
             const long long gr = r0 + row;
-            const bool keep = TRAIN && gr < a.n;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 const int c0 = 128 * hc + 32 * c;
                 float v[32];
-                tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
+                fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] += bias[2 * W + c0 + j];
-                if (keep) {
-                    float *z = a.Z[2] + e * a.as + gr * W + c0;
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4 *>(z + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                }
-#pragma unroll
-                for (int j = 0; j < 32; j += 8) {
-                    __nv_bfloat162 h2[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) h2[t] = __floats2bfloat162_rn(gelu(v[j + 2 * t]), gelu(v[j + 2 * t + 1]));
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const float h0 = __low2float(h2[t]), h1 = __high2float(h2[t]);
-                        o0 = fmaf(h0, w3[c0 + j + 2 * t], o0);
-                        o1 = fmaf(h0, w3[W + c0 + j + 2 * t], o1);
-                        o0 = fmaf(h1, w3[c0 + j + 2 * t + 1], o0);
-                        o1 = fmaf(h1, w3[W + c0 + j + 2 * t + 1], o1);
-                    }
-                    if (keep) {
-                        *reinterpret_cast<uint4 *>(a.H[2] + e * a.as + gr * W + c0 + j) = *reinterpret_cast<const uint4 *>(h2);
-                        __nv_bfloat16 *ht = a.HT[2] + e * a.as + (long long)(c0 + j) * a.n + gr;
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            ht[(long long)(2 * t) * a.n] = __low2bfloat16(h2[t]);
-                            ht[(long long)(2 * t + 1) * a.n] = __high2bfloat16(h2[t]);
-                        }
-                    }
+                for (int j = 0; j < 32; ++j) {
+                    const float h = __bfloat162float(__float2bfloat16(gelu_as(v[j] + bias[2 * W + c0 + j])));
+                    o0 = fmaf(h, w3[c0 + j], o0);
+                    o1 = fmaf(h, w3[W + c0 + j], o1);
                 }
             }
             if (hc == 1) { part[2 * row] = o0; part[2 * row + 1] = o1; }
@@ -638,10 +809,87 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
                 const float r0u = o0 + part[2 * row] + w3[2 * W];    // raw outputs (standardised units)
                 const float y1 = o1 + part[2 * row + 1] + w3[2 * W + 1];
                 if (TRAIN) {
-                    if (gr < a.n) { a.OUT[e * a.os + 2 * gr] = r0u; a.OUT[e * a.os + 2 * gr + 1] = y1; }
+                    // loss and its gradient for the row: squared error of the
+                    // standardised regression output plus BCE-with-logits of
+                    // the class output, both averaged over the batch
+                    float l = 0.f, g0 = 0.f, g1 = 0.f;
+                    if (gr < a.n) {
+                        const float t = (a.Y[2 * gr] - a.ymean) * a.yinv, cl = a.Y[2 * gr + 1];
+                        const float d0 = r0u - t;
+                        const float sig = 1.0f / (1.0f + expf(-y1));
+                        l = d0 * d0 + fmaxf(y1, 0.0f) - y1 * cl + log1pf(expf(-fabsf(y1)));
+                        g0 = 2.0f * d0 / (float)a.n;
+                        g1 = (sig - cl) / (float)a.n;
+                    }
+                    part[2 * row] = g0;
+                    part[2 * row + 1] = g1;
+                    float ls = l, gs0 = g0, gs1 = g1;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        ls += __shfl_xor_sync(0xffffffffu, ls, o);
+                        gs0 += __shfl_xor_sync(0xffffffffu, gs0, o);
+                        gs1 += __shfl_xor_sync(0xffffffffu, gs1, o);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(a.loss, ls / (float)a.n);
+                        float *Gm = a.G + (long long)e * a.nparam;
+                        atomicAdd(Gm + a.b3, gs0);
+                        atomicAdd(Gm + a.b3 + 1, gs1);
+                    }
                 } else {
                     const float y0 = r0u * a.ystd + a.ymean;
                     s0 += y0; q0 += y0 * y0; s1 += y1; q1 += y1 * y1;
+                }
+            }
+            if (TRAIN) {
+                __syncthreads();
+                // backward through the output layer from the layer-2
+                // accumulator still in TMEM: dW3 += g^T H2, dz2 = (g W3) * gelu'(Z2),
+                // b2's gradient += column sums of dz2
+                const float g0 = part[2 * row], g1 = part[2 * row + 1];
+                const bool keep = gr < a.n;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    const int c0 = 128 * hc + 32 * c;
+                    float hv[32], dz[32], t[32];
+                    fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, hv);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float gl, dg;
+                        gelu_dgelu_as(hv[j] + bias[2 * W + c0 + j], gl, dg);
+                        hv[j] = __bfloat162float(__float2bfloat16(gl));
+                        dz[j] = fmaf(g0, w3[c0 + j], g1 * w3[W + c0 + j]) * dg;
+                    }
+                    if (keep) {
+                        __nv_bfloat16 *dzr = a.DZ + e * a.as + gr * W + c0;
+                        __nv_bfloat16 *dzt = a.DZT + e * a.as + (long long)c0 * a.n + gr;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 8) {
+                            __nv_bfloat162 q2[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) q2[u] = __floats2bfloat162_rn(dz[j + 2 * u], dz[j + 2 * u + 1]);
+                            *reinterpret_cast<uint4 *>(dzr + j) = *reinterpret_cast<const uint4 *>(q2);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                dzt[(long long)(j + 2 * u) * a.n] = __low2bfloat16(q2[u]);
+                                dzt[(long long)(j + 2 * u + 1) * a.n] = __high2bfloat16(q2[u]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) t[j] = g0 * hv[j];
+                    atomicAdd(&red[c0 + lane], colsum32(t, lane));
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) t[j] = g1 * hv[j];
+                    atomicAdd(&red[W + c0 + lane], colsum32(t, lane));
+                    atomicAdd(&red[2 * W + c0 + lane], colsum32(dz, lane));
+                }
+                __syncthreads();
+                float *Gm = a.G + (long long)e * a.nparam;
+                for (int i = tid; i < 3 * W; i += 256) {
+                    const float v = red[i];
+                    red[i] = 0.0f;
+                    atomicAdd(Gm + (i < 2 * W ? a.w3 + i : a.b2 + (i - 2 * W)), v);
                 }
             }
             ok = s_bad == 0;
@@ -667,6 +915,176 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Input gradient of a 256 x 256 hidden layer, fused with the GELU derivative
+// and the bias gradient of the layer below:
+//   dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * D[b][i],   D = gelu'(Z_prev),
+//   bgrad[i] += sum_b dz_prev[b][i].
+// Persistent CTAs of 8 warps take (member, 128-row tile) items, member-major,
+// so that a member's W^T (the K-major B operand, 128 KB) stays in shared
+// memory across its tiles.  Per item: one thread issues the 16 tcgen05.mma
+// (M = 128, N = 256, K = 256) into 256 TMEM columns; once they commit, the
+// next item's dz tile is copied in (cp.async) while the 8 warps run the
+// epilogue: tcgen05.ld, times D, bf16 dz_prev stored row-major (the next
+// input gradient's A operand) and transposed (the next weight gradient's A
+// operand), and column sums reduced over each warp's rows by shuffles.
+// ---------------------------------------------------------------------------
+struct DxArgs {
+    const __nv_bfloat16 *dz;   // [n][256] per member (stride sa)
+    const __nv_bfloat16 *WT;   // [256][256] W^T per member (stride sw)
+    const __nv_bfloat16 *D;    // [n][256] gelu'(Z) of the layer below (stride sa)
+    __nv_bfloat16 *out, *outT; // dz_prev [n][256] and its transpose [256][n] (stride sa)
+    float *bgrad;              // [256] per member (stride sw)
+    long long n, sa, sw;
+    int E;
+    int *err;
+};
+
+namespace dxk {
+constexpr int W = 256;
+constexpr size_t OFF_B = 0, OFF_A = OFF_B + (size_t)W * W * 2, OFF_RED = OFF_A + (size_t)128 * W * 2,
+                 SMEM = OFF_RED + W * 4;
+static_assert(SMEM <= 227 * 1024, "input-gradient kernel shared memory");
+}  // namespace dxk
+
+__global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
+    using namespace dxk;
+    constexpr uint32_t SBO = (W / 8) * 128, LBO = 128;
+    extern __shared__ __align__(1024) unsigned char sx[];
+    unsigned char *Bs = sx + OFF_B, *As = sx + OFF_A;
+    float *red = reinterpret_cast<float *>(sx + OFF_RED);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t taddr_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hc = warp >> 2;
+    const int row = 32 * q + lane;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&taddr_s)), "r"(W));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    for (int i = tid; i < W; i += 256) red[i] = 0.0f;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    const long long ntiles = (a.n + 127) / 128, nitems = ntiles * a.E;
+    // [rows][256] bf16 row-major -> K-major core-matrix layout; rows past
+    // `valid` are zero-filled
+    auto stage = [&](unsigned char *dst, const __nv_bfloat16 *src, int rows, long long valid) {
+        for (int i = tid; i < rows * (W / 8); i += 256) {
+            const int r = i / (W / 8), c8 = i % (W / 8);
+            const bool in = r < valid;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+                         "l"(src + (in ? (long long)r * W + c8 * 8 : 0)), "r"(in ? 16 : 0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto issue = [&](long long item, int cur) -> int {   // copies of an item; returns its member
+        const int e = (int)(item / ntiles);
+        const long long r0 = (item % ntiles) * 128;
+        if (e != cur) stage(Bs, a.WT + e * a.sw, W, W);
+        stage(As, a.dz + e * a.sa + r0 * W, 128, a.n - r0);
+        return e;
+    };
+    uint32_t phase = 0;
+    bool ok = true;
+    int cur = -1;
+    if ((long long)blockIdx.x < nitems) cur = issue(blockIdx.x, cur);
+    for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        const int e = (int)(item / ntiles);
+        const long long r0 = (item % ntiles) * 128;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            constexpr uint32_t id = tc::idesc_bf16(128, W);
+#pragma unroll
+            for (int kk = 0; kk < W / 16; ++kk) {
+                const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
+                const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
+                const uint32_t acc = kk > 0 ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bar))
+                         : "memory");
+        }
+        // this thread's 128 values of D (row gr, its column half), loaded
+        // while the MMAs run
+        const long long gr = r0 + row;
+        const bool keep = gr < a.n;
+        uint4 dv[16];
+        {
+            const uint4 *d = reinterpret_cast<const uint4 *>(a.D + e * a.sa + (keep ? gr : r0) * W + 128 * hc);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) dv[k] = d[k];
+        }
+        uint32_t done = 0;
+        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(tc::su32(&bar)), "r"(phase & 1u) : "memory");
+        ++phase;
+        ok = __syncthreads_and(done) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+        // the operands are free: the next item's copies run under the epilogue
+        if (item + gridDim.x < nitems) cur = issue(item + gridDim.x, cur);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int c0 = 128 * hc + 32 * c;
+            float v[32];
+            fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
+            if (keep) {
+                __nv_bfloat16 *o = a.out + e * a.sa + gr * W + c0;
+                __nv_bfloat16 *ot = a.outT + e * a.sa + (long long)c0 * a.n + gr;
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    const __nv_bfloat162 *d2 = reinterpret_cast<const __nv_bfloat162 *>(&dv[4 * c + j / 8]);
+                    __nv_bfloat162 q2[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        v[j + 2 * t] *= __low2float(d2[t]);
+                        v[j + 2 * t + 1] *= __high2float(d2[t]);
+                        q2[t] = __floats2bfloat162_rn(v[j + 2 * t], v[j + 2 * t + 1]);
+                    }
+                    *reinterpret_cast<uint4 *>(o + j) = *reinterpret_cast<const uint4 *>(q2);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        ot[(long long)(j + 2 * t) * a.n] = __low2bfloat16(q2[t]);
+                        ot[(long long)(j + 2 * t + 1) * a.n] = __high2bfloat16(q2[t]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+            }
+            atomicAdd(&red[c0 + lane], colsum32(v, lane));
+        }
+        __syncthreads();
+        for (int i = tid; i < W; i += 256) {
+            const float v = red[i];
+            red[i] = 0.0f;
+            atomicAdd(a.bgrad + e * a.sw + i, v);
+        }
+    }
+    if (!ok && tid == 0) atomicOr(a.err, 2);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(W));
+    }
+}
+
 // W [out][in] fp32 -> W^T [in][out] bf16 (K-major operand for dX = dz W)
 __global__ void k_transpose_bf16(const float *W, int out, int in, __nv_bfloat16 *WT, long long s_member) {
     W += blockIdx.y * s_member;  // ensemble member
@@ -677,14 +1095,16 @@ __global__ void k_transpose_bf16(const float *W, int out, int in, __nv_bfloat16 
     WT[(long long)c * out + o] = __float2bfloat16(W[i]);
 }
 
-// x (fp32, [n][n_in]) -> standardised bf16 [n][kin_pad] (zero padded)
+// x (fp32, [n][n_in]) -> standardised bf16 [n][kin_pad] (zero padded) and,
+// if out_t is set, its transpose [kin_pad][n] (the weight gradient's operand)
 __global__ void k_standardise(const float *x, int n, int n_in, int kpad, const float *mean,
-                              const float *inv_std, __nv_bfloat16 *out) {
+                              const float *inv_std, __nv_bfloat16 *out, __nv_bfloat16 *out_t) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)n * kpad) return;
     const int r = (int)(i / kpad), k = (int)(i % kpad);
     const float v = k < n_in ? (x[(long long)r * n_in + k] - mean[k]) * inv_std[k] : 0.0f;
     out[i] = __float2bfloat16(v);
+    if (out_t) out_t[(long long)k * n + r] = __float2bfloat16(v);
 }
 
 // loss and output gradient; out [n][2] = (regression, logit), y [n][2]
@@ -731,35 +1151,67 @@ __global__ void k_colsum_tiles(const __nv_bfloat16 *g, int n, int cols, float *o
 
 // Weight gradient of a thin layer (the first, width x n_in, and the last,
 // 2 x width): C[o][i] += sum_b dz[b][o] act[b][i] over the batch, where one
-// of the two sides is narrow (R columns).  Thread w owns one column of the
-// wide side and keeps the R products with the narrow side in registers; a
-// block sums RB rows (coalesced loads of the wide row, broadcast loads of the
-// narrow one) and adds its partial sums to C with atomics.  NARROW_IN: the
-// narrow side is the layer input (C index w R + r), else the output (r W + w).
+// of the two sides is narrow (R columns).  Thread t owns wide columns 2t and
+// 2t + 1 (coalesced bf16x2 loads) and keeps their 2R products with the
+// narrow side in registers; a block sums rb rows, the loads of U rows in
+// flight at once, and adds its partial sums to C with vector atomics.
+// NARROW_IN: the narrow side is the layer input (C index w R + r), else the
+// output (r W + w).  The narrow rows are 16-byte aligned (R % 8 == 0) or R = 2.
 template <int R, bool NARROW_IN>
-__global__ void __launch_bounds__(256) k_dw_thin(const __nv_bfloat16 *wide, int ldw, const __nv_bfloat16 *narrow, int ldn,
+__global__ void __launch_bounds__(128) k_dw_thin(const __nv_bfloat16 *wide, int ldw, const __nv_bfloat16 *narrow, int ldn,
                                                  int n, int W, int rb, float *C, long long s_wide, long long s_narrow,
                                                  long long s_C) {
-    wide += blockIdx.y * s_wide;       // ensemble member
+    static_assert(R == 2 || R % 8 == 0, "narrow side: 2 or a multiple of 8 columns");
+    constexpr int U = R >= 32 ? 4 : 8;
+    constexpr int NV = R >= 8 ? R / 8 : 1;   // 16-byte vectors of a narrow row
+    wide += blockIdx.y * s_wide;             // ensemble member
     narrow += blockIdx.y * s_narrow;
     C += blockIdx.y * s_C;
     const int b0 = blockIdx.x * rb, b1 = min(n, b0 + rb);
-    for (int w = threadIdx.x; w < W; w += blockDim.x) {
-        float acc[R];
+    for (int w2 = threadIdx.x; 2 * w2 < W; w2 += blockDim.x) {
+        float a0[R], a1[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = 0.0f;
-        for (int b = b0; b < b1; ++b) {
-            const float x = __bfloat162float(wide[(long long)b * ldw + w]);
-            const __nv_bfloat16 *nr = narrow + (long long)b * ldn;
+        for (int r = 0; r < R; ++r) { a0[r] = 0.0f; a1[r] = 0.0f; }
+        for (int b = b0; b < b1; b += U) {
+            __nv_bfloat162 x[U];
+            uint4 nv[U][NV];
 #pragma unroll
-            for (int r = 0; r < R; r += 2) {
-                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(nr + r);
-                acc[r] = fmaf(x, __low2float(v), acc[r]);
-                acc[r + 1] = fmaf(x, __high2float(v), acc[r + 1]);
+            for (int u = 0; u < U; ++u) {
+                const bool in = b + u < b1;
+                const long long row = in ? b + u : b0;
+                x[u] = *reinterpret_cast<const __nv_bfloat162 *>(wide + row * ldw + 2 * w2);
+                if (!in) x[u] = __floats2bfloat162_rn(0.0f, 0.0f);
+                if (R >= 8) {
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) nv[u][k] = reinterpret_cast<const uint4 *>(narrow + row * ldn)[k];
+                } else {
+                    nv[u][0].x = *reinterpret_cast<const uint32_t *>(narrow + row * ldn);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float x0 = __low2float(x[u]), x1 = __high2float(x[u]);
+                const __nv_bfloat162 *q = reinterpret_cast<const __nv_bfloat162 *>(&nv[u][0]);
+#pragma unroll
+                for (int r = 0; r < R; r += 2) {
+                    const float y0 = __low2float(q[r / 2]), y1 = __high2float(q[r / 2]);
+                    a0[r] = fmaf(x0, y0, a0[r]); a0[r + 1] = fmaf(x0, y1, a0[r + 1]);
+                    a1[r] = fmaf(x1, y0, a1[r]); a1[r + 1] = fmaf(x1, y1, a1[r + 1]);
+                }
             }
         }
+        if (NARROW_IN) {
+            float *c0 = C + (long long)(2 * w2) * R, *c1 = c0 + R;
 #pragma unroll
-        for (int r = 0; r < R; ++r) atomicAdd(C + (NARROW_IN ? (long long)w * R + r : (long long)r * W + w), acc[r]);
+            for (int r = 0; r < R; r += 4) {
+                atomicAdd(reinterpret_cast<float4 *>(c0 + r), make_float4(a0[r], a0[r + 1], a0[r + 2], a0[r + 3]));
+                atomicAdd(reinterpret_cast<float4 *>(c1 + r), make_float4(a1[r], a1[r + 1], a1[r + 2], a1[r + 3]));
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                atomicAdd(reinterpret_cast<float2 *>(C + (long long)r * W + 2 * w2), make_float2(a0[r], a1[r]));
+        }
     }
 }
 
@@ -893,6 +1345,7 @@ struct qs_mlp {
     __nv_bfloat16 *Pb = nullptr;         // [E][nparam]
     // activations for max_batch
     __nv_bfloat16 *X0 = nullptr;         // [B][kin]
+    __nv_bfloat16 *X0T = nullptr;        // [kin][B] (training: operand of the first layer's weight gradient)
     std::vector<float *> Z;              // per hidden layer [B][width]
     std::vector<__nv_bfloat16 *> H;      // per hidden layer [B][width]
     float *OUT = nullptr;                // [E][B][n_out]
@@ -907,6 +1360,7 @@ struct qs_mlp {
     __nv_bfloat16 *TDZ = nullptr, *TACT = nullptr;   // [width][B]: dZ^T and act^T (K-major operands of dW)
     std::vector<__nv_bfloat16 *> HT;     // per hidden layer [width][B]: H^T written by the forward epilogue
     std::vector<char> ht_valid;          // HT[l] holds this batch (the forward ran on the tcgen05 path)
+    std::vector<__nv_bfloat16 *> D;      // fused training: gelu'(Z) of the first depth - 1 hidden layers [B][width]
     long long astride = 0;               // per-member stride of the activation buffers (max_batch * width)
     int *errw = nullptr;                 // device error word (bounded waits)
     bool use_tc = true;
@@ -1041,58 +1495,77 @@ void forward(qs_mlp *m, int n, bool want_ht = false) {
     }
 }
 
-// backward of every member (after forward + loss); gradients into G
-void backward(qs_mlp *m, int n) {
+// backward of every member (after forward + loss); gradients into G.  After
+// the fused training forward (fused), G already holds the output layer's
+// gradients and b2's, and DG1 / TDZ hold dz of the last hidden layer.
+void backward(qs_mlp *m, int n, bool fused) {
     const long long as = m->astride, os = (long long)m->max_batch * m->n_out;
     float *G = m->G;
-    cudaMemsetAsync(G, 0, sizeof(float) * (size_t)m->nparam * m->E, m->stream);   // every path accumulates
-    const __nv_bfloat16 *dz = m->DOUT;   // dL/dz of the current layer, bf16 [n][lout] per member
-    long long sdz = os;
+    if (!fused) cudaMemsetAsync(G, 0, sizeof(float) * (size_t)m->nparam * m->E, m->stream);
+    const __nv_bfloat16 *dz = fused ? m->DG1 : m->DOUT;   // dL/dz of the current layer, bf16 [n][lout] per member
+    long long sdz = fused ? as : os;
     __nv_bfloat16 *ping[2] = {m->DG0, m->DG1};
-    bool dzt_ready = false;              // TDZ holds dz^T (written by the previous dX epilogue)
-    for (int l = m->depth; l >= 0; --l) {
+    bool dzt_ready = fused;              // TDZ holds dz^T
+    bool bsum_done = fused;              // G holds the current layer's bias gradient
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (int l = fused ? m->depth - 1 : m->depth; l >= 0; --l) {
         const int in = m->lin[l], out = m->lout[l];
         const __nv_bfloat16 *act = l == 0 ? m->X0 : m->H[l - 1];
         const long long sact = l == 0 ? 0 : as;
         const int lda_act = l == 0 ? m->kin : m->width;
+        const bool actT_ready = l >= 1 && m->ht_valid[l - 1];
         // dW[o][i] = sum_b dz[b][o] act[b][i]
-        if (m->use_tc && in % 128 == 0 && out >= 128 && n % 8 == 0) {
-            // tensor cores: dz and act K-major [width][batch], then one 128 x 128
-            // tile per CTA over a slice of the batch, slices summed atomically
+        const bool tc_ok = m->use_tc && out % 128 == 0 && n % 8 == 0;
+        if (tc_ok && (in % 128 == 0 || (l == 0 && in % 4 == 0))) {
+            // tensor cores: dz^T and act^T K-major [width][batch] (the first
+            // layer's act^T is the standardised input's transpose); the batch
+            // is split over enough CTAs to fill the GPU, slices summed atomically
             const dim3 tb(32, 8);
             if (!dzt_ready)
                 mlp::k_transpose_b16<<<dim3((out + 31) / 32, (n + 31) / 32, m->E), tb, 0, m->stream>>>(
                     dz, n, out, m->TDZ, sdz, as);
             const __nv_bfloat16 *actT = m->TACT;
-            if (l >= 1 && m->ht_valid[l - 1]) actT = m->HT[l - 1];
+            long long sactT = as;
+            if (l == 0) { actT = m->X0T; sactT = 0; }
+            else if (actT_ready) actT = m->HT[l - 1];
             else mlp::k_transpose_b16<<<dim3((in + 31) / 32, (n + 31) / 32, m->E), tb, 0, m->stream>>>(
                      act, n, in, m->TACT, sact, as);
-            mlp::GemmArgs gt{};
-            gt.A = m->TDZ; gt.sA = as; gt.lda = n;   // A(m=o, k=b) = dz^T[o][b]
-            gt.B = actT; gt.sB = as; gt.ldb = n;     // B(n=i, k=b) = act^T[i][b]
-            gt.M = out; gt.N = in; gt.K = 256;
-            gt.C = G + m->woff[l]; gt.sC = m->nparam; gt.ldc = in;
-            gt.epi = mlp::EPI_ATOMIC;
-            const int S = std::max(1, std::min(32, (n + 255) / 256));
-            gt.kchunks = (n + 256 * S - 1) / (256 * S);
-            gt.Ktot = n;
-            gt.zper = S;
-            mlp::k_gemm_tc<256, 128><<<dim3((out + 127) / 128, in / 128, S * m->E), 128, (size_t)(128 + 128) * 256 * 2,
-                                       m->stream>>>(gt, m->errw);
+            const int tiles = (out / 128) * ((in + 127) / 128) * m->E;
+            const int nkt = (n + mlp::wg::KC - 1) / mlp::wg::KC;
+            const int want = std::max(1, nsm / std::max(1, tiles));
+            const int cpc = (nkt + want - 1) / want;
+            const int zper = (nkt + cpc - 1) / cpc;
+            mlp::k_wgrad_tc<<<dim3(out / 128, (in + 127) / 128, zper * m->E), 128, mlp::wg::SMEM, m->stream>>>(
+                m->TDZ, actT, n, out, in, n, cpc, G + m->woff[l], in, as, sactT, m->nparam, zper, m->errw);
         } else if ((in == 16 || in == 32) || out == 2) {
             // a thin layer: one pass over the batch, the narrow side in registers
-            const int rb = 256;
+            const int rb = 128;
             const dim3 grid((unsigned)((n + rb - 1) / rb), m->E);
             float *C = G + m->woff[l];
             if (out == 2)
-                mlp::k_dw_thin<2, false><<<grid, 256, 0, m->stream>>>(act, lda_act, dz, out, n, in, rb, C, sact, sdz,
+                mlp::k_dw_thin<2, false><<<grid, 128, 0, m->stream>>>(act, lda_act, dz, out, n, in, rb, C, sact, sdz,
                                                                        m->nparam);
             else if (in == 16)
-                mlp::k_dw_thin<16, true><<<grid, 256, 0, m->stream>>>(dz, out, act, lda_act, n, out, rb, C, sdz, sact,
+                mlp::k_dw_thin<16, true><<<grid, 128, 0, m->stream>>>(dz, out, act, lda_act, n, out, rb, C, sdz, sact,
                                                                        m->nparam);
             else
-                mlp::k_dw_thin<32, true><<<grid, 256, 0, m->stream>>>(dz, out, act, lda_act, n, out, rb, C, sdz, sact,
+                mlp::k_dw_thin<32, true><<<grid, 128, 0, m->stream>>>(dz, out, act, lda_act, n, out, rb, C, sdz, sact,
                                                                        m->nparam);
+        } else if (dzt_ready && actT_ready) {
+            // the transposed copies are the only ones written (fused forward)
+            mlp::GemmArgs gw{};
+            gw.A = m->TDZ; gw.sA = as; gw.lda = n;           // A(m=o, k=b) = dz^T[o][b]
+            gw.B = m->HT[l - 1]; gw.sB = as; gw.ldb = n;     // B(n=i, k=b) = act^T[i][b]
+            gw.M = out; gw.N = in; gw.K = n;
+            gw.C = G + m->woff[l]; gw.sC = m->nparam; gw.ldc = in;
+            gw.epi = mlp::EPI_STORE;
+            gw.accumulate = 1;
+            const int tiles = ((out + mlp::BM - 1) / mlp::BM) * ((in + mlp::BN - 1) / mlp::BN) * m->E;
+            int split = std::max(2, std::min(64, 296 / std::max(1, tiles)));
+            split = std::min(split, std::max(2, n / 256));
+            gemm(m, 0, 0, gw, split);   // split > 1: the mma.sync kernel, atomic accumulation
         } else {
             mlp::GemmArgs gw{};
             gw.A = dz; gw.sA = sdz; gw.lda = out;        // A(m=o, k=b) = dz[b*out + o]  (TA = 1)
@@ -1108,22 +1581,37 @@ void backward(qs_mlp *m, int n) {
             gw.accumulate = 1;
             gemm(m, 1, 1, gw, split);
         }
-        // bias gradient: column sums of dz
-        mlp::k_colsum_tiles<<<dim3((n + 31) / 32, m->E), std::max(32, (out / 2 + 31) / 32 * 32), 0, m->stream>>>(
-            dz, n, out, G + m->boff[l], sdz, m->nparam);
+        // bias gradient: column sums of dz (unless an epilogue already added them)
+        if (!bsum_done)
+            mlp::k_colsum_tiles<<<dim3((n + 31) / 32, m->E), std::max(32, (out / 2 + 31) / 32 * 32), 0, m->stream>>>(
+                dz, n, out, G + m->boff[l], sdz, m->nparam);
         if (l == 0) break;
         // dz_prev[b][i] = (sum_o dz[b][o] W[o][i]) * gelu'(Z[l-1][b][i])
-        mlp::GemmArgs gx{};
-        gx.A = dz; gx.sA = sdz; gx.lda = out;                          // A(m=b, k=o), TA = 0
-        gx.B = m->PT + m->woff[l]; gx.sB = m->nparam; gx.ldb = out;    // B(n=i, k=o) = W^T[i*out + o]
-        gx.M = n; gx.N = in; gx.K = out;
-        gx.C = m->Z[l - 1]; gx.sC = as; gx.ldc = m->width;             // read as Z in the epilogue
-        gx.Z = m->Z[l - 1]; gx.sZ = as;
         __nv_bfloat16 *dst = ping[l & 1];
-        gx.H = dst; gx.sH = as; gx.ldh = m->width;
-        gx.Ht = m->TDZ; gx.sHt = as; gx.ldht = n;   // dz^T for the next weight gradient (tcgen05 path)
-        gx.epi = mlp::EPI_DGELU;
-        dzt_ready = gemm(m, 0, 0, gx);
+        if (fused) {
+            // gelu'(Z) from the fused forward; the layer below's bias gradient
+            // and dz_prev^T in the same pass
+            mlp::DxArgs da{};
+            da.dz = dz; da.WT = m->PT + m->woff[l]; da.D = m->D[l - 1];
+            da.out = dst; da.outT = m->TDZ; da.bgrad = G + m->boff[l - 1];
+            da.n = n; da.sa = as; da.sw = m->nparam; da.E = m->E; da.err = m->errw;
+            const long long items = (n + 127) / 128 * (long long)m->E;
+            mlp::k_dx_tc<<<(unsigned)std::min<long long>(nsm, items), 256, mlp::dxk::SMEM, m->stream>>>(da);
+            dzt_ready = true;
+            bsum_done = true;
+        } else {
+            mlp::GemmArgs gx{};
+            gx.A = dz; gx.sA = sdz; gx.lda = out;                          // A(m=b, k=o), TA = 0
+            gx.B = m->PT + m->woff[l]; gx.sB = m->nparam; gx.ldb = out;    // B(n=i, k=o) = W^T[i*out + o]
+            gx.M = n; gx.N = in; gx.K = out;
+            gx.C = m->Z[l - 1]; gx.sC = as; gx.ldc = m->width;             // read as Z in the epilogue
+            gx.Z = m->Z[l - 1]; gx.sZ = as;
+            gx.H = dst; gx.sH = as; gx.ldh = m->width;
+            gx.Ht = m->TDZ; gx.sHt = as; gx.ldht = n;   // dz^T for the next weight gradient (tcgen05 path)
+            gx.epi = mlp::EPI_DGELU;
+            dzt_ready = gemm(m, 0, 0, gx);
+            bsum_done = false;
+        }
         dz = dst;
         sdz = as;
     }
@@ -1161,6 +1649,7 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     if ((s = mdev(m, pb, &m->P)) || (s = mdev(m, pb, &m->Mm)) || (s = mdev(m, pb, &m->Vv)) ||
         (s = mdev(m, pb, &m->G)) || (s = mdev(m, pb / 2, &m->Pb)) ||
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * m->kin, &m->X0)) ||
+        (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)max_batch * m->kin, &m->X0T)) ||
         (s = mdev(m, sizeof(float) * (size_t)ensemble * max_batch * n_out, &m->OUT)) ||
         (s = mdev(m, sizeof(float) * (size_t)ensemble * max_batch * n_out, &m->DOUTF)) ||
         (s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * n_out, &m->DOUT)) ||
@@ -1226,14 +1715,24 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     cudaMemsetAsync(m->PT, 0, pb / 2, m->stream);
     cudaMemsetAsync(m->errw, 0, sizeof(int) * 4, m->stream);
     refresh_wt(m);
-    cudaFuncSetAttribute(mlp::k_gemm_tc<256, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 256 * 2);
     cudaFuncSetAttribute(mlp::k_gemm_tc<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 16 * 2);
     cudaFuncSetAttribute(mlp::k_gemm_tc<256, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (128 + 64) * 256 * 2);
+    cudaFuncSetAttribute(mlp::k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp::wg::SMEM);
+    cudaFuncSetAttribute(mlp::k_dx_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp::dxk::SMEM);
     if (const char *v = getenv("QS_MLP_NO_TCGEN05")) m->use_tc = v[0] == '0';
     // the fused inference kernel serves the surrogate's shape; QS_MLP_NO_FUSED=1
     // selects the layer-by-layer path (used to compare the two)
     m->fused_ok = m->kin == 16 && width == 256 && depth == 3 && n_out == 2;
     if (const char *v = getenv("QS_MLP_NO_FUSED")) m->fused_ok = m->fused_ok && v[0] == '0';
+    if (m->fused_ok)
+        for (int l = 0; l + 1 < depth; ++l) {
+            __nv_bfloat16 *d;
+            if ((s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &d))) {
+                qs_mlp_free(m);
+                return s;
+            }
+            m->D.push_back(d);
+        }
     if (cudaGetLastError() != cudaSuccess) { qs_mlp_free(m); return QS_ERR_CUDA; }
     *out = m;
     return QS_OK;
@@ -1293,26 +1792,30 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
     if (!m || !X || !Y || n < 1 || n > m->max_batch) return QS_ERR_ARG;
     const int nb = (int)n;
     mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(
-        X, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0);
+        X, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0, m->X0T);
     cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream);
     ++m->step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     // every member in the same launches (member = the launch's z or y index)
-    if (m->use_tc && m->fused_ok) {
-        // one fused launch: Z, H, H^T of every hidden layer and the outputs
+    const bool fused = m->use_tc && m->fused_ok;
+    if (fused) {
+        // one fused launch: the forward of every member, what the backward
+        // GEMMs read (H^T, gelu'(Z)), the loss and the output layer's backward
+        cudaMemsetAsync(m->G, 0, sizeof(float) * (size_t)m->nparam * m->E, m->stream);
         mlp::FusedArgs fa = fused_args(m, X, nb);
-        for (int l = 0; l < 3; ++l) { fa.Z[l] = m->Z[l]; fa.H[l] = m->H[l]; fa.HT[l] = m->HT[l]; m->ht_valid[l] = 1; }
+        for (int l = 0; l < 2; ++l) { fa.HT[l] = m->HT[l]; fa.D[l] = m->D[l]; m->ht_valid[l] = 1; }
+        m->ht_valid[2] = 0;
+        fa.DZ = m->DG1; fa.DZT = m->TDZ;
         fa.as = m->astride;
-        fa.OUT = m->OUT;
-        fa.os = (long long)m->max_batch * m->n_out;
+        fa.Y = Y; fa.yinv = 1.0f / m->ystd; fa.loss = m->loss; fa.G = m->G;
         if (!fused_launch(m, fa, true)) return mfail(m, QS_ERR_CUDA, "fused forward launch failed");
     } else {
         forward(m, nb, true);
+        mlp::k_loss<<<dim3((nb + 255) / 256, m->E), 256, 0, m->stream>>>(
+            m->OUT, Y, nb, m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss, (long long)m->max_batch * 2);
     }
-    mlp::k_loss<<<dim3((nb + 255) / 256, m->E), 256, 0, m->stream>>>(
-        m->OUT, Y, nb, m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss, (long long)m->max_batch * 2);
-    backward(m, nb);
+    backward(m, nb, fused);
     if (do_update) {
         const long long np = m->nparam * m->E;   // members' parameters are contiguous
         mlp::k_adam<<<(unsigned)((np + 255) / 256), 256, 0, m->stream>>>(m->P, m->Mm, m->Vv, m->G, np, lr, b1, b2,
@@ -1357,7 +1860,7 @@ qs_status qs_mlp_infer(qs_mlp *m, const float *X, int64_t n, float *mean, float 
     for (int64_t r0 = 0; r0 < n; r0 += m->max_batch) {
         const int nb = (int)std::min<int64_t>(m->max_batch, n - r0);
         mlp::k_standardise<<<(unsigned)(((long long)nb * m->kin + 255) / 256), 256, 0, m->stream>>>(
-            X + r0 * m->n_in, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0);
+            X + r0 * m->n_in, nb, m->n_in, m->kin, m->stats, m->stats + 32, m->X0, nullptr);
         forward(m, nb);
         mlp::k_ensemble<<<(nb + 255) / 256, 256, 0, m->stream>>>(
             m->OUT, (long long)m->max_batch * 2, m->E, nb, m->ymean, m->ystd, mean + r0 * 2, var + r0 * 2,
