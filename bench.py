@@ -542,9 +542,11 @@ def narrow_leg(args, pk, pk_kind):
     t, _ = time_job(stream, lambda: g.step(n), args.narrow_reps)
     g.sync()
     clocks = clk.stop()
-    # algorithmic bytes per transverse-point cell update: n_b read (phase A) +
-    # n_p write, then n_p read twice, n_b and G read and written (phase B)
-    bpu = 4 + 4 + 4 + 4 + 16
+    # algorithmic bytes per transverse-point cell update: n_b read and n_p
+    # written by the xi march, then n_p read, n_b and G read and written by
+    # the slice solve and push (the second n_p read and the spectral
+    # intermediates between the transform kernels are overhead)
+    bpu = 4 + 4 + 4 + 16
     achieved = bpu * cells * n / t / 1e9
     out = {"value": cells * n / t, "unit": "point·ξ-cell updates/s", "ms_per_slow_time_step": 1e3 * t / n,
            "slow_time_steps_per_call": n, "calls": args.narrow_reps,

@@ -75,19 +75,23 @@ __device__ float2 *fft_rows(float2 *src, float2 *dst, int rows, const float2 *tw
 // does the 16-point DFT over t; thread t then holds X[t + 16 k2].  The
 // 16-point DFT is radix 4 x 4.  tw256[j] = exp(-2 pi i j / 256).
 // ---------------------------------------------------------------------------
+// complex add and subtract as packed FP32x2 operations (a - b = fma(b, -1, a),
+// rounded exactly like the subtraction)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
 template <bool INV>
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-    const float2 t0 = make_float2(a0.x + a2.x, a0.y + a2.y), t1 = make_float2(a0.x - a2.x, a0.y - a2.y);
-    const float2 t2 = make_float2(a1.x + a3.x, a1.y + a3.y), t3 = make_float2(a1.x - a3.x, a1.y - a3.y);
-    const float2 m3 = make_float2(t3.y, -t3.x);   // -i t3
-    a0 = make_float2(t0.x + t2.x, t0.y + t2.y);
-    a2 = make_float2(t0.x - t2.x, t0.y - t2.y);
+    const float2 t0 = add2(a0, a2), t1 = sub2(a0, a2), t2 = add2(a1, a3), t3 = sub2(a1, a3);
+    a0 = add2(t0, t2);
+    a2 = sub2(t0, t2);
+    // t1 -/+ i t3 (forward: -i t3 = (t3.y, -t3.x))
     if (INV) {
-        a1 = make_float2(t1.x - m3.x, t1.y - m3.y);
-        a3 = make_float2(t1.x + m3.x, t1.y + m3.y);
+        a1 = make_float2(t1.x - t3.y, t1.y + t3.x);
+        a3 = make_float2(t1.x + t3.y, t1.y - t3.x);
     } else {
-        a1 = make_float2(t1.x + m3.x, t1.y + m3.y);
-        a3 = make_float2(t1.x - m3.x, t1.y - m3.y);
+        a1 = make_float2(t1.x + t3.y, t1.y - t3.x);
+        a3 = make_float2(t1.x - t3.y, t1.y + t3.x);
     }
 }
 
@@ -98,18 +102,37 @@ __device__ __forceinline__ float2 twid(const float2 *tw256, int j) {
     return w;
 }
 
+// a W16^k, W16 = exp(-2 pi i / 16) (conjugate when INV), for the k = b r
+// (b, r < 4) of a radix-4 x 4 16-point DFT; k is a constant once the
+// callers' loops are unrolled, so the multiplier folds to literals
+template <bool INV>
+__device__ __forceinline__ float2 w16mul(float2 a, int k) {
+    constexpr float C1 = 0.923879532511286756f, S1 = 0.382683432365089772f, R2 = 0.707106781186547524f;
+    float c, s;   // W16^k = (c, -s)
+    switch (k) {
+    case 0: return a;
+    case 4: return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    case 1: c = C1; s = S1; break;
+    case 2: c = R2; s = R2; break;
+    case 3: c = S1; s = C1; break;
+    case 6: c = -R2; s = R2; break;
+    default: c = -C1; s = -S1; break;   // k = 9
+    }
+    return cmul(a, make_float2(c, INV ? s : -s));
+}
+
 // x[k] <- sum_m x[m] W16^(m k) (conjugate twiddles when INV)
 template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&x)[16], const float2 *tw256) {
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
     float2 y[16];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         float2 a0 = x[b], a1 = x[4 + b], a2 = x[8 + b], a3 = x[12 + b];
         dft4<INV>(a0, a1, a2, a3);
         y[4 * b + 0] = a0;
-        y[4 * b + 1] = cmul(a1, twid<INV>(tw256, 16 * b));
-        y[4 * b + 2] = cmul(a2, twid<INV>(tw256, 32 * b));
-        y[4 * b + 3] = cmul(a3, twid<INV>(tw256, 48 * b));
+        y[4 * b + 1] = w16mul<INV>(a1, b);
+        y[4 * b + 2] = w16mul<INV>(a2, 2 * b);
+        y[4 * b + 3] = w16mul<INV>(a3, 3 * b);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -119,20 +142,30 @@ __device__ __forceinline__ void dft16(float2 (&x)[16], const float2 *tw256) {
     }
 }
 
-// in-place FFT of one 256-entry row in shared memory by a 16-thread team;
-// every thread of the warp must call it (both half-warp teams in step)
+// 256-point FFT of values held by a 16-thread team: on entry x[m] is entry
+// t + 16 m, on return x[k] is entry t + 16 k of the transform.  T is the
+// team's [16][17] exchange buffer; every thread of the warp must call it
+// (both half-warp teams in step).
+template <bool INV>
+__device__ __forceinline__ void fft256_reg(float2 (&x)[16], float2 *T, const float2 *tw256, int t) {
+    dft16<INV>(x);
+    T[t] = x[0];   // W256^0
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) T[k1 * 17 + t] = cmul(x[k1], twid<INV>(tw256, t * k1));
+    __syncwarp();
+#pragma unroll
+    for (int tt = 0; tt < 16; ++tt) x[tt] = T[t * 17 + tt];
+    dft16<INV>(x);
+    __syncwarp();
+}
+
+// in-place FFT of one 256-entry row in shared memory by a 16-thread team
 template <bool INV>
 __device__ __forceinline__ void fft256_team(float2 *row, float2 *T, const float2 *tw256, int t) {
     float2 x[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) x[m] = row[t + 16 * m];
-    dft16<INV>(x, tw256);
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) T[k1 * 17 + t] = cmul(x[k1], twid<INV>(tw256, t * k1));
-    __syncwarp();
-#pragma unroll
-    for (int tt = 0; tt < 16; ++tt) x[tt] = T[t * 17 + tt];
-    dft16<INV>(x, tw256);
+    fft256_reg<INV>(x, T, tw256, t);
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) row[t + 16 * k2] = x[k2];
     __syncwarp();
@@ -180,57 +213,109 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
     }
 }
 
-// K2 for N = 256: 16 spectral columns per CTA, one team per column
-__global__ void __launch_bounds__(256) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
+// K2 for N = 256: 128 threads = 8 teams, spectral columns 8 b .. 8 b + 7 of
+// one slice, one per team.  Columns 0 and 128 (k_z = 0 and the Nyquist
+// column) are real sequences along y, so team 0 of block 0 transforms them
+// as the real and imaginary parts of one complex column and 16 blocks cover
+// the 129 columns.  The columns are staged in shared memory (padded column
+// stride; 8-byte asynchronous copies, all in flight at once); each team
+// keeps its column in registers through the forward transform, the kappa
+// and i k_y kappa products and both inverse transforms, and the results
+// pass through the staging buffer again for row-contiguous stores.
+__global__ void __launch_bounds__(128) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
                                                    float2 *__restrict__ T2, float ly, float lz) {
-    constexpr int N = 256, NH = 129, CBn = 16, LD = N + 1;   // padded column stride
+    constexpr int N = 256, NH = 129, CB = 8, LD = N + 1, TSZ = 272;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + 256, *A2 = A + CBn * LD, *T = A2 + CBn * LD;
+    float2 *tw = sm, *A = sm + 256, *Ts = A + (CB + 1) * LD + (threadIdx.x >> 4) * TSZ;
     const long long slice = blockIdx.y;
-    const int c0 = blockIdx.x * CBn;
-    const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int c0 = blockIdx.x * CB;
+    const int tm = threadIdx.x >> 4, t = threadIdx.x & 15, warp = threadIdx.x >> 5;
+    const bool first = blockIdx.x == 0;
+    const bool pk = first && tm == 0;            // columns 0 and 128 packed
+    const bool w0 = first && warp == 0;          // (warp-uniform) the warp holding the packed pair
     make_tw256(tw);
     const float2 *src = S1 + slice * (long long)N * NH;
-    // 8-byte asynchronous copies, all in flight at once (zero fill past the
-    // last spectral column)
-    for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
-        const int y = i >> 4, c = i & 15;
-        const bool in = c0 + c < NH;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(A + c * LD + y)),
-                     "l"(src + (in ? (long long)y * NH + c0 + c : 0)), "r"(in ? 8 : 0) : "memory");
+    for (int i = threadIdx.x; i < CB * N; i += blockDim.x) {
+        const int y = i >> 3, c = i & 7;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(A + c * LD + y)),
+                     "l"(src + (long long)y * NH + c0 + c) : "memory");
     }
+    if (first)   // the Nyquist column in slot CB
+        for (int y = threadIdx.x; y < N; y += blockDim.x)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(A + CB * LD + y)),
+                         "l"(src + (long long)y * NH + 128) : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    float2 *col = A + team * LD, *col2 = A2 + team * LD;
-    fft256_team<false>(col, T + team * 272, tw, t);
-    const int kzi = c0 + team;
+    float2 x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        x[m] = A[tm * LD + t + 16 * m];
+        if (pk) x[m].y = A[CB * LD + t + 16 * m].x;
+    }
+    fft256_reg<false>(x, Ts, tw, t);
+    // the packed pair needs X at -j: entry (256 - t - 16 k) % 256 sits in
+    // thread (16 - t) % 16 at index 15 - k (t > 0) or (16 - k) % 16 (t = 0)
+    if (w0) {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) Ts[t * 17 + k2] = x[k2];
+        __syncwarp();
+    }
+    const int pt = (16 - t) & 15;
     const float inv = 1.0f / (256.0f * 256.0f);
     const float ty = 6.283185307179586f / ly, tz = 6.283185307179586f / lz;
-    const float kz = tz * (float)(kzi == 128 ? -128 : kzi);
-#pragma unroll 4
-    for (int m = 0; m < 16; ++m) {
-        const int jy = t + 16 * m;
-        const float sy = (float)(jy < 128 ? jy : jy - 256);
-        const float ky = ty * sy, kyd = jy == 128 ? 0.0f : ky;
-        const float kap = inv / (1.0f + ky * ky + kz * kz);
-        const float2 X = col[jy];
-        const float2 P = make_float2(kap * X.x, kap * X.y);
-        col[jy] = P;
-        col2[jy] = make_float2(-kyd * P.y, kyd * P.x);
-    }
-    __syncwarp();
-    fft256_team<true>(col, T + team * 272, tw, t);
-    fft256_team<true>(col2, T + team * 272, tw, t);
-    __syncthreads();
-    float2 *d1 = T1 + slice * (long long)N * NH, *d2 = T2 + slice * (long long)N * NH;
-    for (int i = threadIdx.x; i < CBn * N; i += blockDim.x) {
-        const int y = i >> 4, c = i & 15;
-        if (c0 + c < NH) {
-            __stcg(d1 + (long long)y * NH + c0 + c, A[c * LD + y]);
-            __stcg(d2 + (long long)y * NH + c0 + c, A2[c * LD + y]);
+    const float kzv = tz * (float)(c0 + tm);
+    float2 D[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+        const int j = t + 16 * k2;
+        const float sy = (float)(j < 128 ? j : j - 256);
+        const float ky = ty * sy, kyd = j == 128 ? 0.0f : ky;
+        if (pk) {
+            // F0 = (X + conj Xm) / 2 (column 0), F1 = (X - conj Xm) / 2i (column 128)
+            const float2 X = x[k2], Xm = Ts[pt * 17 + (t == 0 ? ((16 - k2) & 15) : 15 - k2)];
+            const float2 F0 = make_float2(0.5f * (X.x + Xm.x), 0.5f * (X.y - Xm.y));
+            const float2 F1 = make_float2(0.5f * (X.y + Xm.y), -0.5f * (X.x - Xm.x));
+            const float kzn = tz * -128.0f;
+            const float k0 = inv / (1.0f + ky * ky), k1 = inv / (1.0f + ky * ky + kzn * kzn);
+            const float2 P0 = make_float2(k0 * F0.x, k0 * F0.y), P1 = make_float2(k1 * F1.x, k1 * F1.y);
+            const float2 D0 = make_float2(-kyd * P0.y, kyd * P0.x), D1 = make_float2(-kyd * P1.y, kyd * P1.x);
+            x[k2] = make_float2(P0.x - P1.y, P0.y + P1.x);   // P0 + i P1
+            D[k2] = make_float2(D0.x - D1.y, D0.y + D1.x);   // D0 + i D1
+        } else {
+            const float kap = inv / (1.0f + ky * ky + kzv * kzv);
+            const float2 P = make_float2(kap * x[k2].x, kap * x[k2].y);
+            x[k2] = P;
+            D[k2] = make_float2(-kyd * P.y, kyd * P.x);
         }
     }
+    if (w0) __syncwarp();   // the exchange buffer is read before the transforms reuse it
+    fft256_reg<true>(x, Ts, tw, t);
+    fft256_reg<true>(D, Ts, tw, t);
+    float2 *d1 = T1 + slice * (long long)N * NH, *d2 = T2 + slice * (long long)N * NH;
+    // results -> staging buffer (column 0 and 128 of the packed pair as real values) -> rows
+    auto out = [&](const float2 (&v)[16], float2 *dst) {
+        __syncthreads();   // the staging buffer is free
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const int y = t + 16 * k2;
+            if (pk) {
+                A[y] = make_float2(v[k2].x, 0.0f);
+                A[CB * LD + y] = make_float2(v[k2].y, 0.0f);
+            } else {
+                A[tm * LD + y] = v[k2];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < CB * N; i += blockDim.x) {
+            const int y = i >> 3, c = i & 7;
+            __stcg(dst + (long long)y * NH + c0 + c, A[c * LD + y]);
+        }
+        if (first)
+            for (int y = threadIdx.x; y < N; y += blockDim.x) __stcg(dst + (long long)y * NH + 128, A[CB * LD + y]);
+    };
+    out(x, d1);
+    out(D, d2);
 }
 
 // signed spectral index and its derivative version (Nyquist zeroed)
@@ -244,7 +329,10 @@ __global__ void k_plasma(const float *__restrict__ nb, float *__restrict__ np, l
                          float c, float s, float ch, float sh) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
-    constexpr int U = 8;
+    // U cells of the line in flight per thread: with one thread per
+    // transverse point (65,536 at N = 256) that keeps about 8 MB of loads
+    // outstanding, enough to cover the HBM latency
+    constexpr int U = 32;
     float n = 0.0f, d = 0.0f;
     float buf[U];
     for (int j0 = 0; j0 < Nxi; j0 += U) {
@@ -406,83 +494,101 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
     if (bad) atomicOr(a.err, 1);
 }
 
-// K3 for N = 256: 16 rows per CTA -> 16 Z1 rows + 8 Z2 rows; teams 0..7
-// transform two rows, teams 8..15 one (uniform within each warp).
-__global__ void __launch_bounds__(256) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
+// K3 for N = 256: 128 threads = 8 teams, rows r0 .. r0 + 15 of one slice;
+// team m owns rows y0 = r0 + 2m and y0 + 1 and needs nothing from the other
+// teams: d_y Psi of both rows from one packed inverse transform of their T2
+// rows, then Psi and d_z Psi of each row from one of its T1 row.  The
+// transform inputs are read from HBM straight into registers (the next
+// transform's while the current one runs); a transform leaves entry t + 16 k
+// in thread t, and the results are re-read through a padded [16][17] layout
+// so that thread t pushes the contiguous points 16 t .. 16 t + 15 with
+// 16-byte loads and stores, issued one transform ahead.
+__global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
                                                         const PushArgs a) {
-    constexpr int N = 256, NH = 129, RBn = 16;
-    extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + 256, *T = A + (RBn + RBn / 2) * N;
+    constexpr int N = 256, NH = 129, TSZ = 272;
+    __shared__ float2 tw[256];
+    __shared__ float2 scr[8][2][TSZ];   // per team: transform scratch, d_y Psi of the two rows
     const long long slice = blockIdx.y;
-    const int r0 = blockIdx.x * RBn;
-    const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int tm = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int y0 = blockIdx.x * 16 + 2 * tm;
+    float2 *Ts = scr[tm][0], *Dy = scr[tm][1];
     make_tw256(tw);
-    // issue the push operands' loads first: they land while the transforms run
-    const long long base = slice * (long long)N * N;
-    constexpr int PER = RBn * N / 256;          // 16 elements per thread
-    float pnp[PER], pnb[PER], pg[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int i = threadIdx.x + u * 256;
-        const long long o = base + (long long)(r0 + (i >> 8)) * N + (i & 255);
-        pnp[u] = __ldcg(a.np + o);
-        pnb[u] = __ldcg(a.nb + o);
-        pg[u] = __ldcg(a.G + o);
-    }
     const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
+    const long long base = slice * (long long)N * N;
     const float tz = 6.283185307179586f / a.lz;
-    // stage the raw half spectra of the CTA's rows (T1 and T2, RBn rows each)
-    // in the FFT scratch with 8-byte asynchronous copies, all in flight at once
-    float2 *S1s = T, *S2s = T + RBn * NH;        // 2 RBn NH <= 16 * 272 entries
-    for (int i = threadIdx.x; i < RBn * NH; i += blockDim.x) {
-        const int r = i / NH, k = i - r * NH;
-        const long long o = (long long)(r0 + r) * NH + k;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(S1s + i)),
-                     "l"(t1 + o) : "memory");
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(S2s + i)),
-                     "l"(t2 + o) : "memory");
+    // entry k = t + 16 m of a row's Hermitian extension is (conjugated past 128) entry kk
+    auto kk_of = [&](int m) { const int k = t + 16 * m; return k <= 128 ? k : N - k; };
+    float2 x[16], r1[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        float2 U = t2[(long long)y0 * NH + kk_of(m)], V = t2[(long long)(y0 + 1) * NH + kk_of(m)];
+        if (t + 16 * m > 128) { U.y = -U.y; V.y = -V.y; }
+        x[m] = make_float2(U.x - V.y, U.y + V.x);   // U + i V
+        r1[m] = t1[(long long)y0 * NH + kk_of(m)];
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    for (int i = threadIdx.x; i < RBn * N; i += blockDim.x) {
-        const int r = i >> 8, k = i & 255;
-        const bool lo = k <= 128;
-        const int kk = lo ? k : N - k;
-        float2 X = S1s[r * NH + kk];
-        if (!lo) X.y = -X.y;
-        const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
-        A[r * N + k] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
-    }
-    for (int i = threadIdx.x; i < (RBn / 2) * N; i += blockDim.x) {
-        const int pr = i >> 8, k = i & 255;
-        const bool lo = k <= 128;
-        const int kk = lo ? k : N - k;
-        float2 U = S2s[(2 * pr) * NH + kk], V = S2s[(2 * pr + 1) * NH + kk];
-        if (!lo) { U.y = -U.y; V.y = -V.y; }
-        A[(RBn + pr) * N + k] = make_float2(U.x - V.y, U.y + V.x);
-    }
-    __syncthreads();   // the FFTs below reuse the scratch
-    fft256_team<true>(A + team * N, T + team * 272, tw, t);
-    if (team < 8) fft256_team<true>(A + (RBn + team) * N, T + team * 272, tw, t);
-    __syncthreads();
+    float4 lnp[4], lnb[4], lg[4], ln0[4], lgy[4], lgz[4];
+    auto issue = [&](int rr) {
+        const long long o = base + (long long)(y0 + rr) * N + 16 * t;
+        const int q = (y0 + rr) * N + 16 * t;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            lnp[i] = __ldcg(reinterpret_cast<const float4 *>(a.np + o) + i);
+            lnb[i] = __ldcg(reinterpret_cast<const float4 *>(a.nb + o) + i);
+            lg[i] = __ldcg(reinterpret_cast<const float4 *>(a.G + o) + i);
+            ln0[i] = __ldg(reinterpret_cast<const float4 *>(a.nb0 + q) + i);
+            lgy[i] = __ldg(reinterpret_cast<const float4 *>(a.gy + q) + i);
+            lgz[i] = __ldg(reinterpret_cast<const float4 *>(a.gz + q) + i);
+        }
+    };
+    issue(0);
+    __syncthreads();   // twiddles
+    fft256_reg<true>(x, Ts, tw, t);
+    // entry z of the row pair's d_y Psi at (z % 16) 17 + z / 16
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) Dy[t * 17 + k2] = x[k2];
     bool bad = false;
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-        const int i = threadIdx.x + u * 256;
-        const int r = i >> 8, z = i & 255;
-        const int y = r0 + r;
-        const float2 Z1 = A[r * N + z];
-        const float2 Z2 = A[(RBn + (r >> 1)) * N + z];
-        const float psi = Z1.x, dz = Z1.y, dy = (r & 1) ? Z2.y : Z2.x;
-        const long long o = base + (long long)y * N + z;
-        const int q = y * N + z;
-        const float S = a.coef * (a.nb0[q] * (psi - pnp[u]) + a.gy[q] * dy + a.gz[q] * dz);
-        const float g = fmaf(a.h, S, pg[u]);
-        const float n = fmaf(a.dt, g, pnb[u]);
-        __stcg(a.G + o, g);
-        __stcg(a.nb + o, n);
-        bad |= !(fabsf(n) <= 3.0e38f) || !(fabsf(g) <= 3.0e38f);
+    for (int rr = 0; rr < 2; ++rr) {
+        // Psi + i d_z Psi = inverse transform of X - k_z X (X the Hermitian extension of the T1 row)
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int k = t + 16 * m;
+            float2 X = r1[m];
+            if (k > 128) X.y = -X.y;
+            const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
+            x[m] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
+        }
+        if (rr == 0) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) r1[m] = t1[(long long)(y0 + 1) * NH + kk_of(m)];
+        }
+        fft256_reg<true>(x, Ts, tw, t);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) Ts[t * 17 + k2] = x[k2];
+        __syncwarp();
+        const long long o = base + (long long)(y0 + rr) * N + 16 * t;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float e[4], f[4];
+            const float npa[4] = {lnp[i].x, lnp[i].y, lnp[i].z, lnp[i].w}, nbv[4] = {lnb[i].x, lnb[i].y, lnb[i].z, lnb[i].w};
+            const float gv[4] = {lg[i].x, lg[i].y, lg[i].z, lg[i].w}, n0[4] = {ln0[i].x, ln0[i].y, ln0[i].z, ln0[i].w};
+            const float gyv[4] = {lgy[i].x, lgy[i].y, lgy[i].z, lgy[i].w}, gzv[4] = {lgz[i].x, lgz[i].y, lgz[i].z, lgz[i].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = 4 * i + c;                       // point 16 t + j
+                const float2 pz = Ts[j * 17 + t];
+                const float2 dyp = Dy[j * 17 + t];
+                const float dyv = rr ? dyp.y : dyp.x;
+                const float S = a.coef * (n0[c] * (pz.x - npa[c]) + gyv[c] * dyv + gzv[c] * pz.y);
+                f[c] = fmaf(a.h, S, gv[c]);
+                e[c] = fmaf(a.dt, f[c], nbv[c]);
+                bad |= !(fabsf(e[c]) <= 3.0e38f) || !(fabsf(f[c]) <= 3.0e38f);
+            }
+            __stcg(reinterpret_cast<float4 *>(a.G + o) + i, make_float4(f[0], f[1], f[2], f[3]));
+            __stcg(reinterpret_cast<float4 *>(a.nb + o) + i, make_float4(e[0], e[1], e[2], e[3]));
+        }
+        __syncwarp();   // Ts is reused by the next transform
+        if (rr == 0) issue(1);
     }
     if (bad) atomicOr(a.err, 1);
 }
@@ -550,15 +656,13 @@ template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
 constexpr size_t SMEM_K1_256 = sizeof(float2) * (256 + 16 * 256 + 16 * 272);
-constexpr size_t SMEM_K2_256 = sizeof(float2) * (256 + 2 * 16 * 257 + 16 * 272);
-constexpr size_t SMEM_K3_256 = sizeof(float2) * (256 + 24 * 256 + 16 * 272);
+constexpr size_t SMEM_K2_256 = sizeof(float2) * (256 + 9 * 257 + 8 * 272);
 
 template <int N>
 cudaError_t set_attrs() {
     if constexpr (N == 256) {
         cudaError_t e = cudaFuncSetAttribute(r2::k_rowfft256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K1_256);
         if (!e) e = cudaFuncSetAttribute(r2::k_colfft256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K2_256);
-        if (!e) e = cudaFuncSetAttribute(r2::k_rowinv_push256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K3_256);
         return e;
     }
     cudaError_t e = cudaFuncSetAttribute(r2::k_rowfft<N, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k1<N>());
@@ -580,9 +684,9 @@ cudaError_t step_n(qs_r2 *c, float h) {
                    (float)(-p.species.q / (p.species.m * p.gamma_b)), h, (float)p.dt, (float)p.L_perp, c->err};
     if constexpr (N == 256) {
         r2::k_rowfft256<<<dim3(256 / 32, p.n_xi), 256, SMEM_K1_256, c->stream>>>(c->np, c->S1);
-        r2::k_colfft256<<<dim3((129 + 15) / 16, p.n_xi), 256, SMEM_K2_256, c->stream>>>(
+        r2::k_colfft256<<<dim3(16, p.n_xi), 128, SMEM_K2_256, c->stream>>>(
             c->S1, c->T1, c->T2, (float)p.L_perp, (float)p.L_perp);
-        r2::k_rowinv_push256<<<dim3(256 / 16, p.n_xi), 256, SMEM_K3_256, c->stream>>>(c->T1, c->T2, a);
+        r2::k_rowinv_push256<<<dim3(256 / 16, p.n_xi), 128, 0, c->stream>>>(c->T1, c->T2, a);
         c->launches += 4;
         return cudaGetLastError();
     }

@@ -25,7 +25,7 @@ def _case(n, n_xi, **kw):
     return p
 
 
-@pytest.mark.parametrize("n,n_xi,steps", [(32, 120, 25), (64, 37, 9), (128, 9, 4), (256, 5, 3)])
+@pytest.mark.parametrize("n,n_xi,steps", [(32, 120, 25), (64, 37, 9), (128, 9, 4), (256, 5, 3), (256, 41, 2)])
 def test_matches_oracle(R, n, n_xi, steps):
     p = _case(n, n_xi)
     noise = synth.normals((n_xi, n, n), 11)
