@@ -73,7 +73,9 @@ __device__ float2 *fft_rows(float2 *src, float2 *dst, int rows, const float2 *tw
 // holds x[t + 16 m] (m = 0..15), does a 16-point DFT over m in registers,
 // multiplies by W256^(t k1), exchanges through a padded [16][17] buffer, and
 // does the 16-point DFT over t; thread t then holds X[t + 16 k2].  The
-// 16-point DFT is radix 4 x 4.  tw256[j] = exp(-2 pi i j / 256).
+// 16-point DFT is radix 4 x 4.  The inter-step twiddles W256^(t k1),
+// W256 = exp(-2 pi i / 256), sit at tw[k1 * 17 + t] (TWN entries), so the
+// 16 threads of a team read 16 consecutive entries.
 // ---------------------------------------------------------------------------
 // complex add and subtract as packed FP32x2 operations (a - b = fma(b, -1, a),
 // rounded exactly like the subtraction)
@@ -95,12 +97,7 @@ __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ float2 twid(const float2 *tw256, int j) {
-    float2 w = tw256[j & 255];
-    if (INV) w.y = -w.y;
-    return w;
-}
+constexpr int TWN = 16 * 17;
 
 // a W16^k, W16 = exp(-2 pi i / 16) (conjugate when INV), for the k = b r
 // (b, r < 4) of a radix-4 x 4 16-point DFT; k is a constant once the
@@ -151,7 +148,11 @@ __device__ __forceinline__ void fft256_reg(float2 (&x)[16], float2 *T, const flo
     dft16<INV>(x);
     T[t] = x[0];   // W256^0
 #pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) T[k1 * 17 + t] = cmul(x[k1], twid<INV>(tw256, t * k1));
+    for (int k1 = 1; k1 < 16; ++k1) {
+        float2 w = tw256[k1 * 17 + t];
+        if (INV) w.y = -w.y;
+        T[k1 * 17 + t] = cmul(x[k1], w);
+    }
     __syncwarp();
 #pragma unroll
     for (int tt = 0; tt < 16; ++tt) x[tt] = T[t * 17 + tt];
@@ -173,9 +174,10 @@ __device__ __forceinline__ void fft256_team(float2 *row, float2 *T, const float2
 
 __device__ __forceinline__ void make_tw256(float2 *tw) {
     for (int j = threadIdx.x; j < 256; j += blockDim.x) {
+        const int k1 = j >> 4, t = j & 15;
         float s, c;
-        sincospif(-2.0f * j / 256.0f, &s, &c);
-        tw[j] = make_float2(c, s);
+        sincospif(-2.0f * (float)(t * k1) / 256.0f, &s, &c);
+        tw[k1 * 17 + t] = make_float2(c, s);
     }
 }
 
@@ -183,7 +185,7 @@ __device__ __forceinline__ void make_tw256(float2 *tw) {
 __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np, float2 *__restrict__ S1) {
     constexpr int N = 256, NH = 129, PR = 16;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + 256, *T = A + PR * N;
+    float2 *tw = sm, *A = sm + TWN, *T = A + PR * N;
     const long long slice = blockIdx.y;
     const int r0 = blockIdx.x * 2 * PR;
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
@@ -224,9 +226,9 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
 // pass through the staging buffer again for row-contiguous stores.
 __global__ void __launch_bounds__(128) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
                                                    float2 *__restrict__ T2, float ly, float lz) {
-    constexpr int N = 256, NH = 129, CB = 8, LD = N + 1, TSZ = 272;
+    constexpr int N = 256, NH = 129, CB = 8, LD = N + 4, TSZ = 272;   // LD: the 8 columns of a row in distinct banks
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + 256, *Ts = A + (CB + 1) * LD + (threadIdx.x >> 4) * TSZ;
+    float2 *tw = sm, *A = sm + TWN, *Ts = A + (CB + 1) * LD + (threadIdx.x >> 4) * TSZ;
     const long long slice = blockIdx.y;
     const int c0 = blockIdx.x * CB;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15, warp = threadIdx.x >> 5;
@@ -497,51 +499,61 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
 // K3 for N = 256: 128 threads = 8 teams, rows r0 .. r0 + 15 of one slice;
 // team m owns rows y0 = r0 + 2m and y0 + 1 and needs nothing from the other
 // teams: d_y Psi of both rows from one packed inverse transform of their T2
-// rows, then Psi and d_z Psi of each row from one of its T1 row.  The
-// transform inputs are read from HBM straight into registers (the next
-// transform's while the current one runs); a transform leaves entry t + 16 k
-// in thread t, and the results are re-read through a padded [16][17] layout
-// so that thread t pushes the contiguous points 16 t .. 16 t + 15 with
-// 16-byte loads and stores, issued one transform ahead.
+// rows, then Psi and d_z Psi of each row from one of its T1 row.  The four
+// half-spectrum rows are staged in shared memory (8-byte asynchronous
+// copies, each entry read once; the Hermitian extension reads entries k and
+// 256 - k).  A transform leaves entry t + 16 k in thread t; the results are
+// re-read through a padded [16][17] layout so that the push runs on points
+// 4 t + 64 i + c, whose operands the team loads and stores as 256
+// contiguous bytes per i, issued one transform ahead.
 __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
-                                                        const PushArgs a) {
-    constexpr int N = 256, NH = 129, TSZ = 272;
-    __shared__ float2 tw[256];
-    __shared__ float2 scr[8][2][TSZ];   // per team: transform scratch, d_y Psi of the two rows
+                                                           const PushArgs a) {
+    constexpr int N = 256, NH = 129, TSZ = 272, RS = 130;
+    extern __shared__ float2 sm[];
     const long long slice = blockIdx.y;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15;
     const int y0 = blockIdx.x * 16 + 2 * tm;
-    float2 *Ts = scr[tm][0], *Dy = scr[tm][1];
-    make_tw256(tw);
+    float2 *tw = sm, *Ts = sm + TWN + tm * 2 * TSZ, *Dy = Ts + TSZ;
+    float2 *R = sm + TWN + 8 * 2 * TSZ + tm * 4 * RS;   // T2 rows y0, y0 + 1, T1 rows y0, y0 + 1
     const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
+    for (int i = t; i < 4 * NH; i += 16) {
+        const int r = i / NH, k = i - r * NH;
+        const float2 *src = (r < 2 ? t2 : t1) + (long long)(y0 + (r & 1)) * NH + k;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(R + r * RS + k)),
+                     "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     const long long base = slice * (long long)N * N;
     const float tz = 6.283185307179586f / a.lz;
-    // entry k = t + 16 m of a row's Hermitian extension is (conjugated past 128) entry kk
-    auto kk_of = [&](int m) { const int k = t + 16 * m; return k <= 128 ? k : N - k; };
-    float2 x[16], r1[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        float2 U = t2[(long long)y0 * NH + kk_of(m)], V = t2[(long long)(y0 + 1) * NH + kk_of(m)];
-        if (t + 16 * m > 128) { U.y = -U.y; V.y = -V.y; }
-        x[m] = make_float2(U.x - V.y, U.y + V.x);   // U + i V
-        r1[m] = t1[(long long)y0 * NH + kk_of(m)];
-    }
     float4 lnp[4], lnb[4], lg[4], ln0[4], lgy[4], lgz[4];
     auto issue = [&](int rr) {
-        const long long o = base + (long long)(y0 + rr) * N + 16 * t;
-        const int q = (y0 + rr) * N + 16 * t;
+        const long long o = base + (long long)(y0 + rr) * N;
+        const int q = (y0 + rr) * N;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            lnp[i] = __ldcg(reinterpret_cast<const float4 *>(a.np + o) + i);
-            lnb[i] = __ldcg(reinterpret_cast<const float4 *>(a.nb + o) + i);
-            lg[i] = __ldcg(reinterpret_cast<const float4 *>(a.G + o) + i);
-            ln0[i] = __ldg(reinterpret_cast<const float4 *>(a.nb0 + q) + i);
-            lgy[i] = __ldg(reinterpret_cast<const float4 *>(a.gy + q) + i);
-            lgz[i] = __ldg(reinterpret_cast<const float4 *>(a.gz + q) + i);
+            const int z = 4 * t + 64 * i;
+            lnp[i] = __ldcg(reinterpret_cast<const float4 *>(a.np + o + z));
+            lnb[i] = __ldcg(reinterpret_cast<const float4 *>(a.nb + o + z));
+            lg[i] = __ldcg(reinterpret_cast<const float4 *>(a.G + o + z));
+            ln0[i] = __ldg(reinterpret_cast<const float4 *>(a.nb0 + q + z));
+            lgy[i] = __ldg(reinterpret_cast<const float4 *>(a.gy + q + z));
+            lgz[i] = __ldg(reinterpret_cast<const float4 *>(a.gz + q + z));
         }
     };
     issue(0);
-    __syncthreads();   // twiddles
+    make_tw256(tw);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();   // twiddles and staged rows
+    // entry k = t + 16 m of a row's Hermitian extension: entry kk of the half
+    // spectrum, conjugated past 128
+    float2 x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
+        float2 U = R[kk], V = R[RS + kk];
+        if (k > 128) { U.y = -U.y; V.y = -V.y; }
+        x[m] = make_float2(U.x - V.y, U.y + V.x);   // U + i V
+    }
     fft256_reg<true>(x, Ts, tw, t);
     // entry z of the row pair's d_y Psi at (z % 16) 17 + z / 16
 #pragma unroll
@@ -552,21 +564,17 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
         // Psi + i d_z Psi = inverse transform of X - k_z X (X the Hermitian extension of the T1 row)
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
-            const int k = t + 16 * m;
-            float2 X = r1[m];
+            const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
+            float2 X = R[(2 + rr) * RS + kk];
             if (k > 128) X.y = -X.y;
             const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
             x[m] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
-        }
-        if (rr == 0) {
-#pragma unroll
-            for (int m = 0; m < 16; ++m) r1[m] = t1[(long long)(y0 + 1) * NH + kk_of(m)];
         }
         fft256_reg<true>(x, Ts, tw, t);
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) Ts[t * 17 + k2] = x[k2];
         __syncwarp();
-        const long long o = base + (long long)(y0 + rr) * N + 16 * t;
+        const long long o = base + (long long)(y0 + rr) * N;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float e[4], f[4];
@@ -575,17 +583,19 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
             const float gyv[4] = {lgy[i].x, lgy[i].y, lgy[i].z, lgy[i].w}, gzv[4] = {lgz[i].x, lgz[i].y, lgz[i].z, lgz[i].w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int j = 4 * i + c;                       // point 16 t + j
-                const float2 pz = Ts[j * 17 + t];
-                const float2 dyp = Dy[j * 17 + t];
+                // point z = 4 t + 64 i + c: z % 16 = 4 (t % 4) + c, z / 16 = t / 4 + 4 i
+                const int pz_i = (4 * (t & 3) + c) * 17 + (t >> 2) + 4 * i;
+                const float2 pz = Ts[pz_i];
+                const float2 dyp = Dy[pz_i];
                 const float dyv = rr ? dyp.y : dyp.x;
                 const float S = a.coef * (n0[c] * (pz.x - npa[c]) + gyv[c] * dyv + gzv[c] * pz.y);
                 f[c] = fmaf(a.h, S, gv[c]);
                 e[c] = fmaf(a.dt, f[c], nbv[c]);
                 bad |= !(fabsf(e[c]) <= 3.0e38f) || !(fabsf(f[c]) <= 3.0e38f);
             }
-            __stcg(reinterpret_cast<float4 *>(a.G + o) + i, make_float4(f[0], f[1], f[2], f[3]));
-            __stcg(reinterpret_cast<float4 *>(a.nb + o) + i, make_float4(e[0], e[1], e[2], e[3]));
+            const int z = 4 * t + 64 * i;
+            __stcg(reinterpret_cast<float4 *>(a.G + o + z), make_float4(f[0], f[1], f[2], f[3]));
+            __stcg(reinterpret_cast<float4 *>(a.nb + o + z), make_float4(e[0], e[1], e[2], e[3]));
         }
         __syncwarp();   // Ts is reused by the next transform
         if (rr == 0) issue(1);
@@ -655,14 +665,16 @@ size_t smem_k2() { return sizeof(float2) * (N / 2 + 4 * CB * N); }
 template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
-constexpr size_t SMEM_K1_256 = sizeof(float2) * (256 + 16 * 256 + 16 * 272);
-constexpr size_t SMEM_K2_256 = sizeof(float2) * (256 + 9 * 257 + 8 * 272);
+constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 256 + 16 * 272);
+constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 9 * 260 + 8 * 272);
+constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 2 * 272 + 8 * 4 * 130);
 
 template <int N>
 cudaError_t set_attrs() {
     if constexpr (N == 256) {
         cudaError_t e = cudaFuncSetAttribute(r2::k_rowfft256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K1_256);
         if (!e) e = cudaFuncSetAttribute(r2::k_colfft256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K2_256);
+        if (!e) e = cudaFuncSetAttribute(r2::k_rowinv_push256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_K3_256);
         return e;
     }
     cudaError_t e = cudaFuncSetAttribute(r2::k_rowfft<N, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k1<N>());
@@ -686,7 +698,7 @@ cudaError_t step_n(qs_r2 *c, float h) {
         r2::k_rowfft256<<<dim3(256 / 32, p.n_xi), 256, SMEM_K1_256, c->stream>>>(c->np, c->S1);
         r2::k_colfft256<<<dim3(16, p.n_xi), 128, SMEM_K2_256, c->stream>>>(
             c->S1, c->T1, c->T2, (float)p.L_perp, (float)p.L_perp);
-        r2::k_rowinv_push256<<<dim3(256 / 16, p.n_xi), 128, 0, c->stream>>>(c->T1, c->T2, a);
+        r2::k_rowinv_push256<<<dim3(256 / 16, p.n_xi), 128, SMEM_K3_256, c->stream>>>(c->T1, c->T2, a);
         c->launches += 4;
         return cudaGetLastError();
     }
