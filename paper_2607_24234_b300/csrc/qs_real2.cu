@@ -191,20 +191,27 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
     make_tw256(tw);
     const float *src = np + slice * (long long)N * N;
-    // 4-byte asynchronous copies of the two real rows into the (re, im)
-    // halves of each packed complex row, all in flight at once
-    for (int i = threadIdx.x; i < PR * N; i += blockDim.x) {
-        const int pr = i >> 8, x = i & 255;
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(A + i);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + (long long)(r0 + 2 * pr) * N + x)
-                     : "memory");
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4u), "l"(src + (long long)(r0 + 2 * pr + 1) * N + x)
-                     : "memory");
+    // 16-byte asynchronous copies, all in flight at once: rows r0 + 2 pr and
+    // r0 + 2 pr + 1 land side by side (as floats) in packed row pr
+    for (int i = threadIdx.x; i < 2 * PR * N / 4; i += blockDim.x) {
+        const int row = i >> 6, c4 = i & 63;
+        float *d = reinterpret_cast<float *>(A + (row >> 1) * N) + (row & 1) * N + 4 * c4;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(d)),
+                     "l"(src + (long long)(r0 + row) * N + 4 * c4) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    fft256_team<false>(A + team * N, T + team * 272, tw, t);
+    {
+        // team pr: the complex row (row 2 pr) + i (row 2 pr + 1), transformed in place
+        const float *rf = reinterpret_cast<const float *>(A + team * N);
+        float2 x[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) x[m] = make_float2(rf[t + 16 * m], rf[N + t + 16 * m]);
+        fft256_reg<false>(x, T + team * 272, tw, t);   // (its warp barriers order the reads before the writes)
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) A[team * N + t + 16 * k2] = x[k2];
+    }
     __syncthreads();
     float2 *dst = S1 + slice * (long long)N * NH;
     for (int i = threadIdx.x; i < PR * NH; i += blockDim.x) {
@@ -268,24 +275,29 @@ __global__ void __launch_bounds__(128) k_colfft256(const float2 *__restrict__ S1
     const float ty = 6.283185307179586f / ly, tz = 6.283185307179586f / lz;
     const float kzv = tz * (float)(c0 + tm);
     float2 D[16];
+    // (kappa to within 2 ulp: __fdividef; the branch is uniform in all but one warp)
+    if (pk) {
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
-        const int j = t + 16 * k2;
-        const float sy = (float)(j < 128 ? j : j - 256);
-        const float ky = ty * sy, kyd = j == 128 ? 0.0f : ky;
-        if (pk) {
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const int j = t + 16 * k2;
+            const float ky = ty * (float)(j < 128 ? j : j - 256), kyd = j == 128 ? 0.0f : ky;
             // F0 = (X + conj Xm) / 2 (column 0), F1 = (X - conj Xm) / 2i (column 128)
             const float2 X = x[k2], Xm = Ts[pt * 17 + (t == 0 ? ((16 - k2) & 15) : 15 - k2)];
             const float2 F0 = make_float2(0.5f * (X.x + Xm.x), 0.5f * (X.y - Xm.y));
             const float2 F1 = make_float2(0.5f * (X.y + Xm.y), -0.5f * (X.x - Xm.x));
             const float kzn = tz * -128.0f;
-            const float k0 = inv / (1.0f + ky * ky), k1 = inv / (1.0f + ky * ky + kzn * kzn);
+            const float k0 = __fdividef(inv, 1.0f + ky * ky), k1 = __fdividef(inv, 1.0f + ky * ky + kzn * kzn);
             const float2 P0 = make_float2(k0 * F0.x, k0 * F0.y), P1 = make_float2(k1 * F1.x, k1 * F1.y);
             const float2 D0 = make_float2(-kyd * P0.y, kyd * P0.x), D1 = make_float2(-kyd * P1.y, kyd * P1.x);
             x[k2] = make_float2(P0.x - P1.y, P0.y + P1.x);   // P0 + i P1
             D[k2] = make_float2(D0.x - D1.y, D0.y + D1.x);   // D0 + i D1
-        } else {
-            const float kap = inv / (1.0f + ky * ky + kzv * kzv);
+        }
+    } else {
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const int j = t + 16 * k2;
+            const float ky = ty * (float)(j < 128 ? j : j - 256), kyd = j == 128 ? 0.0f : ky;
+            const float kap = __fdividef(inv, 1.0f + ky * ky + kzv * kzv);
             const float2 P = make_float2(kap * x[k2].x, kap * x[k2].y);
             x[k2] = P;
             D[k2] = make_float2(-kyd * P.y, kyd * P.x);
@@ -298,15 +310,15 @@ __global__ void __launch_bounds__(128) k_colfft256(const float2 *__restrict__ S1
     // results -> staging buffer (column 0 and 128 of the packed pair as real values) -> rows
     auto out = [&](const float2 (&v)[16], float2 *dst) {
         __syncthreads();   // the staging buffer is free
+        if (pk) {
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const int y = t + 16 * k2;
-            if (pk) {
-                A[y] = make_float2(v[k2].x, 0.0f);
-                A[CB * LD + y] = make_float2(v[k2].y, 0.0f);
-            } else {
-                A[tm * LD + y] = v[k2];
+            for (int k2 = 0; k2 < 16; ++k2) {
+                A[t + 16 * k2] = make_float2(v[k2].x, 0.0f);
+                A[CB * LD + t + 16 * k2] = make_float2(v[k2].y, 0.0f);
             }
+        } else {
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) A[tm * LD + t + 16 * k2] = v[k2];
         }
         __syncthreads();
         for (int i = threadIdx.x; i < CB * N; i += blockDim.x) {
@@ -508,7 +520,7 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
 // contiguous bytes per i, issued one transform ahead.
 __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
                                                            const PushArgs a) {
-    constexpr int N = 256, NH = 129, TSZ = 272, RS = 130;
+    constexpr int N = 256, NH = 129, TSZ = 272, RS = NH;
     extern __shared__ float2 sm[];
     const long long slice = blockIdx.y;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15;
@@ -516,10 +528,12 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
     float2 *tw = sm, *Ts = sm + TWN + tm * 2 * TSZ, *Dy = Ts + TSZ;
     float2 *R = sm + TWN + 8 * 2 * TSZ + tm * 4 * RS;   // T2 rows y0, y0 + 1, T1 rows y0, y0 + 1
     const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
-    for (int i = t; i < 4 * NH; i += 16) {
-        const int r = i / NH, k = i - r * NH;
-        const float2 *src = (r < 2 ? t2 : t1) + (long long)(y0 + (r & 1)) * NH + k;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(R + r * RS + k)),
+    // rows y0 and y0 + 1 (y0 even) are one 16-byte aligned block of 2 NH
+    // entries in each of T2 and T1: 16-byte copies
+    for (int i = t; i < 2 * NH; i += 16) {
+        const int h = i >= NH, j = i - h * NH;           // block (T2, T1), 16-byte piece
+        const float2 *src = (h ? t1 : t2) + (long long)y0 * NH + 2 * j;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(R + h * 2 * RS + 2 * j)),
                      "l"(src) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -667,7 +681,7 @@ size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
 constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 256 + 16 * 272);
 constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 9 * 260 + 8 * 272);
-constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 2 * 272 + 8 * 4 * 130);
+constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 2 * 272 + 8 * 4 * 129);
 
 template <int N>
 cudaError_t set_attrs() {
