@@ -37,6 +37,7 @@ struct InstDev {
     double qm_g[2];       // (q/m)/gamma
     double qm_g3[2];      // (q/m)/gamma^3, 0 for the reduced model
     int noise_inst;       // instance word of the noise seed's Philox counter
+    float wu[2];          // dt n_bs0 of every cell when the profile is uniform (the FP32 weight)
 };
 
 struct SweepArgs {

@@ -89,8 +89,12 @@ __device__ __forceinline__ float p2(int e) { return __int_as_float((max(-127, mi
 // stride).  TT = 0 keeps Theta in registers and only the weights in shared
 // memory, as (w, w) pairs in rows [v * NS + sp][thread] of the CTA's size,
 // so that each cell's weight is one 8-byte load already in the packed form.
-template <int NS, int V, int TT>
+// UW (uniform profile, every instance, and lines that fill whole warps of
+// V-cell threads; the host checks both): the weight of every cell of a line
+// is the instance's I.wu, held in a register pair, with no per-cell load.
+template <int NS, int V, int TT, bool UW = false>
 __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs a) {
+    static_assert(!UW || TT > 0, "a uniform weight replaces the shared-memory weight rows");
     constexpr bool THS = TT > 0;
     static_assert(GRP % V == 0, "a thread's cells lie in one exponent group");
     constexpr unsigned FULL = 0xffffffffu;
@@ -149,6 +153,9 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
             q[sp] = (float)I.q[sp];
         }
         const float c = (float)I.c, s = (float)I.s, ch = (float)I.ch, sh = (float)I.sh;
+        [[maybe_unused]] float2 W2[NS];
+#pragma unroll
+        for (int sp = 0; sp < NS; ++sp) W2[sp] = make_float2(I.wu[sp], I.wu[sp]);
         // rotation tables: registers when Theta is in registers, else shared
         // by the CTA's lines (one instance per item; visible after the first
         // barrier below)
@@ -204,12 +211,13 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     ld_cell(a, row, mode, y);
                     const float f = fin * q[sp];
                     y.nr *= f; y.ni *= f; y.tr *= f; y.ti *= f;
-                    wv = QS_CHK(a, row, a.rows_total) ? __ldg(reinterpret_cast<const float *>(a.w) + row) : 0.f;
+                    if constexpr (!UW)
+                        wv = QS_CHK(a, row, a.rows_total) ? __ldg(reinterpret_cast<const float *>(a.w) + row) : 0.f;
                 }
                 xn[v][sp] = make_float2(y.nr, y.ni);
                 if constexpr (THS) {
                     sT[(v * NS + sp) * T] = make_float2(y.tr, y.ti);
-                    sWt[(v * NS + sp) * T] = wv;
+                    if constexpr (!UW) sWt[(v * NS + sp) * T] = wv;
                 } else {
                     xt[v][sp] = make_float2(y.tr, y.ti);
                     sWr[(v * NS + sp) * T] = make_float2(wv, wv);   // only this thread reads it back
@@ -323,7 +331,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
 #pragma unroll
                     for (int sp = 0; sp < NS; ++sp) {
                         pt[u][sp] = sT[(u * NS + sp) * T];
-                        pw[u][sp] = sWt[(u * NS + sp) * T];
+                        if constexpr (!UW) pw[u][sp] = sWt[(u * NS + sp) * T];
                     }
             }
 #pragma unroll
@@ -336,7 +344,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
 #pragma unroll
                         for (int sp = 0; sp < NS; ++sp) {
                             zt[u][sp] = pt[u][sp];
-                            zw[u][sp] = pw[u][sp];
+                            if constexpr (!UW) zw[u][sp] = pw[u][sp];
                         }
                     if (vb + CB < V) {
 #pragma unroll
@@ -344,7 +352,7 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
 #pragma unroll
                             for (int sp = 0; sp < NS; ++sp) {
                                 pt[u][sp] = sT[((vb + CB + u) * NS + sp) * T];
-                                pw[u][sp] = sWt[((vb + CB + u) * NS + sp) * T];
+                                if constexpr (!UW) pw[u][sp] = sWt[((vb + CB + u) * NS + sp) * T];
                             }
                     }
                 }
@@ -373,7 +381,8 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                         float2 &y = xn[v][sp];
                         float2 &th = THS ? zt[THS ? u : 0][sp] : xt[THS ? 0 : v][sp];
                         float2 wv2;
-                        if constexpr (THS) wv2 = F2(zw[THS ? u : 0][sp]);
+                        if constexpr (UW) wv2 = W2[sp];
+                        else if constexpr (THS) wv2 = F2(zw[THS ? u : 0][sp]);
                         else wv2 = sWr[(v * NS + sp) * T];
                         if (NS == 1) th = pfma(Ach, uu, pfma(Ash, d, pfma(AB, r, th)));
                         else th = pfma(F2(A[sp]), m, pfma(F2(-B[sp]), r, th));

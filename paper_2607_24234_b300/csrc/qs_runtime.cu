@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -106,6 +107,9 @@ struct qs_ctx {
     int tx_extra = 0;
     int res_every = 16;             // resident variant's renormalisation interval (0: variant refused)
     long long dbg_rows_cut = 0;     // test hook: state rows the bounds checker is told are missing
+    bool uw_fit = false;            // uniform profile and every line a whole number of 1024-cell warps
+    bool dbg_no_uw = false;         // QS_RES_NO_UNIFORM=1: the resident sweep reads per-cell weights even for a
+                                    // uniform profile (compares the two kernels)
     double growth = 0.0;            // largest per-step growth bound of the instances (e-folds)
     std::string err;
 };
@@ -406,18 +410,18 @@ SweepArgs sweep_args(qs_ctx *c, long long step0, int n_steps, int update, int re
     return a;
 }
 
-template <int NS, int V, int TT>
+template <int NS, int V, int TT, bool UW = false>
 cudaError_t launch_res_t(qs_ctx *c, const SweepArgs &a, dim3 grid, int threads) {
     const size_t smem = qsk::res_smem_bytes(NS, V, TT, threads);
     // shared-memory opt-in (dynamic + static may pass 48 KiB), raised as larger CTAs appear
     static size_t opted = 0;
     if (smem > opted) {
-        cudaError_t e = cudaFuncSetAttribute(qsk::k_sweep_res<NS, V, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(qsk::k_sweep_res<NS, V, TT, UW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         opted = smem;
     }
-    qsk::k_sweep_res<NS, V, TT><<<grid, threads, smem, c->stream>>>(a);
+    qsk::k_sweep_res<NS, V, TT, UW><<<grid, threads, smem, c->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -429,6 +433,17 @@ cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V, b
     if (regs && c->NS == 1 && V == 32) return T <= 256 ? launch_res_t<1, 32, 0>(c, a, grid, T) : cudaErrorInvalidValue;
     if (regs && c->NS == 2 && V == 16) return T <= 256 ? launch_res_t<2, 16, 0>(c, a, grid, T) : cudaErrorInvalidValue;
     if (c->NS == 1) {
+        // uniform profiles whose lines fill whole warps: the cell weight in a register
+        if (V == 32 && c->uw_fit && !c->dbg_no_uw) switch (T) {
+            case 64: return launch_res_t<1, 32, 64, true>(c, a, grid, T);
+            case 96: return launch_res_t<1, 32, 96, true>(c, a, grid, T);
+            case 128: return launch_res_t<1, 32, 128, true>(c, a, grid, T);
+            case 160: return launch_res_t<1, 32, 160, true>(c, a, grid, T);
+            case 192: return launch_res_t<1, 32, 192, true>(c, a, grid, T);
+            case 224: return launch_res_t<1, 32, 224, true>(c, a, grid, T);
+            case 256: return launch_res_t<1, 32, 256, true>(c, a, grid, T);
+            default: return cudaErrorInvalidValue;
+            }
         if (V == 32) switch (T) {   // every whole number of 64-thread lines up to 4, and 96 .. 224 for 96-thread lines
             case 64: return launch_res_t<1, 32, 64>(c, a, grid, T);
             case 96: return launch_res_t<1, 32, 96>(c, a, grid, T);
@@ -696,6 +711,8 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
             for (int s = 0; s < c->NS; ++s) w_all.push_back(q.dt * q.species[s].density_ratio * shp[j]);
             uni = uni && shp[j] == shp[0];
         }
+        for (int s = 0; s < 2; ++s)   // the cell weight of a uniform profile, as the FP32 path stores it
+            I.wu[s] = s < c->NS ? (float)(q.dt * q.species[s].density_ratio * shp[0]) : 0.0f;
         c->uniform = (i == 0 || c->uniform) && uni;
         {
             double lc = 0.0;
@@ -709,6 +726,9 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
     }
     c->cells_total = cell;
     c->groups_total = grp;
+    if (const char *v = getenv("QS_RES_NO_UNIFORM")) c->dbg_no_uw = v[0] == '1';
+    c->uw_fit = c->uniform;
+    for (int i = 0; i < n_inst; ++i) c->uw_fit = c->uw_fit && c->inst[i].n_xi % (32 * 32) == 0;
     c->pin.assign(n_inst, *p);
     for (int i = 0; per_inst && i < n_inst; ++i) c->pin[i] = per_inst[i];
     // per-mode tables (padding modes: k = 0, never stepped)

@@ -401,3 +401,22 @@ def test_renormalisation_interval_from_growth_bound(qs):
         s.step_green(1)
     assert e.value.status == qs.QS_ERR_UNSUPPORTED
     s.close()
+
+
+def test_uniform_weight_kernel(qs, monkeypatch):
+    """Uniform profile whose lines fill whole warps (1024 cells, 32 per
+    thread): the resident kernel that holds the cell weight in a register
+    against the one that reads per-cell weights, bit for bit, and against the
+    FP64 oracle; 40 steps include renormalisation checks."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=1024, dxi=0.05, length=1024 * 0.05, k_list=[0.3, 0.9, 1.7, 2.6],
+                     profile="flattop", gamma_b=20.0, dt=1.5)
+    out = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("QS_RES_NO_UNIFORM", env)
+        s, nb, th = _run_gpu(qs, p, "fp32", 40, seed=("noise", 5, 1e-6), launch=_res(32, 2))
+        out[env] = (nb, th)
+        s.close()
+    assert np.array_equal(out["0"][0], out["1"][0]) and np.array_equal(out["0"][1], out["1"][1])
+    nb_o, th_o = _run_oracle(p, 40, seed=("noise", 5, 1e-6))
+    assert _log_err(out["0"][0], nb_o) <= FP32_LOG_TOL
+    assert _log_err(out["0"][1], th_o) <= FP32_LOG_TOL
