@@ -77,34 +77,47 @@ __device__ __forceinline__ GemmArgs for_member(const GemmArgs &g0, int &zz, int 
 }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-// GELU with erf from Abramowitz & Stegun, Handbook of Mathematical Functions,
-// formula 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^(-x^2),
-// t = 1 / (1 + p x) for x >= 0, odd in x, |error| <= 1.5e-7 on the real line.
-// Used by the fused kernel, whose activations are rounded to bf16 next (the
-// GELU's relative error, <= 4e-6, is far below bf16's 2^-8).
-__device__ __forceinline__ float gelu_as(float z) {
-    const float x = z * 0.70710678118654752f, ax = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    const float e = 1.0f - poly * __expf(-ax * ax);
-    return 0.5f * z * (1.0f + copysignf(e, x));
-}
 __device__ __forceinline__ float dgelu(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// GELU and its derivative from one exponential (Abramowitz & Stegun 7.1.26
-// as in gelu_as): gelu'(z) = Phi(z) + z phi(z), phi(z) = e^(-z^2/2)/sqrt(2 pi)
-__device__ __forceinline__ void gelu_dgelu_as(float z, float &g, float &dg) {
-    const float x = z * 0.70710678118654752f, ax = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    const float ex = __expf(-ax * ax);
-    const float Phi = 0.5f * (1.0f + copysignf(1.0f - poly * ex, x));
-    g = z * Phi;
-    dg = fmaf(z * 0.39894228040143268f, ex, Phi);
+// GELU and its derivative for the fused kernels, on a pair of values, with
+// erf from Abramowitz & Stegun, Handbook of Mathematical Functions, formula
+// 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^(-x^2),
+// t = 1 / (1 + p x) for x >= 0, odd in x, |error| <= 1.5e-7 on the real
+// line.  The activations are rounded to bf16 next (spacing 2^-8), far above
+// the GELU's relative error (<= 4e-6).  gelu'(z) = Phi(z) + z phi(z),
+// phi(z) = e^(-z^2/2)/sqrt(2 pi), reuses the same exponential.  The
+// polynomial and the products are packed FP32x2 operations (each lane
+// rounded as its scalar counterpart), the reciprocal and the exponential
+// per lane.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ void gelu_as_core2(float2 z, float2 &phi2, float2 &ex) {
+    const float2 x = __fmul2_rn(z, f2(0.70710678118654752f));
+    const float2 ax = make_float2(fabsf(x.x), fabsf(x.y));
+    const float2 den = __ffma2_rn(f2(0.3275911f), ax, f2(1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    float2 p = __ffma2_rn(t, f2(1.061405429f), f2(-1.453152027f));
+    p = __ffma2_rn(t, p, f2(1.421413741f));
+    p = __ffma2_rn(t, p, f2(-0.284496736f));
+    p = __ffma2_rn(t, p, f2(0.254829592f));
+    p = __fmul2_rn(t, p);
+    const float2 sq = __fmul2_rn(ax, ax);
+    ex = make_float2(__expf(-sq.x), __expf(-sq.y));
+    const float2 e = __ffma2_rn(make_float2(-p.x, -p.y), ex, f2(1.0f));   // erf(|x|)
+    // Phi(z) = (1 + erf(x)) / 2 with erf odd in x
+    phi2 = __ffma2_rn(make_float2(copysignf(e.x, x.x), copysignf(e.y, x.y)), f2(0.5f), f2(0.5f));
+}
+__device__ __forceinline__ float2 gelu2_as(float2 z) {
+    float2 phi, ex;
+    gelu_as_core2(z, phi, ex);
+    return __fmul2_rn(z, phi);
+}
+__device__ __forceinline__ void gelu_dgelu2_as(float2 z, float2 &g, float2 &dg) {
+    float2 phi, ex;
+    gelu_as_core2(z, phi, ex);
+    g = __fmul2_rn(z, phi);
+    dg = __ffma2_rn(__fmul2_rn(z, f2(0.39894228040143268f)), ex, phi);   // Phi + z phi(z)
 }
 
 // Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j):
@@ -621,7 +634,7 @@ constexpr int W = 256, KIN = 16;
 constexpr uint32_t SBO_W = (W / 8) * 128, SBO_I = (KIN / 8) * 128, LBO = 128;
 constexpr size_t OFF_WB = 0, OFF_AB = OFF_WB + (size_t)W * W * 2, OFF_W0 = OFF_AB + (size_t)128 * W * 2,
                  OFF_A0 = OFF_W0 + (size_t)W * KIN * 2, OFF_BIAS = OFF_A0 + (size_t)128 * KIN * 2,
-                 OFF_W3 = OFF_BIAS + 3 * W * 4, OFF_PART = OFF_W3 + 2 * W * 4 + 16, OFF_RED = OFF_PART + 128 * 2 * 4,
+                 OFF_W3 = OFF_BIAS + 3 * W * 4, OFF_PART = OFF_W3 + 2 * W * 4 + 16, OFF_RED = OFF_PART + 3 * 128 * 2 * 4,
                  SMEM = OFF_RED + 3 * W * 4;
 static_assert(SMEM <= 227 * 1024, "fused kernel shared memory");
 
@@ -640,9 +653,13 @@ __device__ __forceinline__ void stage(unsigned char *dst, const __nv_bfloat16 *s
 
 }  // namespace fz
 
-template <bool TRAIN>
-__global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
+// NT threads: NT / 128 groups of 4 warps, each group one TMEM lane quarter
+// per warp and W / (NT / 128) accumulator columns (training: 256 threads)
+template <bool TRAIN, int NT = 256>
+__global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
     using namespace fz;
+    static_assert(NT == 256 || (NT == 512 && !TRAIN), "256 threads, or 512 for inference");
+    constexpr int NQ = NT / 128, CW = W / NQ, NCH = CW / 32;   // column groups, columns per group, 32-column chunks
     extern __shared__ __align__(1024) unsigned char sf[];
     unsigned char *Wb = sf + OFF_WB, *Ab = sf + OFF_AB, *W0s = sf + OFF_W0, *A0 = sf + OFF_A0;
     float *bias = reinterpret_cast<float *>(sf + OFF_BIAS), *w3 = reinterpret_cast<float *>(sf + OFF_W3);
@@ -652,7 +669,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
     __shared__ uint32_t taddr_s;
     __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, hc = warp >> 2;    // TMEM lane quarter, column half
+    const int q = warp & 3, hc = warp >> 2;    // TMEM lane quarter, column group
     const int row = 32 * q + lane;             // the tile row this thread's TMEM lane holds
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&taddr_s)), "r"(W));
@@ -664,7 +681,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
         s_bad = 0;
     }
     if (TRAIN)
-        for (int i = tid; i < 3 * W; i += 256) red[i] = 0.0f;
+        for (int i = tid; i < 3 * W; i += NT) red[i] = 0.0f;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -710,25 +727,25 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
         const long long gr = r0 + row;
         const bool keep = TRAIN && gr < a.n;
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            const int c0 = 128 * hc + 32 * c;
+        for (int c = 0; c < NCH; ++c) {
+            const int c0 = CW * hc + 32 * c;
             float v[32];
             fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] += b[c0 + j];
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
                 __nv_bfloat162 h2[4], d2[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
+                    const float2 z = __fadd2_rn(make_float2(v[j + 2 * t], v[j + 2 * t + 1]),
+                                                *reinterpret_cast<const float2 *>(b + c0 + j + 2 * t));
                     if (TRAIN) {
-                        float g0, g1, dg0, dg1;
-                        gelu_dgelu_as(v[j + 2 * t], g0, dg0);
-                        gelu_dgelu_as(v[j + 2 * t + 1], g1, dg1);
-                        h2[t] = __floats2bfloat162_rn(g0, g1);
-                        d2[t] = __floats2bfloat162_rn(dg0, dg1);
+                        float2 g, dg;
+                        gelu_dgelu2_as(z, g, dg);
+                        h2[t] = __floats2bfloat162_rn(g.x, g.y);
+                        d2[t] = __floats2bfloat162_rn(dg.x, dg.y);
                     } else {
-                        h2[t] = __floats2bfloat162_rn(gelu_as(v[j + 2 * t]), gelu_as(v[j + 2 * t + 1]));
+                        const float2 g = gelu2_as(z);
+                        h2[t] = __floats2bfloat162_rn(g.x, g.y);
                     }
                 }
                 *reinterpret_cast<uint4 *>(Ab + (row / 8) * SBO_W + ((c0 + j) / 8) * LBO + (row % 8) * 16) =
@@ -769,19 +786,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
         for (int e = e_lo; e < e_hi && ok; ++e) {
             const __nv_bfloat16 *Pm = a.Pb + (long long)e * a.nparam;
             const float *Pf = a.P + (long long)e * a.nparam;
-            stage<KIN>(W0s, Pm + a.w0, W, tid, 256);
-            for (int i = tid; i < W; i += 256) {
+            stage<KIN>(W0s, Pm + a.w0, W, tid, NT);
+            for (int i = tid; i < W; i += NT) {
                 bias[i] = Pf[a.b0 + i]; bias[W + i] = Pf[a.b1 + i]; bias[2 * W + i] = Pf[a.b2 + i];
                 w3[i] = __bfloat162float(Pm[a.w3 + i]); w3[W + i] = __bfloat162float(Pm[a.w3 + W + i]);
             }
             if (tid < 2) w3[2 * W + tid] = Pf[a.b3 + tid];
             sync_for_mma();
             mma_layer(A0, W0s, 1, SBO_I);                       // layer 0: K = 16
-            stage<W>(Wb, Pm + a.w1, W, tid, 256);               // W1 lands during the epilogue
+            stage<W>(Wb, Pm + a.w1, W, tid, NT);               // W1 lands during the epilogue
             epilogue_hidden(bias, 0, r0, e);
             sync_for_mma();
             mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 1
-            stage<W>(Wb, Pm + a.w2, W, tid, 256);               // W2 lands during the epilogue
+            stage<W>(Wb, Pm + a.w2, W, tid, NT);               // W2 lands during the epilogue
             epilogue_hidden(bias + W, 1, r0, e);
             sync_for_mma();
             mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 2
@@ -790,24 +807,32 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
             float o0 = 0.f, o1 = 0.f;
             const long long gr = r0 + row;
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                const int c0 = 128 * hc + 32 * c;
+            for (int c = 0; c < NCH; ++c) {
+                const int c0 = CW * hc + 32 * c;
                 float v[32];
                 fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float h = __bfloat162float(__float2bfloat16(gelu_as(v[j] + bias[2 * W + c0 + j])));
-                    o0 = fmaf(h, w3[c0 + j], o0);
-                    o1 = fmaf(h, w3[W + c0 + j], o1);
+                for (int j = 0; j < 32; j += 2) {
+                    const float2 z = __fadd2_rn(make_float2(v[j], v[j + 1]),
+                                                *reinterpret_cast<const float2 *>(bias + 2 * W + c0 + j));
+                    const float2 g = gelu2_as(z);
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(g.x, g.y);
+                    const float h0 = __low2float(hb), h1 = __high2float(hb);
+                    o0 = fmaf(h0, w3[c0 + j], o0);
+                    o1 = fmaf(h0, w3[W + c0 + j], o1);
+                    o0 = fmaf(h1, w3[c0 + j + 1], o0);
+                    o1 = fmaf(h1, w3[W + c0 + j + 1], o1);
                 }
             }
-            if (hc == 1) { part[2 * row] = o0; part[2 * row + 1] = o1; }
+            if (hc > 0) { part[(hc - 1) * 256 + 2 * row] = o0; part[(hc - 1) * 256 + 2 * row + 1] = o1; }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (hc == 0) {
-                const float r0u = o0 + part[2 * row] + w3[2 * W];    // raw outputs (standardised units)
-                const float y1 = o1 + part[2 * row + 1] + w3[2 * W + 1];
+#pragma unroll
+                for (int g = 1; g < NQ; ++g) { o0 += part[(g - 1) * 256 + 2 * row]; o1 += part[(g - 1) * 256 + 2 * row + 1]; }
+                const float r0u = o0 + w3[2 * W];    // raw outputs (standardised units)
+                const float y1 = o1 + w3[2 * W + 1];
                 if (TRAIN) {
                     // loss and its gradient for the row: squared error of the
                     // standardised regression output plus BCE-with-logits of
@@ -849,16 +874,21 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
                 const float g0 = part[2 * row], g1 = part[2 * row + 1];
                 const bool keep = gr < a.n;
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    const int c0 = 128 * hc + 32 * c;
+                for (int c = 0; c < NCH; ++c) {
+                    const int c0 = CW * hc + 32 * c;
                     float hv[32], dz[32], t[32];
                     fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, hv);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float gl, dg;
-                        gelu_dgelu_as(hv[j] + bias[2 * W + c0 + j], gl, dg);
-                        hv[j] = __bfloat162float(__float2bfloat16(gl));
-                        dz[j] = fmaf(g0, w3[c0 + j], g1 * w3[W + c0 + j]) * dg;
+                    for (int j = 0; j < 32; j += 2) {
+                        float2 gl, dg;
+                        gelu_dgelu2_as(__fadd2_rn(make_float2(hv[j], hv[j + 1]),
+                                                  *reinterpret_cast<const float2 *>(bias + 2 * W + c0 + j)),
+                                       gl, dg);
+                        const __nv_bfloat162 hb = __floats2bfloat162_rn(gl.x, gl.y);
+                        hv[j] = __low2float(hb);
+                        hv[j + 1] = __high2float(hb);
+                        dz[j] = fmaf(g0, w3[c0 + j], g1 * w3[W + c0 + j]) * dg.x;
+                        dz[j + 1] = fmaf(g0, w3[c0 + j + 1], g1 * w3[W + c0 + j + 1]) * dg.y;
                     }
                     if (keep) {
                         __nv_bfloat16 *dzr = a.DZ + e * a.as + gr * W + c0;
@@ -886,7 +916,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fused(const FusedArgs a) {
                 }
                 __syncthreads();
                 float *Gm = a.G + (long long)e * a.nparam;
-                for (int i = tid; i < 3 * W; i += 256) {
+                for (int i = tid; i < 3 * W; i += NT) {
                     const float v = red[i];
                     red[i] = 0.0f;
                     atomicAdd(Gm + (i < 2 * W ? a.w3 + i : a.b2 + (i - 2 * W)), v);
@@ -1450,7 +1480,7 @@ mlp::FusedArgs fused_args(qs_mlp *m, const float *X, long long n) {
 bool fused_launch(qs_mlp *m, const mlp::FusedArgs &fa, bool train) {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(mlp::k_mlp_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(mlp::k_mlp_fused<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)mlp::fz::SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(mlp::k_mlp_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)mlp::fz::SMEM) != cudaSuccess)
@@ -1463,7 +1493,7 @@ bool fused_launch(qs_mlp *m, const mlp::FusedArgs &fa, bool train) {
     const long long items = (fa.n + 127) / 128 * (train ? fa.E : 1);
     const unsigned grid = (unsigned)std::min<long long>(nsm, items);
     if (train) mlp::k_mlp_fused<true><<<grid, 256, mlp::fz::SMEM, m->stream>>>(fa);
-    else mlp::k_mlp_fused<false><<<grid, 256, mlp::fz::SMEM, m->stream>>>(fa);
+    else mlp::k_mlp_fused<false, 512><<<grid, 512, mlp::fz::SMEM, m->stream>>>(fa);
     return cudaGetLastError() == cudaSuccess;
 }
 
