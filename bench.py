@@ -710,9 +710,11 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers ----
     # Two contexts on two streams: while one sweeps job i, the other's state
-    # for job i + 1 is restored from pinned host memory (copy engine), and job
-    # i's per-mode maxima are read back after it ends.  Every job still pays
-    # its own H2D restore and D2H read inside the timed region.
+    # for job i + 1 is restored from pinned host memory (copy engine); then
+    # job i's per-mode maxima are read back, and only then is job i + 1's
+    # sweep launched, so that the small read-back kernel is not queued behind
+    # the next sweep's blocks and the two sweeps never share the SMs.  Every
+    # job still pays its own H2D restore and D2H read inside the timed region.
     e2e = None
     if args.e2e and args.steps > 0:
         s.seed_noise(rank, p["amplitude"])
@@ -744,9 +746,9 @@ def run_ours(args):
         for i in range(args.steps):
             sv = ctxs[i % 2]
             restore(sv)             # overlaps the previous job's sweep on the other stream
-            sv.step(job)
             if prev is not None:
-                read_max(prev)
+                read_max(prev)      # the previous job's result (waits for its sweep)
+            sv.step(job)
             prev = sv
         read_max(prev)
         barrier()

@@ -877,9 +877,11 @@ qs_status qs_r2_read(qs_r2 *c, int what, float *out, size_t out_bytes, int on_ho
 
 qs_status qs_r2_sync(qs_r2 *c) {
     if (!c) return QS_ERR_ARG;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return QS_ERR_CUDA;
     int e = 0;
-    if (cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return QS_ERR_CUDA;
+    // on the context's stream (a plain cudaMemcpy would wait for every blocking stream)
+    if (cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return QS_ERR_CUDA;
     return e ? QS_ERR_NONFINITE : QS_OK;
 }
 

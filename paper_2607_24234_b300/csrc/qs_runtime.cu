@@ -64,6 +64,8 @@ struct qs_ctx {
     bool has_alloc = false;
     cudaStream_t stream = nullptr;
     std::vector<DevBuf> bufs;
+    void *diag_tmp = nullptr;           // staging of host-form qs_diag results (kept: a free would
+    size_t diag_tmp_bytes = 0;          // synchronise the whole device), one of bufs
     void *st = nullptr, *th = nullptr;
     int *ex = nullptr;
     InstDev *inst_d = nullptr;
@@ -817,7 +819,10 @@ qs_status qs_seed(qs_ctx *c, uint64_t seed, double amplitude, int kind, const vo
         int64_t hdr[8];
         cudaMemcpyKind k = user_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
         if (user_on_host) memcpy(hdr, user, 64);
-        else CU(c, cudaMemcpy(hdr, user, 64, cudaMemcpyDeviceToHost));
+        else {
+            CU(c, cudaMemcpyAsync(hdr, user, 64, cudaMemcpyDeviceToHost, c->stream));
+            CU(c, cudaStreamSynchronize(c->stream));
+        }
         if (hdr[0] != 0x51534350 || hdr[1] != c->prec || hdr[2] != c->NS || hdr[3] != c->Mp ||
             hdr[4] != c->cells_total)
             return fail(c, QS_ERR_ARG, "checkpoint does not match this context");
@@ -970,7 +975,6 @@ qs_status qs_diag(qs_ctx *c, int kind, void *out, size_t out_bytes, int out_on_h
     }
     size_t need;
     double *dst = nullptr;
-    void *tmp = nullptr;
     if (kind == QS_DIAG_WAKE0) {
         need = (size_t)c->cells_total * 2 * sizeof(double);
     } else if (kind >= 1 && kind <= 7) {
@@ -982,9 +986,23 @@ qs_status qs_diag(qs_ctx *c, int kind, void *out, size_t out_bytes, int out_on_h
     }
     if (out_bytes < need) return fail(c, QS_ERR_ARG, "diag needs %zu bytes", need);
     if (out_on_host) {
-        qs_status s = dalloc(c, need, &tmp);
-        if (s) return s;
-        dst = static_cast<double *>(tmp);
+        if (c->diag_tmp_bytes < need) {   // grow the staging buffer (rare)
+            if (c->diag_tmp) {
+                CU(c, cudaStreamSynchronize(c->stream));
+                for (size_t i = 0; i < c->bufs.size(); ++i)
+                    if (c->bufs[i].p == c->diag_tmp) {
+                        if (c->has_alloc) c->alloc.free(c->diag_tmp, c->alloc.user); else cudaFree(c->diag_tmp);
+                        c->bufs.erase(c->bufs.begin() + i);
+                        break;
+                    }
+                c->diag_tmp = nullptr;
+                c->diag_tmp_bytes = 0;
+            }
+            qs_status s = dalloc(c, need, &c->diag_tmp);
+            if (s) return s;
+            c->diag_tmp_bytes = need;
+        }
+        dst = static_cast<double *>(c->diag_tmp);
     } else {
         dst = static_cast<double *>(out);
     }
@@ -1003,12 +1021,6 @@ qs_status qs_diag(qs_ctx *c, int kind, void *out, size_t out_bytes, int out_on_h
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) s = fail(c, QS_ERR_CUDA, "diag copy: %s", cudaGetErrorString(e));
         }
-        for (size_t i = 0; i < c->bufs.size(); ++i)
-            if (c->bufs[i].p == tmp) {
-                if (c->has_alloc) c->alloc.free(tmp, c->alloc.user); else cudaFree(tmp);
-                c->bufs.erase(c->bufs.begin() + i);
-                break;
-            }
         if (s == QS_OK) s = qs_sync(c);
     }
     return s;
@@ -1107,9 +1119,11 @@ qs_status qs_sync(qs_ctx *c) {
     if (!c) return QS_ERR_ARG;
     qs_status cs = check_canaries(c);
     if (cs) return cs;
-    CU(c, cudaStreamSynchronize(c->stream));
     int e[4] = {0, 0, 0, 0};
-    CU(c, cudaMemcpy(e, c->err_d, sizeof e, cudaMemcpyDeviceToHost));
+    // on the context's stream: a plain cudaMemcpy would also wait for every
+    // other blocking stream of the device
+    CU(c, cudaMemcpyAsync(e, c->err_d, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
     if (e[0]) {
         c->poisoned = true;
         if (e[0] & qsk::ERR_CANARY)
