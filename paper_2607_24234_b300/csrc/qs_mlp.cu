@@ -4,10 +4,18 @@
 // erf form) -> n_out, BF16 weights and activations, FP32 accumulation, FP32
 // master weights, Adam.  Loss per sample: (p0 - y0)^2 + BCE-with-logits(p1,
 // y1).  Inputs are standardised in the first kernel with stored statistics.
-// GEMMs run on the tensor cores (mma.sync m16n8k16 BF16 -> FP32) from
-// shared-memory tiles; bias, GELU, GELU' and the casts are fused into the
-// GEMM epilogues.  The members of an ensemble are independent networks
-// (different initial weights) trained on the same batches.
+// The surrogate's shape (16 -> 256 x 3 -> 2) runs on the fifth-generation
+// tensor cores (tcgen05.mma, accumulators in tensor memory):
+//   k_mlp_fused  inference: every layer of a 128-row tile on chip, the
+//                ensemble statistics in the last epilogue; training: the
+//                forward, the loss and the output layer's backward;
+//   k_dx_tc      input gradients, fused with gelu' and the bias gradient;
+//   k_wgrad_tc   weight gradients (a cp.async ring over batch slices).
+// Other shapes take a layer-by-layer path: k_gemm_tc (tcgen05) and k_gemm
+// (mma.sync m16n8k16) with bias, GELU, GELU' and the casts fused into the
+// epilogues.  The members of an ensemble are independent networks
+// (different initial weights) trained on the same batches, in the same
+// launches.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -7,7 +7,9 @@
 //      exact cell propagator and writes n_p at the cell centres;
 //   B. per xi slice, the screened Poisson solve of Eq. (14),
 //      Psi^ = n_p^ / (1 + k^2), and grad_perp Psi by spectral derivatives,
-//      with hand-written radix-2 Stockham FFTs in shared memory:
+//      with hand-written FFTs: at N = 256 register four-step transforms by
+//      16-thread teams (k_rowfft256, k_colfft256, k_rowinv_push256), at
+//      N = 32..128 radix-2 Stockham transforms in shared memory:
 //        K1  row FFTs along z (two real rows packed per complex FFT) ->
 //            half spectrum S1 [xi][y][N/2+1];
 //        K2  column FFTs along y, multiply by kappa and i k_y kappa, two
