@@ -590,3 +590,20 @@ def test_beam3d_full_size_sampled(qs, prec):
         assert _line_rel(nb, nb_o) <= FP64_TOL and _line_rel(th, th_o) <= FP64_TOL
     else:
         assert _log_err(nb, nb_o) <= FP32_LOG_TOL and _log_err(th, th_o) <= FP32_LOG_TOL
+
+
+def test_host_diag_staging_reuse(qs):
+    """Host-form snapshots share one staging buffer per context, grown when a
+    larger kind is asked for: small, large, small again, each equal to the
+    device-form snapshot of the same step (the entries of real modes; the
+    padding modes' entries are not written)."""
+    p, held, user, sd, steps = _small_problem(max(SMALL, key=lambda c: c[0] * len(c[1])))
+    s, _, _ = _run_gpu(qs, p, "fp32", 3, seed=sd, held=held, user=user)
+    M = len(p["k_list"])
+    for kind in (qs.REC_MODEMAX, qs.REC_MAG | qs.REC_NP, qs.REC_MODEMAX, qs.REC_MAG):
+        h = s.split_snapshot(s.diag(kind, host=True), kind)
+        d = s.split_snapshot(s.diag(kind, host=False).cpu().numpy(), kind)
+        assert h.keys() == d.keys()
+        for key in h:
+            assert np.array_equal(h[key][..., :M], d[key][..., :M]), (kind, key)
+    s.close()
