@@ -94,8 +94,13 @@ def sweep_roofline(launch, upd, launch_s, traffic, pk, pk_kind, alu=None):
             peak = fp32_alu_peak_derived(pk)
             src = "derived: 148 SMs x 128 FP32 lanes x max SM clock (an FMA is one op)"
         ach = FP32_INSTR_PER_UPDATE * upd / launch_s
+        extra = {}
+        if alu and alu.get("ffma2", {}).get("lane_ops_per_s"):
+            # the kernel's FMAs are packed f32x2: their own measured rate
+            pp = alu["ffma2"]["lane_ops_per_s"]
+            extra = {"packed_fma_peak": pp / 1e12, "frac_of_packed_fma": ach / pp}
         return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "T FP32-ops/s",
-                "frac": ach / peak, "traffic": traffic, "peak_source": src,
+                "frac": ach / peak, **extra, "traffic": traffic, "peak_source": src,
                 "algorithmic_fp32_ops_per_update": FP32_INSTR_PER_UPDATE,
                 "kernel": f"qsk::k_sweep_res<1,{launch.get('prefetch')},T> (CTA of T <= {32 * launch.get('warps_per_cta')} "
                           "threads: a whole number of lines)",
