@@ -420,3 +420,34 @@ def test_uniform_weight_kernel(qs, monkeypatch):
     nb_o, th_o = _run_oracle(p, 40, seed=("noise", 5, 1e-6))
     assert _log_err(out["0"][0], nb_o) <= FP32_LOG_TOL
     assert _log_err(out["0"][1], th_o) <= FP32_LOG_TOL
+
+
+@pytest.mark.parametrize("pers", [0, 1])
+def test_uniform_weight_kernel_instances(qs, monkeypatch, pers):
+    """Two uniform instances of different density, gamma and length (1024 and
+    2048 cells: one and two warps per line, four and two lines per 128-thread
+    CTA) through the uniform-weight kernel, each line with its own instance's
+    weight: bit for bit the per-cell-weight kernel, and each instance against
+    its oracle."""
+    base = synth.scaled(synth.SLAB_2D, dxi=0.05, k_list=[0.3, 0.9, 1.7, 2.6], profile="flattop", dt=1.5)
+    insts = [synth.scaled(base, n_xi=1024, length=1024 * 0.05, gamma_b=20.0, species=[(-1.0, 1.0, 0.02)]),
+             synth.scaled(base, n_xi=2048, length=2048 * 0.05, gamma_b=50.0, species=[(-1.0, 1.0, 0.05)])]
+    out = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("QS_RES_NO_UNIFORM", env)
+        s = qs.Solver(insts, prec="fp32")
+        s.set_launch(**_res(32, 4, pers, 2))
+        s.seed_noise(0, 1e-6)
+        s.step(40)
+        s.sync()
+        out[env] = s.state_arrays()
+        s.close()
+    for a, b in zip(out["0"], out["1"]):
+        for i in range(2):
+            assert np.array_equal(a[i], b[i]), i
+    nb, th = out["0"]
+    for i, p in enumerate(insts):
+        nb_o, th_o = oracle.seed_noise(p, 0, 1e-6, inst=i)
+        oracle.sweep(p, nb_o, th_o, 0, 40)
+        assert _log_err(nb[i], nb_o) <= FP32_LOG_TOL, i
+        assert _log_err(th[i], th_o) <= FP32_LOG_TOL, i
