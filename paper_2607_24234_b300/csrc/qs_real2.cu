@@ -11,15 +11,18 @@
 //      16-thread teams (k_rowfft256, k_colfft256, k_rowinv_push256), at
 //      N = 32..128 radix-2 Stockham transforms in shared memory:
 //        K1  row FFTs along z (two real rows packed per complex FFT) ->
-//            half spectrum S1 [xi][y][N/2+1];
+//            half spectrum S1 [xi][y][N/2+1] ([xi][N/2+1][y] at N = 256);
 //        K2  column FFTs along y, multiply by kappa and i k_y kappa, two
-//            inverse column FFTs -> T1 = Psi~, T2 = (d_y Psi)~ [xi][y][N/2+1];
+//            inverse column FFTs -> T1 = Psi~, T2 = (d_y Psi)~ (same layout);
 //        K3  inverse row FFTs (Psi and d_z Psi packed as real/imag of one
 //            FFT, d_y Psi of two rows packed in another) fused with the push
 //            d_tau G = -(q/(m gamma)) [n_b0 (Psi - n_p) + grad n_b0 . grad Psi],
 //            n_b += dt G (kick-drift leapfrog, first kick dt/2).
 // The gamma^-3 term is dropped here (gamma_b >> 1 for narrow-beam cases).
-// State and intermediates are FP32, laid out [xi][y][z] with z fastest.
+// State and intermediates are FP32; the state is laid out [xi][y][z] with z
+// fastest.  At N = 256 the half spectra are column-major, so the column
+// transforms move whole columns as contiguous runs and the row kernels do
+// the transposition in the shared-memory staging they need anyway.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -183,11 +186,13 @@ __device__ __forceinline__ void make_tw256(float2 *tw) {
     }
 }
 
-// K1 for N = 256: 32 rows (16 packed) per CTA, 16 teams
+// K1 for N = 256: 32 rows (16 packed) per CTA, 16 teams.  S1 is stored
+// column-major, [xi][k_z][y], so that the column transforms read and write
+// whole 256-entry columns as contiguous runs.
 __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np, float2 *__restrict__ S1) {
-    constexpr int N = 256, NH = 129, PR = 16;
+    constexpr int N = 256, NH = 129, PR = 16, LA = N + 2;   // LA: packed-row stride (16-byte aligned rows)
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + TWN, *T = A + PR * N;
+    float2 *tw = sm, *A = sm + TWN, *T = A + PR * LA;
     const long long slice = blockIdx.y;
     const int r0 = blockIdx.x * 2 * PR;
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
     // r0 + 2 pr + 1 land side by side (as floats) in packed row pr
     for (int i = threadIdx.x; i < 2 * PR * N / 4; i += blockDim.x) {
         const int row = i >> 6, c4 = i & 63;
-        float *d = reinterpret_cast<float *>(A + (row >> 1) * N) + (row & 1) * N + 4 * c4;
+        float *d = reinterpret_cast<float *>(A + (row >> 1) * LA) + (row & 1) * N + 4 * c4;
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(d)),
                      "l"(src + (long long)(r0 + row) * N + 4 * c4) : "memory");
     }
@@ -206,21 +211,24 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
     __syncthreads();
     {
         // team pr: the complex row (row 2 pr) + i (row 2 pr + 1), transformed in place
-        const float *rf = reinterpret_cast<const float *>(A + team * N);
+        const float *rf = reinterpret_cast<const float *>(A + team * LA);
         float2 x[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) x[m] = make_float2(rf[t + 16 * m], rf[N + t + 16 * m]);
         fft256_reg<false>(x, T + team * 272, tw, t);   // (its warp barriers order the reads before the writes)
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) A[team * N + t + 16 * k2] = x[k2];
+        for (int k2 = 0; k2 < 16; ++k2) A[team * LA + t + 16 * k2] = x[k2];
     }
     __syncthreads();
-    float2 *dst = S1 + slice * (long long)N * NH;
+    // split each packed transform into its two rows' half spectra; the two
+    // rows' entries at one k_z are neighbours in S1 (one 16-byte store), and
+    // a warp stores 256 contiguous bytes for each of two k_z
+    float2 *dst = S1 + slice * (long long)N * NH + r0;
     for (int i = threadIdx.x; i < PR * NH; i += blockDim.x) {
-        const int pr = i / NH, k = i - pr * NH;
-        const float2 Z = A[pr * N + k], Zc = A[pr * N + ((N - k) & (N - 1))];
-        dst[(long long)(r0 + 2 * pr) * NH + k] = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y));
-        dst[(long long)(r0 + 2 * pr + 1) * NH + k] = make_float2(0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x));
+        const int pr = i & (PR - 1), k = i >> 4;
+        const float2 Z = A[pr * LA + k], Zc = A[pr * LA + ((N - k) & (N - 1))];
+        __stcg(reinterpret_cast<float4 *>(dst + (long long)k * N + 2 * pr),
+               make_float4(0.5f * (Z.x + Zc.x), 0.5f * (Z.y - Zc.y), 0.5f * (Z.y + Zc.y), -0.5f * (Z.x - Zc.x)));
     }
 }
 
@@ -228,42 +236,34 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
 // one slice, one per team.  Columns 0 and 128 (k_z = 0 and the Nyquist
 // column) are real sequences along y, so team 0 of block 0 transforms them
 // as the real and imaginary parts of one complex column and 16 blocks cover
-// the 129 columns.  The columns are staged in shared memory (padded column
-// stride; 8-byte asynchronous copies, all in flight at once); each team
-// keeps its column in registers through the forward transform, the kappa
-// and i k_y kappa products and both inverse transforms, and the results
-// pass through the staging buffer again for row-contiguous stores.
-__global__ void __launch_bounds__(128) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
-                                                   float2 *__restrict__ T2, float ly, float lz) {
-    constexpr int N = 256, NH = 129, CB = 8, LD = N + 4, TSZ = 272;   // LD: the 8 columns of a row in distinct banks
+// the 129 columns.  S1, T1 and T2 are column-major ([xi][k_z][y]): a team
+// loads its column straight into registers (16 threads read 128 contiguous
+// bytes per access, a warp's two teams 256), keeps it there through the
+// forward transform, the kappa and i k_y kappa products and both inverse
+// transforms, and stores the results the same way; shared memory holds only
+// the twiddles and the transforms' exchange buffers.
+__global__ void __launch_bounds__(128, 4) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
+                                                      float2 *__restrict__ T2, float ly, float lz) {
+    constexpr int N = 256, NH = 129, CB = 8, TSZ = 272;
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + TWN, *Ts = A + (CB + 1) * LD + (threadIdx.x >> 4) * TSZ;
-    const long long slice = blockIdx.y;
+    float2 *tw = sm, *Ts = sm + TWN + (threadIdx.x >> 4) * TSZ;
+    const long long so = blockIdx.y * (long long)N * NH;
     const int c0 = blockIdx.x * CB;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15, warp = threadIdx.x >> 5;
     const bool first = blockIdx.x == 0;
     const bool pk = first && tm == 0;            // columns 0 and 128 packed
     const bool w0 = first && warp == 0;          // (warp-uniform) the warp holding the packed pair
-    make_tw256(tw);
-    const float2 *src = S1 + slice * (long long)N * NH;
-    for (int i = threadIdx.x; i < CB * N; i += blockDim.x) {
-        const int y = i >> 3, c = i & 7;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(A + c * LD + y)),
-                     "l"(src + (long long)y * NH + c0 + c) : "memory");
-    }
-    if (first)   // the Nyquist column in slot CB
-        for (int y = threadIdx.x; y < N; y += blockDim.x)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(A + CB * LD + y)),
-                         "l"(src + (long long)y * NH + 128) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
+    const float2 *src = S1 + so + (long long)(c0 + tm) * N + t;
     float2 x[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        x[m] = A[tm * LD + t + 16 * m];
-        if (pk) x[m].y = A[CB * LD + t + 16 * m].x;
+    for (int m = 0; m < 16; ++m) x[m] = __ldcs(src + 16 * m);
+    if (pk) {
+        const float *nq = reinterpret_cast<const float *>(S1 + so + 128LL * N + t);   // the Nyquist column (real)
+#pragma unroll
+        for (int m = 0; m < 16; ++m) x[m].y = __ldcs(nq + 32 * m);
     }
+    make_tw256(tw);
+    __syncthreads();
     fft256_reg<false>(x, Ts, tw, t);
     // the packed pair needs X at -j: entry (256 - t - 16 k) % 256 sits in
     // thread (16 - t) % 16 at index 15 - k (t > 0) or (16 - k) % 16 (t = 0)
@@ -308,30 +308,25 @@ __global__ void __launch_bounds__(128) k_colfft256(const float2 *__restrict__ S1
     if (w0) __syncwarp();   // the exchange buffer is read before the transforms reuse it
     fft256_reg<true>(x, Ts, tw, t);
     fft256_reg<true>(D, Ts, tw, t);
-    float2 *d1 = T1 + slice * (long long)N * NH, *d2 = T2 + slice * (long long)N * NH;
-    // results -> staging buffer (column 0 and 128 of the packed pair as real values) -> rows
-    auto out = [&](const float2 (&v)[16], float2 *dst) {
-        __syncthreads();   // the staging buffer is free
-        if (pk) {
+    // entry y = t + 16 k2 of the column: columns 0 and 128 of the packed pair
+    // are the real and imaginary parts
+    float2 *d1 = T1 + so + (long long)(c0 + tm) * N + t, *d2 = T2 + so + (long long)(c0 + tm) * N + t;
+    if (pk) {
+        float2 *e1 = T1 + so + 128LL * N + t, *e2 = T2 + so + 128LL * N + t;
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) {
-                A[t + 16 * k2] = make_float2(v[k2].x, 0.0f);
-                A[CB * LD + t + 16 * k2] = make_float2(v[k2].y, 0.0f);
-            }
-        } else {
+        for (int k2 = 0; k2 < 16; ++k2) {
+            __stcg(d1 + 16 * k2, make_float2(x[k2].x, 0.0f));
+            __stcg(e1 + 16 * k2, make_float2(x[k2].y, 0.0f));
+            __stcg(d2 + 16 * k2, make_float2(D[k2].x, 0.0f));
+            __stcg(e2 + 16 * k2, make_float2(D[k2].y, 0.0f));
+        }
+    } else {
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) A[tm * LD + t + 16 * k2] = v[k2];
+        for (int k2 = 0; k2 < 16; ++k2) {
+            __stcg(d1 + 16 * k2, x[k2]);
+            __stcg(d2 + 16 * k2, D[k2]);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < CB * N; i += blockDim.x) {
-            const int y = i >> 3, c = i & 7;
-            __stcg(dst + (long long)y * NH + c0 + c, A[c * LD + y]);
-        }
-        if (first)
-            for (int y = threadIdx.x; y < N; y += blockDim.x) __stcg(dst + (long long)y * NH + 128, A[CB * LD + y]);
-    };
-    out(x, d1);
-    out(D, d2);
+    }
 }
 
 // signed spectral index and its derivative version (Nyquist zeroed)
@@ -512,30 +507,30 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
 
 // K3 for N = 256: 128 threads = 8 teams, rows r0 .. r0 + 15 of one slice;
 // team m owns rows y0 = r0 + 2m and y0 + 1 and needs nothing from the other
-// teams: d_y Psi of both rows from one packed inverse transform of their T2
-// rows, then Psi and d_z Psi of each row from one of its T1 row.  The four
-// half-spectrum rows are staged in shared memory (8-byte asynchronous
-// copies, each entry read once; the Hermitian extension reads entries k and
-// 256 - k).  A transform leaves entry t + 16 k in thread t; the results are
-// re-read through a padded [16][17] layout so that the push runs on points
-// 4 t + 64 i + c, whose operands the team loads and stores as 256
-// contiguous bytes per i, issued one transform ahead.
+// teams' results: d_y Psi of both rows from one packed inverse transform of
+// their T2 rows, then Psi and d_z Psi of each row from one of its T1 row.
+// T1 and T2 are column-major ([xi][k_z][y]), so the block's 16 rows at one
+// k_z are 128 contiguous bytes of each; they are staged in shared memory as
+// [T2, T1][k_z][row] (16-byte asynchronous copies, each entry read once; the
+// Hermitian extension reads entries k and 256 - k).  A transform leaves
+// entry t + 16 k in thread t; the results are re-read through a padded
+// [16][17] layout so that the push runs on points 4 t + 64 i + c, whose
+// operands the team loads and stores as 256 contiguous bytes per i, issued
+// one transform ahead.
 __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
                                                            const PushArgs a) {
-    constexpr int N = 256, NH = 129, TSZ = 272, RS = NH;
+    constexpr int N = 256, NH = 129, TSZ = 272, LR = 18;   // LR: staged k_z stride (16 rows, 16-byte aligned)
     extern __shared__ float2 sm[];
     const long long slice = blockIdx.y;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15;
     const int y0 = blockIdx.x * 16 + 2 * tm;
     float2 *tw = sm, *Ts = sm + TWN + tm * 2 * TSZ, *Dy = Ts + TSZ;
-    float2 *R = sm + TWN + 8 * 2 * TSZ + tm * 4 * RS;   // T2 rows y0, y0 + 1, T1 rows y0, y0 + 1
-    const float2 *t1 = T1 + slice * (long long)N * NH, *t2 = T2 + slice * (long long)N * NH;
-    // rows y0 and y0 + 1 (y0 even) are one 16-byte aligned block of 2 NH
-    // entries in each of T2 and T1: 16-byte copies
-    for (int i = t; i < 2 * NH; i += 16) {
-        const int h = i >= NH, j = i - h * NH;           // block (T2, T1), 16-byte piece
-        const float2 *src = (h ? t1 : t2) + (long long)y0 * NH + 2 * j;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(R + h * 2 * RS + 2 * j)),
+    float2 *R = sm + TWN + 8 * 2 * TSZ;   // [T2, T1][k_z][16 rows]
+    const long long so = slice * (long long)N * NH + blockIdx.x * 16;
+    for (int i = threadIdx.x; i < 2 * NH * 8; i += blockDim.x) {
+        const int h = i >= NH * 8, r = i - h * NH * 8, k = r >> 3, q = r & 7;   // (T2, T1), k_z, 16-byte piece
+        const float2 *src = (h ? T1 : T2) + so + (long long)k * N + 2 * q;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(R + (h * NH + k) * LR + 2 * q)),
                      "l"(src) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -566,7 +561,8 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
-        float2 U = R[kk], V = R[RS + kk];
+        const float4 uv = *reinterpret_cast<const float4 *>(R + kk * LR + 2 * tm);   // rows y0, y0 + 1 of T2
+        float2 U = make_float2(uv.x, uv.y), V = make_float2(uv.z, uv.w);
         if (k > 128) { U.y = -U.y; V.y = -V.y; }
         x[m] = make_float2(U.x - V.y, U.y + V.x);   // U + i V
     }
@@ -581,7 +577,7 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
-            float2 X = R[(2 + rr) * RS + kk];
+            float2 X = R[(NH + kk) * LR + 2 * tm + rr];
             if (k > 128) X.y = -X.y;
             const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
             x[m] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
@@ -681,9 +677,9 @@ size_t smem_k2() { return sizeof(float2) * (N / 2 + 4 * CB * N); }
 template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
-constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 256 + 16 * 272);
-constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 9 * 260 + 8 * 272);
-constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 2 * 272 + 8 * 4 * 129);
+constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 258 + 16 * 272);
+constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 8 * 272);
+constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 2 * 272 + 2 * 129 * 18);
 
 template <int N>
 cudaError_t set_attrs() {
