@@ -510,66 +510,78 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
 // teams' results: d_y Psi of both rows from one packed inverse transform of
 // their T2 rows, then Psi and d_z Psi of each row from one of its T1 row.
 // T1 and T2 are column-major ([xi][k_z][y]), so the block's 16 rows at one
-// k_z are 128 contiguous bytes of each; they are staged in shared memory as
-// [T2, T1][k_z][row] (16-byte asynchronous copies, each entry read once; the
-// Hermitian extension reads entries k and 256 - k).  A transform leaves
-// entry t + 16 k in thread t; the results are re-read through a padded
-// [16][17] layout so that the push runs on points 4 t + 64 i + c, whose
-// operands the team loads and stores as 256 contiguous bytes per i, issued
-// one transform ahead.
-__global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
+// k_z are 128 contiguous bytes of each.  They are staged in shared memory as
+// [T2, T1][k_z][8 pieces of two rows] (16-byte asynchronous copies, T2 and
+// T1 in separate groups so that the d_y Psi transform starts while T1 is in
+// flight; piece q of entry k sits at slot q ^ (k & 7), which spreads a
+// team's reads over the banks).  The Hermitian extension reads entries k and
+// 256 - k.  Once a team has read its T2 pieces, d_y Psi goes into those
+// slots.  A transform leaves entry t + 16 k in thread t; the results are
+// re-read so that the push runs on points 4 t + 64 i + c, whose operands the
+// team loads and stores as 256 contiguous bytes per i, issued one transform
+// ahead.  Shared memory is 52.6 KB per block, so four blocks fit on an SM.
+__global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
                                                            const PushArgs a) {
-    constexpr int N = 256, NH = 129, TSZ = 272, LR = 18;   // LR: staged k_z stride (16 rows, 16-byte aligned)
+    constexpr int N = 256, NH = 129, TSZ = 272;
     extern __shared__ float2 sm[];
     const long long slice = blockIdx.y;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15;
     const int y0 = blockIdx.x * 16 + 2 * tm;
-    float2 *tw = sm, *Ts = sm + TWN + tm * 2 * TSZ, *Dy = Ts + TSZ;
-    float2 *R = sm + TWN + 8 * 2 * TSZ;   // [T2, T1][k_z][16 rows]
+    float2 *tw = sm, *Ts = sm + TWN + tm * TSZ;
+    float2 *R = sm + TWN + 8 * TSZ;   // [T2, T1][k_z][16 rows]
     const long long so = slice * (long long)N * NH + blockIdx.x * 16;
-    for (int i = threadIdx.x; i < 2 * NH * 8; i += blockDim.x) {
-        const int h = i >= NH * 8, r = i - h * NH * 8, k = r >> 3, q = r & 7;   // (T2, T1), k_z, 16-byte piece
-        const float2 *src = (h ? T1 : T2) + so + (long long)k * N + 2 * q;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(R + (h * NH + k) * LR + 2 * q)),
-                     "l"(src) : "memory");
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 *src = (h ? T1 : T2) + so;
+        for (int i = threadIdx.x; i < NH * 8; i += blockDim.x) {
+            const int k = i >> 3, q = i & 7;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(
+                             R + (h * NH + k) * 16 + 2 * (q ^ (k & 7)))),
+                         "l"(src + (long long)k * N + 2 * q) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
     const long long base = slice * (long long)N * N;
     const float tz = 6.283185307179586f / a.lz;
-    float4 lnp[4], lnb[4], lg[4], ln0[4], lgy[4], lgz[4];
+    float4 lnp[4], lnb[4], lg[4];
     auto issue = [&](int rr) {
         const long long o = base + (long long)(y0 + rr) * N;
-        const int q = (y0 + rr) * N;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int z = 4 * t + 64 * i;
             lnp[i] = __ldcg(reinterpret_cast<const float4 *>(a.np + o + z));
             lnb[i] = __ldcg(reinterpret_cast<const float4 *>(a.nb + o + z));
             lg[i] = __ldcg(reinterpret_cast<const float4 *>(a.G + o + z));
-            ln0[i] = __ldg(reinterpret_cast<const float4 *>(a.nb0 + q + z));
-            lgy[i] = __ldg(reinterpret_cast<const float4 *>(a.gy + q + z));
-            lgz[i] = __ldg(reinterpret_cast<const float4 *>(a.gz + q + z));
         }
     };
     issue(0);
     make_tw256(tw);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();   // twiddles and staged rows
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();   // twiddles and the staged T2 block
     // entry k = t + 16 m of a row's Hermitian extension: entry kk of the half
     // spectrum, conjugated past 128
     float2 x[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
-        const float4 uv = *reinterpret_cast<const float4 *>(R + kk * LR + 2 * tm);   // rows y0, y0 + 1 of T2
+        const float4 uv = *reinterpret_cast<const float4 *>(R + kk * 16 + 2 * (tm ^ (kk & 7)));   // rows y0, y0 + 1 of T2
         float2 U = make_float2(uv.x, uv.y), V = make_float2(uv.z, uv.w);
         if (k > 128) { U.y = -U.y; V.y = -V.y; }
         x[m] = make_float2(U.x - V.y, U.y + V.x);   // U + i V
     }
     fft256_reg<true>(x, Ts, tw, t);
-    // entry z of the row pair's d_y Psi at (z % 16) 17 + z / 16
+    // entry z of the row pair's d_y Psi goes to this team's slot of entry
+    // u / 2, half u % 2, u = (z & ~15) | ((z & 15) ^ ((z / 16) & 3)): the
+    // stores (z = t + 16 k) and the push's loads (z = 4 t + 64 i + c) each
+    // touch 16 distinct bank pairs
+    auto dslot = [&](int z) {
+        const int u = (z & ~15) | ((z & 15) ^ ((z >> 4) & 3)), k = u >> 1;
+        return k * 16 + 2 * (tm ^ (k & 7)) + (u & 1);
+    };
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) Dy[t * 17 + k2] = x[k2];
+    for (int k2 = 0; k2 < 16; ++k2) R[dslot(t + 16 * k2)] = x[k2];
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // the staged T1 block
     bool bad = false;
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -577,7 +589,7 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
-            float2 X = R[(NH + kk) * LR + 2 * tm + rr];
+            float2 X = R[(NH + kk) * 16 + 2 * (tm ^ (kk & 7)) + rr];
             if (k > 128) X.y = -X.y;
             const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
             x[m] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
@@ -587,25 +599,28 @@ __global__ void __launch_bounds__(128, 3) k_rowinv_push256(const float2 *__restr
         for (int k2 = 0; k2 < 16; ++k2) Ts[t * 17 + k2] = x[k2];
         __syncwarp();
         const long long o = base + (long long)(y0 + rr) * N;
+        const int q = (y0 + rr) * N;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
+            const int z = 4 * t + 64 * i;
+            const float4 n0v = __ldg(reinterpret_cast<const float4 *>(a.nb0 + q + z));
+            const float4 gyv4 = __ldg(reinterpret_cast<const float4 *>(a.gy + q + z));
+            const float4 gzv4 = __ldg(reinterpret_cast<const float4 *>(a.gz + q + z));
             float e[4], f[4];
             const float npa[4] = {lnp[i].x, lnp[i].y, lnp[i].z, lnp[i].w}, nbv[4] = {lnb[i].x, lnb[i].y, lnb[i].z, lnb[i].w};
-            const float gv[4] = {lg[i].x, lg[i].y, lg[i].z, lg[i].w}, n0[4] = {ln0[i].x, ln0[i].y, ln0[i].z, ln0[i].w};
-            const float gyv[4] = {lgy[i].x, lgy[i].y, lgy[i].z, lgy[i].w}, gzv[4] = {lgz[i].x, lgz[i].y, lgz[i].z, lgz[i].w};
+            const float gv[4] = {lg[i].x, lg[i].y, lg[i].z, lg[i].w}, n0[4] = {n0v.x, n0v.y, n0v.z, n0v.w};
+            const float gyv[4] = {gyv4.x, gyv4.y, gyv4.z, gyv4.w}, gzv[4] = {gzv4.x, gzv4.y, gzv4.z, gzv4.w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                // point z = 4 t + 64 i + c: z % 16 = 4 (t % 4) + c, z / 16 = t / 4 + 4 i
-                const int pz_i = (4 * (t & 3) + c) * 17 + (t >> 2) + 4 * i;
-                const float2 pz = Ts[pz_i];
-                const float2 dyp = Dy[pz_i];
+                // point z + c: (z + c) % 16 = 4 (t % 4) + c, (z + c) / 16 = t / 4 + 4 i
+                const float2 pz = Ts[(4 * (t & 3) + c) * 17 + (t >> 2) + 4 * i];
+                const float2 dyp = R[dslot(z + c)];
                 const float dyv = rr ? dyp.y : dyp.x;
                 const float S = a.coef * (n0[c] * (pz.x - npa[c]) + gyv[c] * dyv + gzv[c] * pz.y);
                 f[c] = fmaf(a.h, S, gv[c]);
                 e[c] = fmaf(a.dt, f[c], nbv[c]);
                 bad |= !(fabsf(e[c]) <= 3.0e38f) || !(fabsf(f[c]) <= 3.0e38f);
             }
-            const int z = 4 * t + 64 * i;
             __stcg(reinterpret_cast<float4 *>(a.G + o + z), make_float4(f[0], f[1], f[2], f[3]));
             __stcg(reinterpret_cast<float4 *>(a.nb + o + z), make_float4(e[0], e[1], e[2], e[3]));
         }
@@ -679,7 +694,7 @@ size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
 constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 258 + 16 * 272);
 constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 8 * 272);
-constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 2 * 272 + 2 * 129 * 18);
+constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 272 + 2 * 129 * 16);
 
 template <int N>
 cudaError_t set_attrs() {
