@@ -147,10 +147,12 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
 // 256-point FFT of values held by a 16-thread team: on entry x[m] is entry
 // t + 16 m, on return x[k] is entry t + 16 k of the transform.  T is the
 // team's [16][17] exchange buffer; every thread of the warp must call it
-// (both half-warp teams in step).
+// (both half-warp teams in step), and T may hold the inputs the team has
+// just read (the entry barrier orders those reads before the writes).
 template <bool INV>
 __device__ __forceinline__ void fft256_reg(float2 (&x)[16], float2 *T, const float2 *tw256, int t) {
     dft16<INV>(x);
+    __syncwarp();
     T[t] = x[0];   // W256^0
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
@@ -189,10 +191,10 @@ __device__ __forceinline__ void make_tw256(float2 *tw) {
 // K1 for N = 256: 32 rows (16 packed) per CTA, 16 teams.  S1 is stored
 // column-major, [xi][k_z][y], so that the column transforms read and write
 // whole 256-entry columns as contiguous runs.
-__global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np, float2 *__restrict__ S1) {
-    constexpr int N = 256, NH = 129, PR = 16, LA = N + 2;   // LA: packed-row stride (16-byte aligned rows)
+__global__ void __launch_bounds__(256, 5) k_rowfft256(const float *__restrict__ np, float2 *__restrict__ S1) {
+    constexpr int N = 256, NH = 129, PR = 16, LA = 274;   // LA: packed-row stride (16-byte aligned, room for the exchange)
     extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + TWN, *T = A + PR * LA;
+    float2 *tw = sm, *A = sm + TWN;
     const long long slice = blockIdx.y;
     const int r0 = blockIdx.x * 2 * PR;
     const int team = threadIdx.x >> 4, t = threadIdx.x & 15;
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(256) k_rowfft256(const float *__restrict__ np,
         float2 x[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) x[m] = make_float2(rf[t + 16 * m], rf[N + t + 16 * m]);
-        fft256_reg<false>(x, T + team * 272, tw, t);   // (its warp barriers order the reads before the writes)
+        fft256_reg<false>(x, A + team * LA, tw, t);   // exchange in the team's own row (read above)
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) A[team * LA + t + 16 * k2] = x[k2];
     }
@@ -336,20 +338,21 @@ template <int N>
 __device__ __forceinline__ float didx(int j) { return j == N / 2 ? 0.0f : sidx<N>(j); }
 
 // ---------------------------------------------------------------- phase A
-__global__ void k_plasma(const float *__restrict__ nb, float *__restrict__ np, long long P, int Nxi, float q,
+__global__ void __launch_bounds__(128, 4) k_plasma(const float *__restrict__ nb, float *__restrict__ np, long long P, int Nxi, float q,
                          float c, float s, float ch, float sh) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
-    // U cells of the line in flight per thread: with one thread per
-    // transverse point (65,536 at N = 256) that keeps about 8 MB of loads
-    // outstanding, enough to cover the HBM latency
+    // two buffers of U cells of the line: the next U cells are in flight
+    // while the current ones are marched (with one thread per transverse
+    // point, 65,536 at N = 256, that keeps about 8 MB of loads outstanding)
     constexpr int U = 32;
     float n = 0.0f, d = 0.0f;
-    float buf[U];
-    for (int j0 = 0; j0 < Nxi; j0 += U) {
+    float ba[U], bb[U];
+    auto load = [&](float (&buf)[U], int j0) {
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            buf[u] = (j0 + u < Nxi) ? __ldcg(nb + (long long)(j0 + u) * P + p) : 0.0f;
+        for (int u = 0; u < U; ++u) buf[u] = (j0 + u < Nxi) ? __ldcg(nb + (long long)(j0 + u) * P + p) : 0.0f;
+    };
+    auto march = [&](const float (&buf)[U], int j0) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (j0 + u >= Nxi) break;
@@ -360,6 +363,13 @@ __global__ void k_plasma(const float *__restrict__ nb, float *__restrict__ np, l
             d = fmaf(-s, un, c * d);
             n = x;
         }
+    };
+    load(ba, 0);
+    for (int j0 = 0; j0 < Nxi; j0 += 2 * U) {
+        load(bb, j0 + U);
+        march(ba, j0);
+        load(ba, j0 + 2 * U);
+        march(bb, j0 + U);
     }
 }
 
@@ -692,7 +702,7 @@ size_t smem_k2() { return sizeof(float2) * (N / 2 + 4 * CB * N); }
 template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
-constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 258 + 16 * 272);
+constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 274);
 constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 8 * 272);
 constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 272 + 2 * 129 * 16);
 
