@@ -815,10 +815,14 @@ qs_status qs_r2_init(const qs_r2_params *p, const qs_allocator *alloc, void *str
             t[2 * c->P + k] = p->uniform ? 0.0f : (float)(-(z / s2) * n0);
             t[3 * c->P + k] = 0.0f;
         }
-    cudaError_t e = cudaMemcpy(c->nb0, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemset(c->err, 0, sizeof(int) * 4);
-    if (!e) e = cudaMemset(c->nb, 0, sizeof(float) * c->cells);
-    if (!e) e = cudaMemset(c->G, 0, sizeof(float) * c->cells);
+    // all on the context's stream, then one wait for it (the host vector t
+    // must outlive the copy; the stream may be one that does not synchronise
+    // with the legacy default stream)
+    cudaError_t e = cudaMemcpyAsync(c->nb0, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemsetAsync(c->err, 0, sizeof(int) * 4, c->stream);
+    if (!e) e = cudaMemsetAsync(c->nb, 0, sizeof(float) * c->cells, c->stream);
+    if (!e) e = cudaMemsetAsync(c->G, 0, sizeof(float) * c->cells, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
     if (!e) e = N == 32 ? set_attrs<32>() : N == 64 ? set_attrs<64>() : N == 128 ? set_attrs<128>() : set_attrs<256>();
     if (e) { cudaGetLastError(); qs_r2_free(c); return QS_ERR_CUDA; }
     *out = c;
