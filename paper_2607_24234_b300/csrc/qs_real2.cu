@@ -149,16 +149,43 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
 // team's [16][17] exchange buffer; every thread of the warp must call it
 // (both half-warp teams in step), and T may hold the inputs the team has
 // just read (the entry barrier orders those reads before the writes).
-template <bool INV>
+// TWP: only W^t, W^2t, W^4t and W^8t are read from the table and the other
+// inter-step twiddles are formed as products of them (at most two
+// multiplications deep, a few ulp), for kernels whose shared-memory pipe is
+// their limit.
+template <bool INV, bool TWP = false>
 __device__ __forceinline__ void fft256_reg(float2 (&x)[16], float2 *T, const float2 *tw256, int t) {
     dft16<INV>(x);
     __syncwarp();
     T[t] = x[0];   // W256^0
+    if constexpr (TWP) {
+        auto ld = [&](int k1) {
+            float2 w = tw256[k1 * 17 + t];
+            if (INV) w.y = -w.y;
+            return w;
+        };
+        const float2 w1 = ld(1), w2 = ld(2), w4 = ld(4), w8 = ld(8);
+        // w_k for k < 8, and w_(k + 8) = w_k w8
+        auto put = [&](int k1, float2 w) {
+            T[k1 * 17 + t] = cmul(x[k1], w);
+            T[(k1 + 8) * 17 + t] = cmul(x[k1 + 8], cmul(w, w8));
+        };
+        T[8 * 17 + t] = cmul(x[8], w8);
+        put(1, w1);
+        put(2, w2);
+        put(3, cmul(w1, w2));
+        put(4, w4);
+        put(5, cmul(w1, w4));
+        const float2 w6 = cmul(w2, w4);
+        put(6, w6);
+        put(7, cmul(w1, w6));
+    } else {
 #pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) {
-        float2 w = tw256[k1 * 17 + t];
-        if (INV) w.y = -w.y;
-        T[k1 * 17 + t] = cmul(x[k1], w);
+        for (int k1 = 1; k1 < 16; ++k1) {
+            float2 w = tw256[k1 * 17 + t];
+            if (INV) w.y = -w.y;
+            T[k1 * 17 + t] = cmul(x[k1], w);
+        }
     }
     __syncwarp();
 #pragma unroll
@@ -579,7 +606,7 @@ __global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restr
         if (k > 128) { U.y = -U.y; V.y = -V.y; }
         x[m] = make_float2(U.x - V.y, U.y + V.x);   // U + i V
     }
-    fft256_reg<true>(x, Ts, tw, t);
+    fft256_reg<true, true>(x, Ts, tw, t);
     // entry z of the row pair's d_y Psi goes to this team's slot of entry
     // u / 2, half u % 2, u = (z & ~15) | ((z & 15) ^ ((z / 16) & 3)): the
     // stores (z = t + 16 k) and the push's loads (z = 4 t + 64 i + c) each
@@ -604,7 +631,7 @@ __global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restr
             const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
             x[m] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
         }
-        fft256_reg<true>(x, Ts, tw, t);
+        fft256_reg<true, true>(x, Ts, tw, t);
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) Ts[t * 17 + k2] = x[k2];
         __syncwarp();
