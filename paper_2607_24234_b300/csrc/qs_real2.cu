@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(128, 4) k_colfft256(const float2 *__restrict__
     }
     make_tw256(tw);
     __syncthreads();
-    fft256_reg<false>(x, Ts, tw, t);
+    fft256_reg<false, true>(x, Ts, tw, t);
     // the packed pair needs X at -j: entry (256 - t - 16 k) % 256 sits in
     // thread (16 - t) % 16 at index 15 - k (t > 0) or (16 - k) % 16 (t = 0)
     if (w0) {
@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(128, 4) k_colfft256(const float2 *__restrict__
         }
     }
     if (w0) __syncwarp();   // the exchange buffer is read before the transforms reuse it
-    fft256_reg<true>(x, Ts, tw, t);
-    fft256_reg<true>(D, Ts, tw, t);
+    fft256_reg<true, true>(x, Ts, tw, t);
+    fft256_reg<true, true>(D, Ts, tw, t);
     // entry y = t + 16 k2 of the column: columns 0 and 128 of the packed pair
     // are the real and imaginary parts
     float2 *d1 = T1 + so + (long long)(c0 + tm) * N + t, *d2 = T2 + so + (long long)(c0 + tm) * N + t;
