@@ -365,7 +365,7 @@ template <int N>
 __device__ __forceinline__ float didx(int j) { return j == N / 2 ? 0.0f : sidx<N>(j); }
 
 // ---------------------------------------------------------------- phase A
-__global__ void __launch_bounds__(128, 4) k_plasma(const float *__restrict__ nb, float *__restrict__ np, long long P, int Nxi, float q,
+__global__ void __launch_bounds__(64, 8) k_plasma(const float *__restrict__ nb, float *__restrict__ np, long long P, int Nxi, float q,
                          float c, float s, float ch, float sh) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -752,7 +752,7 @@ cudaError_t step_n(qs_r2 *c, float h) {
     const qs_r2_params &p = c->p;
     const double D = p.dxi;
     const float q = (float)p.species.q;
-    r2::k_plasma<<<(unsigned)((c->P + 127) / 128), 128, 0, c->stream>>>(
+    r2::k_plasma<<<(unsigned)((c->P + 63) / 64), 64, 0, c->stream>>>(
         c->nb, c->np, c->P, p.n_xi, q, (float)std::cos(D), (float)std::sin(D), (float)std::cos(0.5 * D),
         (float)std::sin(0.5 * D));
     constexpr int NH = N / 2 + 1;
