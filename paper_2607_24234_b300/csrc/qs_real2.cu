@@ -25,6 +25,7 @@
 // the transposition in the shared-memory staging they need anyway.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -215,6 +216,16 @@ __device__ __forceinline__ void make_tw256(float2 *tw) {
     }
 }
 
+// only the rows k1 = 1, 2, 4, 8 that the product-twiddle transforms read
+__device__ __forceinline__ void make_tw256_p2(float2 *tw) {
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+        const int k1 = 1 << (j >> 4), t = j & 15;
+        float s, c;
+        sincospif(-2.0f * (float)(t * k1) / 256.0f, &s, &c);
+        tw[k1 * 17 + t] = make_float2(c, s);
+    }
+}
+
 // K1 for N = 256: 32 rows (16 packed) per CTA, 16 teams.  S1 is stored
 // column-major, [xi][k_z][y], so that the column transforms read and write
 // whole 256-entry columns as contiguous runs.
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(128, 4) k_colfft256(const float2 *__restrict__
 #pragma unroll
         for (int m = 0; m < 16; ++m) x[m].y = __ldcs(nq + 32 * m);
     }
-    make_tw256(tw);
+    make_tw256_p2(tw);
     __syncthreads();
     fft256_reg<false, true>(x, Ts, tw, t);
     // the packed pair needs X at -j: entry (256 - t - 16 k) % 256 sits in
@@ -592,7 +603,7 @@ __global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restr
         }
     };
     issue(0);
-    make_tw256(tw);
+    make_tw256_p2(tw);
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();   // twiddles and the staged T2 block
     // entry k = t + 16 m of a row's Hermitian extension: entry kk of the half
