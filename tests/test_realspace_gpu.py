@@ -78,3 +78,29 @@ def test_narrow_beam_full_size_invariants(R):
     assert drift <= 1e-4 * scale
     assert g.launch_count() == 80
     g.close()
+
+
+@pytest.mark.parametrize("n,n_xi", [(32, 20), (256, 5)])
+def test_nonfinite_state_reported(R, n, n_xi):
+    """A NaN in one seeded cell reaches the fields through the transverse
+    solve and the push writes non-finite values; the push's check reports
+    it at the next sync (QS_ERR_NONFINITE), and a clean reseed clears it.
+    Covers the radix-2 kernels (N = 32) and the four-step ones (N = 256)."""
+    from paper_2607_24234_b300 import QSError
+    p = _case(n, n_xi)
+    noise = synth.normals((n_xi, n, n), 5).astype(np.float32)
+    g = R(p)
+    g.seed(amplitude=1e-4, offset=0.04, noise=noise)
+    g.step(2)
+    g.sync()                      # finite: no error
+    bad = noise.copy()
+    bad[n_xi // 2, n // 3, n // 5] = np.nan
+    g.seed(amplitude=1e-4, offset=0.04, noise=bad)
+    g.step(2)
+    with pytest.raises(QSError) as ei:
+        g.sync()
+    assert ei.value.status == 5
+    g.seed(amplitude=1e-4, offset=0.04, noise=noise)
+    g.step(2)
+    g.sync()
+    g.close()
