@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256, 5) k_rowfft256(const float *__restrict__ 
 // forward transform, the kappa and i k_y kappa products and both inverse
 // transforms, and stores the results the same way; shared memory holds only
 // the twiddles and the transforms' exchange buffers.
-__global__ void __launch_bounds__(128, 4) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
+__global__ void __launch_bounds__(128, 5) k_colfft256(const float2 *__restrict__ S1, float2 *__restrict__ T1,
                                                       float2 *__restrict__ T2, float ly, float lz) {
     constexpr int N = 256, NH = 129, CB = 8, TSZ = 272;
     extern __shared__ float2 sm[];
