@@ -769,19 +769,29 @@ cudaError_t step_n(qs_r2 *c, float h) {
     constexpr int NH = N / 2 + 1;
     r2::PushArgs a{c->np, c->nb, c->G, c->nb0, c->gy, c->gz,
                    (float)(-p.species.q / (p.species.m * p.gamma_b)), h, (float)p.dt, (float)p.L_perp, c->err};
-    if constexpr (N == 256) {
-        r2::k_rowfft256<<<dim3(256 / 32, p.n_xi), 256, SMEM_K1_256, c->stream>>>(c->np, c->S1);
-        r2::k_colfft256<<<dim3(16, p.n_xi), 128, SMEM_K2_256, c->stream>>>(
-            c->S1, c->T1, c->T2, (float)p.L_perp, (float)p.L_perp);
-        r2::k_rowinv_push256<<<dim3(256 / 16, p.n_xi), 128, SMEM_K3_256, c->stream>>>(c->T1, c->T2, a);
-        c->launches += 4;
-        return cudaGetLastError();
+    c->launches += 1;
+    // the transform kernels take the slice from blockIdx.y (at most 65,535
+    // per launch): longer lines go in chunks, with the slice-major arrays
+    // offset to the chunk's first slice
+    constexpr long long MAXY = 65535;
+    for (long long s0 = 0; s0 < p.n_xi; s0 += MAXY) {
+        const unsigned ns = (unsigned)std::min<long long>(MAXY, p.n_xi - s0);
+        const long long po = s0 * c->P, so = s0 * (long long)N * NH;
+        r2::PushArgs as = a;
+        as.np += po; as.nb += po; as.G += po;
+        if constexpr (N == 256) {
+            r2::k_rowfft256<<<dim3(256 / 32, ns), 256, SMEM_K1_256, c->stream>>>(c->np + po, c->S1 + so);
+            r2::k_colfft256<<<dim3(16, ns), 128, SMEM_K2_256, c->stream>>>(
+                c->S1 + so, c->T1 + so, c->T2 + so, (float)p.L_perp, (float)p.L_perp);
+            r2::k_rowinv_push256<<<dim3(256 / 16, ns), 128, SMEM_K3_256, c->stream>>>(c->T1 + so, c->T2 + so, as);
+        } else {
+            r2::k_rowfft<N, RB><<<dim3(N / RB, ns), 256, smem_k1<N>(), c->stream>>>(c->np + po, c->S1 + so);
+            r2::k_colfft<N, CB><<<dim3((NH + CB - 1) / CB, ns), 256, smem_k2<N>(), c->stream>>>(
+                c->S1 + so, c->T1 + so, c->T2 + so, (float)p.L_perp, (float)p.L_perp);
+            r2::k_rowinv_push<N, RB><<<dim3(N / RB, ns), 256, smem_k3<N>(), c->stream>>>(c->T1 + so, c->T2 + so, as);
+        }
+        c->launches += 3;
     }
-    r2::k_rowfft<N, RB><<<dim3(N / RB, p.n_xi), 256, smem_k1<N>(), c->stream>>>(c->np, c->S1);
-    r2::k_colfft<N, CB><<<dim3((NH + CB - 1) / CB, p.n_xi), 256, smem_k2<N>(), c->stream>>>(
-        c->S1, c->T1, c->T2, (float)p.L_perp, (float)p.L_perp);
-    r2::k_rowinv_push<N, RB><<<dim3(N / RB, p.n_xi), 256, smem_k3<N>(), c->stream>>>(c->T1, c->T2, a);
-    c->launches += 4;
     return cudaGetLastError();
 }
 

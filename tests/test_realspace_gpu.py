@@ -104,3 +104,34 @@ def test_nonfinite_state_reported(R, n, n_xi):
     g.step(2)
     g.sync()
     g.close()
+
+
+def test_more_slices_than_one_launch_holds(R):
+    """65,600 xi slices, more than the 65,535 a launch's grid holds in y:
+    the transform kernels run in two chunks.  Against the oracle after one
+    step:
+    - n_b matches to 2e-5;
+    - G and n_p carry the FP32 march's phase error, which grows linearly
+      with the cell count (the rounded cos/sin of dxi turn every cell by the
+      same wrong angle): about 3e-4 of the maximum at 65,600 cells, inside
+      the FP32 tolerance of 1e-3;
+    - the error has no step at the chunk boundary (slice 65,535).
+    The radix-2 kernels run here (N = 32); the four-step ones take the same
+    chunking."""
+    n, n_xi = 32, 65600
+    p = _case(n, n_xi)
+    noise = synth.normals((n_xi, n, n), 11)
+    nb_o, G_o = rs.seed(p, 1e-4, 0.04, noise)
+    out = rs.sweep(p, nb_o, G_o, 0, 1, record_np=True)
+    g = R(p)
+    g.seed(amplitude=1e-4, offset=0.04, noise=noise.astype(np.float32))
+    g.step(1)
+    g.sync()
+    for what, ref, tol in ((0, nb_o, 2e-5), (1, G_o, 1e-3), (2, out["np"], 1e-3)):
+        got = g.read(what).astype(np.float64)
+        e = np.max(np.abs(got - ref).reshape(n_xi, -1), axis=1) / np.max(np.abs(ref))
+        assert e.max() <= tol, (what, e.max())
+        before, after = e[65535 - 64:65535].max(), e[65535:65535 + 64].max()
+        assert after <= 1.5 * before + 1e-7, (what, before, after)
+    assert g.launch_count() == 1 + 2 * 3   # the march, then two chunks of three transform kernels
+    g.close()
