@@ -1257,7 +1257,7 @@ __global__ void __launch_bounds__(128) k_dw_thin(const __nv_bfloat16 *wide, int 
 __global__ void k_transpose_b16(const __nv_bfloat16 *src, int rows, int cols, __nv_bfloat16 *dst, long long s_src,
                                 long long s_dst) {
     __shared__ __nv_bfloat16 tile[32][34];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;   // (rows, the batch, on x: more than 65,535 tiles)
     src += blockIdx.z * s_src;   // ensemble member
     dst += blockIdx.z * s_dst;
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
@@ -1562,13 +1562,13 @@ void backward(qs_mlp *m, int n, bool fused) {
             // is split over enough CTAs to fill the GPU, slices summed atomically
             const dim3 tb(32, 8);
             if (!dzt_ready)
-                mlp::k_transpose_b16<<<dim3((out + 31) / 32, (n + 31) / 32, m->E), tb, 0, m->stream>>>(
+                mlp::k_transpose_b16<<<dim3((n + 31) / 32, (out + 31) / 32, m->E), tb, 0, m->stream>>>(
                     dz, n, out, m->TDZ, sdz, as);
             const __nv_bfloat16 *actT = m->TACT;
             long long sactT = as;
             if (l == 0) { actT = m->X0T; sactT = 0; }
             else if (actT_ready) actT = m->HT[l - 1];
-            else mlp::k_transpose_b16<<<dim3((in + 31) / 32, (n + 31) / 32, m->E), tb, 0, m->stream>>>(
+            else mlp::k_transpose_b16<<<dim3((n + 31) / 32, (in + 31) / 32, m->E), tb, 0, m->stream>>>(
                      act, n, in, m->TACT, sact, as);
             const int tiles = (out / 128) * ((in + 127) / 128) * m->E;
             const int nkt = (n + mlp::wg::KC - 1) / mlp::wg::KC;
