@@ -433,18 +433,21 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                     fkm[k] = lane >= (1 << k) ? f : 0.f;
                 }
             }
+            // (scalar FMAs on the shuffled components: per component the same
+            // roundings as the packed form, without pairing the shuffle
+            // results into register pairs)
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const int dl = 1 << k;
-                const float2 un = make_float2(__shfl_up_sync(FULL, n.x, dl), __shfl_up_sync(FULL, n.y, dl));
-                const float2 ud = make_float2(__shfl_up_sync(FULL, d.x, dl), __shfl_up_sync(FULL, d.y, dl));
+                const float unr = __shfl_up_sync(FULL, n.x, dl), uni = __shfl_up_sync(FULL, n.y, dl);
+                const float udr = __shfl_up_sync(FULL, d.x, dl), udi = __shfl_up_sync(FULL, d.y, dl);
                 RotF R;
                 if constexpr (THS) { const float2 r2 = sRk[k]; R = RotF{r2.x, r2.y}; } else { R = Rk[THS ? 0 : k]; }
-                acc_rot2(n, d, R, fkm[k], un, ud);
+                acc_rot(n.x, n.y, d.x, d.y, R, fkm[k], unr, uni, udr, udi);
             }
             const float fx = fkm[0];
-            float2 Xn = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, n.x, 1), __shfl_up_sync(FULL, n.y, 1)));
-            float2 Xd = pmul(F2(fx), make_float2(__shfl_up_sync(FULL, d.x, 1), __shfl_up_sync(FULL, d.y, 1)));
+            float2 Xn = make_float2(__fmul_rn(fx, __shfl_up_sync(FULL, n.x, 1)), __fmul_rn(fx, __shfl_up_sync(FULL, n.y, 1)));
+            float2 Xd = make_float2(__fmul_rn(fx, __shfl_up_sync(FULL, d.x, 1)), __fmul_rn(fx, __shfl_up_sync(FULL, d.y, 1)));
             if (lane == 31) { sZ[buf][warp] = make_float4(n.x, n.y, d.x, d.y); sE[buf][warp] = e; }
             const int wm = __reduce_max_sync(FULL, e);
             if (lane == 0) sM[buf][warp] = wm;
