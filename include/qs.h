@@ -383,7 +383,8 @@ void qs_r2_free(qs_r2 *c);
 
 /* ---------------------------------------------------------------------
  * Learned surrogate (the paper has no learned component; this serves
- * parameter screening with the solver as fallback and judge).
+ * parameter screening, with the solver as the fallback and as the reference
+ * for the surrogate's error).
  * A small MLP n_in -> width (depth hidden layers, GELU erf form) -> 2
  * (regression output: log growth envelope; logit: CFI (0) / OTSI (1)),
  * BF16 weights and activations, FP32 accumulation on the tensor cores,
@@ -446,7 +447,7 @@ qs_status qs_sur_losses(const qs_sur *s, float *host, int max_n, int *n_out);
 qs_status qs_sur_set_threshold(qs_sur *s, float var_threshold);
 void qs_sur_free(qs_sur *s);
 
-/* Parameter screening with the solver as fallback and judge.  X [n][7]
+/* Parameter screening, the solver answering the flagged queries.  X [n][7]
  * fp32 device: queries as written by qs_sur_points (columns 0..2 name a
  * parameter set, 3..6 the point (xi, t, |k|, angle)).  The ensemble answers
  * every query (y, y_var [n][2] fp32 device, as qs_sur_infer); queries whose

@@ -272,7 +272,7 @@ def test_temporal_cfi_exact(species, model):
         rho = sum(species[s][0] * nb[i, s] for s in range(ns))
         expect = rho0 * cf.leapfrog_temporal(steps, G, p["dt"])
         assert np.max(np.abs(rho / expect - 1)) < 5e-13, (k, G)
-    # the rate tends to (n_b/(n_p gamma))^(1/2) for k >> 1 (spec form)
+    # the rate tends to (n_b/(n_p gamma))^(1/2) for k >> 1 (the k-independent temporal CFI rate)
     G_inf = math.sqrt(0.01 / 1000.0)
     G_big_k = cf.gamma_cfi(cf.sum_omega2([(-1, 1, 0.01)], 1000.0), 1e8)
     assert G_big_k == pytest.approx(G_inf, rel=1e-8)
