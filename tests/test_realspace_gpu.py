@@ -42,19 +42,22 @@ def test_matches_oracle(R, n, n_xi, steps):
     g.close()
 
 
-def test_uniform_single_mode(R):
+@pytest.mark.parametrize("n,n_xi,steps", [(64, 80, 20), (256, 24, 6)])
+def test_uniform_single_mode(R, n, n_xi, steps):
     """Uniform beam, one transverse Fourier mode: the GPU real-space path
-    against the oracle (which equals the pinned Fourier-mode oracle)."""
-    p = _case(64, 80, transverse="uniform")
+    against the oracle (which equals the pinned Fourier-mode oracle); the
+    profile's gradient terms vanish.  N = 64 runs the radix-2 kernels,
+    N = 256 the four-step ones."""
+    p = _case(n, n_xi, transverse="uniform")
     Y, Z = rs.grid(p)
     mode = np.cos(2 * np.pi * 3 / 8.0 * Y + 2 * np.pi * 2 / 8.0 * Z)
-    f = synth.normals(80, 3)
+    f = synth.normals(n_xi, 3)
     noise = (f[:, None, None] * mode[None]).astype(np.float32)
     nb_o, G_o = rs.seed(p, 1e-4, 0.0, noise.astype(np.float64))
-    rs.sweep(p, nb_o, G_o, 0, 20)
+    rs.sweep(p, nb_o, G_o, 0, steps)
     g = R(p)
     g.seed(amplitude=1e-4, offset=0.0, noise=noise)
-    g.step(20)
+    g.step(steps)
     got = g.read(0).astype(np.float64)
     assert np.max(np.abs(got - nb_o)) / np.max(np.abs(nb_o)) <= 2e-5
     g.close()
