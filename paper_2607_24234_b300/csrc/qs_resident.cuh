@@ -89,9 +89,16 @@ __device__ __forceinline__ float p2(int e) { return __int_as_float((max(-127, mi
 // stride).  TT = 0 keeps Theta in registers and only the weights in shared
 // memory, as (w, w) pairs in rows [v * NS + sp][thread] of the CTA's size,
 // so that each cell's weight is one 8-byte load already in the packed form.
-// UW (uniform profile, every instance, and lines that fill whole warps of
-// V-cell threads; the host checks both): the weight of every cell of a line
-// is the instance's I.wu, held in a register pair, with no per-cell load.
+// UW (uniform profile in every instance; the host checks): the weight of
+// every cell is the instance's I.wu, held in a register pair, with no
+// per-cell load.  Cells past the end of a line then carry the weight too and
+// evolve, which changes nothing that is kept: xi is causal, so they feed
+// only later cells, all of them past the end; they are never written back;
+// and threads with no cell of the line keep the sentinel exponent, so the
+// line's largest exponent is unaffected.  The one thread that holds the
+// line's end counts its padding cells in its renormalisation check, so with
+// such lines the results equal the per-cell-weight kernel's to rounding, and
+// bit for bit when lines fill whole warps.
 template <int NS, int V, int TT, bool UW = false>
 __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs a) {
     static_assert(!UW || TT > 0, "a uniform weight replaces the shared-memory weight rows");

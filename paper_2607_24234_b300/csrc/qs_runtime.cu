@@ -109,7 +109,7 @@ struct qs_ctx {
     int tx_extra = 0;
     int res_every = 16;             // resident variant's renormalisation interval (0: variant refused)
     long long dbg_rows_cut = 0;     // test hook: state rows the bounds checker is told are missing
-    bool uw_fit = false;            // uniform profile and every line a whole number of 1024-cell warps
+    bool uw_fit = false;            // uniform profile in every instance (the resident kernel's UW form)
     bool dbg_no_uw = false;         // QS_RES_NO_UNIFORM=1: the resident sweep reads per-cell weights even for a
                                     // uniform profile (compares the two kernels)
     double growth = 0.0;            // largest per-step growth bound of the instances (e-folds)
@@ -435,7 +435,7 @@ cudaError_t launch_res(qs_ctx *c, const SweepArgs &a, dim3 grid, int T, int V, b
     if (regs && c->NS == 1 && V == 32) return T <= 256 ? launch_res_t<1, 32, 0>(c, a, grid, T) : cudaErrorInvalidValue;
     if (regs && c->NS == 2 && V == 16) return T <= 256 ? launch_res_t<2, 16, 0>(c, a, grid, T) : cudaErrorInvalidValue;
     if (c->NS == 1) {
-        // uniform profiles whose lines fill whole warps: the cell weight in a register
+        // uniform profiles: the cell weight in a register
         if (V == 32 && c->uw_fit && !c->dbg_no_uw) switch (T) {
             case 64: return launch_res_t<1, 32, 64, true>(c, a, grid, T);
             case 96: return launch_res_t<1, 32, 96, true>(c, a, grid, T);
@@ -730,7 +730,6 @@ qs_status qs_init(const qs_params *p, int n_inst, const qs_params *per_inst,
     c->groups_total = grp;
     if (const char *v = getenv("QS_RES_NO_UNIFORM")) c->dbg_no_uw = v[0] == '1';
     c->uw_fit = c->uniform;
-    for (int i = 0; i < n_inst; ++i) c->uw_fit = c->uw_fit && c->inst[i].n_xi % (32 * 32) == 0;
     c->pin.assign(n_inst, *p);
     for (int i = 0; per_inst && i < n_inst; ++i) c->pin[i] = per_inst[i];
     // per-mode tables (padding modes: k = 0, never stepped)

@@ -422,6 +422,31 @@ def test_uniform_weight_kernel(qs, monkeypatch):
     assert _log_err(out["0"][1], th_o) <= FP32_LOG_TOL
 
 
+@pytest.mark.parametrize("n_xi,w", [(1000, 2), (1100, 2), (257, 2), (33, 2)])
+def test_uniform_weight_ragged_lines(qs, monkeypatch, n_xi, w):
+    """Uniform profile whose lines end inside a thread's chunk: the
+    register-weight kernel lets the cells past the end evolve (they feed only
+    later padding cells and are never written), the per-cell-weight kernel
+    keeps them at zero.  Both against the FP64 oracle, and against each other
+    at rounding level (only the end thread's renormalisation sees the
+    padding); 60 steps include renormalisation checks and a growth of about
+    e^6."""
+    p = synth.scaled(synth.SLAB_2D, n_xi=n_xi, dxi=0.05, length=n_xi * 0.05, k_list=[0.3, 0.9, 1.7, 2.6],
+                     profile="flattop", gamma_b=20.0, dt=1.5)
+    out = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("QS_RES_NO_UNIFORM", env)
+        s, nb, th = _run_gpu(qs, p, "fp32", 60, seed=("noise", 7, 1e-6), launch=_res(32, w))
+        out[env] = (nb, th)
+        s.close()
+    nb_o, th_o = _run_oracle(p, 60, seed=("noise", 7, 1e-6))
+    for env in ("0", "1"):
+        assert _log_err(out[env][0], nb_o) <= FP32_LOG_TOL, env
+        assert _log_err(out[env][1], th_o) <= FP32_LOG_TOL, env
+    assert _log_err(out["0"][0], out["1"][0]) <= 1e-5
+    assert _log_err(out["0"][1], out["1"][1]) <= 1e-5
+
+
 @pytest.mark.parametrize("pers", [0, 1])
 def test_uniform_weight_kernel_instances(qs, monkeypatch, pers):
     """Two uniform instances of different density, gamma and length (1024 and
