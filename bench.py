@@ -493,14 +493,14 @@ def run_surrogate(args):
     m.close()
 
 
-def run_mlp(args):
+def mlp_leg(args, pk, pk_kind):
     """The surrogate network alone on seeded random rows: --mlp-steps training
     steps of 16,384 rows x 4 members (16 -> 256 x 3 -> 2, BF16 on tcgen05)
-    and ensemble inference of --mlp-rows rows, each timed with CUDA events."""
+    and ensemble inference of --mlp-rows rows, each timed with CUDA events,
+    against the measured BF16 tensor rate (burst: each timed region is a
+    few milliseconds)."""
     import torch
     from paper_2607_24234_b300 import surrogate as sur
-    torch.cuda.set_device(0)
-    pk, _ = peaks()
     rng = np.random.default_rng(0)
     n = 16384
     X = torch.from_numpy((rng.standard_normal((args.mlp_rows, 7)) * 3).astype(np.float32)).cuda()
@@ -511,20 +511,39 @@ def run_mlp(args):
     stream = torch.cuda.current_stream()
     for _ in range(3):
         m.train_step(X[:n], Y[:n], 1e-3)
+    m.infer(X[:n])
+    torch.cuda.synchronize()
+    # (each timed region lasts milliseconds, shorter than the clock sampling
+    # interval: the line's clock record comes from the headline's region)
     t_step, _ = time_job(stream, lambda: [m.train_step(X[i * n % (args.mlp_rows - n):][:n], Y[:n], 1e-3)
                                           for i in range(args.mlp_steps)], 1)
-    m.infer(X[:n])
     t_inf, _ = time_job(stream, lambda: m.infer(X), 3)
+    m.close()
     nparam = 7 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 2 + 2
     flops_step = 6.0 * nparam * n * 4
     ms = 1e3 * t_step / args.mlp_steps
-    print(json.dumps({"metric": "surrogate MLP: training step time and inference queries/s", "workload": "mlp_16384x4",
-                      "train_ms_per_step": ms, "train_tflops": flops_step / (ms / 1e3) / 1e12,
-                      "train_frac_of_bf16_peak": flops_step / (ms / 1e3) / 1e12 / pk.get("bf16_tflops", 1800.0),
-                      "infer_rows": args.mlp_rows, "infer_queries_per_s": args.mlp_rows / t_inf,
-                      "infer_tflops": 2.0 * nparam * 4 * args.mlp_rows / t_inf / 1e12,
-                      "gelu_per_query": 3 * 256 * 4}), flush=True)
-    m.close()
+    train_tf = flops_step / (ms / 1e3) / 1e12
+    infer_tf = 2.0 * nparam * 4 * args.mlp_rows / t_inf / 1e12
+    peak = pk.get("bf16_tflops", 1800.0)
+    src = "measured (cuBLAS bf16 burst)" if pk_kind == "measured" else "fallback"
+    return {"workload": "mlp_16384x4", "dtype": "bf16 (fp32 accumulate)",
+            "train_ms_per_step": ms, "train_tflops": train_tf, "train_frac_of_bf16_peak": train_tf / peak,
+            "infer_rows": args.mlp_rows, "infer_queries_per_s": args.mlp_rows / t_inf, "infer_tflops": infer_tf,
+            "roofline": {"bound": "tensor", "achieved": train_tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": train_tf / peak, "traffic": None, "peak_source": src,
+                         "note": "algorithmic forward + backward FLOPs (6 x params x rows x members) per training step; "
+                                 "the step is bound by its epilogues (GELU and its derivative), not by the MMAs"},
+            "infer_roofline": {"bound": "tensor", "achieved": infer_tf, "peak": peak, "unit": "TFLOP/s",
+                               "frac": infer_tf / peak, "traffic": None, "peak_source": src},
+            "gelu_per_query": 3 * 256 * 4}
+
+
+def run_mlp(args):
+    import torch
+    torch.cuda.set_device(0)
+    pk, pk_kind = peaks()
+    r = mlp_leg(args, pk, pk_kind)
+    print(json.dumps({"metric": "surrogate MLP: training step time and inference queries/s", **r}), flush=True)
 
 
 def narrow_leg(args, pk, pk_kind):
@@ -809,6 +828,8 @@ def run_ours(args):
     torch.cuda.empty_cache()
     batch = batch_leg(args, pk, pk_kind, alu) if (rank == 0 and args.batch) else None
     torch.cuda.empty_cache()
+    mlp = mlp_leg(args, pk, pk_kind) if (rank == 0 and args.mlp) else None
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu:
@@ -829,7 +850,7 @@ def run_ours(args):
             "roofline": roofline,
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "diag_on": diag_on,
             "green_path": green, "fp64": fp64, "hbm_streaming": hbm_streaming, "batch": batch,
-            "narrow": narrow, "alu_peaks": alu,
+            "narrow": narrow, "mlp": mlp, "alu_peaks": alu,
             "cpu_baseline": cpu, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
@@ -880,6 +901,7 @@ def main():
     ap.add_argument("--narrow-reps", type=int, default=2)
     ap.add_argument("--narrow-nxi", type=int, default=None, help="xi slices of the narrow beam (profiling)")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batched-workload leg")
+    ap.add_argument("--no-mlp", dest="mlp", action="store_false", help="skip the surrogate-network leg")
     ap.add_argument("--batch-jobs", type=int, default=1)
     ap.add_argument("--batch-shape", default="3,32,8,0,1",
                     help="batched workload launch 'variant,prefetch,warps_per_cta,persistent,ctas_per_sm[,scan_cells]'")
