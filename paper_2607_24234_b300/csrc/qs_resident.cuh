@@ -521,13 +521,21 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
                 const int e_rec = e;
                 if (a.update) gmax = pass2(Y_(), Y_(), Y_(), n, d, A, B, mx, rc, An, Ad);
                 else pass2(N_(), Y_(), N_(), n, d, A, B, mx, rc, An, Ad);
-                // thread maxima as logs (mantissa log + exponent), then the line's maximum
+                // the warp's maxima at one scale 2^(2 Ew), Ew the warp's
+                // largest exponent (power-of-two rescaling: exact, so the
+                // maximum is that of the values; lanes more than 64 octaves
+                // below it cannot hold it), reduced in FP32, then the log:
+                // the mantissa part in FP32, only Ew ln 2 added in FP64 (the
+                // FP64 pipe is far narrower than the FP32 one)
+                const int Ew = __reduce_max_sync(FULL, has ? e_rec : RES_NONE);
+                const float fsc = p2(2 * max(e_rec - Ew, -64));
                 double lg[3];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    lg[i] = (has && mx[i] > 0.f) ? 0.5 * log((double)mx[i]) + e_rec * 0.69314718055994530942 : -INFINITY;
+                    float m = (has && mx[i] > 0.f) ? mx[i] * fsc : 0.f;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) lg[i] = fmax(lg[i], __shfl_xor_sync(FULL, lg[i], o));
+                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+                    lg[i] = m > 0.f ? (double)(0.5f * logf(m)) + Ew * 0.69314718055994530942 : -INFINITY;
                 }
                 if (lane == 0) { sMM[warp][0] = lg[0]; sMM[warp][1] = lg[1]; sMM[warp][2] = lg[2]; }
                 __syncthreads();
