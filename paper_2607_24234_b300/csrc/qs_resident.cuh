@@ -422,6 +422,17 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
         pass1(An, Ad);
         float fkm[5];        // scan scale factors (see the scan below)
         bool echg = true;    // this thread's exponent changed since fkm was formed
+        // recording steps (per-mode maxima): step `it` records snapshot
+        // rec_snap when it == rec_it; the one division happens here
+        const bool rec_on = (a.rec_kinds & 4) != 0;
+        int rec_it = -1;            // (steps of one call: int)
+        long long rec_snap = 0;
+        if (rec_on) {
+            const long long d0 = a.step0 - a.rec_g0;   // the record clock at it = 0
+            rec_snap = d0 >= 0 ? (d0 + a.rec_stride - 1) / a.rec_stride : 0;
+            const long long f = rec_snap * a.rec_stride - d0;
+            rec_it = f < a.n_steps ? (int)f : -1;
+        }
         for (int it = 0; it < a.n_steps; ++it) {
             const float hf = (a.step0 + it) == 0 ? 0.5f : 1.0f;
             float A[NS], B[NS];
@@ -498,9 +509,10 @@ __global__ void __maxnreg__(res_maxnreg(NS, V, TT)) k_sweep_res(const SweepArgs 
             using Y_ = std::integral_constant<bool, true>;
             using N_ = std::integral_constant<bool, false>;
             long long snap = -1;   // recording step (per-mode maxima), uniform over the CTA
-            if (a.rec_kinds & 4) {
-                const long long dg = a.step0 + it - a.rec_g0;
-                if (dg >= 0 && dg % a.rec_stride == 0 && dg / a.rec_stride < a.rec_max_snap) snap = dg / a.rec_stride;
+            if (rec_on && it == rec_it) {
+                if (rec_snap < a.rec_max_snap) snap = rec_snap;
+                ++rec_snap;
+                rec_it += a.rec_stride;
             }
             float gmax = 0.f;
             if (snap >= 0) {
