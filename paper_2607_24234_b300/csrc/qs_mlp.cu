@@ -635,6 +635,36 @@ struct FusedArgs {
     const float *Y;                  // [n][2] targets (regression, class)
     float yinv;                      // 1 / ystd
     float *loss, *G;
+    int split;                       // allow the last round's items to be split in halves (Units)
+};
+
+// Work units of a grid of G CTAs over `items` 128-row items.  The first
+// R = items / G rounds take whole items.  When the last round's rem items
+// would leave at least half of the CTAs idle (2 rem <= G), each of them is
+// split into two 64-row halves taken by 2 rem CTAs: the MMAs still cover the
+// whole tile, but only the warps whose TMEM lane quarters hold the unit's
+// half run the epilogue, so a half costs well under a whole item and the
+// last round ends sooner.  Every row is still handled exactly once.
+struct Units {
+    long long R, rem, G, n;
+    bool split;
+    __device__ Units(long long items, long long g, bool allow) : G(g) {
+        R = items / G;
+        rem = items - R * G;
+        split = allow && rem > 0 && 2 * rem <= G;
+        n = split ? R * G + 2 * rem : items;
+    }
+    // item of unit u and its half (-1: the whole item)
+    __device__ void at(long long u, long long &item, int &half) const {
+        if (split && u >= R * G) {
+            const long long h = u - R * G;
+            item = R * G + h / 2;
+            half = (int)(h & 1);
+        } else {
+            item = u;
+            half = -1;
+        }
+    }
 };
 
 namespace fz {
@@ -729,9 +759,13 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
         if (!done) atomicOr(&s_bad, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
+    // this warp's rows belong to the current unit (a half unit leaves the
+    // other half's warps without epilogue work; they still meet every barrier)
+    bool wact = true;
     // accumulator -> bias + GELU -> bf16 activations in the A operand layout;
     // training also stores H^T and D = gelu'(Z) of rows inside the batch
     auto epilogue_hidden = [&](const float *b, int layer, long long r0, int e) {
+        if (!wact) return;
         const long long gr = r0 + row;
         const bool keep = TRAIN && gr < a.n;
 #pragma unroll 1
@@ -774,7 +808,14 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
     // inference: one item per tile, members inside (the ensemble statistics);
     // training: one item per (tile, member)
     const long long nitems = TRAIN ? ntiles * a.E : ntiles;
-    for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    // (training only: inference runs 2^20-row batches, where the last round
+    // is a small part of the launch)
+    const Units U(nitems, gridDim.x, TRAIN && a.split != 0);
+    for (long long u = blockIdx.x; u < U.n && ok; u += gridDim.x) {
+        long long item = u;
+        int half = -1;
+        if constexpr (TRAIN) U.at(u, item, half);
+        wact = half < 0 || (q >> 1) == half;
         const long long tile = TRAIN ? item / a.E : item;
         const int e_lo = TRAIN ? (int)(item % a.E) : 0, e_hi = TRAIN ? e_lo + 1 : a.E;
         const long long r0 = tile * 128;
@@ -815,7 +856,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
             float o0 = 0.f, o1 = 0.f;
             const long long gr = r0 + row;
 #pragma unroll 1
-            for (int c = 0; c < NCH; ++c) {
+            for (int c = 0; c < NCH && wact; ++c) {
                 const int c0 = CW * hc + 32 * c;
                 float v[32];
                 fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
@@ -832,11 +873,11 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
                     o1 = fmaf(h1, w3[W + c0 + j + 1], o1);
                 }
             }
-            if (hc > 0) { part[(hc - 1) * 256 + 2 * row] = o0; part[(hc - 1) * 256 + 2 * row + 1] = o1; }
+            if (wact && hc > 0) { part[(hc - 1) * 256 + 2 * row] = o0; part[(hc - 1) * 256 + 2 * row + 1] = o1; }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (hc == 0) {
+            if (wact && hc == 0) {
 #pragma unroll
                 for (int g = 1; g < NQ; ++g) { o0 += part[(g - 1) * 256 + 2 * row]; o1 += part[(g - 1) * 256 + 2 * row + 1]; }
                 const float r0u = o0 + w3[2 * W];    // raw outputs (standardised units)
@@ -879,10 +920,10 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
                 // backward through the output layer from the layer-2
                 // accumulator still in TMEM: dW3 += g^T H2, dz2 = (g W3) * gelu'(Z2),
                 // b2's gradient += column sums of dz2
-                const float g0 = part[2 * row], g1 = part[2 * row + 1];
+                const float g0 = wact ? part[2 * row] : 0.f, g1 = wact ? part[2 * row + 1] : 0.f;
                 const bool keep = gr < a.n;
 #pragma unroll 1
-                for (int c = 0; c < NCH; ++c) {
+                for (int c = 0; c < NCH && wact; ++c) {
                     const int c0 = CW * hc + 32 * c;
                     float hv[32], dz[32], t[32];
                     fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, hv);
@@ -932,7 +973,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
             }
             ok = s_bad == 0;
         }
-        if (!TRAIN && hc == 0 && ok) {
+        if (!TRAIN && wact && hc == 0 && ok) {
             const long long gr = r0 + row;
             if (gr < a.n) {
                 const float inv = 1.0f / a.E;
@@ -976,6 +1017,7 @@ struct DxArgs {
     long long n, sa, sw;
     int E;
     int *err;
+    int split;                 // allow the last round's items to be split in halves (Units)
 };
 
 namespace dxk {
@@ -1031,8 +1073,16 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
     uint32_t phase = 0;
     bool ok = true;
     int cur = -1;
-    if ((long long)blockIdx.x < nitems) cur = issue(blockIdx.x, cur);
-    for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    const Units U(nitems, gridDim.x, a.split != 0);
+    long long item = 0;
+    int half = -1;
+    if ((long long)blockIdx.x < U.n) {
+        U.at(blockIdx.x, item, half);
+        cur = issue(item, cur);
+    }
+    for (long long u = blockIdx.x; u < U.n && ok; u += gridDim.x) {
+        U.at(u, item, half);
+        const bool wact = half < 0 || (q >> 1) == half;   // this warp's rows belong to the unit
         const int e = (int)(item / ntiles);
         const long long r0 = (item % ntiles) * 128;
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -1060,7 +1110,7 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
         const long long gr = r0 + row;
         const bool keep = gr < a.n;
         uint4 dv[16];
-        {
+        if (wact) {
             const uint4 *d = reinterpret_cast<const uint4 *>(a.D + e * a.sa + (keep ? gr : r0) * W + 128 * hc);
 #pragma unroll
             for (int k = 0; k < 16; ++k) dv[k] = d[k];
@@ -1073,10 +1123,15 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
         ok = __syncthreads_and(done) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
-        // the operands are free: the next item's copies run under the epilogue
-        if (item + gridDim.x < nitems) cur = issue(item + gridDim.x, cur);
+        // the operands are free: the next unit's copies run under the epilogue
+        if (u + gridDim.x < U.n) {
+            long long nitem;
+            int nhalf;
+            U.at(u + gridDim.x, nitem, nhalf);
+            cur = issue(nitem, cur);
+        }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 4 && wact; ++c) {
             const int c0 = 128 * hc + 32 * c;
             float v[32];
             fz_tmem_ld32(taddr + ((uint32_t)(32 * q) << 16) + c0, v);
@@ -1371,6 +1426,7 @@ __global__ void k_colstats(const float *x, long long n, int d, float *mean, floa
 struct qs_mlp {
     int n_in = 7, width = 256, depth = 3, n_out = 2, E = 4, kin = 16;
     int max_batch = 0;
+    int split = 1;   // fused forward and dX kernels: last-round items split in halves (QS_MLP_NO_SPLIT=1: never)
     cudaStream_t stream = nullptr;
     qs_allocator alloc{};
     bool has_alloc = false;
@@ -1482,6 +1538,7 @@ mlp::FusedArgs fused_args(qs_mlp *m, const float *X, long long n) {
     fa.w0 = m->woff[0]; fa.w1 = m->woff[1]; fa.w2 = m->woff[2]; fa.w3 = m->woff[3];
     fa.b0 = m->boff[0]; fa.b1 = m->boff[1]; fa.b2 = m->boff[2]; fa.b3 = m->boff[3];
     fa.E = m->E; fa.ymean = m->ymean; fa.ystd = m->ystd; fa.err = m->errw;
+    fa.split = m->split;
     return fa;
 }
 
@@ -1632,7 +1689,7 @@ void backward(qs_mlp *m, int n, bool fused) {
             mlp::DxArgs da{};
             da.dz = dz; da.WT = m->PT + m->woff[l]; da.D = m->D[l - 1];
             da.out = dst; da.outT = m->TDZ; da.bgrad = G + m->boff[l - 1];
-            da.n = n; da.sa = as; da.sw = m->nparam; da.E = m->E; da.err = m->errw;
+            da.n = n; da.sa = as; da.sw = m->nparam; da.E = m->E; da.err = m->errw; da.split = m->split;
             const long long items = (n + 127) / 128 * (long long)m->E;
             mlp::k_dx_tc<<<(unsigned)std::min<long long>(nsm, items), 256, mlp::dxk::SMEM, m->stream>>>(da);
             dzt_ready = true;
@@ -1762,6 +1819,7 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     // selects the layer-by-layer path (used to compare the two)
     m->fused_ok = m->kin == 16 && width == 256 && depth == 3 && n_out == 2;
     if (const char *v = getenv("QS_MLP_NO_FUSED")) m->fused_ok = m->fused_ok && v[0] == '0';
+    if (const char *v = getenv("QS_MLP_NO_SPLIT")) m->split = v[0] == '1' ? 0 : 1;
     if (m->fused_ok)
         for (int l = 0; l + 1 < depth; ++l) {
             __nv_bfloat16 *d;

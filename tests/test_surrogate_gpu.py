@@ -77,6 +77,35 @@ def test_forward_and_gradients_match_fp64(sg, monkeypatch, no_fused, n):
     m.close()
 
 
+def test_fused_training_split_last_round(sg, monkeypatch):
+    """16,384 rows x 4 members are 512 (tile, member) items; on 148 SMs the
+    last round's 68 items are split into 64-row halves by the fused forward
+    and the input-gradient kernel.  The loss and every member's gradients
+    equal those of the unsplit launches (QS_MLP_NO_SPLIT=1) up to the order
+    of the atomic sums.  A 64-row half dropped or counted twice would move
+    them by about 64/16,384 = 4e-3, far above the 1e-5 bound."""
+    import torch
+    qs, sur = sg
+    n = 16384
+    rng = np.random.default_rng(3)
+    X = (rng.standard_normal((n, 7)) * np.array([1.0, 2.0, 50.0, 30.0, 500.0, 2.0, 1.5])
+         + np.array([-4.0, 6.0, 100.0, 40.0, 900.0, 3.0, 0.0])).astype(np.float32)
+    Y = np.stack([10 * rng.standard_normal(n) + 20, (rng.random(n) > 0.4)], axis=1).astype(np.float32)
+    Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    out = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("QS_MLP_NO_SPLIT", env)
+        m = sur.MLP(width=256, depth=3, ensemble=4, max_batch=n, seed=1)
+        m.set_norm(Xt, Yt)
+        loss = m.train_step(Xt, Yt, 0.0, update=False, want_loss=True)
+        out[env] = (loss, [m.grads(e) for e in range(4)])
+        m.close()
+    assert abs(out["0"][0] - out["1"][0]) <= 1e-5 * abs(out["1"][0])
+    for e in range(4):
+        assert _rel(out["0"][1][e], out["1"][1][e]) <= 1e-5, e
+    assert np.isfinite(out["0"][0]) and out["0"][0] > 0
+
+
 def test_training_samples_match_oracle_targets(sg):
     import torch
     qs, sur = sg
