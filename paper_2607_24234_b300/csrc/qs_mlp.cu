@@ -1342,8 +1342,17 @@ __global__ void k_colsum(const __nv_bfloat16 *g, int n, int cols, float *out) {
 }
 
 // Adam on fp32 master weights; refreshes the bf16 copy.
+// where Adam also writes the bf16 transposes W^T [in][out] of layers
+// 1..nl (the input-gradient kernels' operands), so that no separate pass
+// over the weights follows the update; PT = nullptr: no transposes
+struct WtOut {
+    __nv_bfloat16 *PT;
+    int nparam, nl;
+    int off[8], lin[8], lout[8];
+};
+
 __global__ void k_adam(float *w, float *m, float *v, const float *g, long long n, float lr, float b1, float b2,
-                       float eps, float c1, float c2, __nv_bfloat16 *wb) {
+                       float eps, float c1, float c2, __nv_bfloat16 *wb, const WtOut wt) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -1353,7 +1362,19 @@ __global__ void k_adam(float *w, float *m, float *v, const float *g, long long n
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     w[i] = wi;
-    if (wb) wb[i] = __float2bfloat16(wi);
+    const __nv_bfloat16 bw = __float2bfloat16(wi);
+    if (wb) wb[i] = bw;
+    if (wt.PT) {
+        const int e = (int)(i / wt.nparam), j = (int)(i - (long long)e * wt.nparam);   // member, index within it
+        for (int l = 0; l < wt.nl; ++l) {
+            const int r = j - wt.off[l];
+            if (r >= 0 && r < wt.lin[l] * wt.lout[l]) {
+                const int o = r / wt.lin[l], c = r - o * wt.lin[l];
+                wt.PT[(long long)e * wt.nparam + wt.off[l] + (long long)c * wt.lout[l] + o] = bw;
+                break;
+            }
+        }
+    }
 }
 
 __global__ void k_to_bf16(const float *w, long long n, __nv_bfloat16 *wb) {
@@ -1427,6 +1448,7 @@ struct qs_mlp {
     int n_in = 7, width = 256, depth = 3, n_out = 2, E = 4, kin = 16;
     int max_batch = 0;
     int split = 1;   // fused forward and dX kernels: last-round items split in halves (QS_MLP_NO_SPLIT=1: never)
+    int wt_pass = 0; // 1: W^T copies by a separate pass after Adam instead of by Adam (QS_MLP_WT_PASS=1)
     cudaStream_t stream = nullptr;
     qs_allocator alloc{};
     bool has_alloc = false;
@@ -1820,6 +1842,7 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     m->fused_ok = m->kin == 16 && width == 256 && depth == 3 && n_out == 2;
     if (const char *v = getenv("QS_MLP_NO_FUSED")) m->fused_ok = m->fused_ok && v[0] == '0';
     if (const char *v = getenv("QS_MLP_NO_SPLIT")) m->split = v[0] == '1' ? 0 : 1;
+    if (const char *v = getenv("QS_MLP_WT_PASS")) m->wt_pass = v[0] == '1' ? 1 : 0;
     if (m->fused_ok)
         for (int l = 0; l + 1 < depth; ++l) {
             __nv_bfloat16 *d;
@@ -1914,9 +1937,20 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
     backward(m, nb, fused);
     if (do_update) {
         const long long np = m->nparam * m->E;   // members' parameters are contiguous
+        mlp::WtOut wt{};
+        if (m->depth <= 8 && !m->wt_pass) {   // the W^T copies with the update
+            wt.PT = m->PT;
+            wt.nparam = (int)m->nparam;
+            wt.nl = m->depth;
+            for (int l = 1; l <= m->depth; ++l) {
+                wt.off[l - 1] = (int)m->woff[l];
+                wt.lin[l - 1] = m->lin[l];
+                wt.lout[l - 1] = m->lout[l];
+            }
+        }
         mlp::k_adam<<<(unsigned)((np + 255) / 256), 256, 0, m->stream>>>(m->P, m->Mm, m->Vv, m->G, np, lr, b1, b2,
-                                                                           1e-8f, c1, c2, m->Pb);
-        refresh_wt(m);
+                                                                           1e-8f, c1, c2, m->Pb, wt);
+        if (!wt.PT) refresh_wt(m);
     }
     if (!do_update) --m->step;
     if (cudaGetLastError() != cudaSuccess) return mfail(m, QS_ERR_CUDA, "mlp launch failed");

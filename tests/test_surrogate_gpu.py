@@ -106,6 +106,35 @@ def test_fused_training_split_last_round(sg, monkeypatch):
     assert np.isfinite(out["0"][0]) and out["0"][0] > 0
 
 
+def test_adam_writes_the_transposed_weights(sg, monkeypatch):
+    """Adam writes the bf16 copies W^T that the next step's input-gradient
+    kernels read.  Three updating steps, then the loss and the gradients of
+    a fourth, against the same run with the copies made by a separate pass
+    after the update (QS_MLP_WT_PASS=1).  The values written are the same;
+    the runs differ only in the order of their atomic sums.  A wrong or
+    stale W^T would give wrong input gradients from the second step on."""
+    import torch
+    qs, sur = sg
+    n = 4096
+    rng = np.random.default_rng(5)
+    X = (rng.standard_normal((n, 7)) * 3).astype(np.float32)
+    Y = np.stack([10 * rng.standard_normal(n) + 20, (rng.random(n) > 0.4)], axis=1).astype(np.float32)
+    Xt, Yt = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    out = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("QS_MLP_WT_PASS", env)
+        m = sur.MLP(width=256, depth=3, ensemble=2, max_batch=n, seed=2)
+        m.set_norm(Xt, Yt)
+        for _ in range(3):
+            m.train_step(Xt, Yt, 3e-3)
+        loss = m.train_step(Xt, Yt, 0.0, update=False, want_loss=True)
+        out[env] = (loss, [m.grads(e) for e in range(2)])
+        m.close()
+    assert abs(out["0"][0] - out["1"][0]) <= 1e-4 * abs(out["1"][0])
+    for e in range(2):
+        assert _rel(out["0"][1][e], out["1"][1][e]) <= 1e-3, e
+
+
 def test_training_samples_match_oracle_targets(sg):
     import torch
     qs, sur = sg
