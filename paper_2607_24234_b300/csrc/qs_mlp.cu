@@ -1341,40 +1341,104 @@ __global__ void k_colsum(const __nv_bfloat16 *g, int n, int cols, float *out) {
     if (threadIdx.x == 0) out[c] = red[0];
 }
 
-// Adam on fp32 master weights; refreshes the bf16 copy.
-// where Adam also writes the bf16 transposes W^T [in][out] of layers
-// 1..nl (the input-gradient kernels' operands), so that no separate pass
-// over the weights follows the update; PT = nullptr: no transposes
-struct WtOut {
-    __nv_bfloat16 *PT;
-    int nparam, nl;
-    int off[8], lin[8], lout[8];
+// Adam on fp32 master weights (bias-corrected by c1 = 1 - b1^t and
+// c2 = 1 - b2^t); returns the updated weight rounded to bf16.
+struct AdamC {
+    float lr, b1, b2, eps, c1, c2;
 };
 
-__global__ void k_adam(float *w, float *m, float *v, const float *g, long long n, float lr, float b1, float b2,
-                       float eps, float c1, float c2, __nv_bfloat16 *wb, const WtOut wt) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+__device__ __forceinline__ __nv_bfloat16 adam_reg(float *w, float *m, float *v, long long i, float gi, float m0,
+                                                  float v0, float w0, const AdamC &a) {
+    const float mi = a.b1 * m0 + (1.0f - a.b1) * gi;
+    const float vi = a.b2 * v0 + (1.0f - a.b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float wi = w0 - a.lr * (mi / a.c1) / (sqrtf(vi / a.c2) + a.eps);
     w[i] = wi;
-    const __nv_bfloat16 bw = __float2bfloat16(wi);
-    if (wb) wb[i] = bw;
-    if (wt.PT) {
-        const int e = (int)(i / wt.nparam), j = (int)(i - (long long)e * wt.nparam);   // member, index within it
-        for (int l = 0; l < wt.nl; ++l) {
-            const int r = j - wt.off[l];
-            if (r >= 0 && r < wt.lin[l] * wt.lout[l]) {
-                const int o = r / wt.lin[l], c = r - o * wt.lin[l];
-                wt.PT[(long long)e * wt.nparam + wt.off[l] + (long long)c * wt.lout[l] + o] = bw;
-                break;
+    return __float2bfloat16(wi);
+}
+
+__device__ __forceinline__ __nv_bfloat16 adam_one(float *w, float *m, float *v, const float *g, long long i,
+                                                  const AdamC &a) {
+    return adam_reg(w, m, v, i, g[i], m[i], v[i], w[i], a);
+}
+
+// Flat update of n parameters; refreshes the bf16 copy wb.
+__global__ void k_adam(float *w, float *m, float *v, const float *g, long long n, const AdamC a,
+                       __nv_bfloat16 *wb) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) wb[i] = adam_one(w, m, v, g, i, a);
+}
+
+// The update that also writes the bf16 transposes W^T [in][out] of the
+// layers the input-gradient kernels read, so that no separate pass over
+// the weights follows it.  Per member the parameters split into those
+// layers' weight matrices (row-major [out][in] at off[l]) and the rest,
+// nseg contiguous segments (sbeg[s], spre[s + 1] - spre[s] long).
+//   blocks [0, E * tile0[nl]): one 32 x 32 tile of one matrix each; the
+//     tile's bf16 values pass through shared memory so that both W and
+//     W^T are written along rows;
+//   the blocks after them: the rest, one parameter per thread.
+struct WtOut {
+    __nv_bfloat16 *PT;
+    int E, nparam, nl, nseg;
+    int off[8], lin[8], lout[8];
+    int tile0[9];              // prefix of 32 x 32 tile counts over the layers
+    int sbeg[9], spre[10];     // the other parameters' segments, prefix of their lengths
+};
+
+__global__ void __launch_bounds__(256) k_adam_wt(float *w, float *m, float *v, const float *g, const AdamC a,
+                                                 __nv_bfloat16 *wb, const WtOut wt) {
+    __shared__ __nv_bfloat16 tile[32][34];   // odd word stride: the column reads hit 32 banks
+    const int T = wt.tile0[wt.nl];
+    const int b = blockIdx.x;
+    if (b < wt.E * T) {
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+        const int e = b / T;
+        int t = b - e * T, l = 0;
+        while (t >= wt.tile0[l + 1]) ++l;
+        t -= wt.tile0[l];
+        const int lin = wt.lin[l], lout = wt.lout[l], ntx = (lin + 31) >> 5;
+        const int o0 = (t / ntx) * 32, c0 = (t - (t / ntx) * ntx) * 32;
+        const long long base = (long long)e * wt.nparam + wt.off[l];
+        // the four rows' operands are loaded before any store, so that their
+        // DRAM reads overlap
+        float gk[4], mk[4], vk[4], wk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int o = o0 + ty + 8 * k, c = c0 + tx;
+            if (o < lout && c < lin) {
+                const long long i = base + (long long)o * lin + c;
+                gk[k] = g[i]; mk[k] = m[i]; vk[k] = v[i]; wk[k] = w[i];
             }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int o = o0 + ty + 8 * k, c = c0 + tx;
+            if (o < lout && c < lin) {
+                const long long i = base + (long long)o * lin + c;
+                const __nv_bfloat16 bw = adam_reg(w, m, v, i, gk[k], mk[k], vk[k], wk[k], a);
+                wb[i] = bw;
+                tile[ty + 8 * k][tx] = bw;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + ty + 8 * k, o = o0 + tx;
+            if (o < lout && c < lin) wt.PT[base + (long long)c * lout + o] = tile[tx][ty + 8 * k];
+        }
+        return;
     }
+    const long long R = wt.spre[wt.nseg];
+    const long long k = (long long)(b - wt.E * T) * blockDim.x + threadIdx.x;
+    if (k >= (long long)wt.E * R) return;
+    const int e = (int)(k / R);
+    const int r = (int)(k - (long long)e * R);
+    int s = 0;
+    while (r >= wt.spre[s + 1]) ++s;
+    const long long i = (long long)e * wt.nparam + wt.sbeg[s] + (r - wt.spre[s]);
+    wb[i] = adam_one(w, m, v, g, i, a);
 }
 
 __global__ void k_to_bf16(const float *w, long long n, __nv_bfloat16 *wb) {
@@ -1550,6 +1614,46 @@ void refresh_wt(qs_mlp *m) {
         mlp::k_transpose_bf16<<<dim3((unsigned)((nw + 255) / 256), m->E), 256, 0, m->stream>>>(
             m->P + m->woff[l], m->lout[l], m->lin[l], m->PT + m->woff[l], m->nparam);
     }
+}
+
+// The tiled update's work split: the weight matrices of layers 1..depth
+// (whose transposes dX reads) in 32 x 32 tiles, every other parameter of a
+// member in the segments between them.  False if the layout does not fit
+// the kernel's tables.
+bool adam_wt_plan(const qs_mlp *m, mlp::WtOut &wt) {
+    wt.PT = m->PT;
+    wt.E = m->E;
+    wt.nparam = (int)m->nparam;
+    wt.nl = m->depth;
+    wt.tile0[0] = 0;
+    for (int l = 1; l <= m->depth; ++l) {
+        wt.off[l - 1] = (int)m->woff[l];
+        wt.lin[l - 1] = m->lin[l];
+        wt.lout[l - 1] = m->lout[l];
+        wt.tile0[l] = wt.tile0[l - 1] + ((m->lout[l] + 31) / 32) * ((m->lin[l] + 31) / 32);
+    }
+    // the complement of the matrices in [0, nparam), in offset order
+    int ord[8];
+    for (int l = 0; l < wt.nl; ++l) ord[l] = l;
+    std::sort(ord, ord + wt.nl, [&](int x, int y) { return wt.off[x] < wt.off[y]; });
+    long long at = 0;
+    wt.nseg = 0;
+    wt.spre[0] = 0;
+    auto seg = [&](long long b, long long e) {
+        if (e <= b) return;
+        wt.sbeg[wt.nseg] = (int)b;
+        wt.spre[wt.nseg + 1] = wt.spre[wt.nseg] + (int)(e - b);
+        ++wt.nseg;
+    };
+    for (int q = 0; q < wt.nl; ++q) {
+        const int l = ord[q];
+        if (wt.off[l] < at) return false;   // overlapping matrices
+        seg(at, wt.off[l]);
+        at = wt.off[l] + (long long)wt.lin[l] * wt.lout[l];
+    }
+    if (at > m->nparam) return false;
+    seg(at, m->nparam);
+    return true;
 }
 
 // fused forward (k_mlp_fused): the common arguments
@@ -1937,20 +2041,17 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
     backward(m, nb, fused);
     if (do_update) {
         const long long np = m->nparam * m->E;   // members' parameters are contiguous
+        const mlp::AdamC ac{lr, b1, b2, 1e-8f, c1, c2};
         mlp::WtOut wt{};
-        if (m->depth <= 8 && !m->wt_pass) {   // the W^T copies with the update
-            wt.PT = m->PT;
-            wt.nparam = (int)m->nparam;
-            wt.nl = m->depth;
-            for (int l = 1; l <= m->depth; ++l) {
-                wt.off[l - 1] = (int)m->woff[l];
-                wt.lin[l - 1] = m->lin[l];
-                wt.lout[l - 1] = m->lout[l];
-            }
+        if (m->depth <= 8 && !m->wt_pass && adam_wt_plan(m, wt)) {   // the W^T copies with the update
+            const long long rest = (long long)wt.E * wt.spre[wt.nseg];
+            const unsigned nblk = (unsigned)(wt.E * wt.tile0[wt.nl] + (rest + 255) / 256);
+            mlp::k_adam_wt<<<nblk, 256, 0, m->stream>>>(m->P, m->Mm, m->Vv, m->G, ac, m->Pb, wt);
+        } else {
+            mlp::k_adam<<<(unsigned)((np + 255) / 256), 256, 0, m->stream>>>(m->P, m->Mm, m->Vv, m->G, np, ac,
+                                                                               m->Pb);
+            refresh_wt(m);
         }
-        mlp::k_adam<<<(unsigned)((np + 255) / 256), 256, 0, m->stream>>>(m->P, m->Mm, m->Vv, m->G, np, lr, b1, b2,
-                                                                           1e-8f, c1, c2, m->Pb, wt);
-        if (!wt.PT) refresh_wt(m);
     }
     if (!do_update) --m->step;
     if (cudaGetLastError() != cudaSuccess) return mfail(m, QS_ERR_CUDA, "mlp launch failed");

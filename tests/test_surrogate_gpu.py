@@ -106,13 +106,17 @@ def test_fused_training_split_last_round(sg, monkeypatch):
     assert np.isfinite(out["0"][0]) and out["0"][0] > 0
 
 
-def test_adam_writes_the_transposed_weights(sg, monkeypatch):
+@pytest.mark.parametrize("width,depth", [(256, 3), (48, 2)])
+def test_adam_writes_the_transposed_weights(sg, monkeypatch, width, depth):
     """Adam writes the bf16 copies W^T that the next step's input-gradient
-    kernels read.  Three updating steps, then the loss and the gradients of
-    a fourth, against the same run with the copies made by a separate pass
-    after the update (QS_MLP_WT_PASS=1).  The values written are the same;
-    the runs differ only in the order of their atomic sums.  A wrong or
-    stale W^T would give wrong input gradients from the second step on."""
+    kernels read, in 32 x 32 tiles of each weight matrix.  Three updating
+    steps, then the loss and the gradients of a fourth, against the same run
+    with the copies made by a separate pass after the update
+    (QS_MLP_WT_PASS=1).  The values written are the same; the runs differ
+    only in the order of their atomic sums.  A wrong or stale W^T would give
+    wrong input gradients from the second step on.  Width 48 leaves tiles
+    16 columns wide at each matrix's edge, and the 2-row output layer fills
+    two rows of its tiles."""
     import torch
     qs, sur = sg
     n = 4096
@@ -123,7 +127,7 @@ def test_adam_writes_the_transposed_weights(sg, monkeypatch):
     out = {}
     for env in ("0", "1"):
         monkeypatch.setenv("QS_MLP_WT_PASS", env)
-        m = sur.MLP(width=256, depth=3, ensemble=2, max_batch=n, seed=2)
+        m = sur.MLP(width=width, depth=depth, ensemble=2, max_batch=n, seed=2)
         m.set_norm(Xt, Yt)
         for _ in range(3):
             m.train_step(Xt, Yt, 3e-3)
