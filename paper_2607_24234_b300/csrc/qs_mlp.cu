@@ -609,6 +609,16 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __nv_bfloat16 *A, con
 // and the ensemble's mean, variance and fallback mask per row, so nothing but
 // the inputs and the final statistics touches global memory.
 // ---------------------------------------------------------------------------
+// gelu'(Z) as the fused forward stores it and the input-gradient kernel
+// reads it: 128-row tiles of 16-byte column chunks, element (r, c) of a
+// member (256 columns) at ((r / 128) * 32 + c / 8) * 1024 + (r % 128) * 8 +
+// c % 8.  The 32 rows of a warp then store or load one chunk as 512
+// contiguous bytes; a member holds whole tiles (d_stride).
+__host__ __device__ __forceinline__ long long d_tile(long long r, int c) {
+    return (((r >> 7) * 32 + (c >> 3)) << 10) + ((r & 127) << 3) + (c & 7);
+}
+inline long long d_stride(long long rows) { return (rows + 127) / 128 * 128 * 256; }
+
 struct FusedArgs {
     const float *X;                  // [n][n_in] raw inputs
     long long n;
@@ -625,13 +635,14 @@ struct FusedArgs {
     int *err;
     // training (TRAIN): per (tile, member) item the forward stores what the
     // backward GEMMs read: H^T of the first two hidden layers (bf16 [256][n])
-    // and D = gelu'(Z) of the same layers (bf16 [n][256]), member stride
-    // `as`.  The output layer's backward runs in the last epilogue: the loss
+    // (member stride `as`) and D = gelu'(Z) of the same layers (bf16, in
+    // the tile layout of d_tile, member stride `ds`).  The output layer's
+    // backward runs in the last epilogue: the loss
     // (summed into *loss), dL/dz of the last hidden layer (DZ bf16 [n][256]
     // and its transpose DZT [256][n]), and the gradients of W3, b3 and b2,
     // added to G (fp32, member stride nparam, zeroed by the caller).
     __nv_bfloat16 *HT[2], *D[2], *DZ, *DZT;
-    long long as;
+    long long as, ds;
     const float *Y;                  // [n][2] targets (regression, class)
     float yinv;                      // 1 / ystd
     float *loss, *G;
@@ -793,7 +804,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
                 *reinterpret_cast<uint4 *>(Ab + (row / 8) * SBO_W + ((c0 + j) / 8) * LBO + (row % 8) * 16) =
                     *reinterpret_cast<const uint4 *>(h2);
                 if (keep) {
-                    *reinterpret_cast<uint4 *>(a.D[layer] + e * a.as + gr * W + c0 + j) = *reinterpret_cast<const uint4 *>(d2);
+                    *reinterpret_cast<uint4 *>(a.D[layer] + e * a.ds + d_tile(gr, c0 + j)) = *reinterpret_cast<const uint4 *>(d2);
                     __nv_bfloat16 *ht = a.HT[layer] + e * a.as + (long long)(c0 + j) * a.n + gr;
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
@@ -1011,10 +1022,10 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
 struct DxArgs {
     const __nv_bfloat16 *dz;   // [n][256] per member (stride sa)
     const __nv_bfloat16 *WT;   // [256][256] W^T per member (stride sw)
-    const __nv_bfloat16 *D;    // [n][256] gelu'(Z) of the layer below (stride sa)
+    const __nv_bfloat16 *D;    // gelu'(Z) of the layer below, tile layout d_tile (stride sd)
     __nv_bfloat16 *out, *outT; // dz_prev [n][256] and its transpose [256][n] (stride sa)
     float *bgrad;              // [256] per member (stride sw)
-    long long n, sa, sw;
+    long long n, sa, sw, sd;
     int E;
     int *err;
     int split;                 // allow the last round's items to be split in halves (Units)
@@ -1111,9 +1122,11 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
         const bool keep = gr < a.n;
         uint4 dv[16];
         if (wact) {
-            const uint4 *d = reinterpret_cast<const uint4 *>(a.D + e * a.sa + (keep ? gr : r0) * W + 128 * hc);
+            // (16-byte chunks 1024 elements = 128 uint4 apart; rows past n
+            // read the tile's first row)
+            const uint4 *d = reinterpret_cast<const uint4 *>(a.D + e * a.sd + d_tile(keep ? gr : r0, 128 * hc));
 #pragma unroll
-            for (int k = 0; k < 16; ++k) dv[k] = d[k];
+            for (int k = 0; k < 16; ++k) dv[k] = d[128 * k];
         }
         uint32_t done = 0;
         for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
@@ -1540,7 +1553,8 @@ struct qs_mlp {
     __nv_bfloat16 *TDZ = nullptr, *TACT = nullptr;   // [width][B]: dZ^T and act^T (K-major operands of dW)
     std::vector<__nv_bfloat16 *> HT;     // per hidden layer [width][B]: H^T written by the forward epilogue
     std::vector<char> ht_valid;          // HT[l] holds this batch (the forward ran on the tcgen05 path)
-    std::vector<__nv_bfloat16 *> D;      // fused training: gelu'(Z) of the first depth - 1 hidden layers [B][width]
+    std::vector<__nv_bfloat16 *> D;      // fused training: gelu'(Z) of the first depth - 1 hidden layers (d_tile layout)
+    long long dstride = 0;               // per-member stride of D (whole 128-row tiles)
     long long astride = 0;               // per-member stride of the activation buffers (max_batch * width)
     int *errw = nullptr;                 // device error word (bounded waits)
     bool use_tc = true;
@@ -1815,7 +1829,8 @@ void backward(qs_mlp *m, int n, bool fused) {
             mlp::DxArgs da{};
             da.dz = dz; da.WT = m->PT + m->woff[l]; da.D = m->D[l - 1];
             da.out = dst; da.outT = m->TDZ; da.bgrad = G + m->boff[l - 1];
-            da.n = n; da.sa = as; da.sw = m->nparam; da.E = m->E; da.err = m->errw; da.split = m->split;
+            da.n = n; da.sa = as; da.sw = m->nparam; da.sd = m->dstride; da.E = m->E; da.err = m->errw;
+            da.split = m->split;
             const long long items = (n + 127) / 128 * (long long)m->E;
             mlp::k_dx_tc<<<(unsigned)std::min<long long>(nsm, items), 256, mlp::dxk::SMEM, m->stream>>>(da);
             dzt_ready = true;
@@ -1947,10 +1962,11 @@ qs_status qs_mlp_create(int n_in, int width, int depth, int n_out, int ensemble,
     if (const char *v = getenv("QS_MLP_NO_FUSED")) m->fused_ok = m->fused_ok && v[0] == '0';
     if (const char *v = getenv("QS_MLP_NO_SPLIT")) m->split = v[0] == '1' ? 0 : 1;
     if (const char *v = getenv("QS_MLP_WT_PASS")) m->wt_pass = v[0] == '1' ? 1 : 0;
+    m->dstride = mlp::d_stride(max_batch);
     if (m->fused_ok)
         for (int l = 0; l + 1 < depth; ++l) {
             __nv_bfloat16 *d;
-            if ((s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * max_batch * width, &d))) {
+            if ((s = mdev(m, sizeof(__nv_bfloat16) * (size_t)ensemble * m->dstride, &d))) {
                 qs_mlp_free(m);
                 return s;
             }
@@ -2031,6 +2047,7 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
         m->ht_valid[2] = 0;
         fa.DZ = m->DG1; fa.DZT = m->TDZ;
         fa.as = m->astride;
+        fa.ds = m->dstride;
         fa.Y = Y; fa.yinv = 1.0f / m->ystd; fa.loss = m->loss; fa.G = m->G;
         if (!fused_launch(m, fa, true)) return mfail(m, QS_ERR_CUDA, "fused forward launch failed");
     } else {
