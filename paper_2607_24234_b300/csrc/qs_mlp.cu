@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
         const int r = i / (K / 8), c8 = i % (K / 8);
         const bool in = m0 + r < g.M;
         const __nv_bfloat16 *src = g.A + (in ? (long long)(m0 + r) * g.lda + c8 * 8 : 0);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(As + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
                      "l"(src), "r"(in ? 16 : 0) : "memory");
     }
 #pragma unroll 4
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
         const int r = i / (K / 8), c8 = i % (K / 8);
         const bool in = n0 + r < g.N;
         const __nv_bfloat16 *src = g.B + (in ? (long long)(n0 + r) * g.ldb + c8 * 8 : 0);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(Bs + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
                      "l"(src), "r"(in ? 16 : 0) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -510,12 +510,12 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __nv_bfloat16 *A, con
 #pragma unroll
         for (int it = 0; it < 8; ++it)
             if (rr + 16 * it < ra)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + it * 2 * SBO), "l"(pa + it * step16 + off),
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(st + it * 2 * SBO), "l"(pa + it * step16 + off),
                              "r"(sz) : "memory");
 #pragma unroll
         for (int it = 0; it < 8; ++it)
             if (rr + 16 * it < rbr)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st + (uint32_t)TILE + it * 2 * SBO),
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(st + (uint32_t)TILE + it * 2 * SBO),
                              "l"(pb + it * step16 + off), "r"(sz) : "memory");
     };
     auto wait_bar = [&](int kc) -> uint32_t {
@@ -694,7 +694,7 @@ __device__ __forceinline__ void stage(unsigned char *dst, const __nv_bfloat16 *s
     constexpr uint32_t SBO = (K / 8) * 128;
     for (int i = tid; i < rows * (K / 8); i += nthr) {
         const int r = i / (K / 8), c8 = i % (K / 8);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
                      "l"(src + (long long)r * K + c8 * 8) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
         for (int i = tid; i < rows * (W / 8); i += 256) {
             const int r = i / (W / 8), c8 = i % (W / 8);
             const bool in = r < valid;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
                          "l"(src + (in ? (long long)r * W + c8 * 8 : 0)), "r"(in ? 16 : 0) : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
