@@ -10,14 +10,16 @@
 //                ensemble statistics in the last epilogue; training: the
 //                forward, the loss and the output layer's backward;
 //   k_dx_tc      input gradients, fused with gelu' and the bias gradient;
-//   k_wgrad_tc   weight gradients (a cp.async ring over batch slices).
+//   k_wgrad_tc   weight gradients (a TMA ring over batch slices).
 // Other shapes take a layer-by-layer path: k_gemm_tc (tcgen05) and k_gemm
 // (mma.sync m16n8k16) with bias, GELU, GELU' and the casts fused into the
 // epilogues.  The members of an ensemble are independent networks
 // (different initial weights) trained on the same batches, in the same
 // launches.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -447,41 +449,67 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g0, int *err) {
 // ---------------------------------------------------------------------------
 // Weight gradient on the tensor cores: C[o][i] += sum_b A[o][b] B[i][b] over
 // this CTA's slice of the batch, A = dz^T and B = act^T, both K-major (the
-// batch contiguous, row stride ld).  One 128 x 128 output tile per CTA, the
-// accumulator in 128 TMEM columns.  The slice streams through a ring of NST
-// shared-memory stages of KC batch columns: the copies of chunk k + PD are
-// issued before the MMAs of chunk k, so copies and MMAs overlap.  A stage is
-// refilled only after the MMAs that read it have committed (bounded mbarrier
-// waits); with PD = NST - 2 that is chunk k - 2, issued two chunks earlier,
-// so the wait rarely stalls.  The partial tile is added to C with vector
+// batch contiguous).  One 128 x 128 output tile per CTA, the accumulator in
+// 128 TMEM columns.  The slice streams through a ring of NST shared-memory
+// stages of KC = 64 batch columns.  One thread fills them with tensor copies
+// (TMA), PD chunks ahead, and issues the MMAs: a copy with the 128-byte
+// swizzle lands a (rows x 128-byte) box exactly as the K-major operand tile
+// that a SWIZZLE_128B descriptor reads.  A stage is refilled only after the
+// MMAs that read it have committed.  (Per-thread 16-byte cp.async copies of
+// the same tiles were held to about 25 GB/s per SM by their issue.)  Batch
+// columns past n and rows past a map's extent arrive as zeros; operand rows
+// past rowsA / rowsB only reach accumulator rows / columns that are never
+// stored.  Every wait is bounded: on a timeout the thread waits, again
+// bounded, for its copies and MMAs in flight, the error word is set and the
+// partial tile is dropped.  The partial tile is added to C with vector
 // atomics.
 // ---------------------------------------------------------------------------
 namespace wg {
-constexpr int KC = 64, NST = 6, PD = NST - 2;   // stages, prefetch distance
-constexpr uint32_t SBO = (KC / 8) * 128, LBO = 128;   // 8-row groups 1 KB apart
+constexpr int KC = 64, NST = 6, PD = NST - 2;          // stages, prefetch distance
 constexpr size_t TILE = (size_t)128 * KC * 2;          // one operand tile, 16 KB
-constexpr size_t SMEM = (size_t)NST * 2 * TILE;        // 192 KB
+constexpr size_t SMEM = (size_t)NST * 2 * TILE + 1024; // 192 KB + alignment slack
 }  // namespace wg
 
-__global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int ld, int rowsA,
-                                                     int rowsB, int n, int cpc, float *C, int ldc, long long sA,
-                                                     long long sB, long long sC, int zper, int *err) {
+namespace tc {
+// K-major operand in the 128-byte swizzle: 128-byte rows, 8-row groups
+// 1024 bytes apart (the tile base 1024-byte aligned); a K step of 16
+// elements advances the start address by 32 bytes
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB, int bmem, int rowsA,
+                                                     int rowsB, int n, int cpc, float *C, int ldc, long long sC,
+                                                     int zper, uint32_t txb, int *err) {
     using namespace wg;
     extern __shared__ __align__(1024) unsigned char sw[];
-    __shared__ __align__(8) uint64_t bars[NST];
+    __shared__ __align__(8) uint64_t bars[NST];   // MMAs of a stage committed
+    __shared__ __align__(8) uint64_t full[NST];   // copies of a stage landed
     __shared__ uint32_t taddr_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mem = blockIdx.z / zper, sl = blockIdx.z - mem * zper;
-    A += mem * sA;
-    B += mem * sB;
     C += mem * sC;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
+    const uint32_t base = (tc::su32(sw) + 1023u) & ~1023u;   // stage s: A at base + 2 s TILE, B after it
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&taddr_s)), "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int i = 0; i < NST; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bars[i])));
+        for (int i = 0; i < NST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bars[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&full[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -490,72 +518,43 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __nv_bfloat16 *A, con
     const uint32_t taddr = taddr_s;
     const int nkt = (n + KC - 1) / KC;
     const int kb = sl * cpc, nk = max(0, min(nkt, kb + cpc) - kb);
-    // chunk kc of the slice -> stage kc % NST.  Thread t copies the 16-byte
-    // column t % 8 of rows t / 8 + 16 it of both operands, so its source and
-    // shared-memory addresses are fixed up to the chunk offset.  Batch columns
-    // past n read as zero; operand rows past rowsA / rowsB are not loaded
-    // (they only reach accumulator rows / columns that are never stored).
-    const int ra = min(128, rowsA - m0), rbr = min(128, rowsB - n0);
-    const int c8 = tid & 7, rr = tid >> 3;
-    const __nv_bfloat16 *pa = A + (long long)(m0 + min(rr, ra - 1)) * ld + c8 * 8;
-    const __nv_bfloat16 *pb = B + (long long)(n0 + min(rr, rbr - 1)) * ld + c8 * 8;
-    const long long step16 = 16LL * ld;
-    const uint32_t sbase = tc::su32(sw) + (rr / 8) * SBO + c8 * LBO + (rr % 8) * 16;
-    auto load = [&](int kc) {
-        const uint32_t st = sbase + (uint32_t)(kc % NST) * (uint32_t)(2 * TILE);
-        const long long k0 = (long long)(kb + kc) * KC;
-        const bool in = k0 + c8 * 8 < n;
-        const long long off = in ? k0 : 0;
-        const uint32_t sz = in ? 16u : 0u;
-#pragma unroll
-        for (int it = 0; it < 8; ++it)
-            if (rr + 16 * it < ra)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(st + it * 2 * SBO), "l"(pa + it * step16 + off),
-                             "r"(sz) : "memory");
-#pragma unroll
-        for (int it = 0; it < 8; ++it)
-            if (rr + 16 * it < rbr)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(st + (uint32_t)TILE + it * 2 * SBO),
-                             "l"(pb + it * step16 + off), "r"(sz) : "memory");
-    };
-    auto wait_bar = [&](int kc) -> uint32_t {
-        uint32_t done = 0;
-        const uint32_t par = (uint32_t)((kc / NST) & 1);
-        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
-            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                         : "=r"(done) : "r"(tc::su32(&bars[kc % NST])), "r"(par) : "memory");
-        return done;
-    };
-#pragma unroll 1
-    for (int kc = 0; kc < PD; ++kc) {
-        if (kc < nk) load(kc);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
     bool ok = true;
-#pragma unroll 1
-    for (int kc = 0; kc < nk; ++kc) {
-        const int pre = kc + PD;
-        uint32_t done = 1;
-        if (pre < nk) {
-            // the stage of chunk pre last held chunk pre - NST = kc - 2: its
-            // MMAs must be done
-            if (pre >= NST) done = wait_bar(pre - NST);
-            if (done) load(pre);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(PD) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        ok = __syncthreads_and(done) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) break;
-        if (tid == 0) {
-            constexpr uint32_t id = tc::idesc_bf16(128, 128);
-            const unsigned char *st = sw + (size_t)(kc % NST) * 2 * TILE;
+    if (tid == 0) {
+        auto copy = [&](const CUtensorMap *tm, uint32_t dst, int x, int y, int z, int s) {
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(tc::su32(&full[s]))
+                : "memory");
+        };
+        auto issue = [&](int kc) {
+            const int s = kc % NST;
+            const uint32_t sa = base + (uint32_t)(2 * s) * (uint32_t)TILE;
+            const int x = (kb + kc) * KC;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::su32(&full[s])), "r"(txb)
+                         : "memory");
+            copy(&tmA, sa, x, m0, mem, s);
+            copy(&tmB, sa + (uint32_t)TILE, x, n0, bmem ? mem : 0, s);
+        };
+        int issued = 0, landed = 0, committed = 0;   // chunks copied / waited for / whose MMAs were issued
+        for (; issued < PD && issued < nk; ++issued) issue(issued);
+        constexpr uint32_t id = tc::idesc_bf16(128, 128);
+        for (int kc = 0; kc < nk; ++kc) {
+            if (issued < nk) {
+                // the stage of chunk `issued` last held chunk issued - NST = kc - 2
+                if (issued >= NST && !tc::bar_wait(tc::su32(&bars[(issued - NST) % NST]), ((issued - NST) / NST) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue(issued++);
+            }
+            if (!tc::bar_wait(tc::su32(&full[kc % NST]), (kc / NST) & 1)) { ok = false; break; }
+            ++landed;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = base + (uint32_t)(2 * (kc % NST)) * (uint32_t)TILE;
 #pragma unroll
             for (int kk = 0; kk < KC / 16; ++kk) {
-                const uint64_t ad = tc::sdesc(tc::su32(st) + kk * 2 * LBO, LBO, SBO);
-                const uint64_t bd = tc::sdesc(tc::su32(st + TILE) + kk * 2 * LBO, LBO, SBO);
+                const uint64_t ad = tc::sdesc_sw128(sa + 32 * kk);
+                const uint64_t bd = tc::sdesc_sw128(sa + (uint32_t)TILE + 32 * kk);
                 const uint32_t acc = (kk > 0 || kc > 0) ? 1u : 0u;
                 asm volatile(
                     "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
@@ -564,13 +563,18 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __nv_bfloat16 *A, con
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc::su32(&bars[kc % NST]))
                          : "memory");
+            committed = kc + 1;
+        }
+        // the last chunk's MMAs (they complete in order); on a timeout, what
+        // is still in flight: the copies not yet waited for, the last MMAs
+        if (ok && nk > 0) ok = tc::bar_wait(tc::su32(&bars[(nk - 1) % NST]), ((nk - 1) / NST) & 1);
+        if (!ok) {
+            for (int c = landed; c < issued; ++c) tc::bar_wait(tc::su32(&full[c % NST]), (c / NST) & 1);
+            if (committed > 0) tc::bar_wait(tc::su32(&bars[(committed - 1) % NST]), ((committed - 1) / NST) & 1);
         }
     }
-    if (ok && nk > 0) {
-        ok = __syncthreads_and(wait_bar(nk - 1)) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    ok = __syncthreads_and(tid == 0 ? (ok ? 1 : 0) : 1) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok && tid == 0) atomicOr(err, 2);
     if (ok && nk > 0) {
         const int o = m0 + warp * 32 + lane;
@@ -1730,10 +1734,33 @@ void forward(qs_mlp *m, int n, bool want_ht = false) {
     }
 }
 
+// 3-D tensor map of a batch-contiguous bf16 operand of k_wgrad_tc: (batch
+// column, row, member), rows n elements apart, members ms apart; boxes of 64
+// columns (128 bytes, 128-byte swizzle) x min(128, rows) rows.  Columns past
+// n and rows past `rows` read as zeros.
+bool wg_tmap(CUtensorMap *tm, const __nv_bfloat16 *p, long long n, int rows, int members, long long ms) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)rows, (cuuint64_t)members};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)ms * 2};
+    const cuuint32_t box[3] = {64u, (cuuint32_t)std::min(128, rows), 1u};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // backward of every member (after forward + loss); gradients into G.  After
 // the fused training forward (fused), G already holds the output layer's
 // gradients and b2's, and DG1 / TDZ hold dz of the last hidden layer.
-void backward(qs_mlp *m, int n, bool fused) {
+bool backward(qs_mlp *m, int n, bool fused) {
     const long long as = m->astride, os = (long long)m->max_batch * m->n_out;
     float *G = m->G;
     if (!fused) cudaMemsetAsync(G, 0, sizeof(float) * (size_t)m->nparam * m->E, m->stream);
@@ -1772,8 +1799,15 @@ void backward(qs_mlp *m, int n, bool fused) {
             const int want = std::max(1, nsm / std::max(1, tiles));
             const int cpc = (nkt + want - 1) / want;
             const int zper = (nkt + cpc - 1) / cpc;
+            // operands through tensor maps (n % 8 == 0: 16-byte row strides)
+            CUtensorMap tA, tB;
+            const bool bm = sactT != 0;   // B per member (X^T of the first layer is shared)
+            if (!wg_tmap(&tA, m->TDZ, n, out, m->E, as) ||
+                !wg_tmap(&tB, actT, n, in, bm ? m->E : 1, bm ? sactT : (long long)in * n))
+                return false;
+            const uint32_t txb = (uint32_t)(std::min(128, out) + std::min(128, in)) * 128u;   // bytes per stage
             mlp::k_wgrad_tc<<<dim3(out / 128, (in + 127) / 128, zper * m->E), 128, mlp::wg::SMEM, m->stream>>>(
-                m->TDZ, actT, n, out, in, n, cpc, G + m->woff[l], in, as, sactT, m->nparam, zper, m->errw);
+                tA, tB, bm ? 1 : 0, out, in, n, cpc, G + m->woff[l], in, m->nparam, zper, txb, m->errw);
         } else if ((in == 16 || in == 32) || out == 2) {
             // a thin layer: one pass over the batch, the narrow side in registers
             const int rb = 128;
@@ -1851,6 +1885,7 @@ void backward(qs_mlp *m, int n, bool fused) {
         dz = dst;
         sdz = as;
     }
+    return true;
 }
 
 }  // namespace
@@ -2055,7 +2090,7 @@ qs_status qs_mlp_train_step(qs_mlp *m, const float *X, const float *Y, int64_t n
         mlp::k_loss<<<dim3((nb + 255) / 256, m->E), 256, 0, m->stream>>>(
             m->OUT, Y, nb, m->ymean, 1.0f / m->ystd, m->DOUTF, m->DOUT, m->loss, (long long)m->max_batch * 2);
     }
-    backward(m, nb, fused);
+    if (!backward(m, nb, fused)) return mfail(m, QS_ERR_CUDA, "weight-gradient tensor map");
     if (do_update) {
         const long long np = m->nparam * m->E;   // members' parameters are contiguous
         const mlp::AdamC ac{lr, b1, b2, 1e-8f, c1, c2};
