@@ -688,7 +688,7 @@ constexpr uint32_t SBO_W = (W / 8) * 128, SBO_I = (KIN / 8) * 128, LBO = 128;
 constexpr size_t OFF_WB = 0, OFF_AB = OFF_WB + (size_t)W * W * 2, OFF_W0 = OFF_AB + (size_t)128 * W * 2,
                  OFF_A0 = OFF_W0 + (size_t)W * KIN * 2, OFF_BIAS = OFF_A0 + (size_t)128 * KIN * 2,
                  OFF_W3 = OFF_BIAS + 3 * W * 4, OFF_PART = OFF_W3 + 2 * W * 4 + 16, OFF_RED = OFF_PART + 3 * 128 * 2 * 4,
-                 SMEM = OFF_RED + 3 * W * 4;
+                 SMEM = OFF_RED + 3 * W * 4 + 1024;   // + slack to align the layout to 1024 bytes
 static_assert(SMEM <= 227 * 1024, "fused kernel shared memory");
 
 // 16-byte asynchronous copies of a [rows][K] bf16 row-major matrix into the
@@ -709,16 +709,20 @@ __device__ __forceinline__ void stage(unsigned char *dst, const __nv_bfloat16 *s
 // NT threads: NT / 128 groups of 4 warps, each group one TMEM lane quarter
 // per warp and W / (NT / 128) accumulator columns (training: 256 threads)
 template <bool TRAIN, int NT = 256>
-__global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a, const __grid_constant__ CUtensorMap tw1,
+                                                    const __grid_constant__ CUtensorMap tw2) {
     using namespace fz;
     static_assert(NT == 256 || (NT == 512 && !TRAIN), "256 threads, or 512 for inference");
     constexpr int NQ = NT / 128, CW = W / NQ, NCH = CW / 32;   // column groups, columns per group, 32-column chunks
-    extern __shared__ __align__(1024) unsigned char sf[];
+    extern __shared__ __align__(1024) unsigned char sf_raw[];
+    // the layout from a 1024-byte boundary (Wb: 128-byte-swizzled tensor copies)
+    unsigned char *sf = sf_raw + ((1024u - (tc::su32(sf_raw) & 1023u)) & 1023u);
     unsigned char *Wb = sf + OFF_WB, *Ab = sf + OFF_AB, *W0s = sf + OFF_W0, *A0 = sf + OFF_A0;
     float *bias = reinterpret_cast<float *>(sf + OFF_BIAS), *w3 = reinterpret_cast<float *>(sf + OFF_W3);
     float *part = reinterpret_cast<float *>(sf + OFF_PART);
     float *red = reinterpret_cast<float *>(sf + OFF_RED);   // training: per-item partial gradients
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t wbar;   // W1 / W2 tensor copies landed
     __shared__ uint32_t taddr_s;
     __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -730,6 +734,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&wbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_bad = 0;
     }
@@ -750,13 +755,41 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
-    // one thread issues the layer's MMAs and commits; everyone waits (bounded)
-    auto mma_layer = [&](const unsigned char *A, const unsigned char *B, int ksteps, uint32_t sbo) {
+    // W1 / W2 of member e into Wb by one thread: four 64-column boxes of
+    // 256 rows (128-byte swizzle, 32 KB each), completing on wbar; the other
+    // threads go on with the epilogue while they land
+    uint32_t wphase = 0;       // (thread 0) copies issued and waited for
+    bool w_pending = false;
+    auto load_w = [&](const CUtensorMap *tm, int e) {
         if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::su32(&wbar)),
+                         "r"((uint32_t)(W * W * 2)) : "memory");
+#pragma unroll
+            for (int kx = 0; kx < W / 64; ++kx)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(tc::su32(Wb) + (uint32_t)(kx * W * 128)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(kx * 64), "r"(0),
+                    "r"(e), "r"(tc::su32(&wbar)) : "memory");
+            w_pending = true;
+        }
+    };
+    // one thread issues the layer's MMAs and commits; everyone waits (bounded).
+    // wtma: B is Wb from load_w (waited for first; SWIZZLE_128B descriptors,
+    // K step kk in box kk / 4 at 32 (kk % 4) bytes); on a timeout the MMAs
+    // are skipped and the commit still arrives
+    auto mma_layer = [&](const unsigned char *A, const unsigned char *B, int ksteps, uint32_t sbo, bool wtma) {
+        if (tid == 0) {
+            bool go = true;
+            if (wtma) {
+                go = tc::bar_wait(tc::su32(&wbar), wphase & 1u);
+                if (go) { ++wphase; w_pending = false; }
+                else atomicOr(&s_bad, 1);
+            }
             constexpr uint32_t id = tc::idesc_bf16(128, W);
-            for (int kk = 0; kk < ksteps; ++kk) {
+            for (int kk = 0; kk < ksteps && go; ++kk) {
                 const uint64_t ad = tc::sdesc(tc::su32(A) + kk * 2 * LBO, LBO, sbo);
-                const uint64_t bd = tc::sdesc(tc::su32(B) + kk * 2 * LBO, LBO, sbo);
+                const uint64_t bd = wtma ? tc::sdesc_sw128(tc::su32(B) + (uint32_t)((kk >> 2) * W * 128 + (kk & 3) * 32))
+                                         : tc::sdesc(tc::su32(B) + kk * 2 * LBO, LBO, sbo);
                 const uint32_t acc = kk > 0 ? 1u : 0u;
                 asm volatile(
                     "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
@@ -857,15 +890,15 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
             }
             if (tid < 2) w3[2 * W + tid] = Pf[a.b3 + tid];
             sync_for_mma();
-            mma_layer(A0, W0s, 1, SBO_I);                       // layer 0: K = 16
-            stage<W>(Wb, Pm + a.w1, W, tid, NT);               // W1 lands during the epilogue
+            mma_layer(A0, W0s, 1, SBO_I, false);                // layer 0: K = 16
+            load_w(&tw1, e);                                    // W1 lands during the epilogue
             epilogue_hidden(bias, 0, r0, e);
             sync_for_mma();
-            mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 1
-            stage<W>(Wb, Pm + a.w2, W, tid, NT);               // W2 lands during the epilogue
+            mma_layer(Ab, Wb, W / 16, SBO_W, true);             // layer 1
+            load_w(&tw2, e);                                    // W2 lands during the epilogue
             epilogue_hidden(bias + W, 1, r0, e);
             sync_for_mma();
-            mma_layer(Ab, Wb, W / 16, SBO_W);                   // layer 2
+            mma_layer(Ab, Wb, W / 16, SBO_W, true);             // layer 2
             // output layer: GELU activations (rounded to bf16 as the operand of
             // the unfused path) dotted with W3 in FP32
             float o0 = 0.f, o1 = 0.f;
@@ -1001,6 +1034,7 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_fused(const FusedArgs a) {
         }
     }
     if (!ok && tid == 0) atomicOr(a.err, 2);
+    if (tid == 0 && w_pending) tc::bar_wait(tc::su32(&wbar), wphase & 1u);   // a copy still in flight (bounded)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -1686,6 +1720,34 @@ mlp::FusedArgs fused_args(qs_mlp *m, const float *X, long long n) {
     return fa;
 }
 
+// the driver's tensor-map encoder (looked up once)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    return encode;
+}
+
+// tensor map of one W x W bf16 weight matrix per member (row-major [out][in]
+// at p + e * nparam): (in column, out row, member), boxes of 64 columns
+// (128 bytes, 128-byte swizzle) x W rows
+bool w_tmap(CUtensorMap *tm, const __nv_bfloat16 *p, int W, int E, long long nparam) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)W, (cuuint64_t)E};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)nparam * 2};
+    const cuuint32_t box[3] = {64u, (cuuint32_t)W, 1u};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool fused_launch(qs_mlp *m, const mlp::FusedArgs &fa, bool train) {
     static bool attr = false;
     if (!attr) {
@@ -1701,8 +1763,12 @@ bool fused_launch(qs_mlp *m, const mlp::FusedArgs &fa, bool train) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long items = (fa.n + 127) / 128 * (train ? fa.E : 1);
     const unsigned grid = (unsigned)std::min<long long>(nsm, items);
-    if (train) mlp::k_mlp_fused<true><<<grid, 256, mlp::fz::SMEM, m->stream>>>(fa);
-    else mlp::k_mlp_fused<false, 512><<<grid, 512, mlp::fz::SMEM, m->stream>>>(fa);
+    CUtensorMap tw1, tw2;
+    if (!w_tmap(&tw1, m->Pb + m->woff[1], m->width, m->E, m->nparam) ||
+        !w_tmap(&tw2, m->Pb + m->woff[2], m->width, m->E, m->nparam))
+        return false;
+    if (train) mlp::k_mlp_fused<true><<<grid, 256, mlp::fz::SMEM, m->stream>>>(fa, tw1, tw2);
+    else mlp::k_mlp_fused<false, 512><<<grid, 512, mlp::fz::SMEM, m->stream>>>(fa, tw1, tw2);
     return cudaGetLastError() == cudaSuccess;
 }
 
@@ -1739,15 +1805,8 @@ void forward(qs_mlp *m, int n, bool want_ht = false) {
 // columns (128 bytes, 128-byte swizzle) x min(128, rows) rows.  Columns past
 // n and rows past `rows` read as zeros.
 bool wg_tmap(CUtensorMap *tm, const __nv_bfloat16 *p, long long n, int rows, int members, long long ms) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void *fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-            return false;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+    if (!encode) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)rows, (cuuint64_t)members};
     const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)ms * 2};
     const cuuint32_t box[3] = {64u, (cuuint32_t)std::min(128, rows), 1u};
