@@ -1072,17 +1072,20 @@ struct DxArgs {
 namespace dxk {
 constexpr int W = 256;
 constexpr size_t OFF_B = 0, OFF_A = OFF_B + (size_t)W * W * 2, OFF_RED = OFF_A + (size_t)128 * W * 2,
-                 SMEM = OFF_RED + W * 4;
+                 SMEM = OFF_RED + W * 4 + 1024;   // + slack to align the layout to 1024 bytes
 static_assert(SMEM <= 227 * 1024, "input-gradient kernel shared memory");
 }  // namespace dxk
 
-__global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
+__global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a, const __grid_constant__ CUtensorMap tdz,
+                                                  const __grid_constant__ CUtensorMap twt) {
     using namespace dxk;
-    constexpr uint32_t SBO = (W / 8) * 128, LBO = 128;
-    extern __shared__ __align__(1024) unsigned char sx[];
+    extern __shared__ __align__(1024) unsigned char sx_raw[];
+    // the layout from a 1024-byte boundary (128-byte-swizzled tensor copies)
+    unsigned char *sx = sx_raw + ((1024u - (tc::su32(sx_raw) & 1023u)) & 1023u);
     unsigned char *Bs = sx + OFF_B, *As = sx + OFF_A;
     float *red = reinterpret_cast<float *>(sx + OFF_RED);
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t lbar;   // an item's operand copies landed
     __shared__ uint32_t taddr_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hc = warp >> 2;
@@ -1093,6 +1096,7 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&lbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     for (int i = tid; i < W; i += 256) red[i] = 0.0f;
@@ -1101,22 +1105,33 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = taddr_s;
     const long long ntiles = (a.n + 127) / 128, nitems = ntiles * a.E;
-    // [rows][256] bf16 row-major -> K-major core-matrix layout; rows past
-    // `valid` are zero-filled
-    auto stage = [&](unsigned char *dst, const __nv_bfloat16 *src, int rows, long long valid) {
-        for (int i = tid; i < rows * (W / 8); i += 256) {
-            const int r = i / (W / 8), c8 = i % (W / 8);
-            const bool in = r < valid;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(tc::su32(dst + (r / 8) * SBO + c8 * LBO + (r % 8) * 16)),
-                         "l"(src + (in ? (long long)r * W + c8 * 8 : 0)), "r"(in ? 16 : 0) : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    auto issue = [&](long long item, int cur) -> int {   // copies of an item; returns its member
+    // an item's operands by thread 0 as tensor copies with the 128-byte
+    // swizzle, completing on lbar: the dz tile as four 64-column boxes of
+    // 128 rows (rows past n arrive as zeros), and W^T of the item's member
+    // (four boxes of 256 rows) when the member changes
+    uint32_t lphase = 0;       // (thread 0) copies issued and waited for
+    bool l_pending = false;
+    auto issue = [&](long long item, int cur) -> int {   // returns the item's member
         const int e = (int)(item / ntiles);
-        const long long r0 = (item % ntiles) * 128;
-        if (e != cur) stage(Bs, a.WT + e * a.sw, W, W);
-        stage(As, a.dz + e * a.sa + r0 * W, 128, a.n - r0);
+        const int r0 = (int)((item % ntiles) * 128);
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(128 * W * 2) + (e != cur ? (uint32_t)(W * W * 2) : 0u);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::su32(&lbar)), "r"(bytes)
+                         : "memory");
+#pragma unroll
+            for (int kx = 0; kx < W / 64; ++kx) {
+                if (e != cur)
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                        ::"r"(tc::su32(Bs) + (uint32_t)(kx * W * 128)), "l"(reinterpret_cast<uint64_t>(&twt)), "r"(kx * 64),
+                        "r"(0), "r"(e), "r"(tc::su32(&lbar)) : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(tc::su32(As) + (uint32_t)(kx * 128 * 128)), "l"(reinterpret_cast<uint64_t>(&tdz)), "r"(kx * 64),
+                    "r"(r0), "r"(e), "r"(tc::su32(&lbar)) : "memory");
+            }
+            l_pending = true;
+        }
         return e;
     };
     uint32_t phase = 0;
@@ -1134,17 +1149,21 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
         const bool wact = half < 0 || (q >> 1) == half;   // this warp's rows belong to the unit
         const int e = (int)(item / ntiles);
         const long long r0 = (item % ntiles) * 128;
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool lok = true;   // (thread 0) the operands landed
         if (tid == 0) {
+            lok = tc::bar_wait(tc::su32(&lbar), lphase & 1u);
+            if (lok) { ++lphase; l_pending = false; }
             constexpr uint32_t id = tc::idesc_bf16(128, W);
+            // SWIZZLE_128B operands: K step kk in box kk / 4 at 32 (kk % 4) bytes
+            // (on a timeout no MMAs; the commit still arrives)
 #pragma unroll
             for (int kk = 0; kk < W / 16; ++kk) {
-                const uint64_t ad = tc::sdesc(tc::su32(As) + kk * 2 * LBO, LBO, SBO);
-                const uint64_t bd = tc::sdesc(tc::su32(Bs) + kk * 2 * LBO, LBO, SBO);
+                if (!lok) break;
+                const uint64_t ad = tc::sdesc_sw128(tc::su32(As) + (uint32_t)((kk >> 2) * 128 * 128 + (kk & 3) * 32));
+                const uint64_t bd = tc::sdesc_sw128(tc::su32(Bs) + (uint32_t)((kk >> 2) * W * 128 + (kk & 3) * 32));
                 const uint32_t acc = kk > 0 ? 1u : 0u;
                 asm volatile(
                     "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(taddr),
@@ -1171,7 +1190,7 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
             asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                          : "=r"(done) : "r"(tc::su32(&bar)), "r"(phase & 1u) : "memory");
         ++phase;
-        ok = __syncthreads_and(done) != 0;
+        ok = __syncthreads_and(done && lok) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
         // the operands are free: the next unit's copies run under the epilogue
@@ -1220,7 +1239,7 @@ __global__ void __launch_bounds__(256, 1) k_dx_tc(const DxArgs a) {
         }
     }
     if (!ok && tid == 0) atomicOr(a.err, 2);
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (tid == 0 && l_pending) tc::bar_wait(tc::su32(&lbar), lphase & 1u);   // copies still in flight (bounded)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -1748,6 +1767,21 @@ bool w_tmap(CUtensorMap *tm, const __nv_bfloat16 *p, int W, int E, long long npa
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// tensor map of dz, bf16 [n][256] per member (members ms elements apart):
+// (column, row, member), boxes of 64 columns (128-byte swizzle) x 128 rows;
+// rows past n read as zeros
+bool dz_tmap(CUtensorMap *tm, const __nv_bfloat16 *p, long long n, int E, long long ms) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[3] = {256u, (cuuint64_t)n, (cuuint64_t)E};
+    const cuuint64_t strides[2] = {256u * 2, (cuuint64_t)ms * 2};
+    const cuuint32_t box[3] = {64u, 128u, 1u};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool fused_launch(qs_mlp *m, const mlp::FusedArgs &fa, bool train) {
     static bool attr = false;
     if (!attr) {
@@ -1925,7 +1959,11 @@ bool backward(qs_mlp *m, int n, bool fused) {
             da.n = n; da.sa = as; da.sw = m->nparam; da.sd = m->dstride; da.E = m->E; da.err = m->errw;
             da.split = m->split;
             const long long items = (n + 127) / 128 * (long long)m->E;
-            mlp::k_dx_tc<<<(unsigned)std::min<long long>(nsm, items), 256, mlp::dxk::SMEM, m->stream>>>(da);
+            // dz [n][256] per member (rows past n read as zeros) and W^T
+            CUtensorMap tdz, twt;
+            if (!dz_tmap(&tdz, dz, n, m->E, as) || !w_tmap(&twt, m->PT + m->woff[l], 256, m->E, m->nparam))
+                return false;
+            mlp::k_dx_tc<<<(unsigned)std::min<long long>(nsm, items), 256, mlp::dxk::SMEM, m->stream>>>(da, tdz, twt);
             dzt_ready = true;
             bsum_done = true;
         } else {
