@@ -23,7 +23,9 @@
 // fastest.  At N = 256 the half spectra are column-major, so the column
 // transforms move whole columns as contiguous runs and the row kernels do
 // the transposition in the shared-memory staging they need anyway.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -568,27 +570,60 @@ __global__ void __launch_bounds__(256) k_rowinv_push(const float2 *__restrict__ 
 // re-read so that the push runs on points 4 t + 64 i + c, whose operands the
 // team loads and stores as 256 contiguous bytes per i, issued one transform
 // ahead.  Shared memory is 52.6 KB per block, so four blocks fit on an SM.
-__global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restrict__ T1, const float2 *__restrict__ T2,
+// The block's 16-column strips of T2 and T1 (129 k_z rows of 128 bytes
+// each) are staged by one thread as two tensor copies with the 128-byte
+// swizzle: row k's 16-byte piece q lands at piece q ^ (k % 8) of the row,
+// the layout the team reads, provided each strip starts on a 1024-byte
+// boundary (T2 at row 0, T1 at row T1ROW = 136 of R).  The copies take no
+// load/store-unit issue slots, which this kernel's shared-memory traffic
+// keeps busy.  The maps view T1 / T2 as [n_xi * 129 rows][512 floats]; s0 is
+// the launch's first slice.
+constexpr int T1ROW = 136;
+__global__ void __launch_bounds__(128, 4) k_rowinv_push256(const __grid_constant__ CUtensorMap tm1,
+                                                           const __grid_constant__ CUtensorMap tm2, int s0,
                                                            const PushArgs a) {
     constexpr int N = 256, NH = 129, TSZ = 272;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(1024) float2 sm_raw[];
+    float2 *sm = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(sm_raw) +
+                                            ((1024u - ((uint32_t)__cvta_generic_to_shared(sm_raw) & 1023u)) & 1023u));
+    __shared__ __align__(8) uint64_t tbar[2];   // T2, T1 strips landed
     const long long slice = blockIdx.y;
     const int tm = threadIdx.x >> 4, t = threadIdx.x & 15;
     const int y0 = blockIdx.x * 16 + 2 * tm;
-    float2 *tw = sm, *Ts = sm + TWN + tm * TSZ;
-    float2 *R = sm + TWN + 8 * TSZ;   // [T2, T1][k_z][16 rows]
-    const long long so = slice * (long long)N * NH + blockIdx.x * 16;
+    float2 *R = sm;                                 // [T2 rows 0..128, T1 rows T1ROW..][16 columns]
+    float2 *tw = sm + (T1ROW + NH) * 16, *Ts = tw + TWN + tm * TSZ;
+    if (threadIdx.x == 0) {
+        const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(&tbar[0]), b1 = (uint32_t)__cvta_generic_to_shared(&tbar[1]);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const int x = blockIdx.x * 32, y = (s0 + (int)slice) * NH;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float2 *src = (h ? T1 : T2) + so;
-        for (int i = threadIdx.x; i < NH * 8; i += blockDim.x) {
-            const int k = i >> 3, q = i & 7;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(
-                             R + (h * NH + k) * 16 + 2 * (q ^ (k & 7)))),
-                         "l"(src + (long long)k * N + 2 * q) : "memory");
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t b = h ? b1 : b0;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(NH * 128) : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                ::"r"((uint32_t)__cvta_generic_to_shared(R + (h ? T1ROW : 0) * 16)),
+                "l"(reinterpret_cast<uint64_t>(h ? &tm1 : &tm2)), "r"(x), "r"(y), "r"(b) : "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    // bounded wait on a strip (every thread); false: it did not land
+    auto strip_wait = [&](int h) {
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(&tbar[h]);
+        uint32_t done = 0;
+        for (long long spin = 0; spin < (1LL << 24) && !done; ++spin)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(b) : "memory");
+        return done != 0;
+    };
+    // a strip that did not land in time: wait once more (bounded) and report it
+    auto strip = [&](int h) {
+        if (!strip_wait(h)) {
+            strip_wait(h);
+            atomicOr(a.err, 2);
+        }
+    };
     const long long base = slice * (long long)N * N;
     const float tz = 6.283185307179586f / a.lz;
     float4 lnp[4], lnb[4], lg[4];
@@ -604,8 +639,8 @@ __global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restr
     };
     issue(0);
     make_tw256_p2(tw);
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-    __syncthreads();   // twiddles and the staged T2 block
+    __syncthreads();   // twiddles; the strip barriers initialised
+    strip(0);   // the staged T2 strip
     // entry k = t + 16 m of a row's Hermitian extension: entry kk of the half
     // spectrum, conjugated past 128
     float2 x[16];
@@ -628,8 +663,8 @@ __global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restr
     };
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) R[dslot(t + 16 * k2)] = x[k2];
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();   // the staged T1 block
+    strip(1);   // the staged T1 strip
+    __syncthreads();
     bool bad = false;
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -637,7 +672,7 @@ __global__ void __launch_bounds__(128, 4) k_rowinv_push256(const float2 *__restr
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int k = t + 16 * m, kk = k <= 128 ? k : N - k;
-            float2 X = R[(NH + kk) * 16 + 2 * (tm ^ (kk & 7)) + rr];
+            float2 X = R[(T1ROW + kk) * 16 + 2 * (tm ^ (kk & 7)) + rr];
             if (k > 128) X.y = -X.y;
             const float kzd = tz * (k == 128 ? 0.0f : (float)(k < 128 ? k : k - 256));
             x[m] = make_float2(X.x - kzd * X.x, X.y - kzd * X.y);
@@ -724,6 +759,7 @@ struct qs_r2 {
     std::vector<void *> bufs;
     float *nb = nullptr, *G = nullptr, *np = nullptr, *nb0 = nullptr, *gy = nullptr, *gz = nullptr, *base = nullptr;
     float2 *S1 = nullptr, *T1 = nullptr, *T2 = nullptr;
+    CUtensorMap tmT1{}, tmT2{};          // N = 256: T1 / T2 as [n_xi * 129][512] floats (the push kernel's strips)
     int *err = nullptr;
     long long step = 0;
     long long launches = 0;
@@ -740,9 +776,31 @@ size_t smem_k2() { return sizeof(float2) * (N / 2 + 4 * CB * N); }
 template <int N>
 size_t smem_k3() { return sizeof(float2) * (N / 2 + 2 * (RB + RB / 2) * N); }
 
+// T1 or T2 (n_xi slices of [129 k_z][256 y] float2) as a 2-D tensor of
+// floats, [n_xi * 129 rows][512], for the push kernel's strips: boxes of 32
+// floats (16 columns, 128 bytes) x 129 rows with the 128-byte swizzle
+bool r2_tmap(CUtensorMap *tm, float2 *T, long long n_xi) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {512u, (cuuint64_t)n_xi * 129};
+    const cuuint64_t strides[1] = {512u * 4};
+    const cuuint32_t box[2] = {32u, 129u};
+    const cuuint32_t es[2] = {1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, T, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 constexpr size_t SMEM_K1_256 = sizeof(float2) * (r2::TWN + 16 * 274);
 constexpr size_t SMEM_K2_256 = sizeof(float2) * (r2::TWN + 8 * 272);
-constexpr size_t SMEM_K3_256 = sizeof(float2) * (r2::TWN + 8 * 272 + 2 * 129 * 16);
+constexpr size_t SMEM_K3_256 = 1024 + sizeof(float2) * ((r2::T1ROW + 129) * 16 + r2::TWN + 8 * 272);   // + alignment slack
 
 template <int N>
 cudaError_t set_attrs() {
@@ -783,7 +841,7 @@ cudaError_t step_n(qs_r2 *c, float h) {
             r2::k_rowfft256<<<dim3(256 / 32, ns), 256, SMEM_K1_256, c->stream>>>(c->np + po, c->S1 + so);
             r2::k_colfft256<<<dim3(16, ns), 128, SMEM_K2_256, c->stream>>>(
                 c->S1 + so, c->T1 + so, c->T2 + so, (float)p.L_perp, (float)p.L_perp);
-            r2::k_rowinv_push256<<<dim3(256 / 16, ns), 128, SMEM_K3_256, c->stream>>>(c->T1 + so, c->T2 + so, as);
+            r2::k_rowinv_push256<<<dim3(256 / 16, ns), 128, SMEM_K3_256, c->stream>>>(c->tmT1, c->tmT2, (int)s0, as);
         } else {
             r2::k_rowfft<N, RB><<<dim3(N / RB, ns), 256, smem_k1<N>(), c->stream>>>(c->np + po, c->S1 + so);
             r2::k_colfft<N, CB><<<dim3((NH + CB - 1) / CB, ns), 256, smem_k2<N>(), c->stream>>>(
@@ -846,6 +904,10 @@ qs_status qs_r2_init(const qs_r2_params *p, const qs_allocator *alloc, void *str
         (s = r2_alloc_t(c, sizeof(float) * c->P * 4, &c->nb0)) || (s = r2_alloc_t(c, sizeof(int) * 4, &c->err))) {
         qs_r2_free(c);
         return s;
+    }
+    if (N == 256 && (!r2_tmap(&c->tmT1, c->T1, p->n_xi) || !r2_tmap(&c->tmT2, c->T2, p->n_xi))) {
+        qs_r2_free(c);
+        return QS_ERR_CUDA;
     }
     c->gy = c->nb0 + c->P;
     c->gz = c->nb0 + 2 * c->P;
