@@ -608,7 +608,8 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(const __grid_constant__ CUt
 // epilogue reads the accumulator with tcgen05.ld, adds the bias, applies GELU
 // and writes the bf16 activations straight into the next layer's shared-
 // memory A operand.  The next layer's 128 KB of weights (L2-resident: every
-// CTA reads the same ones) are copied with cp.async while the epilogue runs.
+// CTA reads the same ones) arrive by TMA, issued by one thread, while the
+// epilogue runs.
 // The last epilogue also forms the 2 outputs (dot products with W3 in FP32)
 // and the ensemble's mean, variance and fallback mask per row, so nothing but
 // the inputs and the final statistics touches global memory.
