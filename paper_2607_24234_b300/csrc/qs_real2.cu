@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -830,8 +831,13 @@ cudaError_t step_n(qs_r2 *c, float h) {
     c->launches += 1;
     // the transform kernels take the slice from blockIdx.y (at most 65,535
     // per launch): longer lines go in chunks, with the slice-major arrays
-    // offset to the chunk's first slice
-    constexpr long long MAXY = 65535;
+    // offset to the chunk's first slice.  QS_R2_CHUNK sets a smaller chunk
+    // (tests: the chunked launches at sizes an oracle can check)
+    long long MAXY = 65535;
+    if (const char *v = getenv("QS_R2_CHUNK")) {
+        const long long k = atoll(v);
+        if (k >= 1 && k < MAXY) MAXY = k;
+    }
     for (long long s0 = 0; s0 < p.n_xi; s0 += MAXY) {
         const unsigned ns = (unsigned)std::min<long long>(MAXY, p.n_xi - s0);
         const long long po = s0 * c->P, so = s0 * (long long)N * NH;

@@ -109,6 +109,37 @@ def test_nonfinite_state_reported(R, n, n_xi):
     g.close()
 
 
+def test_chunked_launches_at_256(R, monkeypatch):
+    """The four-step kernels in chunks of slices (QS_R2_CHUNK = 16: three
+    chunks of 16, 16 and 9 slices).  The push kernel stages its half-spectrum
+    strips with tensor copies whose row coordinate counts from the chunk's
+    first slice.  Chunking changes no arithmetic, so every field equals the
+    single-launch run's bit for bit, and both match the oracle."""
+    n, n_xi, steps = 256, 41, 2
+    p = _case(n, n_xi)
+    noise = synth.normals((n_xi, n, n), 11)
+    nb_o, G_o = rs.seed(p, 1e-4, 0.04, noise)
+    out = rs.sweep(p, nb_o, G_o, 0, steps, record_np=True)
+    got = {}
+    for chunk in (None, "16"):
+        if chunk is None:
+            monkeypatch.delenv("QS_R2_CHUNK", raising=False)
+        else:
+            monkeypatch.setenv("QS_R2_CHUNK", chunk)
+        g = R(p)
+        g.seed(amplitude=1e-4, offset=0.04, noise=noise.astype(np.float32))
+        g.step(steps)
+        g.sync()
+        got[chunk] = [g.read(w) for w in (0, 1, 2)]
+        if chunk is not None:
+            assert g.launch_count() == steps * (1 + 3 * 3)   # per step: the march, three chunks of three kernels
+        g.close()
+    for w, ref in zip((0, 1, 2), (nb_o, G_o, out["np"])):
+        assert np.array_equal(got[None][w], got["16"][w]), w
+        err = np.max(np.abs(got["16"][w].astype(np.float64) - ref)) / np.max(np.abs(ref))
+        assert err <= 1e-3, (w, err)
+
+
 def test_more_slices_than_one_launch_holds(R):
     """65,600 xi slices, more than the 65,535 a launch's grid holds in y:
     the transform kernels run in two chunks.  Against the oracle after one
