@@ -38,15 +38,17 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("no_fused,n", [("0", 1000), ("1", 1000), ("0", 1003)])
-def test_forward_and_gradients_match_fp64(sg, monkeypatch, no_fused, n):
-    """Both training paths: the fused forward (loss and output-layer backward
-    in its epilogue, gelu' stored for the backward GEMMs) and the layer-by-
-    layer path; n = 1003 is not a multiple of 8 (no tensor-core weight
-    gradient: the transposed operands go through the mma.sync kernel)."""
+@pytest.mark.parametrize("no_fused,no_tc,n", [("0", "0", 1000), ("1", "0", 1000), ("0", "0", 1003), ("0", "1", 1000)])
+def test_forward_and_gradients_match_fp64(sg, monkeypatch, no_fused, no_tc, n):
+    """Every training path: the fused forward (loss and output-layer backward
+    in its epilogue, gelu' stored for the backward GEMMs), the layer-by-
+    layer tcgen05 path, and the mma.sync kernels (QS_MLP_NO_TCGEN05=1);
+    n = 1003 is not a multiple of 8 (no tensor-core weight gradient: the
+    transposed operands go through the mma.sync kernel)."""
     import torch
     qs, sur = sg
     monkeypatch.setenv("QS_MLP_NO_FUSED", no_fused)
+    monkeypatch.setenv("QS_MLP_NO_TCGEN05", no_tc)
     rng = np.random.default_rng(0)
     X = (rng.standard_normal((n, 7)) * np.array([1.0, 2.0, 50.0, 30.0, 500.0, 2.0, 1.5])
          + np.array([-4.0, 6.0, 100.0, 40.0, 900.0, 3.0, 0.0])).astype(np.float32)
