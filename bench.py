@@ -25,7 +25,8 @@ The same line carries, each with its own roofline and clocks:
                  20 slow-time steps;
   alu_peaks      the FP32 and FP64 FMA rates measured on this GPU by
                  qs_probe_alu, which the ALU-bound rooflines divide by.
-Multi-GPU (torchrun): every rank runs an independent instance (seed = rank),
+Multi-GPU (torchrun): every rank runs an independent 3D-beam instance (seed =
+rank; the batched leg instead splits its one job with lpt_partition),
 no data-path collective; value = all ranks' updates / max rank time.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (rank 0 only), with the same sampling routine as cpu_baseline.
@@ -225,6 +226,27 @@ def aggregate(ws, units_per_rank, local_seconds, reduce_max=None):
     return ws * units_per_rank / t, t
 
 
+def lpt_partition(weights, n_parts):
+    """Split independent work units over n_parts ranks, longest processing
+    time first: units in decreasing weight (ties by index), each given to
+    the rank with the least load so far (ties by rank).  Returns one
+    ascending index list per rank.  The largest load is at most the mean
+    plus the largest weight, and at most (4/3 - 1/(3 n_parts)) times the
+    best possible split (Graham's bound for LPT).  Raises ValueError when a
+    rank would get no unit."""
+    import heapq
+    if n_parts < 1 or len(weights) < n_parts:
+        raise ValueError(f"cannot split {len(weights)} units over {n_parts} ranks")
+    order = sorted(range(len(weights)), key=lambda i: (-weights[i], i))
+    heap = [(0, r) for r in range(n_parts)]
+    parts = [[] for _ in range(n_parts)]
+    for i in order:
+        load, r = heapq.heappop(heap)
+        parts[r].append(i)
+        heapq.heappush(heap, (load + weights[i], r))
+    return [sorted(q) for q in parts]
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -352,18 +374,29 @@ def streaming_leg(s, p, stream, pk, pk_kind, job=200, reps=3, rank=0):
             "error_vs_oracle": "<= 1e-3 in log-amplitude, fitted rates <= 0.5% (tests)"}
 
 
-def batch_leg(args, pk, pk_kind, alu=None):
+def batch_leg(args, pk, pk_kind, alu=None, ws=1, rank=0, reduce_max=None, barrier=None):
     """Batched workload: 512 instances (n_b/n_p 10^U(-3,-1), gamma 10^U(1,4),
     L U(5,200) at dxi = 0.025, seed 0), 64 x 64 disc grid (3,228 modes),
     one 1000-step job per timed call, FP32, resident launch shape (forced
-    with --batch-shape, or the autotuner's with --batch-tune)."""
+    with --batch-shape, or the autotuner's with --batch-tune).
+
+    With ws > 1 ranks the one job is split: lpt_partition over the
+    instances' cell counts (every instance has the same modes and steps, so
+    its work is proportional to n_xi) gives each rank its share, every rank
+    times its share, and the value is the whole job's updates over the
+    slowest rank's time (total work fixed: strong scaling).  Each rank's
+    context numbers its instances from 0, so their noise draws differ from
+    the single-GPU job's; the work is the same."""
     import torch
     import paper_2607_24234_b300 as qs
-    insts = synth.batch_instances(args.batch_instances, param_seed=0)
+    insts_all = synth.batch_instances(args.batch_instances, param_seed=0)
+    parts = lpt_partition([p["n_xi"] for p in insts_all], ws)
+    insts = [insts_all[i] for i in parts[rank]]
     stream = torch.cuda.current_stream()
     s = qs.Solver(insts, prec="fp32", stream=stream)
     job = args.batch_job_steps
     cells = sum(p["n_xi"] for p in insts)
+    cells_all = sum(p["n_xi"] for p in insts_all)
     upd_job = cells * s.n_modes * job
     s.seed_noise(0, 1e-6)
     if args.batch_tune:
@@ -375,7 +408,9 @@ def batch_leg(args, pk, pk_kind, alu=None):
                      scan_cells=f[5] if len(f) > 5 else 8)
     s.step(2)
     torch.cuda.synchronize()
-    clk = Clocks(0)
+    if barrier is not None:
+        barrier()
+    clk = Clocks(torch.cuda.current_device())
     n0 = s.launch_count()
     ts = []
     for _ in range(args.batch_jobs):
@@ -384,30 +419,55 @@ def batch_leg(args, pk, pk_kind, alu=None):
         ts.append(t)
     s.sync()
     clocks = clk.stop()
-    t = float(np.mean(ts))
+    t_rank = float(np.mean(ts))
+    t = reduce_max(t_rank) if (ws > 1 and reduce_max) else t_rank
     launch = s.get_launch()
-    out = {"value": upd_job / t, "unit": UNIT, "ms_per_job": 1e3 * t, "jobs": args.batch_jobs,
-           "config": {"workload": f"batch_{len(insts)}inst_64sq_disc_{job}steps", "instances": len(insts),
-                      "modes": s.n_modes, "total_cells": cells, "slow_time_steps_per_job": job,
+    out = {"value": cells_all * s.n_modes * job / t, "unit": UNIT, "ms_per_job": 1e3 * t,
+           "jobs": args.batch_jobs,
+           "config": {"workload": f"batch_{len(insts_all)}inst_64sq_disc_{job}steps",
+                      "instances": len(insts_all), "modes": s.n_modes, "total_cells": cells_all,
+                      "slow_time_steps_per_job": job,
                       "state_bytes": int(s.query(qs.Q_STATE_BYTES)), "launch": launch},
-           "roofline": sweep_roofline(launch, upd_job, t, None, pk, pk_kind, alu),
+           "roofline": sweep_roofline(launch, upd_job, t_rank, None, pk, pk_kind, alu),
            "clocks": clocks, "gpu_launches": s.launch_count() - n0,
            "error_vs_oracle": "<= 1e-3 in log-amplitude on sampled lines of all 512 instances (tests)"}
+    if ws > 1:
+        out["scaling"] = "strong"
+        out["config"]["parallelism"] = f"lpt split of the instances over {ws} ranks"
+        out["config"]["rank0_share"] = {"instances": len(insts), "cells": cells, "ms_per_job": 1e3 * t_rank}
     s.close()
     return out
 
 
 def run_batch(args):
     import torch
-    torch.cuda.set_device(0)
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    reduce_max = barrier = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+        def reduce_max(x):
+            t = torch.tensor([x], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+
+        def barrier():
+            torch.cuda.synchronize()
+            dist.barrier()
     pk, pk_kind = peaks()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     alu = measure_alu_peaks(stream, args.alu_ms) if args.alu else None
-    r = batch_leg(args, pk, pk_kind, alu)
-    print(json.dumps({"metric": METRIC, "n_gpus": 1, "steps": r["jobs"], "warmup": 1,
-                      "ms_per_step": r["ms_per_job"], "higher_is_better": True, "scaling": "weak",
-                      "vs_baseline": None, "dtype": "f32", "data": "synthetic", **r}), flush=True)
+    r = batch_leg(args, pk, pk_kind, alu, ws, rank, reduce_max, barrier)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "n_gpus": ws, "steps": r["jobs"], "warmup": 1,
+                          "ms_per_step": r["ms_per_job"], "higher_is_better": True,
+                          "scaling": r.pop("scaling", "weak"), "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic", **r}), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def run_surrogate(args):
@@ -826,7 +886,8 @@ def run_ours(args):
     # ---- the other workloads, full size (rank 0) ----
     narrow = narrow_leg(args, pk, pk_kind) if (rank == 0 and args.narrow) else None
     torch.cuda.empty_cache()
-    batch = batch_leg(args, pk, pk_kind, alu) if (rank == 0 and args.batch) else None
+    # every rank runs its share of the one batched job (lpt_partition)
+    batch = batch_leg(args, pk, pk_kind, alu, ws, rank, reduce_max, barrier) if args.batch else None
     torch.cuda.empty_cache()
     mlp = mlp_leg(args, pk, pk_kind) if (rank == 0 and args.mlp) else None
     torch.cuda.empty_cache()

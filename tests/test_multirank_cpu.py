@@ -1,6 +1,8 @@
 """The multi-GPU path shards independent lines/instances over ranks with no
 data-path collective; only the timing is reduced (max over ranks).  This
-covers that host logic with two gloo ranks on the CPU."""
+covers that host logic with two gloo ranks on the CPU, and the longest-
+processing-time split of the batched job's instances over ranks."""
+import itertools
 import os
 import socket
 
@@ -33,6 +35,14 @@ def _worker(rank, ws, port, out):
     out[rank] = (value, t)
     # ranks run independent instances: seeds differ, no data exchanged
     assert bench.dist_env() == (ws, rank, 0)
+    # each rank takes its LPT share of the batched job; together the shares
+    # are every instance exactly once
+    import synth
+    insts = synth.batch_instances(64, param_seed=0)
+    mine = bench.lpt_partition([p["n_xi"] for p in insts], ws)[rank]
+    got = [None] * ws
+    dist.all_gather_object(got, mine)
+    out[f"share{rank}"] = got
     dist.barrier()
     dist.destroy_process_group()
 
@@ -40,7 +50,7 @@ def _worker(rank, ws, port, out):
 def test_two_rank_aggregation_gloo():
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     os.environ.pop("LOCAL_RANK", None)
     mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
@@ -48,8 +58,60 @@ def test_two_rank_aggregation_gloo():
         value, t = out[r]
         assert t == 2.0
         assert value == pytest.approx(ws * 1000 / 2.0)
+        shares = out[f"share{r}"]
+        assert sorted(itertools.chain(*shares)) == list(range(64))
+        assert all(len(q) > 0 for q in shares)
+    assert out["share0"] == out["share1"]      # every rank computes the same split
 
 
 def test_single_rank_aggregation():
     import bench
     assert bench.aggregate(1, 500, 2.0) == (250.0, 2.0)
+
+
+def _best_max_load(w, m):
+    """Brute force: the smallest largest load over every assignment."""
+    best = float("inf")
+    for a in itertools.product(range(m), repeat=len(w)):
+        loads = [0] * m
+        for i, r in enumerate(a):
+            loads[r] += w[i]
+        best = min(best, max(loads))
+    return best
+
+
+def test_lpt_partition_graham_bound_brute_force():
+    """On small random inputs the LPT split's largest load is within
+    (4/3 - 1/(3m)) of the best split found by trying every assignment, and
+    every unit is placed exactly once."""
+    import random
+    import bench
+    rng = random.Random(7)
+    for _ in range(60):
+        m = rng.choice([2, 3])
+        w = [rng.randint(1, 50) for _ in range(rng.randint(m, 8))]
+        parts = bench.lpt_partition(w, m)
+        assert sorted(itertools.chain(*parts)) == list(range(len(w)))
+        assert all(q == sorted(q) for q in parts)
+        lpt = max(sum(w[i] for i in q) for q in parts)
+        assert lpt <= (4 / 3 - 1 / (3 * m)) * _best_max_load(w, m) + 1e-9
+    # Graham's tight case for m = 2: weights 3,3,2,2,2 -> LPT 7 against 6
+    parts = bench.lpt_partition([3, 3, 2, 2, 2], 2)
+    assert max(sum([3, 3, 2, 2, 2][i] for i in q) for q in parts) == 7
+
+
+def test_lpt_partition_batched_job_balance():
+    """The 512-instance batched job over 2, 4 and 8 ranks: every rank's cells
+    lie within one instance of the mean, which is under 0.5 % of a share."""
+    import bench
+    import synth
+    n = [p["n_xi"] for p in synth.batch_instances(512, param_seed=0)]
+    for m in (1, 2, 4, 8):
+        parts = bench.lpt_partition(n, m)
+        loads = [sum(n[i] for i in q) for q in parts]
+        assert sum(loads) == sum(n)
+        assert max(loads) <= sum(n) / m + max(n)
+        assert max(loads) / (sum(n) / m) < 1.005
+    assert bench.lpt_partition([5, 1], 1) == [[0, 1]]
+    with pytest.raises(ValueError):
+        bench.lpt_partition([1, 2, 3], 4)
